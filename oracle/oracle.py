@@ -1,0 +1,373 @@
+"""CPU oracle for the Monte Carlo DtN estimator (Python side).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA path is
+checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and bench.py's
+cpu_baseline / reference arm may import it.  It never imports the product
+package, and the product never imports it.
+
+The walk part lives in ``mcs_oracle.c`` (plain C, FP64, brute-force closest
+point, -ffp-contract=off); this module loads it with ctypes and adds the steps
+that are plain linear algebra:
+
+* assembly (Sec. 4.2 boxed estimator; Alg. 2 last update): with a nodal basis
+  b(s) = e_v and b(t) = e_bin(t), each walk adds (A_v M_v / 2W) d d^T with
+  d = e_v - e_u, so the estimate is the graph Laplacian of
+  Wsym = (Wm + Wm^T)/2, Wm[v,u] = A_v M_v H[v,u] / W.  Exterior rows carry the
+  extra factors |s~|^3 and |t| (boxed exterior estimator, 1/|t~| = |t|,
+  evaluated at the node of the bin) and a killing diagonal 4 pi |t0| / N0.
+* the Steklov eigenproblem (Eq. steklov-eigenproblem) in Galerkin form
+  Lambda psi = lambda M psi, M = diag(A), solved densely with LAPACK (numpy).
+* closed forms used as pins: the ball Poisson kernel and jump kernel (Eq.
+  ball-jump-kernel, App. B.2), the importance-sampled jump mass, and the
+  cap-corrected sphere spectrum.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "mcs_oracle.c")
+INC = os.path.join(HERE, "tri_impl.inc")
+LIB = os.path.join(HERE, "libmcs_oracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (plain gcc, no FMA contraction, OpenMP over rows)."""
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(INC))
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-o", LIB, SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("nv", C.c_int), ("F", C.c_void_p), ("nf", C.c_int),
+                ("n_rows", C.c_int), ("row_pos", C.c_void_p), ("row_nrm", C.c_void_p),
+                ("tri2bin", C.c_void_p), ("row_list", C.c_void_p), ("n_list", C.c_int),
+                ("walks", C.c_int), ("eps", C.c_double), ("exterior", C.c_int),
+                ("origin", C.c_double * 3), ("seed", C.c_uint64), ("cap_deg", C.c_double),
+                ("bisect_iters", C.c_int), ("kappa", C.c_double), ("max_steps", C.c_int),
+                ("rho_min_factor", C.c_double), ("prec", C.c_int), ("n_threads", C.c_int),
+                ("killing_walks", C.c_longlong)]
+
+
+class _Result(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("H", "Mjump", "kfac", "discarded", "r_t", "rho", "center",
+                                          "steps", "capped", "H0", "kill_stats", "exit_tri", "exit_bary")]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(LIB)
+        _lib.orc_estimate.argtypes = [C.POINTER(_Problem), C.POINTER(_Result)]
+        _lib.orc_walk_from_points.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]
+        _lib.orc_tangent_balls.argtypes = [C.POINTER(_Problem), C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_closest_points.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                            C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_philox_batch.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                          C.c_uint32, C.c_void_p]
+        _lib.orc_directions.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
+        _lib.orc_start_points.argtypes = [C.c_uint64, C.c_double, C.c_void_p, C.c_double, C.c_void_p,
+                                          C.c_uint64, C.c_int, C.c_void_p]
+        _lib.orc_vertex_rows.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        _lib.orc_fps_rows.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_gwn.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        _lib.orc_gwn.restype = C.c_double
+        _lib.orc_num_threads.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# small probes
+# ---------------------------------------------------------------------------
+
+def philox(start: int, n: int, c2: int, c3: int, key: int) -> np.ndarray:
+    """Philox-4x32-10 words for counters (i_lo, i_hi, c2, c3), i = start..start+n-1."""
+    out = np.zeros((n, 4), np.uint32)
+    lib().orc_philox_batch(start, n, c2, c3, key & 0xFFFFFFFF, key >> 32, _p(out))
+    return out
+
+
+def directions(seed: int, g: int, nsteps: int, prec: int = 64) -> np.ndarray:
+    """Walk-step directions of walk g, steps 1..nsteps (Marsaglia 1972)."""
+    out = np.zeros((nsteps, 3))
+    lib().orc_directions(seed, g, nsteps, prec, _p(out))
+    return out
+
+
+def start_points(seed: int, cap_deg: float, c, rho: float, n, npairs: int, prec: int = 64) -> np.ndarray:
+    """Start points of walk pairs 0..npairs-1 of row 0 with W = 2*npairs."""
+    c = np.ascontiguousarray(c, np.float64)
+    n = np.ascontiguousarray(n, np.float64)
+    out = np.zeros((2 * npairs, 3))
+    lib().orc_start_points(seed, cap_deg, _p(c), rho, _p(n), npairs, prec, _p(out))
+    return out
+
+
+def closest_points(V, F, P, prec: int = 64):
+    """Brute-force closest point: (d2, triangle, barycentrics) per query."""
+    V = np.ascontiguousarray(V, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    P = np.ascontiguousarray(P, np.float64)
+    n = P.shape[0]
+    d2 = np.zeros(n)
+    f = np.zeros(n, np.int32)
+    b = np.zeros((n, 3))
+    lib().orc_closest_points(_p(V), V.shape[0], _p(F), F.shape[0], _p(P), n, prec, _p(d2), _p(f), _p(b))
+    return d2, f, b
+
+
+def gwn(V, F, q) -> float:
+    V = np.ascontiguousarray(V, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    q = np.ascontiguousarray(q, np.float64)
+    return float(lib().orc_gwn(_p(V), _p(F), F.shape[0], _p(q)))
+
+
+# ---------------------------------------------------------------------------
+# rows
+# ---------------------------------------------------------------------------
+
+def vertex_rows(V, F):
+    """Rows = mesh vertices: positions, unit area-weighted normals, lumped areas."""
+    V = np.ascontiguousarray(V, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    nv = V.shape[0]
+    pos = np.zeros((nv, 3)); nrm = np.zeros((nv, 3)); area = np.zeros(nv)
+    lib().orc_vertex_rows(_p(V), nv, _p(F), F.shape[0], _p(pos), _p(nrm), _p(area))
+    return dict(pos=pos, nrm=nrm, area=area, tri2bin=None, kind="vertex")
+
+
+def fps_rows(V, F, n: int, orient: bool = True):
+    """Rows = farthest-point samples over face centroids (start at face 0)."""
+    V = np.ascontiguousarray(V, np.float64)
+    F = np.ascontiguousarray(F, np.int32)
+    nf = F.shape[0]
+    sel = np.zeros(n, np.int32); pos = np.zeros((n, 3)); nrm = np.zeros((n, 3)); area = np.zeros(n)
+    t2b = np.zeros(nf, np.int32)
+    lib().orc_fps_rows(_p(V), V.shape[0], _p(F), nf, n, int(orient), _p(sel), _p(pos), _p(nrm), _p(area),
+                       _p(t2b))
+    return dict(pos=pos, nrm=nrm, area=area, tri2bin=t2b, sel=sel, kind="sample")
+
+
+# tangent-ball slack: convex polyhedral vertices admit no exactly tangent ball,
+# so vertex rows need a relative slack; face-interior sample rows take the
+# strict test up to rounding
+KAPPA_VERTEX = 0.05
+KAPPA_SAMPLE = 1e-6
+DEFAULTS = dict(cap_deg=2.5, bisect_iters=10, max_steps=1024, rho_min_factor=4.0)
+
+
+def _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, row_list, n_threads, killing_walks, params):
+    prm = dict(DEFAULTS)
+    prm["kappa"] = KAPPA_SAMPLE if rows.get("tri2bin") is not None else KAPPA_VERTEX
+    prm.update(params or {})
+    keep = []
+    V = np.ascontiguousarray(V, np.float64); keep.append(V)
+    F = np.ascontiguousarray(F, np.int32); keep.append(F)
+    pos = np.ascontiguousarray(rows["pos"], np.float64); keep.append(pos)
+    nrm = np.ascontiguousarray(rows["nrm"], np.float64); keep.append(nrm)
+    t2b = rows.get("tri2bin")
+    if t2b is not None:
+        t2b = np.ascontiguousarray(t2b, np.int32); keep.append(t2b)
+    nr = pos.shape[0]
+    rl = None if row_list is None else np.ascontiguousarray(row_list, np.int32)
+    if rl is not None:
+        keep.append(rl)
+    pb = _Problem()
+    pb.V, pb.nv, pb.F, pb.nf = _p(V), V.shape[0], _p(F), F.shape[0]
+    pb.n_rows, pb.row_pos, pb.row_nrm, pb.tri2bin = nr, _p(pos), _p(nrm), _p(t2b)
+    pb.row_list = _p(rl)
+    pb.n_list = nr if rl is None else rl.shape[0]
+    pb.walks, pb.eps, pb.exterior = walks, eps, int(exterior)
+    o = origin if origin is not None else (0.0, 0.0, 0.0)
+    for i in range(3):
+        pb.origin[i] = float(o[i])
+    pb.seed = seed
+    pb.cap_deg, pb.bisect_iters, pb.kappa = prm["cap_deg"], prm["bisect_iters"], prm["kappa"]
+    pb.max_steps, pb.rho_min_factor = prm["max_steps"], prm["rho_min_factor"]
+    pb.prec = prec
+    pb.n_threads = n_threads
+    pb.killing_walks = killing_walks
+    return pb, keep
+
+
+def tangent_balls(V, F, rows, n_threads: int = 0, params=None):
+    """Interior tangent balls of every row: (r, centre, empty radius rho)."""
+    pb, keep = _problem(V, F, rows, 2, 1e-3, False, None, 0, 64, None, n_threads, 0, params)
+    nr = pb.n_rows
+    r = np.zeros(nr); c = np.zeros((nr, 3)); rho = np.zeros(nr)
+    lib().orc_tangent_balls(C.byref(pb), _p(r), _p(c), _p(rho))
+    return r, c, rho
+
+
+def interior_origin(V, F, rows, n_threads: int = 0, params=None) -> np.ndarray:
+    """Inversion centre for the exterior estimator: the centre of the largest
+    interior tangent ball (largest rho, lowest row on ties); it lies inside
+    Omega, as the Kelvin transform requires (Sec. 4.3, App. B.3)."""
+    r, c, rho = tangent_balls(V, F, rows, n_threads, params)
+    return c[int(np.argmax(rho))].copy()
+
+
+def estimate(V, F, rows, walks: int, eps: float, exterior: bool = False, origin=None, seed: int = 0,
+             prec: int = 64, row_list=None, n_threads: int = 0, killing_walks: int = 0, params=None,
+             record_exits: bool = False):
+    """Run the walk estimator on the rows in ``row_list`` (all rows if None).
+
+    Returns a dict with the hit histogram H (len(row_list) x n_rows, int32),
+    per-row jump mass M, exterior factor |s~|^3, discard flags, tangent-ball
+    data, query counts, and (exterior, killing_walks > 0) the killing
+    histogram H0 over all n_rows bins."""
+    if walks <= 0 or walks % 2:
+        raise ValueError("walks per row must be a positive even number (antithetic pairs)")
+    pb, keep = _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, row_list, n_threads,
+                        killing_walks if exterior else 0, params)
+    nl, nr = pb.n_list, pb.n_rows
+    out = dict(H=np.zeros((nl, nr), np.int32), M=np.zeros(nl), kfac=np.zeros(nl),
+               discarded=np.zeros(nl, np.int32), r_t=np.zeros(nl), rho=np.zeros(nl),
+               center=np.zeros((nl, 3)), steps=np.zeros(nl, np.int64), capped=np.zeros(nl, np.int64),
+               H0=np.zeros(nr, np.int32), kill_stats=np.zeros(3, np.int64))
+    if record_exits:
+        out["exit_tri"] = np.zeros((nl, walks), np.int32)
+        out["exit_bary"] = np.zeros((nl, walks, 3))
+    res = _Result()
+    if record_exits:
+        res.exit_tri, res.exit_bary = _p(out["exit_tri"]), _p(out["exit_bary"])
+    for name, key in (("H", "H"), ("Mjump", "M"), ("kfac", "kfac"), ("discarded", "discarded"),
+                      ("r_t", "r_t"), ("rho", "rho"), ("center", "center"), ("steps", "steps"),
+                      ("capped", "capped"), ("H0", "H0"), ("kill_stats", "kill_stats")):
+        setattr(res, name, _p(out[key]))
+    lib().orc_estimate(C.byref(pb), C.byref(res))
+    out["row_list"] = np.arange(nr, dtype=np.int32) if row_list is None else np.asarray(row_list, np.int32)
+    out["walks"] = walks
+    out["killing_walks"] = killing_walks if exterior else 0
+    return out
+
+
+def walk_from_points(V, F, X, walks: int, eps: float, exterior: bool = False, origin=None, seed: int = 0,
+                     prec: int = 64, n_threads: int = 0, params=None):
+    """W walks from each point of X (primal coordinates); returns exit points
+    (barycentric evaluation on the exit triangle), exit triangles, steps, capped."""
+    rows = dict(pos=np.zeros((1, 3)), nrm=np.zeros((1, 3)))
+    pb, keep = _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, None, n_threads, 0, params)
+    X = np.ascontiguousarray(X, np.float64)
+    n = X.shape[0]
+    tri = np.zeros((n, walks), np.int32)
+    bary = np.zeros((n, walks, 3))
+    st = np.zeros(1, np.int64); cp = np.zeros(1, np.int64)
+    lib().orc_walk_from_points(C.byref(pb), _p(X), n, _p(tri), _p(bary), _p(st), _p(cp))
+    return exit_points(V, F, tri, bary), tri, int(st[0]), int(cp[0])
+
+
+def exit_points(V, F, tri, bary) -> np.ndarray:
+    """Positions of exit points from (triangle, barycentrics)."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    P = V[F[np.maximum(tri, 0)]]  # (..., 3 vertices, 3)
+    return np.einsum("...k,...kj->...j", bary, P)
+
+
+# ---------------------------------------------------------------------------
+# assembly and eigensolve (plain numpy)
+# ---------------------------------------------------------------------------
+
+def column_factor(rows, exterior: bool, origin=None) -> np.ndarray:
+    """Per-column factor: 1 (interior) or |p_u - o| = 1/|p~_u| (exterior)."""
+    pos = np.asarray(rows["pos"], np.float64)
+    if not exterior:
+        return np.ones(pos.shape[0])
+    d = pos - np.asarray(origin, np.float64)[None, :]
+    return np.sqrt(np.einsum("ij,ij->i", d, d))
+
+
+def row_weights(est: dict, rows) -> np.ndarray:
+    """omega_v = A_v M_v (|s~_v|^3 for exterior rows); zero for discarded rows."""
+    return np.asarray(rows["area"], np.float64)[est["row_list"]] * est["M"] * est["kfac"]
+
+
+def assemble(est: dict, rows, exterior: bool = False, origin=None, killing: bool = False) -> np.ndarray:
+    """Dense FP64 DtN stiffness Lambda from a full-row estimate."""
+    H = est["H"].astype(np.float64)
+    nr = H.shape[1]
+    assert H.shape[0] == nr, "assembly needs every row"
+    W = est["walks"]
+    omega = row_weights(est, rows)
+    cf = column_factor(rows, exterior, origin)
+    Wm = omega[:, None] * H / W * cf[None, :]
+    Ws = 0.5 * (Wm + Wm.T)
+    np.fill_diagonal(Ws, 0.0)
+    L = np.diag(Ws.sum(axis=1)) - Ws
+    if exterior and killing and est["killing_walks"] > 0:
+        L = L + np.diag(4.0 * math.pi * cf * est["H0"] / est["killing_walks"])
+    return L
+
+
+def steklov(L: np.ndarray, mass: np.ndarray, k: int):
+    """Smallest k eigenpairs of M^-1/2 L M^-1/2 (Galerkin Steklov problem)."""
+    s = 1.0 / np.sqrt(mass)
+    A = L * s[:, None] * s[None, :]
+    A = 0.5 * (A + A.T)
+    w, X = np.linalg.eigh(A)
+    return w[:k], (X[:, :k] * s[:, None])
+
+
+# ---------------------------------------------------------------------------
+# closed forms (pins)
+# ---------------------------------------------------------------------------
+
+def ball_poisson(x, z, c, r) -> float:
+    """Poisson kernel of the ball B_r(c) (Sec. 4.2): (r^2-|x-c|^2)/(4 pi r |x-z|^3)."""
+    x, z, c = map(np.asarray, (x, z, c))
+    return (r * r - np.sum((x - c) ** 2)) / (4 * math.pi * r * np.linalg.norm(x - z) ** 3)
+
+
+def ball_jump(s, z) -> float:
+    """Ball jump kernel (Eq. ball-jump-kernel): 1/(2 pi |s-z|^3)."""
+    return 1.0 / (2 * math.pi * np.linalg.norm(np.asarray(s) - np.asarray(z)) ** 3)
+
+
+def jump_mass(rho: float, cap_deg: float) -> float:
+    """int over the ball sphere outside the cap of J^B(p,z) dz = (csc(theta0/2) - 1)/(2 rho)."""
+    return (1.0 / math.sin(math.radians(cap_deg) / 2) - 1.0) / (2 * rho)
+
+
+def sphere_eigs_cap(lmax: int, cap_deg: float, R: float = 1.0, n: int = 200001) -> np.ndarray:
+    """lambda_l(theta0) = int_{theta0}^{pi} (1 - P_l(cos t)) J(t) 2 pi R^2 sin t dt with
+    J(t) = 1/(2 pi (2 R sin(t/2))^3): the jump-form quadratic form of the
+    sphere's DtN on Y_lm (Funk-Hecke) with the cap t < theta0 removed.  Equals
+    l/R at theta0 = 0.  Simpson quadrature in t."""
+    from numpy.polynomial import legendre as Lg
+    t0 = math.radians(cap_deg)
+    t = np.linspace(t0, math.pi, n)
+    J = 1.0 / (2 * math.pi * (2 * R * np.sin(t / 2)) ** 3)
+    base = J * 2 * math.pi * R * R * np.sin(t)
+    out = np.zeros(lmax + 1)
+    x = np.cos(t)
+    h = (math.pi - t0) / (n - 1)
+    wts = np.ones(n); wts[1:-1:2] = 4; wts[2:-1:2] = 2
+    for l in range(lmax + 1):
+        c = np.zeros(l + 1); c[l] = 1
+        f = (1 - Lg.legval(x, c)) * base
+        out[l] = h / 3 * np.dot(wts, f)
+    return out
