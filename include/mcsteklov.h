@@ -1,0 +1,181 @@
+/*
+ * mcsteklov.h -- C ABI of the B300 Monte Carlo DtN / Steklov library.
+ *
+ * The library estimates the discrete Dirichlet-to-Neumann (DtN) stiffness
+ * matrix Lambda of a triangle mesh from walk-on-spheres walks, as in
+ * "Monte Carlo Steklov Operators for Large-Scale Geometry Processing in the
+ * Wild" (Sec. 4.2, Alg. 2 "Final Interior DtN Estimator"; Sec. 4.3 exterior
+ * estimator), and computes its smallest Steklov eigenpairs (Eq.
+ * steklov-eigenproblem in Galerkin form Lambda psi = lambda M psi).
+ *
+ * Conventions
+ *  - All functions return an mcs_status; 0 is success, negative values are
+ *    errors, positive values are warnings.  mcs_last_error() returns a
+ *    thread-local message for the last failing call on this thread.
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary CPU memory.  Each argument says which.
+ *  - Output buffers are allocated by the caller, in sizes stated here.  The
+ *    library allocates only inside mcs_build_bvh (the mesh it owns until
+ *    mcs_mesh_destroy) and nothing in the other calls: their scratch is the
+ *    caller's workspace buffer (mcs_estimate_workspace_size bytes).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue their kernels on it and return without waiting,
+ *    except where a host-side result (mcs_stats, a mesh handle) is requested:
+ *    then the call synchronises that stream before returning.
+ *  - Arguments are validated before any launch: invalid sizes, NULL required
+ *    pointers, odd walk counts etc. return MCS_ERR_ARG and launch nothing.
+ *    Failures detected on the device (traversal stack overflow) are reported
+ *    through a device status word, read when stats are requested.
+ *  - Results are deterministic: the same inputs, parameters and seed give
+ *    bit-identical hit histograms on every run and every launch shape.
+ */
+#ifndef MCSTEKLOV_H
+#define MCSTEKLOV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcs_mesh_s *mcs_mesh;
+
+typedef enum {
+    MCS_OK = 0,
+    MCS_WARN_CAPPED = 1,            /* some walks hit max_steps (still counted) */
+    MCS_ERR_ARG = -1,
+    MCS_ERR_CUDA = -2,
+    MCS_ERR_OOM = -3,
+    MCS_ERR_DEVICE = -4,            /* device status word set (see message)   */
+    MCS_ERR_DEGENERATE = -5,        /* zero-extent mesh, non-finite input      */
+    MCS_ERR_NO_INTERIOR_POINT = -6  /* exterior: no interior tangent ball      */
+} mcs_status;
+
+enum { MCS_FP32 = 32, MCS_FP64 = 64 };
+enum { MCS_INTERIOR = 0, MCS_EXTERIOR = 1 };
+
+/* Estimator parameters.  mcs_default_params() fills the paper's / the
+ * design's defaults: eps 1e-3, theta0 = 2.5 deg (Sec. 5: cap of ~2.5 deg
+ * around s excluded and the ball jump kernel importance sampled), 10
+ * bisection iterations (Sec. 5), slack kappa 0.05 (vertex rows; 1e-6 is
+ * used for sample rows when kappa < 0), max_steps 1024, rows with an
+ * empty-ball radius below rho_min_factor * eps discarded (App. A item 2),
+ * FP32 walks, interior, killing off (Sec. 5 footnote), seed 0. */
+typedef struct {
+    double eps;             /* WoS termination shell (inverted units for the exterior) */
+    double cap_deg;         /* excluded cap half-angle theta0, degrees          */
+    int bisect_iters;       /* tangent-ball bisection iterations                */
+    double kappa;           /* tangent-ball slack; < 0: 0.05 vertex rows, 1e-6 sample rows */
+    int max_steps;          /* closest-point queries per walk, >= 2             */
+    double rho_min_factor;  /* discard rows whose empty radius < factor * eps   */
+    int prec;               /* MCS_FP32 (walks in float, FP64 eps-shell) or MCS_FP64 */
+    int domain;             /* MCS_INTERIOR or MCS_EXTERIOR                     */
+    int origin_auto;        /* exterior: 1 = centre of the largest interior tangent ball */
+    double origin[3];       /* exterior inversion centre when origin_auto == 0  */
+    long long killing_walks;/* exterior: walks from the inverted origin (0 = killing off) */
+    uint64_t seed;          /* Philox key                                       */
+    int walks_per_row;      /* W, even (antithetic pairs)                       */
+    int blocks_per_sm;      /* walk-kernel residency; 0 = library default       */
+    int threads_per_block;  /* walk-kernel block size; 0 = library default      */
+    int timing;             /* 1: time the phases with CUDA events (stats.phase_ms) */
+    int count_work;         /* 1: count BVH nodes and triangles visited (slower; stats) */
+} mcs_params;
+
+/* Rows of the estimate.  Vertex rows: n_rows = nv, tri2bin = NULL, a walk's
+ * exit column is the vertex of its exit triangle with the largest
+ * barycentric weight.  Sample rows: tri2bin maps every triangle to its row. */
+typedef struct {
+    int n_rows;
+    const double *pos;      /* device, n_rows x 3 row points s_v                */
+    const double *nrm;      /* device, n_rows x 3 unit outward normals          */
+    const double *area;     /* device, n_rows quadrature areas A_v              */
+    const int32_t *tri2bin; /* device, nf, or NULL for vertex rows              */
+} mcs_rows;
+
+/* Outputs of mcs_estimate_dtn (device, caller-owned).  cap = min(W, n_rows).
+ * The hit histogram is a padded CSR: row v holds hist_nnz[v] (bin, count)
+ * pairs at offset v*cap, bins ascending, counts summing to W (0 for a
+ * discarded row).  Lambda (n_rows x n_rows row-major FP64, optional) is the
+ * assembled stiffness; omega (optional) the FP64 row weights; H0 (optional,
+ * exterior with killing walks) the killing-walk hit counts per column. */
+typedef struct {
+    int32_t *hist_bin;      /* n_rows * cap                                     */
+    int32_t *hist_cnt;      /* n_rows * cap                                     */
+    int32_t *hist_nnz;      /* n_rows                                           */
+    double *Lambda;         /* n_rows * n_rows, or NULL                         */
+    double *omega;          /* n_rows, or NULL                                  */
+    int32_t *H0;            /* n_rows, or NULL                                  */
+    int32_t *exit_tri;      /* optional debug: n_rows * W exit triangle per walk (-1 discarded) */
+} mcs_outputs;
+
+typedef struct {
+    long long walks, steps, capped, lost, discarded_rows;
+    long long killing_steps, killing_capped;
+    double origin[3];       /* exterior inversion centre actually used          */
+    double rmax;            /* tangent-ball radius clamp actually used          */
+    int device_error;       /* 0 = none                                         */
+    float phase_ms[4];      /* timing: row setup + tangent balls, walks, histogram, assembly */
+    long long nodes_visited;/* count_work: BVH nodes whose child boxes were tested */
+    long long tris_tested;  /* count_work: point-triangle tests                 */
+} mcs_stats;
+
+const char *mcs_last_error(void);
+const char *mcs_version(void);
+void mcs_default_params(mcs_params *p);
+
+/* Build the mesh: copies V (nv x 3 FP64) and F (nf x 3 int32, 0-based), in
+ * host or device memory (detected), to the device; builds per-triangle
+ * records in FP64 and FP32 and a linear BVH (Morton codes of triangle
+ * centroids, radix sort, hierarchy of Karras 2012, bottom-up refit with
+ * bounds rounded outward to float).  The paper uses the cuBQL BVH for WoS
+ * closest-point queries (Sec. 5); this is the library's own.  Errors: ARG
+ * (nv < 3, nf < 1, NULL), DEGENERATE (non-finite vertex, index out of range,
+ * zero-extent bounding box), CUDA, OOM.  Synchronises `stream`. */
+mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream, mcs_mesh *out);
+void mcs_mesh_destroy(mcs_mesh m);
+int mcs_mesh_nv(mcs_mesh m);
+int mcs_mesh_nf(mcs_mesh m);
+
+/* Vertex rows (Alg. 2 rows on the lumped P1 basis): pos = V, nrm = unit sum
+ * of incident face normals (b-a)x(c-a) in ascending face order (0 when the
+ * sum vanishes: such a row is discarded), area = (incident face areas)/3.
+ * Device outputs nv x 3, nv x 3, nv. */
+mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, void *stream);
+
+/* Closest point of n query points (device, n x 3 FP64) by BVH traversal in
+ * FP64 (prec 64) or FP32 (prec 32, points rounded to float): squared
+ * distance, triangle id (argmin of (d^2, id)), barycentrics.  Device outputs. */
+mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, double *d2, int32_t *tri,
+                              double *bary, void *stream);
+
+/* Workspace bytes needed by mcs_estimate_dtn for these sizes. */
+size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, long long killing_walks);
+
+/* The DtN estimator (Alg. 2; boxed interior estimator of Sec. 4.2; boxed
+ * exterior estimator of Sec. 4.3 with the killing term):
+ *   row setup   -- Morton (Z-order) row schedule (Sec. 5), tangent balls by
+ *                  bisection (Sec. 5), discard rule (App. A item 2);
+ *   walks       -- W per row from the empty tangent ball, start points
+ *                  importance-sampled by J^B outside the cap, antithetic
+ *                  pairs, Philox-4x32-10 counters (seed, row*W + walk, step);
+ *                  WoS with BVH closest-point queries to the eps-shell;
+ *                  exterior walks in the Kelvin-inverted domain;
+ *   histogram   -- exit bins per row, warp-aggregated shared-memory counts,
+ *                  padded CSR;
+ *   assembly    -- W_vu = omega_v cf_u H_vu / W, Lambda = diag(Wsym 1) - Wsym
+ *                  with Wsym = (W + W^T)/2 (+ diag of the killing measure).
+ * workspace: device, >= mcs_estimate_workspace_size bytes, 256-byte aligned.
+ * stats: host, optional; when given the call synchronises `stream`.
+ * Returns MCS_WARN_CAPPED when stats are requested and some walk was capped. */
+mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
+                            void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream);
+
+/* Test hook: Philox-4x32-10 words for counters (i_lo, i_hi, c2, c3),
+ * i = start .. start+n-1, key (k0, k1); device output n x 4. */
+mcs_status mcs_philox_words(uint64_t start, uint64_t n, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                            uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,233 @@
+"""Python binding of libmcsteklov (the B300 Monte Carlo DtN / Steklov library).
+
+Argument marshalling only: every step runs in the library's CUDA kernels,
+declared in include/mcsteklov.h.  PyTorch provides device memory and the
+current CUDA stream.  There is no CPU fallback: importing this module loads
+the compiled library and raises if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+__all__ = ["lib", "Mesh", "default_params", "vertex_rows", "closest_points", "philox_words", "estimate_dtn",
+           "workspace_size", "MCSError"]
+
+_LIB_PATH = _build.LIB
+
+
+class MCSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mcsteklov status {status}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("cap_deg", C.c_double), ("bisect_iters", C.c_int), ("kappa", C.c_double),
+                ("max_steps", C.c_int), ("rho_min_factor", C.c_double), ("prec", C.c_int), ("domain", C.c_int),
+                ("origin_auto", C.c_int), ("origin", C.c_double * 3), ("killing_walks", C.c_longlong),
+                ("seed", C.c_uint64), ("walks_per_row", C.c_int), ("blocks_per_sm", C.c_int),
+                ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int)]
+
+
+class Rows(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("pos", C.c_void_p), ("nrm", C.c_void_p), ("area", C.c_void_p),
+                ("tri2bin", C.c_void_p)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("hist_bin", C.c_void_p), ("hist_cnt", C.c_void_p), ("hist_nnz", C.c_void_p),
+                ("Lambda", C.c_void_p), ("omega", C.c_void_p), ("H0", C.c_void_p), ("exit_tri", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("walks", C.c_longlong), ("steps", C.c_longlong), ("capped", C.c_longlong), ("lost", C.c_longlong),
+                ("discarded_rows", C.c_longlong), ("killing_steps", C.c_longlong),
+                ("killing_capped", C.c_longlong), ("origin", C.c_double * 3), ("rmax", C.c_double),
+                ("device_error", C.c_int), ("phase_ms", C.c_float * 4), ("nodes_visited", C.c_longlong),
+                ("tris_tested", C.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmcsteklov.so (built in-tree by ``build.py``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libmcsteklov.so not found at {_LIB_PATH}: run paper_2606_05581_b300/build.py")
+        L = C.CDLL(_LIB_PATH)
+        vp, i32, i64, u64, u32, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_uint64, C.c_uint32, C.c_double
+        L.mcs_last_error.restype = C.c_char_p
+        L.mcs_version.restype = C.c_char_p
+        L.mcs_default_params.argtypes = [C.POINTER(Params)]
+        L.mcs_build_bvh.argtypes = [vp, i32, vp, i32, vp, C.POINTER(vp)]
+        L.mcs_mesh_destroy.argtypes = [vp]
+        L.mcs_mesh_nv.argtypes = [vp]
+        L.mcs_mesh_nf.argtypes = [vp]
+        L.mcs_vertex_rows.argtypes = [vp, vp, vp, vp, vp]
+        L.mcs_closest_points.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+        L.mcs_estimate_workspace_size.argtypes = [vp, i32, i32, i64]
+        L.mcs_estimate_workspace_size.restype = C.c_size_t
+        L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
+                                       C.POINTER(Stats), vp]
+        L.mcs_philox_words.argtypes = [u64, u64, u32, u32, u32, u32, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status < 0:
+        raise MCSError(status, lib().mcs_last_error().decode())
+    return status
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().mcs_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "origin":
+            p.origin_auto = 0
+            for i in range(3):
+                p.origin[i] = float(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """A mesh on the device with its BVH (owned by the library)."""
+
+    def __init__(self, V, F):
+        V = V if isinstance(V, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(V, np.float64))
+        F = F if isinstance(F, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(F, np.int32))
+        V = V.to(torch.float64).contiguous()
+        F = F.to(torch.int32).contiguous()
+        self._keep = (V, F)
+        h = C.c_void_p()
+        _check(lib().mcs_build_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(), C.byref(h)))
+        self.handle = h
+        self.nv = int(V.shape[0])
+        self.nf = int(F.shape[0])
+
+    def close(self):
+        if self.handle:
+            lib().mcs_mesh_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vertex_rows(mesh: Mesh):
+    dev = torch.device("cuda")
+    pos = torch.empty((mesh.nv, 3), dtype=torch.float64, device=dev)
+    nrm = torch.empty_like(pos)
+    area = torch.empty(mesh.nv, dtype=torch.float64, device=dev)
+    _check(lib().mcs_vertex_rows(mesh.handle, _ptr(pos), _ptr(nrm), _ptr(area), _stream()))
+    return dict(pos=pos, nrm=nrm, area=area, tri2bin=None)
+
+
+def closest_points(mesh: Mesh, P: torch.Tensor, prec: int = 64):
+    P = P.to(device="cuda", dtype=torch.float64).contiguous()
+    n = P.shape[0]
+    d2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    tri = torch.empty(n, dtype=torch.int32, device="cuda")
+    bary = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    _check(lib().mcs_closest_points(mesh.handle, _ptr(P), n, prec, _ptr(d2), _ptr(tri), _ptr(bary), _stream()))
+    return d2, tri, bary
+
+
+def philox_words(start: int, n: int, c2: int, c3: int, key: int) -> torch.Tensor:
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    _check(lib().mcs_philox_words(start, n, c2, c3, key & 0xFFFFFFFF, key >> 32, _ptr(out), _stream()))
+    return out
+
+
+def workspace_size(mesh: Mesh, n_rows: int, walks: int, killing_walks: int = 0) -> int:
+    return int(lib().mcs_estimate_workspace_size(mesh.handle, n_rows, walks, killing_walks))
+
+
+class Workspace:
+    """Caller-owned device scratch for estimate_dtn, grown on demand."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes + 256:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        return self.buf
+
+
+def _aligned_ptr(buf: torch.Tensor) -> int:
+    p = buf.data_ptr()
+    return (p + 255) & ~255
+
+
+def estimate_dtn(mesh: Mesh, rows: dict, params: Params, assemble: bool = True, want_stats: bool = True,
+                 record_exits: bool = False, workspace: Workspace | None = None, outputs: dict | None = None):
+    """Run the DtN estimator; returns a dict of device tensors (+ stats)."""
+    pos, nrm, area = rows["pos"], rows["nrm"], rows["area"]
+    t2b = rows.get("tri2bin")
+    R = int(pos.shape[0])
+    W = int(params.walks_per_row)
+    cap = min(W, R)
+    dev = pos.device
+    o = outputs or {}
+    if not o:
+        o["hist_bin"] = torch.empty(R * cap, dtype=torch.int32, device=dev)
+        o["hist_cnt"] = torch.empty(R * cap, dtype=torch.int32, device=dev)
+        o["hist_nnz"] = torch.empty(R, dtype=torch.int32, device=dev)
+        o["omega"] = torch.empty(R, dtype=torch.float64, device=dev)
+        o["H0"] = torch.empty(R, dtype=torch.int32, device=dev)
+        o["Lambda"] = torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None
+        o["exit_tri"] = torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None
+    rs = Rows(R, pos.data_ptr(), nrm.data_ptr(), area.data_ptr(), None if t2b is None else t2b.data_ptr())
+    out = Outputs(*[None if o.get(k) is None else o[k].data_ptr()
+                    for k in ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")])
+    nbytes = workspace_size(mesh, R, W, params.killing_walks)
+    ws = (workspace or Workspace()).get(nbytes)
+    st = Stats()
+    status = _check(lib().mcs_estimate_dtn(mesh.handle, C.byref(rs), C.byref(params), C.byref(out),
+                                           C.c_void_p(_aligned_ptr(ws)), nbytes, C.byref(st) if want_stats else None,
+                                           _stream()))
+    res = dict(o)
+    res["cap"] = cap
+    res["walks"] = W
+    res["status"] = status
+    res["_ws"] = ws
+    if want_stats:
+        res["stats"] = {k: (list(getattr(st, k)) if k in ("origin", "phase_ms") else getattr(st, k))
+                        for k, _ in Stats._fields_}
+    return res
+
+
+def dense_hist(res: dict, R: int) -> torch.Tensor:
+    """Padded CSR -> dense R x R int32 hit counts (for tests and small cases)."""
+    cap = res["cap"]
+    nnz = res["hist_nnz"].long()
+    idx = torch.arange(cap, device=nnz.device)[None, :] < nnz[:, None]
+    rows = torch.arange(R, device=nnz.device)[:, None].expand(R, cap)[idx]
+    bins = res["hist_bin"].view(R, cap)[idx].long()
+    cnts = res["hist_cnt"].view(R, cap)[idx]
+    H = torch.zeros((R, R), dtype=torch.int32, device=nnz.device)
+    H[rows, bins] = cnts
+    return H

@@ -1,0 +1,383 @@
+// mcs_device.cuh -- device-side building blocks of the DtN estimator:
+// Philox-4x32-10, exact uniforms, samplers, point-triangle closest point,
+// BVH layout and closest-point traversal.
+//
+// Every floating-point expression that decides a walk (sampler, step,
+// closest point, tangent ball) is written in a fixed operation order and the
+// library is compiled with -fmad=false, IEEE division and square root, so
+// FP64 (and FP32) walks are reproducible operation for operation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcs {
+
+constexpr uint32_t kTagRadial = 0xFFFFFFFFu;
+constexpr uint32_t kKillKeyXor = 0x4B494C4Cu;
+constexpr int kMaxReject = 32;
+constexpr int kStackDepth = 64;
+
+// device status word bits
+constexpr int kErrStack = 1;
+
+// --------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products, key bumped by the Weyl constants after each.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniforms on (0,1): (2k+1) 2^-53 from 52 bits, (2k+1) 2^-24 from 23 bits
+__device__ __forceinline__ double uni64(uint32_t hi, uint32_t lo) {
+    const unsigned long long b = ((((unsigned long long)hi) << 32) | lo) >> 12;
+    return (double)b * (1.0 / 4503599627370496.0) + (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ float uni32(uint32_t x) {
+    return (float)(x >> 9) * (1.0f / 8388608.0f) + (1.0f / 16777216.0f);
+}
+
+template <typename T> struct Uni;
+template <> struct Uni<double> {
+    // signed pair (a, b) in (-1,1)^2 from one Philox block
+    __device__ static void pair(uint4 x, double &a, double &b) {
+        a = 2.0 * uni64(x.x, x.y) - 1.0;
+        b = 2.0 * uni64(x.z, x.w) - 1.0;
+    }
+    __device__ static double one(uint4 x) { return uni64(x.x, x.y); }
+};
+template <> struct Uni<float> {
+    __device__ static void pair(uint4 x, float &a, float &b) {
+        a = 2.0f * uni32(x.x) - 1.0f;
+        b = 2.0f * uni32(x.z) - 1.0f;
+    }
+    __device__ static float one(uint4 x) { return uni32(x.x); }
+};
+
+template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ double rsq<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) { return sqrtf(x); }
+
+template <typename T> struct V3 { T x, y, z; };
+
+// uniform direction on S^2, Marsaglia (1972): (a,b) uniform in the square,
+// accept a^2+b^2 < 1, u = (2a sqrt(1-s), 2b sqrt(1-s), 1-2s)
+template <typename T>
+__device__ __forceinline__ V3<T> direction(uint32_t k0, uint32_t k1, unsigned long long g, uint32_t step) {
+    for (uint32_t t = 0; t < (uint32_t)kMaxReject; t++) {
+        const uint4 x = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), step, t), k0, k1);
+        T a, b;
+        Uni<T>::pair(x, a, b);
+        const T s = a * a + b * b;
+        if (s < (T)1) {
+            const T h = rsq<T>((T)1 - s);
+            return V3<T>{(T)2 * a * h, (T)2 * b * h, (T)1 - (T)2 * s};
+        }
+    }
+    return V3<T>{(T)0, (T)0, (T)1};
+}
+
+// orthonormal basis of a unit n (Duff et al., JCGT 6(1) 2017)
+template <typename T>
+__device__ __forceinline__ void onb(V3<T> n, V3<T> &e1, V3<T> &e2) {
+    const T sg = copysign((T)1, n.z);
+    const T a = (T)-1 / (sg + n.z);
+    const T b = n.x * n.y * a;
+    e1 = V3<T>{(T)1 + sg * n.x * n.x * a, sg * b, -(sg * n.x)};
+    e2 = V3<T>{b, sg + n.y * n.y * a, -n.y};
+}
+
+// Start point of walk pair gp on the empty ball B(c, rho), pole c + rho n:
+// w = sin(theta/2) drawn with density ~1/w^2 on [w0, 1] (the ball jump
+// kernel outside the cap), azimuth uniform, odd partner at phi + pi.
+template <typename T>
+__device__ __forceinline__ V3<T> start_point(uint32_t k0, uint32_t k1, unsigned long long gp, int odd, T iw0,
+                                             V3<T> c, T rho, V3<T> n) {
+    const uint4 xr = philox(make_uint4((uint32_t)gp, (uint32_t)(gp >> 32), 0u, kTagRadial), k0, k1);
+    const T u = Uni<T>::one(xr);
+    const T iw = iw0 - u * (iw0 - (T)1);
+    const T w = (T)1 / iw;
+    const T cth = (T)1 - (T)2 * (w * w);
+    const T sth = ((T)2 * w) * rsq<T>((T)1 - w * w);
+    T cph = (T)1, sph = (T)0;
+    for (uint32_t t = 0; t < (uint32_t)kMaxReject; t++) {
+        const uint4 x = philox(make_uint4((uint32_t)gp, (uint32_t)(gp >> 32), 0u, t), k0, k1);
+        T a, b;
+        Uni<T>::pair(x, a, b);
+        const T s = a * a + b * b;
+        if (s < (T)1) {
+            const T r = rsq<T>(s);
+            cph = a / r;
+            sph = b / r;
+            break;
+        }
+    }
+    if (odd) { cph = -cph; sph = -sph; }
+    V3<T> e1, e2;
+    onb<T>(n, e1, e2);
+    V3<T> z;
+    z.x = c.x + rho * (cth * n.x + sth * (cph * e1.x + sph * e2.x));
+    z.y = c.y + rho * (cth * n.y + sth * (cph * e1.y + sph * e2.y));
+    z.z = c.z + rho * (cth * n.z + sth * (cph * e1.z + sph * e2.z));
+    return z;
+}
+
+// --------------------------------------------------------------------------
+// point-triangle closest point on (a, ab, ac): Voronoi-region tests on dot
+// products (Ericson, Real-Time Collision Detection, Sec. 5.1.5), with
+// bp = ap - ab, cp = ap - ac; zero-length edge regions take parameter 0; a
+// zero normal, or a failed interior test, falls back to the nearest edge.
+// Returns |p - q|^2 and the barycentrics of q.
+// --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T dot3(T a0, T a1, T a2, T b0, T b1, T b2) { return a0 * b0 + a1 * b1 + a2 * b2; }
+
+template <typename T>
+__device__ __forceinline__ T seg_closest(T o0, T o1, T o2, T e0, T e1, T e2, T tnum, T &t) {
+    const T L = e0 * e0 + e1 * e1 + e2 * e2;
+    T tt = L > (T)0 ? tnum / L : (T)0;
+    if (!(tt > (T)0)) tt = (T)0;
+    if (tt > (T)1) tt = (T)1;
+    const T d0 = o0 - tt * e0, d1 = o1 - tt * e1, d2 = o2 - tt * e2;
+    t = tt;
+    return d0 * d0 + d1 * d1 + d2 * d2;
+}
+
+template <typename T>
+__device__ __noinline__ T tri_degenerate(T ap0, T ap1, T ap2, T ab0, T ab1, T ab2, T ac0, T ac1, T ac2, T *bary) {
+    const T bp0 = ap0 - ab0, bp1 = ap1 - ab1, bp2 = ap2 - ab2;
+    const T bc0 = ac0 - ab0, bc1 = ac1 - ab1, bc2 = ac2 - ab2;
+    const T d1 = ab0 * ap0 + ab1 * ap1 + ab2 * ap2;
+    const T d2 = ac0 * ap0 + ac1 * ap1 + ac2 * ap2;
+    T t;
+    T best = seg_closest<T>(ap0, ap1, ap2, ab0, ab1, ab2, d1, t);
+    bary[0] = (T)1 - t; bary[1] = t; bary[2] = (T)0;
+    T cur = seg_closest<T>(ap0, ap1, ap2, ac0, ac1, ac2, d2, t);
+    if (cur < best) { best = cur; bary[0] = (T)1 - t; bary[1] = (T)0; bary[2] = t; }
+    const T dbc = bc0 * bp0 + bc1 * bp1 + bc2 * bp2;
+    cur = seg_closest<T>(bp0, bp1, bp2, bc0, bc1, bc2, dbc, t);
+    if (cur < best) { best = cur; bary[0] = (T)0; bary[1] = (T)1 - t; bary[2] = t; }
+    return best;
+}
+
+template <typename T>
+__device__ __forceinline__ T tri_closest(T p0, T p1, T p2, T a0, T a1, T a2, T ab0, T ab1, T ab2, T ac0, T ac1, T ac2,
+                                         T *bary) {
+    const T ap0 = p0 - a0, ap1 = p1 - a1, ap2 = p2 - a2;
+    const T n0 = ab1 * ac2 - ab2 * ac1;
+    const T n1 = ab2 * ac0 - ab0 * ac2;
+    const T n2 = ab0 * ac1 - ab1 * ac0;
+    if (n0 == (T)0 && n1 == (T)0 && n2 == (T)0)
+        return tri_degenerate<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
+    const T d1 = ab0 * ap0 + ab1 * ap1 + ab2 * ap2;
+    const T d2 = ac0 * ap0 + ac1 * ap1 + ac2 * ap2;
+    if (d1 <= (T)0 && d2 <= (T)0) {
+        bary[0] = (T)1; bary[1] = (T)0; bary[2] = (T)0;
+        return ap0 * ap0 + ap1 * ap1 + ap2 * ap2;
+    }
+    const T bp0 = ap0 - ab0, bp1 = ap1 - ab1, bp2 = ap2 - ab2;
+    const T d3 = ab0 * bp0 + ab1 * bp1 + ab2 * bp2;
+    const T d4 = ac0 * bp0 + ac1 * bp1 + ac2 * bp2;
+    if (d3 >= (T)0 && d4 <= d3) {
+        bary[0] = (T)0; bary[1] = (T)1; bary[2] = (T)0;
+        return bp0 * bp0 + bp1 * bp1 + bp2 * bp2;
+    }
+    const T vc = d1 * d4 - d3 * d2;
+    if (vc <= (T)0 && d1 >= (T)0 && d3 <= (T)0) {
+        const T den = d1 - d3;
+        const T v = den > (T)0 ? d1 / den : (T)0;
+        const T q0 = ap0 - v * ab0, q1 = ap1 - v * ab1, q2 = ap2 - v * ab2;
+        bary[0] = (T)1 - v; bary[1] = v; bary[2] = (T)0;
+        return q0 * q0 + q1 * q1 + q2 * q2;
+    }
+    const T cp0 = ap0 - ac0, cp1 = ap1 - ac1, cp2 = ap2 - ac2;
+    const T d5 = ab0 * cp0 + ab1 * cp1 + ab2 * cp2;
+    const T d6 = ac0 * cp0 + ac1 * cp1 + ac2 * cp2;
+    if (d6 >= (T)0 && d5 <= d6) {
+        bary[0] = (T)0; bary[1] = (T)0; bary[2] = (T)1;
+        return cp0 * cp0 + cp1 * cp1 + cp2 * cp2;
+    }
+    const T vb = d5 * d2 - d1 * d6;
+    if (vb <= (T)0 && d2 >= (T)0 && d6 <= (T)0) {
+        const T den = d2 - d6;
+        const T w = den > (T)0 ? d2 / den : (T)0;
+        const T q0 = ap0 - w * ac0, q1 = ap1 - w * ac1, q2 = ap2 - w * ac2;
+        bary[0] = (T)1 - w; bary[1] = (T)0; bary[2] = w;
+        return q0 * q0 + q1 * q1 + q2 * q2;
+    }
+    const T va = d3 * d6 - d5 * d4;
+    const T e43 = d4 - d3, e56 = d5 - d6;
+    if (va <= (T)0 && e43 >= (T)0 && e56 >= (T)0) {
+        const T den = e43 + e56;
+        const T w = den > (T)0 ? e43 / den : (T)0;
+        const T bc0 = ac0 - ab0, bc1 = ac1 - ab1, bc2 = ac2 - ab2;
+        const T q0 = bp0 - w * bc0, q1 = bp1 - w * bc1, q2 = bp2 - w * bc2;
+        bary[0] = (T)0; bary[1] = (T)1 - w; bary[2] = w;
+        return q0 * q0 + q1 * q1 + q2 * q2;
+    }
+    const T den = (va + vb) + vc;
+    if (den > (T)0) {
+        const T inv = (T)1 / den;
+        const T v = vb * inv, w = vc * inv;
+        const T q0 = (ap0 - v * ab0) - w * ac0;
+        const T q1 = (ap1 - v * ab1) - w * ac1;
+        const T q2 = (ap2 - v * ab2) - w * ac2;
+        bary[0] = ((T)1 - v) - w; bary[1] = v; bary[2] = w;
+        return q0 * q0 + q1 * q1 + q2 * q2;
+    }
+    return tri_degenerate<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
+}
+
+// --------------------------------------------------------------------------
+// mesh on the device
+// --------------------------------------------------------------------------
+// binary BVH node: both children's boxes (float, rounded outward) + children
+// (>= 0 internal node, < 0 leaf: ~k = triangle slot in BVH order)
+struct __align__(16) Node {
+    float4 a;  // lo0.x lo0.y lo0.z hi0.x
+    float4 b;  // hi0.y hi0.z lo1.x lo1.y
+    float4 c;  // lo1.z hi1.x hi1.y hi1.z
+    int4 d;    // child0 child1 - -
+};
+// triangle slot in BVH order, FP32: (a, id) (ab, -) (ac, -)
+struct __align__(16) Tri32 {
+    float4 a;
+    float4 ab;
+    float4 ac;
+};
+// triangle slot in BVH order, FP64
+struct __align__(16) Tri64 {
+    double a[3], ab[3], ac[3];
+    int id, pad;
+};
+
+struct DevMesh {
+    const double *V;       // nv x 3
+    const int32_t *F;      // nf x 3
+    const Node *nodes;     // nf - 1 internal nodes (root 0); none when nf == 1
+    const Tri32 *t32;      // nf slots
+    const Tri64 *t64;      // nf slots
+    int nv, nf;
+    float scale;           // max |coordinate| of the mesh, for the pruning slack
+};
+
+template <typename T> struct Hit {
+    T d2;
+    int id;    // original triangle id
+    int slot;  // BVH slot
+    T b0, b1, b2;
+};
+
+template <typename T> struct Slot;
+template <> struct Slot<float> {
+    __device__ static float test(const DevMesh &m, int s, float px, float py, float pz, float *b, int &id) {
+        const Tri32 t = m.t32[s];
+        id = __float_as_int(t.a.w);
+        return tri_closest<float>(px, py, pz, t.a.x, t.a.y, t.a.z, t.ab.x, t.ab.y, t.ab.z, t.ac.x, t.ac.y, t.ac.z, b);
+    }
+};
+template <> struct Slot<double> {
+    __device__ static double test(const DevMesh &m, int s, double px, double py, double pz, double *b, int &id) {
+        const Tri64 &t = m.t64[s];
+        id = t.id;
+        return tri_closest<double>(px, py, pz, t.a[0], t.a[1], t.a[2], t.ab[0], t.ab[1], t.ab[2], t.ac[0], t.ac[1],
+                                   t.ac[2], b);
+    }
+};
+
+// relative pruning slack: a node is skipped only when its box is farther
+// than the best distance plus tau = rel * (scale + |p|_inf), which bounds
+// the rounding of the box and triangle distance computations, so the
+// traversal returns exactly the brute-force argmin of (d^2, id)
+template <typename T> __device__ __forceinline__ T prune_rel();
+template <> __device__ __forceinline__ float prune_rel<float>() { return 6.103515625e-05f; }        // 2^-14
+template <> __device__ __forceinline__ double prune_rel<double>() { return 1.4551915228366852e-11; } // 2^-36
+
+template <typename T>
+__device__ __forceinline__ T box_d2(T px, T py, T pz, float lx, float ly, float lz, float hx, float hy, float hz) {
+    const T dx = fmax(fmax((T)lx - px, (T)0), px - (T)hx);
+    const T dy = fmax(fmax((T)ly - py, (T)0), py - (T)hy);
+    const T dz = fmax(fmax((T)lz - pz, (T)0), pz - (T)hz);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+template <typename T> __device__ __forceinline__ float store_down(T x);
+template <> __device__ __forceinline__ float store_down<float>(float x) { return x; }
+template <> __device__ __forceinline__ float store_down<double>(double x) { return __double2float_rd(x); }
+
+// optional work counters of a traversal
+struct Work {
+    unsigned long long nodes, tris;
+};
+
+// closest triangle by BVH traversal (nearest child first, explicit stack);
+// guess >= 0 is a slot tested first to tighten the bound
+template <typename T, bool COUNT = false>
+__device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &best, int *err, Work *work = nullptr) {
+    best.d2 = (T)INFINITY;
+    best.id = 0x7FFFFFFF;
+    best.slot = -1;
+    best.b0 = best.b1 = best.b2 = (T)0;
+    const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
+    T thr2 = (T)INFINITY;
+    auto test = [&](int s) {
+        if (COUNT) work->tris++;
+        T b[3];
+        int id;
+        const T d2 = Slot<T>::test(m, s, px, py, pz, b, id);
+        if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
+            best.d2 = d2; best.id = id; best.slot = s;
+            best.b0 = b[0]; best.b1 = b[1]; best.b2 = b[2];
+            const T r = rsq<T>(d2) + tau;
+            thr2 = r * r;
+        }
+    };
+    if (guess >= 0) test(guess);
+    if (m.nf == 1) { if (guess != 0) test(0); return; }
+    int stack[kStackDepth];
+    float sdist[kStackDepth];
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        if (COUNT) work->nodes++;
+        const Node nd = m.nodes[node];
+        const T d0 = box_d2<T>(px, py, pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);
+        const T d1 = box_d2<T>(px, py, pz, nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w);
+        const int c0 = nd.d.x, c1 = nd.d.y;
+        bool h0 = d0 <= thr2, h1 = d1 <= thr2;
+        if (h0 && c0 < 0) { test(~c0); h0 = false; }
+        if (h1 && c1 < 0) { test(~c1); h1 = false; }
+        h0 = h0 && d0 <= thr2;
+        h1 = h1 && d1 <= thr2;
+        if (h0 && h1) {
+            const bool first0 = d0 <= d1;
+            if (sp < kStackDepth) {
+                stack[sp] = first0 ? c1 : c0;
+                sdist[sp] = store_down<T>(first0 ? d1 : d0);
+                sp++;
+            } else {
+                *err |= kErrStack;
+            }
+            node = first0 ? c0 : c1;
+            continue;
+        }
+        if (h0) { node = c0; continue; }
+        if (h1) { node = c1; continue; }
+        bool found = false;
+        while (sp > 0) {
+            sp--;
+            if ((T)sdist[sp] <= thr2) { node = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+}
+
+}  // namespace mcs

@@ -1,0 +1,53 @@
+// mcs_internal.h -- host-side internals shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/mcsteklov.h"
+#include "mcs_device.cuh"
+
+struct mcs_mesh_s {
+    int device = 0;
+    int nv = 0, nf = 0;
+    // device memory owned by the mesh
+    double *V = nullptr;           // nv x 3
+    int32_t *F = nullptr;          // nf x 3
+    mcs::Node *nodes = nullptr;    // nf - 1
+    mcs::Tri32 *t32 = nullptr;     // nf
+    mcs::Tri64 *t64 = nullptr;     // nf
+    int32_t *inc_f = nullptr;      // 3 nf: faces of each vertex, ascending
+    int32_t *vstart = nullptr;     // nv + 1
+    int *err = nullptr;            // device status word of the test hooks
+    // host copies of mesh constants
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    double rmax = 0.0;             // interior tangent-ball clamp: half the shortest AABB side
+    float scale = 0.f;             // max |coordinate|
+    mcs::DevMesh dev() const {
+        mcs::DevMesh d;
+        d.V = V; d.F = F; d.nodes = nodes; d.t32 = t32; d.t64 = t64;
+        d.nv = nv; d.nf = nf; d.scale = scale;
+        return d;
+    }
+};
+
+namespace mcs {
+void set_error(const std::string &msg);
+mcs_status cuda_fail(cudaError_t e, const char *what);
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+int num_sms();
+}  // namespace mcs
+
+#define MCS_CUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return mcs::cuda_fail(e_, #call);            \
+    } while (0)
+
+#define MCS_ARG(cond, msg)                                                  \
+    do {                                                                    \
+        if (!(cond)) {                                                      \
+            mcs::set_error(msg);                                            \
+            return MCS_ERR_ARG;                                             \
+        }                                                                   \
+    } while (0)

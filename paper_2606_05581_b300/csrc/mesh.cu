@@ -1,0 +1,472 @@
+// mesh.cu -- mesh upload, linear BVH build, vertex rows, closest-point and
+// Philox test hooks.
+//
+// BVH: Morton codes of triangle centroids (30 bits) with the triangle id in
+// the low 32 bits (unique keys), CUB radix sort, the parallel hierarchy of
+// Karras (HPG 2012, "Maximizing parallelism in the construction of BVHs,
+// octrees, and k-d trees"), bottom-up refit with per-node arrival counters.
+// Child boxes live in the parent node and are rounded outward to float, so
+// one node array serves both FP32 and FP64 traversals conservatively.
+#include <cub/cub.cuh>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mcs_internal.h"
+
+namespace mcs {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+mcs_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MCS_ERR_OOM : MCS_ERR_CUDA;
+}
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------- kernels
+__global__ void k_validate(const double *V, int nv, const int32_t *F, int nf, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nv; i += gridDim.x * blockDim.x)
+        if (!isfinite(V[i])) atomicOr(bad, 1);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nf; i += gridDim.x * blockDim.x)
+        if (F[i] < 0 || F[i] >= nv) atomicOr(bad, 2);
+}
+
+// per-block min / max of the vertex coordinates, then one block folds them
+__global__ void k_bounds_partial(const double *V, int nv, double *part) {
+    __shared__ double smin[3][256], smax[3][256];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; k++) {
+            const double x = V[3 * v + k];
+            mn[k] = fmin(mn[k], x);
+            mx[k] = fmax(mx[k], x);
+        }
+    for (int k = 0; k < 3; k++) { smin[k][threadIdx.x] = mn[k]; smax[k][threadIdx.x] = mx[k]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 3; k++) {
+                smin[k][threadIdx.x] = fmin(smin[k][threadIdx.x], smin[k][threadIdx.x + s]);
+                smax[k][threadIdx.x] = fmax(smax[k][threadIdx.x], smax[k][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; k++) { part[6 * blockIdx.x + k] = smin[k][0]; part[6 * blockIdx.x + 3 + k] = smax[k][0]; }
+}
+__global__ void k_bounds_final(const double *part, int nb, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; b++)
+        for (int k = 0; k < 3; k++) { mn[k] = fmin(mn[k], part[6 * b + k]); mx[k] = fmax(mx[k], part[6 * b + 3 + k]); }
+    for (int k = 0; k < 3; k++) { out[k] = mn[k]; out[3 + k] = mx[k]; }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+__device__ __forceinline__ uint32_t morton30(double x, double y, double z, const double *lo, const double *inv) {
+    const double fx = fmin(fmax((x - lo[0]) * inv[0], 0.0), 1.0);
+    const double fy = fmin(fmax((y - lo[1]) * inv[1], 0.0), 1.0);
+    const double fz = fmin(fmax((z - lo[2]) * inv[2], 0.0), 1.0);
+    const uint32_t ix = min((uint32_t)(fx * 1024.0), 1023u);
+    const uint32_t iy = min((uint32_t)(fy * 1024.0), 1023u);
+    const uint32_t iz = min((uint32_t)(fz * 1024.0), 1023u);
+    return (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+}
+
+struct BoxFrame { double lo[3], inv[3]; };
+
+__global__ void k_tri_keys(const double *V, const int32_t *F, int nf, BoxFrame fr, unsigned long long *keys) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
+    const double cx = ((a[0] + b[0]) + c[0]) / 3.0, cy = ((a[1] + b[1]) + c[1]) / 3.0, cz = ((a[2] + b[2]) + c[2]) / 3.0;
+    keys[f] = ((unsigned long long)morton30(cx, cy, cz, fr.lo, fr.inv) << 32) | (unsigned)f;
+}
+
+// triangle slots in BVH order: (a, ab, ac) in FP64 and, from float-rounded
+// vertices, in FP32; box of each slot rounded outward to float
+__global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const unsigned long long *keys, Tri32 *t32,
+                            Tri64 *t64, float *slotbox) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nf) return;
+    const int f = (int)(keys[s] & 0xFFFFFFFFull);
+    const double *A = V + 3 * F[3 * f], *B = V + 3 * F[3 * f + 1], *C = V + 3 * F[3 * f + 2];
+    Tri64 t;
+    Tri32 u;
+    float fa[3], fab[3], fac[3];
+    for (int k = 0; k < 3; k++) {
+        t.a[k] = A[k];
+        t.ab[k] = B[k] - A[k];
+        t.ac[k] = C[k] - A[k];
+        const float a = (float)A[k], b = (float)B[k], c = (float)C[k];
+        fa[k] = a;
+        fab[k] = b - a;
+        fac[k] = c - a;
+        slotbox[6 * s + k] = __double2float_rd(fmin(fmin(A[k], B[k]), C[k]));
+        slotbox[6 * s + 3 + k] = __double2float_ru(fmax(fmax(A[k], B[k]), C[k]));
+    }
+    t.id = f;
+    t.pad = 0;
+    u.a = make_float4(fa[0], fa[1], fa[2], __int_as_float(f));
+    u.ab = make_float4(fab[0], fab[1], fab[2], 0.f);
+    u.ac = make_float4(fac[0], fac[1], fac[2], 0.f);
+    t64[s] = t;
+    t32[s] = u;
+}
+
+__device__ __forceinline__ int kdelta(const unsigned long long *k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    return __clzll(k[i] ^ k[j]);
+}
+
+// Karras 2012: internal node i covers a key range [min(i,j), max(i,j)] split
+// at gamma; children >= 0 internal, < 0 leaf (~slot)
+__global__ void k_karras(const unsigned long long *k, int n, int *child, int *parent_int, int *parent_leaf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (kdelta(k, n, i, i + 1) - kdelta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = kdelta(k, n, i, i - d);
+    int lmax = 2;
+    while (kdelta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (kdelta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = kdelta(k, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    int left, right;
+    if (lo == gamma) { left = ~gamma; parent_leaf[gamma] = i; }
+    else { left = gamma; parent_int[gamma] = i; }
+    if (hi == gamma + 1) { right = ~(gamma + 1); parent_leaf[gamma + 1] = i; }
+    else { right = gamma + 1; parent_int[gamma + 1] = i; }
+    child[2 * i] = left;
+    child[2 * i + 1] = right;
+}
+
+// bottom-up refit: one thread per leaf climbs; the second arrival at a node
+// unites its two child boxes and continues
+__global__ void k_refit(int n, const int *child, const int *parent_int, const int *parent_leaf, const float *slotbox,
+                        float *nodebox, int *arrive) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float box[6];
+    for (int k = 0; k < 6; k++) box[k] = slotbox[6 * s + k];
+    int me = ~s;
+    int p = parent_leaf[s];
+    while (true) {
+        const int side = (child[2 * p] == me) ? 0 : 1;
+        volatile float *nb = nodebox + 12 * p;
+        for (int k = 0; k < 6; k++) nb[6 * side + k] = box[k];
+        __threadfence();
+        if (atomicAdd(&arrive[p], 1) == 0) return;
+        __threadfence();
+        for (int k = 0; k < 3; k++) {
+            box[k] = fminf(nb[k], nb[6 + k]);
+            box[3 + k] = fmaxf(nb[3 + k], nb[9 + k]);
+        }
+        if (p == 0) return;
+        me = p;
+        p = parent_int[p];
+    }
+}
+
+__global__ void k_pack_nodes(int n, const int *child, const float *nodebox, Node *nodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const float *b = nodebox + 12 * i;
+    Node nd;
+    nd.a = make_float4(b[0], b[1], b[2], b[3]);
+    nd.b = make_float4(b[4], b[5], b[6], b[7]);
+    nd.c = make_float4(b[8], b[9], b[10], b[11]);
+    nd.d = make_int4(child[2 * i], child[2 * i + 1], 0, 0);
+    nodes[i] = nd;
+}
+
+__global__ void k_incidence(const int32_t *F, int nf, unsigned long long *pairs) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    for (int k = 0; k < 3; k++) pairs[3 * f + k] = ((unsigned long long)(unsigned)F[3 * f + k] << 32) | (unsigned)f;
+}
+__global__ void k_incidence_csr(const unsigned long long *pairs, int m, int nv, int32_t *inc_f, int32_t *vstart) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const unsigned long long p = pairs[i];
+    const int v = (int)(p >> 32);
+    inc_f[i] = (int)(p & 0xFFFFFFFFull);
+    const int vprev = i == 0 ? -1 : (int)(pairs[i - 1] >> 32);
+    for (int w = vprev + 1; w <= v; w++) vstart[w] = i;
+    if (i == m - 1)
+        for (int w = v + 1; w <= nv; w++) vstart[w] = m;
+}
+
+// vertex rows: normal = normalised sum of (b-a)x(c-a) over incident faces in
+// ascending face order; area = (sum of incident face areas) / 3
+__global__ void k_vertex_rows(const double *V, const int32_t *F, const int32_t *inc_f, const int32_t *vstart, int nv,
+                              double *pos, double *nrm, double *area) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0, A = 0.0;
+    for (int e = vstart[v]; e < vstart[v + 1]; e++) {
+        const int f = inc_f[e];
+        const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
+        const double ab0 = b[0] - a[0], ab1 = b[1] - a[1], ab2 = b[2] - a[2];
+        const double ac0 = c[0] - a[0], ac1 = c[1] - a[1], ac2 = c[2] - a[2];
+        const double N0 = ab1 * ac2 - ab2 * ac1;
+        const double N1 = ab2 * ac0 - ab0 * ac2;
+        const double N2 = ab0 * ac1 - ab1 * ac0;
+        const double ar = 0.5 * sqrt(N0 * N0 + N1 * N1 + N2 * N2);
+        S0 += N0; S1 += N1; S2 += N2;
+        A += ar;
+    }
+    const double l = sqrt(S0 * S0 + S1 * S1 + S2 * S2);
+    pos[3 * v] = V[3 * v]; pos[3 * v + 1] = V[3 * v + 1]; pos[3 * v + 2] = V[3 * v + 2];
+    nrm[3 * v] = l > 0.0 ? S0 / l : 0.0;
+    nrm[3 * v + 1] = l > 0.0 ? S1 / l : 0.0;
+    nrm[3 * v + 2] = l > 0.0 ? S2 / l : 0.0;
+    area[v] = A / 3.0;
+}
+
+template <typename T>
+__global__ void k_closest_points(DevMesh m, const double *P, int n, double *d2, int32_t *tri, double *bary,
+                                 int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Hit<T> h;
+    int e = 0;
+    closest<T>(m, (T)P[3 * i], (T)P[3 * i + 1], (T)P[3 * i + 2], -1, h, &e);
+    if (e) atomicOr(err, e);
+    d2[i] = (double)h.d2;
+    tri[i] = h.id;
+    bary[3 * i] = (double)h.b0;
+    bary[3 * i + 1] = (double)h.b1;
+    bary[3 * i + 2] = (double)h.b2;
+}
+
+__global__ void k_philox(unsigned long long start, unsigned long long n, uint32_t c2, uint32_t c3, uint32_t k0,
+                         uint32_t k1, uint32_t *out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long g = start + i;
+        const uint4 w = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), c2, c3), k0, k1);
+        reinterpret_cast<uint4 *>(out)[i] = w;
+    }
+}
+
+}  // namespace mcs
+
+using namespace mcs;
+
+// ---------------------------------------------------------------- host API
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void mesh_free(mcs_mesh_s *m) {
+    if (!m) return;
+    cudaFree(m->V); cudaFree(m->F); cudaFree(m->nodes); cudaFree(m->t32); cudaFree(m->t64);
+    cudaFree(m->inc_f); cudaFree(m->vstart); cudaFree(m->err);
+    delete m;
+}
+
+extern "C" {
+
+const char *mcs_last_error(void) { return g_err.c_str(); }
+const char *mcs_version(void) { return "mcsteklov 0.1 (sm_103a)"; }
+
+void mcs_mesh_destroy(mcs_mesh m) { mesh_free(m); }
+int mcs_mesh_nv(mcs_mesh m) { return m ? m->nv : 0; }
+int mcs_mesh_nf(mcs_mesh m) { return m ? m->nf : 0; }
+
+mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream_, mcs_mesh *out) {
+    MCS_ARG(out != nullptr, "mcs_build_bvh: out is NULL");
+    *out = nullptr;
+    MCS_ARG(V != nullptr && F != nullptr, "mcs_build_bvh: V or F is NULL");
+    MCS_ARG(nv >= 3 && nf >= 1, "mcs_build_bvh: need nv >= 3 and nf >= 1");
+    MCS_ARG((long long)nf * 3 < (1LL << 31) && (long long)nv * 3 < (1LL << 31), "mcs_build_bvh: mesh too large");
+    cudaStream_t st = as_stream(stream_);
+    const bool vdev = is_device_ptr(V), fdev = is_device_ptr(F);
+    mcs_mesh_s *m = new mcs_mesh_s();
+    m->nv = nv;
+    m->nf = nf;
+    cudaGetDevice(&m->device);
+    std::vector<void *> tmp;
+    auto fail = [&](mcs_status s) {
+        for (void *p : tmp) cudaFree(p);
+        mesh_free(m);
+        return s;
+    };
+#define MB_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
+    } while (0)
+    auto talloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        tmp.push_back(p);
+        return p;
+    };
+    MB_CUDA(cudaMalloc(&m->V, sizeof(double) * 3 * nv));
+    MB_CUDA(cudaMalloc(&m->F, sizeof(int32_t) * 3 * nf));
+    MB_CUDA(cudaMalloc(&m->err, sizeof(int)));
+    MB_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), st));
+    MB_CUDA(cudaMemcpyAsync(m->V, V, sizeof(double) * 3 * nv, vdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    MB_CUDA(cudaMemcpyAsync(m->F, F, sizeof(int32_t) * 3 * nf, fdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+
+    int *d_bad = (int *)talloc(sizeof(int) * 2);
+    const int nbp = 256;
+    double *d_part = (double *)talloc(sizeof(double) * 6 * nbp);
+    double *d_box = (double *)talloc(sizeof(double) * 6);
+    if (!d_bad || !d_part || !d_box) return fail(MCS_ERR_OOM);
+    MB_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
+    k_validate<<<num_sms() * 4, 256, 0, st>>>(m->V, nv, m->F, nf, d_bad);
+    k_bounds_partial<<<nbp, 256, 0, st>>>(m->V, nv, d_part);
+    k_bounds_final<<<1, 32, 0, st>>>(d_part, nbp, d_box);
+    int bad = 0;
+    double box[6];
+    MB_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MB_CUDA(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st));
+    MB_CUDA(cudaStreamSynchronize(st));
+    if (bad) {
+        set_error(bad & 1 ? "mcs_build_bvh: non-finite vertex coordinate" : "mcs_build_bvh: face index out of range");
+        return fail(MCS_ERR_DEGENERATE);
+    }
+    double side = INFINITY, scale = 0.0;
+    for (int k = 0; k < 3; k++) {
+        m->lo[k] = box[k];
+        m->hi[k] = box[3 + k];
+        side = fmin(side, box[3 + k] - box[k]);
+        scale = fmax(scale, fmax(fabs(box[k]), fabs(box[3 + k])));
+    }
+    if (!(side > 0.0)) {
+        set_error("mcs_build_bvh: the bounding box has a zero-length side");
+        return fail(MCS_ERR_DEGENERATE);
+    }
+    m->rmax = 0.5 * side;
+    m->scale = (float)scale * (1.0f + 1e-6f);
+
+    BoxFrame fr;
+    for (int k = 0; k < 3; k++) {
+        fr.lo[k] = box[k];
+        fr.inv[k] = 1.0 / (box[3 + k] - box[k]);
+    }
+    unsigned long long *keys = (unsigned long long *)talloc(sizeof(unsigned long long) * nf);
+    unsigned long long *keys_s = (unsigned long long *)talloc(sizeof(unsigned long long) * nf);
+    if (!keys || !keys_s) return fail(MCS_ERR_OOM);
+    const int tb = 256;
+    k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, fr, keys);
+    size_t sort_bytes = 0, sort_bytes2 = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes, keys, keys_s, nf, 0, 62, st);
+    unsigned long long *pairs = nullptr, *pairs_s = nullptr;
+    pairs = (unsigned long long *)talloc(sizeof(unsigned long long) * 3 * nf);
+    pairs_s = (unsigned long long *)talloc(sizeof(unsigned long long) * 3 * nf);
+    if (!pairs || !pairs_s) return fail(MCS_ERR_OOM);
+    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st);
+    void *d_sort = talloc(std::max(sort_bytes, sort_bytes2));
+    if (!d_sort) return fail(MCS_ERR_OOM);
+    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes, keys, keys_s, nf, 0, 62, st));
+
+    MB_CUDA(cudaMalloc(&m->t32, sizeof(Tri32) * nf));
+    MB_CUDA(cudaMalloc(&m->t64, sizeof(Tri64) * nf));
+    float *slotbox = (float *)talloc(sizeof(float) * 6 * nf);
+    if (!slotbox) return fail(MCS_ERR_OOM);
+    k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, m->t32, m->t64, slotbox);
+    if (nf > 1) {
+        int *child = (int *)talloc(sizeof(int) * 2 * (nf - 1));
+        int *par_i = (int *)talloc(sizeof(int) * (nf - 1));
+        int *par_l = (int *)talloc(sizeof(int) * nf);
+        float *nodebox = (float *)talloc(sizeof(float) * 12 * (nf - 1));
+        int *arrive = (int *)talloc(sizeof(int) * (nf - 1));
+        if (!child || !par_i || !par_l || !nodebox || !arrive) return fail(MCS_ERR_OOM);
+        MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
+        k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, child, par_i, par_l);
+        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, child, par_i, par_l, slotbox, nodebox, arrive);
+        MB_CUDA(cudaMalloc(&m->nodes, sizeof(Node) * (nf - 1)));
+        k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, child, nodebox, m->nodes);
+    }
+    // vertex -> incident faces, ascending
+    MB_CUDA(cudaMalloc(&m->inc_f, sizeof(int32_t) * 3 * nf));
+    MB_CUDA(cudaMalloc(&m->vstart, sizeof(int32_t) * (nv + 1)));
+    k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
+    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
+    MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
+    k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, m->inc_f, m->vstart);
+    MB_CUDA(cudaGetLastError());
+    MB_CUDA(cudaStreamSynchronize(st));
+    for (void *p : tmp) cudaFree(p);
+    tmp.clear();
+#undef MB_CUDA
+    *out = m;
+    return MCS_OK;
+}
+
+mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, void *stream_) {
+    MCS_ARG(m != nullptr, "mcs_vertex_rows: mesh is NULL");
+    MCS_ARG(pos && nrm && area, "mcs_vertex_rows: NULL output");
+    cudaStream_t st = as_stream(stream_);
+    k_vertex_rows<<<(m->nv + 255) / 256, 256, 0, st>>>(m->V, m->F, m->inc_f, m->vstart, m->nv, pos, nrm, area);
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, double *d2, int32_t *tri, double *bary,
+                              void *stream_) {
+    MCS_ARG(m != nullptr, "mcs_closest_points: mesh is NULL");
+    MCS_ARG(n >= 0, "mcs_closest_points: n < 0");
+    MCS_ARG(prec == 32 || prec == 64, "mcs_closest_points: prec must be 32 or 64");
+    if (n == 0) return MCS_OK;
+    MCS_ARG(P && d2 && tri && bary, "mcs_closest_points: NULL pointer");
+    cudaStream_t st = as_stream(stream_);
+    int *d_err = m->err;
+    MCS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    if (prec == 64)
+        k_closest_points<double><<<(n + 127) / 128, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+    else
+        k_closest_points<float><<<(n + 127) / 128, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+    int err = 0;
+    MCS_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("mcs_closest_points: BVH traversal stack overflow");
+        return MCS_ERR_DEVICE;
+    }
+    return MCS_OK;
+}
+
+mcs_status mcs_philox_words(uint64_t start, uint64_t n, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                            uint32_t *out, void *stream_) {
+    MCS_ARG(out != nullptr || n == 0, "mcs_philox_words: out is NULL");
+    if (n == 0) return MCS_OK;
+    k_philox<<<num_sms() * 4, 256, 0, as_stream(stream_)>>>(start, n, c2, c3, k0, k1, out);
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Hit counts, closest points, rows and Philox words are compared bit for bit
+(both sides follow the same written arithmetic, in the precision the kernel
+decides in); Lambda within 1e-12 of its largest entry (the FP64 row sums are
+accumulated in a different order).
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_05581_b300 as mcs  # noqa: E402
+
+
+def _rows_to_torch(rows):
+    out = dict(pos=torch.from_numpy(rows["pos"]).cuda(), nrm=torch.from_numpy(rows["nrm"]).cuda(),
+               area=torch.from_numpy(rows["area"]).cuda(), tri2bin=None)
+    if rows.get("tri2bin") is not None:
+        out["tri2bin"] = torch.from_numpy(rows["tri2bin"].astype(np.int32)).cuda()
+    return out
+
+
+def test_philox_words_match(oracle):
+    n = 1 << 20
+    g = mcs.philox_words(5, n, 3, 7, 0x0123456789ABCDEF).cpu().numpy().view(np.uint32)
+    c = oracle.philox(5, n, 3, 7, 0x0123456789ABCDEF)
+    assert np.array_equal(g, c)
+
+
+@pytest.mark.parametrize("which", ["ico2", "two3", "wild"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_closest_points_bit_exact(oracle, which, prec):
+    m = {"ico2": lambda: meshgen.icosphere(2), "two3": lambda: meshgen.two_spheres(3, 0.5, 1.5),
+         "wild": lambda: meshgen.wild_union(6, 6000, seed=4)}[which]()
+    rng = np.random.default_rng(7)
+    lo, hi = m.V.min(0), m.V.max(0)
+    P = rng.uniform(lo - 0.3, hi + 0.3, size=(4000, 3))
+    P[:50] = m.V[:50]                         # on vertices: exact ties between faces
+    P[50:100] = m.V[m.F[:50]].mean(1)         # on faces
+    mesh = mcs.Mesh(m.V, m.F)
+    d2g, fg, bg = (t.cpu().numpy() for t in mcs.closest_points(mesh, torch.from_numpy(P), prec))
+    d2c, fc, bc = oracle.closest_points(m.V, m.F, P, prec)
+    assert np.array_equal(fg, fc)
+    assert np.array_equal(d2g, d2c)
+    assert np.array_equal(bg, bc)
+
+
+def test_vertex_rows_bit_exact(oracle):
+    m = meshgen.wild_union(5, 4000, seed=1)
+    mesh = mcs.Mesh(m.V, m.F)
+    r = mcs.vertex_rows(mesh)
+    o = oracle.vertex_rows(m.V, m.F)
+    for k in ("pos", "nrm", "area"):
+        assert np.array_equal(r[k].cpu().numpy(), o[k]), k
+
+
+def _compare(oracle, m, rows_np, W, eps, prec, exterior=False, killing=0, seed=0, row_list=None, check_L=True,
+             origin=None):
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = _rows_to_torch(rows_np)
+    kw = dict(walks_per_row=W, eps=eps, prec=prec, seed=seed, domain=1 if exterior else 0, killing_walks=killing)
+    if origin is not None:
+        kw["origin"] = origin
+    p = mcs.default_params(**kw)
+    res = mcs.estimate_dtn(mesh, rows, p, assemble=check_L, record_exits=True)
+    torch.cuda.synchronize()
+    R = rows["pos"].shape[0]
+    H = mcs.dense_hist(res, R).cpu().numpy()
+    st = res["stats"]
+    o = np.array(st["origin"]) if exterior else None
+    est = oracle.estimate(m.V, m.F, rows_np, W, eps, exterior=exterior, origin=o, seed=seed, prec=prec,
+                          row_list=row_list, killing_walks=killing, record_exits=True)
+    rl = est["row_list"]
+    assert np.array_equal(H[rl], est["H"]), f"hit counts differ in {np.sum(H[rl] != est['H'])} entries"
+    assert np.array_equal(res["exit_tri"].cpu().numpy()[rl], est["exit_tri"])
+    if killing:
+        assert np.array_equal(res["H0"].cpu().numpy(), est["H0"])
+    om = res["omega"].cpu().numpy()[rl]
+    assert np.array_equal(om, oracle.row_weights(est, rows_np))
+    if check_L and row_list is None:
+        L = res["Lambda"].cpu().numpy()
+        Lo = oracle.assemble(est, rows_np, exterior=exterior, origin=o, killing=killing > 0)
+        assert np.array_equal(L, L.T)
+        assert np.abs(L - Lo).max() <= 1e-12 * np.abs(Lo).max()
+    return res, est
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_interior_icosphere_bit_exact(oracle, prec):
+    """The small sphere workload: icosphere s2, 128 walks per vertex, eps 1e-3, seed 0."""
+    m = meshgen.icosphere(2)
+    rows = oracle.vertex_rows(m.V, m.F)
+    res, est = _compare(oracle, m, rows, 128, 1e-3, prec)
+    assert res["stats"]["steps"] == est["steps"].sum()
+    assert np.all(res["hist_nnz"].cpu().numpy() <= 128)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_exterior_two_spheres_bit_exact(oracle, prec):
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    o = oracle.interior_origin(m.V, m.F, rows)
+    res, est = _compare(oracle, m, rows, 64, 1e-3, prec, exterior=True, killing=2048, seed=3)
+    assert np.array_equal(np.array(res["stats"]["origin"]), o)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_sample_rows_wild_bit_exact(oracle, prec):
+    """FPS sample rows on a small in-the-wild union (flips, noise, slivers), tri2bin columns."""
+    m = meshgen.wild_union(6, 5000, seed=9)
+    rows = oracle.fps_rows(m.V, m.F, 300, orient=True)
+    _compare(oracle, m, rows, 64, 1e-3, prec)
+
+
+def test_two_spheres_full_size_sampled_rows(oracle):
+    """Two s4 spheres, exterior, FP32, 1024 walks per vertex: the full-size launch,
+    checked on sampled rows (the oracle recomputes each row's walks alone)."""
+    m = meshgen.two_spheres(4, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    rl = np.array([0, 1, 777, 2561, 2562, 4000, 5123], np.int32)
+    _compare(oracle, m, rows, 1024, 1e-3, 32, exterior=True, row_list=rl, check_L=False,
+             origin=oracle.interior_origin(m.V, m.F, rows))
+
+
+def test_ragged_and_degenerate_rows(oracle):
+    """Odd row counts, a zero-normal row and a row whose tangent ball is too small."""
+    m = meshgen.icosphere(2)
+    rows = oracle.vertex_rows(m.V, m.F)
+    rows = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in rows.items()}
+    rows["nrm"][3] = 0.0
+    res, est = _compare(oracle, m, rows, 6, 1e-3, 64)
+    assert res["hist_nnz"].cpu().numpy()[3] == 0
+    assert res["stats"]["discarded_rows"] == 1
+
+
+def test_lambda_invariants_icosphere():
+    m = meshgen.icosphere(3)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32))
+    L = res["Lambda"].cpu().numpy()
+    assert np.array_equal(L, L.T)
+    assert np.abs(L.sum(1)).max() < 1e-12 * np.abs(L).max()
+    assert np.linalg.eigvalsh(L).min() > -1e-10 * np.abs(L).max()
+    nnz = res["hist_nnz"].cpu().numpy()
+    cnt = res["hist_cnt"].cpu().numpy().reshape(m.nv, -1)
+    assert all(cnt[v, :nnz[v]].sum() == 256 for v in range(m.nv))
+
+
+def test_invalid_arguments_are_rejected():
+    m = meshgen.icosphere(1)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    with pytest.raises(mcs.MCSError):
+        mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=7))
+    with pytest.raises(mcs.MCSError):
+        mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=8, eps=-1.0))
+    bad = m.V.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(mcs.MCSError):
+        mcs.Mesh(bad, m.F)
+    with pytest.raises(mcs.MCSError):
+        mcs.Mesh(m.V, m.F + 1000)
