@@ -151,7 +151,7 @@ __global__ void k_origin_argmax(const RowBall *ball, int R, Ctrl *ctrl) {
         const int v = si[0];
         ctrl->argmax_row = v;
         if (!(sv[0] > 0.0)) {
-            ctrl->err |= 2;
+            ctrl->err |= kErrNoOrigin;
             ctrl->origin[0] = ctrl->origin[1] = ctrl->origin[2] = 0.0;
         } else {
             ctrl->origin[0] = ball[v].c[0];
@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(128) k_walks(WalkArgs a) {
     auto finish = [&](int bin, int f, bool capped, bool lost) {
         n_capped += capped;
         n_lost += lost;
+        if (bin >= a.R) { err |= kErrBin; bin = -1; }
         if (a.killing) {
             if (bin >= 0) atomicAdd(&a.H0[bin], 1);
         } else {
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const int32_t *exits
     for (int j = threadIdx.x; j < Wr; j += blockDim.x) {
         const int bin = j < W ? ex[j] : -1;
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
-        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+        if (bin >= 0 && bin < R && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
     }
     __syncthreads();
     const int chunk = (R + blockDim.x - 1) / blockDim.x;
@@ -814,12 +815,13 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     for (int k = 0; k < 3; k++) stats->origin[k] = ext ? hc.origin[k] : 0.0;
     stats->rmax = ext ? hc.rmax_ext : m->rmax;
     stats->device_error = hc.err;
-    if (hc.err & 2) {
+    if (hc.err & kErrNoOrigin) {
         set_error("mcs_estimate_dtn: no interior tangent ball to place the inversion centre");
         return MCS_ERR_NO_INTERIOR_POINT;
     }
     if (hc.err) {
-        set_error("mcs_estimate_dtn: BVH traversal stack overflow on the device");
+        set_error(hc.err & kErrBin ? "mcs_estimate_dtn: tri2bin maps a triangle outside [0, n_rows)"
+                                   : "mcs_estimate_dtn: BVH traversal stack or iteration bound exceeded");
         return MCS_ERR_DEVICE;
     }
     return (hc.capped || hc.kill_capped) ? MCS_WARN_CAPPED : MCS_OK;

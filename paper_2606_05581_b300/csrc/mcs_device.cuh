@@ -18,7 +18,10 @@ constexpr int kMaxReject = 32;
 constexpr int kStackDepth = 64;
 
 // device status word bits
-constexpr int kErrStack = 1;
+constexpr int kErrStack = 1;       // traversal stack full (a far child was dropped)
+constexpr int kErrNoOrigin = 2;    // exterior: no interior tangent ball for the inversion centre
+constexpr int kErrTree = 4;        // traversal / refit exceeded its iteration bound
+constexpr int kErrBin = 8;         // an exit bin outside [0, n_rows)
 
 // --------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -346,7 +349,10 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
     float sdist[kStackDepth];
     int sp = 0;
     int node = 0;
-    while (true) {
+    // a tree over nf leaves has nf - 1 internal nodes: a traversal visits each
+    // at most once, so a longer one means a malformed tree
+    for (int guard = 0;; guard++) {
+        if (guard > 2 * m.nf + 64) { *err |= kErrTree; break; }
         if (COUNT) work->nodes++;
         const Node nd = m.nodes[node];
         const T d0 = box_d2<T>(px, py, pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);

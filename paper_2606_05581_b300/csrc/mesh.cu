@@ -168,14 +168,16 @@ __global__ void k_karras(const unsigned long long *k, int n, int *child, int *pa
 // bottom-up refit: one thread per leaf climbs; the second arrival at a node
 // unites its two child boxes and continues
 __global__ void k_refit(int n, const int *child, const int *parent_int, const int *parent_leaf, const float *slotbox,
-                        float *nodebox, int *arrive) {
+                        float *nodebox, int *arrive, int *err) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     float box[6];
     for (int k = 0; k < 6; k++) box[k] = slotbox[6 * s + k];
     int me = ~s;
     int p = parent_leaf[s];
-    while (true) {
+    // 64-bit keys bound the depth of the hierarchy by 64
+    for (int level = 0;; level++) {
+        if (level > 70 || p < 0 || p >= n - 1) { atomicOr(err, kErrTree); return; }
         const int side = (child[2 * p] == me) ? 0 : 1;
         volatile float *nb = nodebox + 12 * p;
         for (int k = 0; k < 6; k++) nb[6 * side + k] = box[k];
@@ -406,8 +408,10 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         int *arrive = (int *)talloc(sizeof(int) * (nf - 1));
         if (!child || !par_i || !par_l || !nodebox || !arrive) return fail(MCS_ERR_OOM);
         MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
+        MB_CUDA(cudaMemsetAsync(par_i, 0xFF, sizeof(int) * (nf - 1), st));
+        MB_CUDA(cudaMemsetAsync(par_l, 0xFF, sizeof(int) * nf, st));
         k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, child, par_i, par_l);
-        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, child, par_i, par_l, slotbox, nodebox, arrive);
+        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, child, par_i, par_l, slotbox, nodebox, arrive, d_bad + 1);
         MB_CUDA(cudaMalloc(&m->nodes, sizeof(Node) * (nf - 1)));
         k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, child, nodebox, m->nodes);
     }
@@ -419,7 +423,13 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
     k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, m->inc_f, m->vstart);
     MB_CUDA(cudaGetLastError());
+    int tree_err = 0;
+    MB_CUDA(cudaMemcpyAsync(&tree_err, d_bad + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     MB_CUDA(cudaStreamSynchronize(st));
+    if (tree_err) {
+        set_error("mcs_build_bvh: internal error, malformed hierarchy");
+        return fail(MCS_ERR_DEVICE);
+    }
     for (void *p : tmp) cudaFree(p);
     tmp.clear();
 #undef MB_CUDA
