@@ -43,6 +43,7 @@ typedef struct mcs_mesh_s *mcs_mesh;
 typedef enum {
     MCS_OK = 0,
     MCS_WARN_CAPPED = 1,            /* some walks hit max_steps (still counted) */
+    MCS_WARN_NOT_CONVERGED = 2,     /* eigensolve: residual tolerance not met  */
     MCS_ERR_ARG = -1,
     MCS_ERR_CUDA = -2,
     MCS_ERR_OOM = -3,
@@ -169,6 +170,42 @@ size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, lo
  * Returns MCS_WARN_CAPPED when stats are requested and some walk was capped. */
 mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
                             void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream);
+
+/* Steklov eigensolve (Eq. steklov-eigenproblem, Galerkin form Lambda psi =
+ * lambda M psi with M = diag(mass); smallest k pairs, Sec. 4.4 / Sec. 5).
+ * Chebyshev-filtered subspace iteration on a block of m = k + 32 vectors
+ * (rounded up to 16, at most 160): filter products A*Y on the tensor cores
+ * (tcgen05 kind::tf32, operands split into tf32 high/low parts), FP64
+ * shifted CholeskyQR + CholeskyQR2 orthonormalisation, Rayleigh-Ritz with a
+ * parallel Jacobi on the block, Ritz values as FP64 Rayleigh quotients. */
+typedef struct {
+    int degree;             /* Chebyshev filter degree per iteration (10)        */
+    int max_iters;          /* outer iterations (60)                             */
+    double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-6) */
+} mcs_eig_params;
+typedef struct {
+    int iterations, converged, block, tc_products;
+    double upper_bound, max_residual;
+    int device_error;
+} mcs_eig_stats;
+void mcs_default_eig_params(mcs_eig_params *p);
+size_t mcs_steklov_workspace_size(int n, int k);
+/* Lambda: device n x n FP64 symmetric (row-major); mass: device n (> 0);
+ * evals: k FP64, host or device (ascending); evecs: device n x k FP64
+ * row-major psi (M-orthonormal), or NULL; workspace: device, 256-byte
+ * aligned, >= mcs_steklov_workspace_size(n, k).  Requires 16 <= n and
+ * 1 <= k <= min(128, n/2 - 1).  Synchronises `stream` (the convergence test
+ * reads the residuals on the host each iteration).  Returns
+ * MCS_WARN_NOT_CONVERGED when max_iters was reached first. */
+mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, int k, double *evals, double *evecs,
+                             void *workspace, size_t workspace_bytes, const mcs_eig_params *params,
+                             mcs_eig_stats *stats, void *stream);
+/* Test hook: Zt = (A X)^T through the same tensor-core product, for a
+ * symmetric A (device n x n FP64) and Xt (device m x n FP64, m a multiple
+ * of 16 in [16, 160]); Zt device m x n FP64. */
+size_t mcs_tc_symm_product_workspace_size(int n, int m);
+mcs_status mcs_tc_symm_product(const double *A, const double *Xt, int n, int m, double *Zt, void *workspace,
+                               size_t workspace_bytes, void *stream);
 
 /* Test hook: Philox-4x32-10 words for counters (i_lo, i_hi, c2, c3),
  * i = start .. start+n-1, key (k0, k1); device output n x 4. */

@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 __all__ = ["lib", "Mesh", "default_params", "vertex_rows", "closest_points", "philox_words", "estimate_dtn",
-           "workspace_size", "MCSError"]
+           "workspace_size", "steklov_modes", "tc_symm_product", "MCSError"]
 
 _LIB_PATH = _build.LIB
 
@@ -53,6 +53,15 @@ class Stats(C.Structure):
                 ("tris_tested", C.c_longlong)]
 
 
+class EigParams(C.Structure):
+    _fields_ = [("degree", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double)]
+
+
+class EigStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("block", C.c_int), ("tc_products", C.c_int),
+                ("upper_bound", C.c_double), ("max_residual", C.c_double), ("device_error", C.c_int)]
+
+
 _lib = None
 
 
@@ -78,6 +87,14 @@ def lib():
         L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
                                        C.POINTER(Stats), vp]
         L.mcs_philox_words.argtypes = [u64, u64, u32, u32, u32, u32, vp, vp]
+        L.mcs_default_eig_params.argtypes = [C.POINTER(EigParams)]
+        L.mcs_steklov_workspace_size.argtypes = [i32, i32]
+        L.mcs_steklov_workspace_size.restype = C.c_size_t
+        L.mcs_steklov_modes.argtypes = [vp, vp, i32, i32, vp, vp, vp, C.c_size_t, C.POINTER(EigParams),
+                                        C.POINTER(EigStats), vp]
+        L.mcs_tc_symm_product_workspace_size.argtypes = [i32, i32]
+        L.mcs_tc_symm_product_workspace_size.restype = C.c_size_t
+        L.mcs_tc_symm_product.argtypes = [vp, vp, i32, i32, vp, vp, C.c_size_t, vp]
         _lib = L
     return _lib
 
@@ -231,3 +248,42 @@ def dense_hist(res: dict, R: int) -> torch.Tensor:
     H = torch.zeros((R, R), dtype=torch.int32, device=nnz.device)
     H[rows, bins] = cnts
     return H
+
+
+def default_eig_params(**kw) -> EigParams:
+    p = EigParams()
+    lib().mcs_default_eig_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def steklov_modes(Lambda: torch.Tensor, mass: torch.Tensor, k: int, params: EigParams | None = None,
+                  vectors: bool = True, workspace: Workspace | None = None):
+    """Smallest k eigenpairs of Lambda psi = lambda M psi; returns (evals, evecs, stats)."""
+    n = int(Lambda.shape[0])
+    L = Lambda.contiguous()
+    M = mass.to(torch.float64).contiguous()
+    ev = torch.empty(k, dtype=torch.float64, device=L.device)
+    X = torch.empty((n, k), dtype=torch.float64, device=L.device) if vectors else None
+    nb = int(lib().mcs_steklov_workspace_size(n, k))
+    ws = (workspace or Workspace()).get(nb)
+    st = EigStats()
+    status = _check(lib().mcs_steklov_modes(_ptr(L), _ptr(M), n, k, _ptr(ev), _ptr(X), C.c_void_p(_aligned_ptr(ws)),
+                                            nb, C.byref(params) if params is not None else None, C.byref(st),
+                                            _stream()))
+    stats = {f: getattr(st, f) for f, _ in EigStats._fields_}
+    stats["status"] = status
+    return ev, X, stats
+
+
+def tc_symm_product(A: torch.Tensor, Xt: torch.Tensor) -> torch.Tensor:
+    """Test hook: (A X)^T via the tensor-core split product (A symmetric n x n, Xt m x n)."""
+    n, m = int(A.shape[0]), int(Xt.shape[0])
+    A = A.to(torch.float64).contiguous()
+    Xt = Xt.to(torch.float64).contiguous()
+    Zt = torch.empty_like(Xt)
+    nb = int(lib().mcs_tc_symm_product_workspace_size(n, m))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=A.device)
+    _check(lib().mcs_tc_symm_product(_ptr(A), _ptr(Xt), n, m, _ptr(Zt), C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return Zt

@@ -1,0 +1,841 @@
+// eig.cu -- Steklov eigenpairs: smallest k eigenpairs of M^-1/2 Lambda M^-1/2
+// (Eq. steklov-eigenproblem in Galerkin form Lambda psi = lambda M psi).
+//
+// Chebyshev-filtered subspace iteration (Zhou & Saad 2007) on a block of
+// m = k + guard vectors:
+//   filter     Y <- p_d(A) Y by the scaled three-term recurrence; each term is
+//              one A*Y product on the tensor cores (tcgen05, kind::tf32) with
+//              A and Y split into tf32 high/low parts (hi*hi + hi*lo + lo*hi,
+//              FP32-level accuracy), fed by TMA into 128B-swizzled shared
+//              memory, accumulated in TMEM, split over K and combined by a
+//              deterministic FP32 kernel that also applies the recurrence;
+//   orthonorm  shifted CholeskyQR followed by CholeskyQR2, all in FP64;
+//   Rayleigh-Ritz  H = X^T A X (FP64 Gram of the tensor-core product), its
+//              eigenvectors by a parallel cyclic Jacobi in FP32 on one SM, the
+//              rotated block re-orthonormalised in FP64 at the next step;
+//              Ritz values as FP64 Rayleigh quotients.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "mcs_internal.h"
+
+namespace mcs {
+namespace eig {
+
+constexpr int BM = 128;          // rows of A per CTA (MMA M)
+constexpr int BK = 32;           // K per pipeline stage: 32 fp32 = one 128-byte swizzle row
+constexpr int kTcThreads = 128;  // 4 warps: TMA producer, MMA issuer, all four drain TMEM
+constexpr int kErrTimeout = 16;  // an mbarrier wait exceeded its time bound
+constexpr int kErrChol = 32;     // Cholesky met a non-positive pivot
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait: gives up after ~2 s of wall time and sets the error flag
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255) == 0) {
+            const uint64_t t = gtime();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 2000000000ull) {
+                atomicOr(err, kErrTimeout);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+// tcgen05 shared-memory descriptor: K-major operand, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart (SBO), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcArgs {
+    float *part;     // splits x m x n_pad partial products, transposed (column-major in rows)
+    int n_pad, m;
+    int ktiles, kt_per_split;
+    int stages;
+    uint32_t idesc;
+    uint32_t tmem_cols;
+    int *err;
+};
+
+// P[split][j][i] = sum_{k in split} A[i][k] * Bt[j][k] with A = Ahi + Alo and
+// Bt = Bhi + Blo (tf32 parts); CTA (tile, split) owns rows [128 tile, +128)
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+              const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[4], empty[4], done;
+    __shared__ uint32_t tmem_slot;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * BM;
+    const int kt0 = blockIdx.y * a.kt_per_split;
+    const int nk = min(a.ktiles, kt0 + a.kt_per_split) - kt0;
+    const int m = a.m, S = a.stages;
+    const uint32_t A_BYTES = BM * 128, B_BYTES = (uint32_t)m * 128;
+    const uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    const uint32_t sbase = smem_u32(smem);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int it = 0; it < nk && ok; it++) {
+            const int s = it % S, r = it / S;
+            if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (r - 1) & 1, a.err)) { ok = false; break; }
+            const uint32_t bar = smem_u32(&full[s]);
+            mbar_expect_tx(bar, STAGE);
+            const uint32_t st = sbase + s * STAGE;
+            const int k = (kt0 + it) * BK;
+            tma_load_2d(st, &tAh, k, row0, bar);
+            tma_load_2d(st + A_BYTES, &tAl, k, row0, bar);
+            tma_load_2d(st + 2 * A_BYTES, &tBh, k, 0, bar);
+            tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tBl, k, 0, bar);
+            issued = it + 1;
+        }
+        // do not leave with copies in flight: wait (bounded) for the last stages
+        for (int it = (issued > S ? issued - S : 0); it < issued; it++)
+            mbar_wait(smem_u32(&full[it % S]), (it / S) & 1, a.err);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 4 K-steps of 8 per stage, three split products each
+        for (int it = 0; it < nk; it++) {
+            const int s = it % S, r = it / S;
+            if (!mbar_wait(smem_u32(&full[s]), r & 1, a.err)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = sbase + s * STAGE;
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; kk++) {
+                const uint64_t ah = sdesc_sw128(st + kk * 32), al = sdesc_sw128(st + A_BYTES + kk * 32);
+                const uint64_t bh = sdesc_sw128(st + 2 * A_BYTES + kk * 32);
+                const uint64_t bl = sdesc_sw128(st + 2 * A_BYTES + B_BYTES + kk * 32);
+                mma_tf32(tmem, ah, bh, a.idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, ah, bl, a.idesc, 1u);
+                mma_tf32(tmem, al, bh, a.idesc, 1u);
+            }
+            mma_commit(smem_u32(&empty[s]));
+        }
+        mma_commit(smem_u32(&done));
+    }
+    __syncwarp();
+    // drain the accumulator: warp w owns TMEM lanes (rows) 32w .. 32w+31
+    const bool got = mbar_wait(smem_u32(&done), 0, a.err);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (got) {
+        const int row = row0 + warp * 32 + lane;
+        float *P = a.part + (size_t)blockIdx.y * m * a.n_pad;
+        for (int c = 0; c < m; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) P[(size_t)(c + j) * a.n_pad + row] = v[j];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------- SIMT kernels
+// A = M^-1/2 Lambda M^-1/2 as tf32 high/low parts (zero padded), and the
+// absolute row sums of A (Gershgorin bound of its spectrum)
+__global__ void k_prep_A(const double *L, const double *mass, int n, int n_pad, float *Ahi, float *Alo,
+                         double *rowabs) {
+    const int i = blockIdx.x;
+    __shared__ double red[256];
+    double acc = 0.0;
+    const double si = i < n ? 1.0 / sqrt(mass[i]) : 0.0;
+    for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
+        float h = 0.f, l = 0.f;
+        if (i < n && j < n) {
+            const double sj = 1.0 / sqrt(mass[j]);
+            const double v = L[(size_t)i * n + j] * (si * sj);
+            acc += fabs(v);
+            const float f = (float)v;
+            h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+            l = f - h;
+        }
+        Ahi[(size_t)i * n_pad + j] = h;
+        Alo[(size_t)i * n_pad + j] = l;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && i < n) rowabs[i] = red[0];
+}
+
+__global__ void k_max_reduce(const double *x, int n, double *out) {
+    __shared__ double red[1024];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, x[i]);
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// deterministic start block: Philox uniforms in (-1, 1)
+__global__ void k_random_block(double *Xt, int m, int n, int n_pad) {
+    const size_t total = (size_t)m * n_pad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n_pad), i = (int)(e % n_pad);
+        double v = 0.0;
+        if (i < n) {
+            const uint4 w = philox(make_uint4((uint32_t)i, (uint32_t)j, 0x5EEDu, 0u), 0x1234567u, 0x89ABCDEu);
+            v = 2.0 * uni64(w.x, w.y) - 1.0;
+        }
+        Xt[e] = v;
+    }
+}
+
+// FP64 block -> tf32 high/low parts
+__global__ void k_split(const double *X, size_t total, float *hi, float *lo) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const float f = (float)X[e];
+        const float h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+        hi[e] = h;
+        lo[e] = f - h;
+    }
+}
+
+// out = alpha * (sum of the K-split partials) + beta * Y + gamma * X, for
+// rows < n (padding stays zero); written as tf32 parts and/or FP64
+__global__ void k_combine(const float *P, int splits, int m, int n, int n_pad, double alpha, double beta,
+                          double gamma, const float *Yh, const float *Yl, const float *Xh, const float *Xl,
+                          float *Oh, float *Ol, double *O64) {
+    const size_t total = (size_t)m * n_pad;
+    const size_t stride = (size_t)m * n_pad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n_pad);
+        float r = 0.f;
+        if (i < n) {
+            float s = 0.f;
+            for (int q = 0; q < splits; q++) s += P[q * stride + e];
+            double v = alpha * (double)s;
+            if (Yh) v += beta * ((double)Yh[e] + (double)Yl[e]);
+            if (Xh) v += gamma * ((double)Xh[e] + (double)Xl[e]);
+            if (O64) O64[e] = v;
+            r = (float)v;
+        } else if (O64) {
+            O64[e] = 0.0;
+        }
+        if (Oh) {
+            const float h = __uint_as_float(__float_as_uint(r) & 0xFFFFE000u);
+            Oh[e] = h;
+            Ol[e] = r - h;
+        }
+    }
+}
+
+// G[a][b] = sum_i A[a][i] B[b][i] (FP64), one block per (a, b); sym: a <= b mirrored
+__global__ void k_gram(const double *A, const double *B, int m, int n_pad, double *G, int sym) {
+    const int a = blockIdx.y, b = blockIdx.x;
+    if (sym && a > b) return;
+    __shared__ double red[256];
+    const double *x = A + (size_t)a * n_pad, *y = B + (size_t)b * n_pad;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) s += x[i] * y[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        G[a * m + b] = red[0];
+        if (sym) G[b * m + a] = red[0];
+    }
+}
+
+// upper Cholesky factor of G + shift I (FP64, one block, G in shared memory)
+__global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, int *err) {
+    extern __shared__ double sg[];
+    __shared__ double tr;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sg[e] = G[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int j = 0; j < m; j++) t += sg[j * m + j];
+        tr = t;
+    }
+    __syncthreads();
+    const double shift = shift_rel * tr;
+    for (int j = 0; j < m; j++) {
+        if (threadIdx.x == 0) {
+            double s = sg[j * m + j] + shift;
+            for (int k = 0; k < j; k++) s -= sg[k * m + j] * sg[k * m + j];
+            if (!(s > 0.0)) { atomicOr(err, kErrChol); s = 1e-300; }
+            sg[j * m + j] = sqrt(s);
+        }
+        __syncthreads();
+        const double d = sg[j * m + j];
+        for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
+            double s = sg[j * m + c];
+            for (int k = 0; k < j; k++) s -= sg[k * m + j] * sg[k * m + c];
+            sg[j * m + c] = s / d;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        R[e] = c >= r ? sg[e] : 0.0;
+    }
+}
+
+// X <- X R^-1 (rows of X = columns of Xt), R upper triangular in shared memory
+__global__ void k_trsm_right(double *Xt, const double *R, int m, int n, int n_pad) {
+    extern __shared__ double sr[];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sr[e] = R[e];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y[256];
+    for (int j = 0; j < m; j++) {
+        double s = Xt[(size_t)j * n_pad + i];
+        for (int k = 0; k < j; k++) s -= y[k] * sr[k * m + j];
+        y[j] = s / sr[j * m + j];
+    }
+    for (int j = 0; j < m; j++) Xt[(size_t)j * n_pad + i] = y[j];
+}
+
+// Xt <- Q^T Xt (X <- X Q), Q m x m FP32 from the Jacobi solver
+__global__ void k_rotate(double *Xt, const float *Q, int m, int n, int n_pad) {
+    extern __shared__ float sq[];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sq[e] = Q[e];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[256];
+    for (int k = 0; k < m; k++) x[k] = Xt[(size_t)k * n_pad + i];
+    for (int j = 0; j < m; j++) {
+        double s = 0.0;
+        for (int k = 0; k < m; k++) s += (double)sq[k * m + j] * x[k];
+        Xt[(size_t)j * n_pad + i] = s;
+    }
+}
+
+// Ritz values theta_j = x_j.z_j / x_j.x_j and residual norms |z_j - theta_j x_j|
+__global__ void k_ritz(const double *Xt, const double *Zt, int n_pad, double *theta, double *res) {
+    const int j = blockIdx.x;
+    __shared__ double r1[256], r2[256], r3[256];
+    const double *x = Xt + (size_t)j * n_pad, *z = Zt + (size_t)j * n_pad;
+    double xz = 0, xx = 0, zz = 0;
+    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) { xz += x[i] * z[i]; xx += x[i] * x[i]; zz += z[i] * z[i]; }
+    r1[threadIdx.x] = xz; r2[threadIdx.x] = xx; r3[threadIdx.x] = zz;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) { r1[threadIdx.x] += r1[threadIdx.x + s]; r2[threadIdx.x] += r2[threadIdx.x + s]; r3[threadIdx.x] += r3[threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double t = r1[0] / r2[0];
+        theta[j] = t;
+        res[j] = sqrt(fmax(r3[0] - 2.0 * t * r1[0] + t * t * r2[0], 0.0) / r2[0]);
+    }
+}
+
+// symmetric eigendecomposition of H (m x m, m even <= 160) by parallel cyclic
+// Jacobi (round-robin pair schedule) in FP32, one block; eigenvalues ascending,
+// eigenvectors in the columns of Q
+__global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int max_sweeps) {
+    extern __shared__ float sj[];
+    float *H = sj, *V = sj + m * m;
+    __shared__ float cs[80], sn[80];
+    __shared__ int pp[80], qq[80];
+    __shared__ float off, nrm;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        H[e] = (float)(0.5 * (Hd[r * m + c] + Hd[c * m + r]));
+        V[e] = r == c ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const int half = m / 2;
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        if (threadIdx.x == 0) {
+            float o = 0.f, t = 0.f;
+            for (int e = 0; e < m * m; e++) {
+                const float v = H[e] * H[e];
+                t += v;
+                if (e / m != e % m) o += v;
+            }
+            off = o; nrm = t;
+        }
+        __syncthreads();
+        if (off <= 1e-14f * nrm) break;
+        for (int r = 0; r < m - 1; r++) {
+            if (threadIdx.x < half) {
+                const int i = threadIdx.x;
+                int p, q;
+                if (i == 0) { p = m - 1; q = r; }
+                else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
+                if (p > q) { const int t = p; p = q; q = t; }
+                pp[i] = p; qq[i] = q;
+                const float apq = H[p * m + q];
+                float c = 1.f, s = 0.f;
+                if (fabsf(apq) > 1e-30f) {
+                    const float tau = (H[q * m + q] - H[p * m + p]) / (2.f * apq);
+                    const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+                    c = 1.f / sqrtf(1.f + t * t);
+                    s = t * c;
+                }
+                cs[i] = c; sn[i] = s;
+            }
+            __syncthreads();
+            // columns: H <- H J, V <- V J
+            for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
+                const int i = e / m, row = e % m;
+                const int p = pp[i], q = qq[i];
+                const float c = cs[i], s = sn[i];
+                const float hp = H[row * m + p], hq = H[row * m + q];
+                H[row * m + p] = c * hp - s * hq;
+                H[row * m + q] = s * hp + c * hq;
+                const float vp = V[row * m + p], vq = V[row * m + q];
+                V[row * m + p] = c * vp - s * vq;
+                V[row * m + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // rows: H <- J^T H
+            for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
+                const int i = e / m, col = e % m;
+                const int p = pp[i], q = qq[i];
+                const float c = cs[i], s = sn[i];
+                const float hp = H[p * m + col], hq = H[q * m + col];
+                H[p * m + col] = c * hp - s * hq;
+                H[q * m + col] = s * hp + c * hq;
+            }
+            __syncthreads();
+        }
+    }
+    // sort ascending (selection of ranks by one thread per column)
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const float d = H[j * m + j];
+        int rank = 0;
+        for (int k = 0; k < m; k++) {
+            const float e = H[k * m + k];
+            rank += (e < d) || (e == d && k < j);
+        }
+        evals[rank] = d;
+        for (int r = 0; r < m; r++) Q[r * m + rank] = V[r * m + j];
+    }
+}
+
+__global__ void k_output(const double *Xt, const double *mass, int n, int n_pad, int k, double *evecs) {
+    const size_t total = (size_t)n * k;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / k), j = (int)(e % k);
+        evecs[e] = Xt[(size_t)j * n_pad + i] / sqrt(mass[i]);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap *tm, const float *ptr, int inner, int rows, int box_rows) {
+    auto enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct Plan {
+    int n, k, m, n_pad, splits, ktiles, kt_per_split, stages, smem;
+    uint32_t tmem_cols, idesc;
+};
+
+static Plan plan_for(int n, int k, int guard) {
+    Plan p;
+    p.n = n;
+    p.k = k;
+    p.m = std::min(160, ((k + guard + 15) / 16) * 16);
+    p.n_pad = ((n + BM - 1) / BM) * BM;
+    p.ktiles = p.n_pad / BK;
+    const int tiles = p.n_pad / BM;
+    int sp = std::max(1, 148 / tiles);
+    sp = std::min(sp, std::max(1, p.ktiles / 4));
+    p.kt_per_split = (p.ktiles + sp - 1) / sp;
+    p.splits = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
+    const int stage = 2 * BM * 128 + 2 * p.m * 128;
+    p.stages = std::max(2, std::min(4, (220 * 1024) / stage));
+    p.smem = p.stages * stage + 1024;
+    p.tmem_cols = 32;
+    while (p.tmem_cols < (uint32_t)p.m) p.tmem_cols <<= 1;
+    // kind::tf32 instruction descriptor: D fp32, A/B tf32, both K-major, N = m, M = 128
+    p.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.m >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return p;
+}
+
+struct Ws {
+    float *Ahi, *Alo, *P;
+    float *vh[4], *vl[4];   // tf32 parts of block vectors (m x n_pad)
+    double *Xt, *Zt, *G, *R, *theta, *res, *rowabs, *bound;
+    float *Q, *qev;
+    int *err;
+    size_t total;
+};
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Ws ws_layout(const Plan &p, char *base) {
+    Ws w;
+    size_t o = 0;
+    auto take = [&](size_t b) { char *r = base ? base + o : nullptr; o = a256(o + b); return r; };
+    const size_t nn = (size_t)p.n_pad * p.n_pad, mv = (size_t)p.m * p.n_pad;
+    w.Ahi = (float *)take(nn * 4);
+    w.Alo = (float *)take(nn * 4);
+    w.P = (float *)take((size_t)p.splits * mv * 4);
+    for (int i = 0; i < 4; i++) { w.vh[i] = (float *)take(mv * 4); w.vl[i] = (float *)take(mv * 4); }
+    w.Xt = (double *)take(mv * 8);
+    w.Zt = (double *)take(mv * 8);
+    w.G = (double *)take((size_t)p.m * p.m * 8);
+    w.R = (double *)take((size_t)p.m * p.m * 8);
+    w.theta = (double *)take(p.m * 8);
+    w.res = (double *)take(p.m * 8);
+    w.rowabs = (double *)take((size_t)p.n * 8);
+    w.bound = (double *)take(8);
+    w.Q = (float *)take((size_t)p.m * p.m * 4);
+    w.qev = (float *)take(p.m * 4);
+    w.err = (int *)take(4);
+    w.total = o;
+    return w;
+}
+
+struct Ctx {
+    Plan p;
+    Ws w;
+    cudaStream_t st;
+    CUtensorMap mAh, mAl, mBh[4], mBl[4];
+};
+
+// P <- A * (block b), the tensor-core product
+static cudaError_t tc_product(Ctx &c, int b) {
+    TcArgs a;
+    a.part = c.w.P;
+    a.n_pad = c.p.n_pad;
+    a.m = c.p.m;
+    a.ktiles = c.p.ktiles;
+    a.kt_per_split = c.p.kt_per_split;
+    a.stages = c.p.stages;
+    a.idesc = c.p.idesc;
+    a.tmem_cols = c.p.tmem_cols;
+    a.err = c.w.err;
+    k_tc_gemm<<<dim3(c.p.n_pad / BM, c.p.splits), kTcThreads, c.p.smem, c.st>>>(c.mAh, c.mAl, c.mBh[b], c.mBl[b], a);
+    return cudaGetLastError();
+}
+
+static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16); }
+
+}  // namespace eig
+}  // namespace mcs
+
+using namespace mcs;
+using namespace mcs::eig;
+
+extern "C" {
+
+size_t mcs_steklov_workspace_size(int n, int k) {
+    if (n <= 0 || k <= 0) return 0;
+    const Plan p = plan_for(n, k, 32);
+    return ws_layout(p, nullptr).total;
+}
+
+mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, int k, double *evals, double *evecs,
+                             void *workspace, size_t workspace_bytes, const mcs_eig_params *ep, mcs_eig_stats *stats,
+                             void *stream_) {
+    MCS_ARG(Lambda && mass && evals, "mcs_steklov_modes: NULL Lambda, mass or evals");
+    MCS_ARG(n >= 16 && k >= 1 && k <= 128 && k < n / 2, "mcs_steklov_modes: need n >= 16 and 1 <= k <= min(128, n/2 - 1)");
+    mcs_eig_params prm;
+    mcs_default_eig_params(&prm);
+    if (ep) prm = *ep;
+    MCS_ARG(prm.degree >= 1 && prm.degree <= 64 && prm.max_iters >= 1 && prm.tol > 0.0, "mcs_steklov_modes: bad params");
+    Ctx c;
+    c.p = plan_for(n, k, 32);
+    c.st = as_stream(stream_);
+    MCS_ARG(c.p.m > k && c.p.m <= 160, "mcs_steklov_modes: block size out of range");
+    c.w = ws_layout(c.p, (char *)workspace);
+    MCS_ARG(workspace && workspace_bytes >= c.w.total, "mcs_steklov_modes: workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_steklov_modes: workspace must be 256-byte aligned");
+    const Plan &p = c.p;
+    const int m = p.m;
+    if (!make_map(&c.mAh, c.w.Ahi, p.n_pad, p.n_pad, BM) || !make_map(&c.mAl, c.w.Alo, p.n_pad, p.n_pad, BM)) {
+        set_error("mcs_steklov_modes: cuTensorMapEncodeTiled unavailable or failed");
+        return MCS_ERR_CUDA;
+    }
+    for (int b = 0; b < 4; b++)
+        if (!make_map(&c.mBh[b], c.w.vh[b], p.n_pad, m, m) || !make_map(&c.mBl[b], c.w.vl[b], p.n_pad, m, m)) {
+            set_error("mcs_steklov_modes: tensor map for the block failed");
+            return MCS_ERR_CUDA;
+        }
+    MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
+    const size_t smm = (size_t)m * m * sizeof(double);
+    MCS_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    MCS_CUDA(cudaFuncSetAttribute(k_trsm_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * m * m * sizeof(float))));
+    cudaStream_t st = c.st;
+    const size_t mv = (size_t)m * p.n_pad;
+    const int g = grid_for(mv);
+    MCS_CUDA(cudaMemsetAsync(c.w.err, 0, sizeof(int), st));
+    k_prep_A<<<p.n_pad, 256, 0, st>>>(Lambda, mass, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.rowabs);
+    k_max_reduce<<<1, 1024, 0, st>>>(c.w.rowabs, n, c.w.bound);
+    k_random_block<<<g, 256, 0, st>>>(c.w.Xt, m, n, p.n_pad);
+    double bound = 0.0;
+    MCS_CUDA(cudaMemcpyAsync(&bound, c.w.bound, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaStreamSynchronize(st));
+    if (!(bound > 0.0)) bound = 1.0;
+    const double ub = bound * 1.01;
+
+    // orthonormalise Xt: shifted CholeskyQR, then CholeskyQR2 (FP64)
+    auto orth = [&]() -> cudaError_t {
+        const double shifts[3] = {11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16, 0.0, 0.0};
+        for (int pass = 0; pass < 3; pass++) {
+            k_gram<<<dim3(m, m), 256, 0, st>>>(c.w.Xt, c.w.Xt, m, p.n_pad, c.w.G, 1);
+            k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
+            k_trsm_right<<<(n + 127) / 128, 128, smm, st>>>(c.w.Xt, c.w.R, m, n, p.n_pad);
+        }
+        return cudaGetLastError();
+    };
+    MCS_CUDA(orth());
+    std::vector<double> theta(m), res(m);
+    double a_cut = ub / 8.0, a_low = 0.0;
+    int iters = 0, converged = 0, gemms = 0;
+    for (iters = 0; iters < prm.max_iters; iters++) {
+        // ---- Chebyshev filter of degree d on [a_cut, ub] applied to X
+        k_split<<<g, 256, 0, st>>>(c.w.Xt, mv, c.w.vh[0], c.w.vl[0]);
+        const double e = 0.5 * (ub - a_cut), cc = 0.5 * (ub + a_cut);
+        double sigma = e / (a_low - cc);
+        const double tau = 2.0 / sigma;
+        int prev = -1, cur = 0;
+        for (int d = 1; d <= prm.degree; d++) {
+            MCS_CUDA(tc_product(c, cur));
+            gemms++;
+            int nxt = (cur + 1) % 3;
+            if (nxt == prev) nxt = (nxt + 1) % 3;
+            const bool last = d == prm.degree;
+            if (d == 1) {
+                const double alpha = sigma / e, beta = -cc * sigma / e;
+                k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, 0.0, c.w.vh[cur],
+                                            c.w.vl[cur], nullptr, nullptr, last ? nullptr : c.w.vh[nxt],
+                                            last ? nullptr : c.w.vl[nxt], last ? c.w.Xt : nullptr);
+            } else {
+                const double sig_new = 1.0 / (tau - sigma);
+                const double alpha = 2.0 * sig_new / e, beta = -2.0 * sig_new * cc / e, gamma = -sigma * sig_new;
+                k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, gamma, c.w.vh[cur],
+                                            c.w.vl[cur], c.w.vh[prev], c.w.vl[prev], last ? nullptr : c.w.vh[nxt],
+                                            last ? nullptr : c.w.vl[nxt], last ? c.w.Xt : nullptr);
+                sigma = sig_new;
+            }
+            prev = cur;
+            cur = nxt;
+        }
+        MCS_CUDA(orth());
+        // ---- Rayleigh-Ritz
+        k_split<<<g, 256, 0, st>>>(c.w.Xt, mv, c.w.vh[3], c.w.vl[3]);
+        MCS_CUDA(tc_product(c, 3));
+        gemms++;
+        k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, c.w.Zt);
+        k_gram<<<dim3(m, m), 256, 0, st>>>(c.w.Xt, c.w.Zt, m, p.n_pad, c.w.G, 0);
+        k_jacobi<<<1, 512, 2 * m * m * sizeof(float), st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
+        k_rotate<<<(n + 127) / 128, 128, (size_t)m * m * sizeof(float), st>>>(c.w.Xt, c.w.Q, m, n, p.n_pad);
+        k_rotate<<<(n + 127) / 128, 128, (size_t)m * m * sizeof(float), st>>>(c.w.Zt, c.w.Q, m, n, p.n_pad);
+        k_ritz<<<m, 256, 0, st>>>(c.w.Xt, c.w.Zt, p.n_pad, c.w.theta, c.w.res);
+        MCS_CUDA(cudaGetLastError());
+        MCS_CUDA(cudaMemcpyAsync(theta.data(), c.w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MCS_CUDA(cudaMemcpyAsync(res.data(), c.w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MCS_CUDA(cudaStreamSynchronize(st));
+        converged = 0;
+        while (converged < k && res[converged] <= prm.tol * ub) converged++;
+        if (converged >= k) { iters++; break; }
+        a_cut = theta[m - 1];
+        a_low = std::min(0.0, theta[0]);
+    }
+    int err = 0;
+    MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaMemcpyAsync(evals, c.w.theta, k * sizeof(double), cudaMemcpyDefault, st));
+    if (evecs) k_output<<<grid_for((size_t)n * k), 256, 0, st>>>(c.w.Xt, mass, n, p.n_pad, k, evecs);
+    MCS_CUDA(cudaGetLastError());
+    MCS_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->iterations = iters;
+        stats->converged = converged;
+        stats->block = m;
+        stats->tc_products = gemms;
+        stats->upper_bound = ub;
+        stats->max_residual = 0.0;
+        for (int j = 0; j < k; j++) stats->max_residual = std::max(stats->max_residual, res[j]);
+        stats->device_error = err;
+    }
+    if (err & kErrTimeout) {
+        set_error("mcs_steklov_modes: a tensor-core pipeline wait timed out");
+        return MCS_ERR_DEVICE;
+    }
+    if (converged < k) {
+        set_error("mcs_steklov_modes: not converged within max_iters");
+        return MCS_WARN_NOT_CONVERGED;
+    }
+    return MCS_OK;
+}
+
+// test hook: Zt = (A X)^T for symmetric A (n x n FP64, row-major) and
+// Xt (m x n FP64), through the same tensor-core product
+mcs_status mcs_tc_symm_product(const double *A, const double *Xt_in, int n, int m_in, double *Zt_out, void *workspace,
+                               size_t workspace_bytes, void *stream_) {
+    MCS_ARG(A && Xt_in && Zt_out, "mcs_tc_symm_product: NULL pointer");
+    MCS_ARG(n >= 16 && m_in >= 16 && m_in <= 160 && m_in % 16 == 0, "mcs_tc_symm_product: need m in {16,...,160}, m % 16 == 0");
+    Ctx c;
+    c.p = plan_for(n, m_in - 32 > 0 ? m_in - 32 : 1, 32);
+    c.p.m = m_in;
+    const int stage = 2 * BM * 128 + 2 * m_in * 128;
+    c.p.stages = std::max(2, std::min(4, (220 * 1024) / stage));
+    c.p.smem = c.p.stages * stage + 1024;
+    c.p.tmem_cols = 32;
+    while (c.p.tmem_cols < (uint32_t)m_in) c.p.tmem_cols <<= 1;
+    c.p.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(m_in >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    c.st = as_stream(stream_);
+    c.w = ws_layout(c.p, (char *)workspace);
+    MCS_ARG(workspace && workspace_bytes >= c.w.total, "mcs_tc_symm_product: workspace too small");
+    const Plan &p = c.p;
+    if (!make_map(&c.mAh, c.w.Ahi, p.n_pad, p.n_pad, BM) || !make_map(&c.mAl, c.w.Alo, p.n_pad, p.n_pad, BM) ||
+        !make_map(&c.mBh[0], c.w.vh[0], p.n_pad, p.m, p.m) || !make_map(&c.mBl[0], c.w.vl[0], p.n_pad, p.m, p.m)) {
+        set_error("mcs_tc_symm_product: tensor map failed");
+        return MCS_ERR_CUDA;
+    }
+    MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
+    cudaStream_t st = c.st;
+    MCS_CUDA(cudaMemsetAsync(c.w.err, 0, sizeof(int), st));
+    // unit mass: A itself
+    double *ones = c.w.rowabs;  // n doubles
+    std::vector<double> h1(n, 1.0);
+    MCS_CUDA(cudaMemcpyAsync(ones, h1.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_prep_A<<<p.n_pad, 256, 0, st>>>(A, ones, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.Zt);
+    const size_t mv = (size_t)p.m * p.n_pad;
+    MCS_CUDA(cudaMemsetAsync(c.w.Xt, 0, mv * sizeof(double), st));
+    MCS_CUDA(cudaMemcpy2DAsync(c.w.Xt, p.n_pad * sizeof(double), Xt_in, n * sizeof(double), n * sizeof(double), p.m,
+                               cudaMemcpyDeviceToDevice, st));
+    k_split<<<grid_for(mv), 256, 0, st>>>(c.w.Xt, mv, c.w.vh[0], c.w.vl[0]);
+    MCS_CUDA(tc_product(c, 0));
+    k_combine<<<grid_for(mv), 256, 0, st>>>(c.w.P, p.splits, p.m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr,
+                                           nullptr, nullptr, nullptr, c.w.Zt);
+    MCS_CUDA(cudaMemcpy2DAsync(Zt_out, n * sizeof(double), c.w.Zt, p.n_pad * sizeof(double), n * sizeof(double), p.m,
+                               cudaMemcpyDeviceToDevice, st));
+    int err = 0;
+    MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("mcs_tc_symm_product: device error (pipeline timeout)");
+        return MCS_ERR_DEVICE;
+    }
+    return MCS_OK;
+}
+
+size_t mcs_tc_symm_product_workspace_size(int n, int m) {
+    Plan p = plan_for(n, std::max(1, m - 32), 32);
+    p.m = m;
+    return ws_layout(p, nullptr).total;
+}
+
+void mcs_default_eig_params(mcs_eig_params *p) {
+    if (!p) return;
+    p->degree = 10;
+    p->max_iters = 60;
+    p->tol = 1e-6;
+}
+
+}  // extern "C"
