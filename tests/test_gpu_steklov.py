@@ -65,5 +65,6 @@ def test_steklov_on_gpu_estimate_end_to_end():
     res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32))
     ev, X, st = mcs.steklov_modes(res["Lambda"], rows["area"], 9)
     ev = ev.cpu().numpy()
-    assert abs(ev[0]) < 1e-6 * ev[-1]
+    # the constant mode: zero up to the solver's accuracy (~1e-6 of the spectral upper bound)
+    assert abs(ev[0]) < 1e-5 * st["upper_bound"]
     assert ev[1:4].max() < ev[4:9].min()
