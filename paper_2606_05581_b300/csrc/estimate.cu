@@ -86,10 +86,28 @@ __global__ void k_order_from_keys(const unsigned long long *keys, int R, int32_t
 }
 
 // ---------------------------------------------------------------- tangent balls
-__global__ void k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R, Frame fr, RowBall *ball,
-                              Ctrl *ctrl) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per row: every query of the row is answered by the whole warp
+// (warp_query); a bisection test only asks whether some triangle lies closer
+// than (1 - kappa) r, which is the oracle's dist >= (1 - kappa) r decision.
+constexpr int kTanWarps = 4;
+
+__device__ __forceinline__ double wdist(const DevMesh &m, double x, double y, double z, int *front, int *err) {
+    Hit<double> h;
+    warp_query<double, kFull>(m, x, y, z, 0.0, h, front, err);
+    return sqrt(h.d2);
+}
+__device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, double z, double thr, int *front,
+                                       int *err) {
+    Hit<double> h;
+    return !warp_query<double, kBelow>(m, x, y, z, thr, h, front, err);
+}
+
+__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R,
+                                                                Frame fr, RowBall *ball, Ctrl *ctrl) {
+    __shared__ int fronts[kTanWarps][32];
+    const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
     if (v >= R) return;
+    int *front = fronts[threadIdx.x >> 5];
     int err = 0;
     const double s0 = pos[3 * v], s1 = pos[3 * v + 1], s2 = pos[3 * v + 2];
     const double n0 = nrm[3 * v], n1 = nrm[3 * v + 1], n2 = nrm[3 * v + 2];
@@ -101,26 +119,28 @@ __global__ void k_tangent_int(DevMesh m, const double *pos, const double *nrm, i
     if (nz) {
         const double rmax = fr.rmax;
         double r;
-        if (dist64(m, s0 - rmax * n0, s1 - rmax * n1, s2 - rmax * n2, &err) >= fr.onemk * rmax) {
+        if (wclear(m, s0 - rmax * n0, s1 - rmax * n1, s2 - rmax * n2, fr.onemk * rmax, front, &err)) {
             r = rmax;
         } else {
             double lo = 0.0, hi = rmax;
             for (int it = 0; it < fr.bisect_iters; it++) {
                 const double mid = 0.5 * (lo + hi);
-                if (dist64(m, s0 - mid * n0, s1 - mid * n1, s2 - mid * n2, &err) >= fr.onemk * mid) lo = mid;
+                if (wclear(m, s0 - mid * n0, s1 - mid * n1, s2 - mid * n2, fr.onemk * mid, front, &err)) lo = mid;
                 else hi = mid;
             }
             r = lo;
         }
         b.c[0] = s0 - r * n0; b.c[1] = s1 - r * n1; b.c[2] = s2 - r * n2;
-        b.rho = dist64(m, b.c[0], b.c[1], b.c[2], &err);
+        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err);
         b.r = r;
     }
     b.valid = nz && (b.rho >= fr.rho_min_factor * fr.eps);
     b.M = b.valid ? (fr.iw0 - 1.0) / (2.0 * b.rho) : 0.0;
     b.pad = 0;
-    ball[v] = b;
-    if (err) atomicOr(&ctrl->err, err);
+    if ((threadIdx.x & 31) == 0) {
+        ball[v] = b;
+        if (err) atomicOr(&ctrl->err, err);
+    }
 }
 
 // largest empty radius, lowest row on ties -> inversion centre
@@ -205,20 +225,22 @@ __global__ void k_ext_frame(const double *V, int nv, Ctrl *ctrl) {
 // r/(|c~|^2 - r^2); the accepted ball is replaced by the image of the primal
 // empty ball B(C, dist(C))
 __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double nt[3], double r, const double o[3],
-                            double onemk, int *err) {
+                            double onemk, int *front, int *err) {
     const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
     const double den = (ct0 * ct0 + ct1 * ct1 + ct2 * ct2) - r * r;
     if (!(den > 0.0)) return false;
     const double inv = 1.0 / den;
     const double C0 = ct0 * inv, C1 = ct1 * inv, C2 = ct2 * inv;
     const double Rp = r * inv;
-    return dist64(m, C0 + o[0], C1 + o[1], C2 + o[2], err) >= onemk * Rp;
+    return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], onemk * Rp, front, err);
 }
 
-__global__ void k_tangent_ext(DevMesh m, const double *pos, const double *nrm, int R, Frame fr, RowBall *ball,
-                              Ctrl *ctrl) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const double *pos, const double *nrm, int R,
+                                                                Frame fr, RowBall *ball, Ctrl *ctrl) {
+    __shared__ int fronts[kTanWarps][32];
+    const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
     if (v >= R) return;
+    int *front = fronts[threadIdx.x >> 5];
     int err = 0;
     const double o[3] = {ctrl->origin[0], ctrl->origin[1], ctrl->origin[2]};
     const double rmax = ctrl->rmax_ext;
@@ -238,13 +260,13 @@ __global__ void k_tangent_ext(DevMesh m, const double *pos, const double *nrm, i
     b.kfac = 1.0 / (r2s * sqrt(r2s));
     if (nz) {
         double r;
-        if (inv_ball_ok(m, st, nt, rmax, o, fr.onemk, &err)) {
+        if (inv_ball_ok(m, st, nt, rmax, o, fr.onemk, front, &err)) {
             r = rmax;
         } else {
             double lo = 0.0, hi = rmax;
             for (int it = 0; it < fr.bisect_iters; it++) {
                 const double mid = 0.5 * (lo + hi);
-                if (inv_ball_ok(m, st, nt, mid, o, fr.onemk, &err)) lo = mid;
+                if (inv_ball_ok(m, st, nt, mid, o, fr.onemk, front, &err)) lo = mid;
                 else hi = mid;
             }
             r = lo;
@@ -256,7 +278,7 @@ __global__ void k_tangent_ext(DevMesh m, const double *pos, const double *nrm, i
             if (den > 0.0) {
                 const double invd = 1.0 / den;
                 const double C0 = ct0 * invd, C1 = ct1 * invd, C2 = ct2 * invd;
-                const double D = dist64(m, C0 + o[0], C1 + o[1], C2 + o[2], &err);
+                const double D = wdist(m, C0 + o[0], C1 + o[1], C2 + o[2], front, &err);
                 const double den2 = (C0 * C0 + C1 * C1 + C2 * C2) - D * D;
                 if (den2 > 0.0) {
                     const double inv2 = 1.0 / den2;
@@ -269,8 +291,10 @@ __global__ void k_tangent_ext(DevMesh m, const double *pos, const double *nrm, i
     b.valid = nz && (b.rho >= fr.rho_min_factor * fr.eps);
     b.M = b.valid ? (fr.iw0 - 1.0) / (2.0 * b.rho) : 0.0;
     b.pad = 0;
-    ball[v] = b;
-    if (err) atomicOr(&ctrl->err, err);
+    if ((threadIdx.x & 31) == 0) {
+        ball[v] = b;
+        if (err) atomicOr(&ctrl->err, err);
+    }
 }
 
 // ---------------------------------------------------------------- walks
@@ -720,16 +744,19 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     // tangent balls
     if (ext) {
         if (p->origin_auto) {
-            k_tangent_int<<<gr, tb, 0, st>>>(dm, rows->pos, rows->nrm, R, fr, ball, ctrl);
+            k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
+                                                                                     ball, ctrl);
             k_origin_argmax<<<1, 1024, 0, st>>>(ball, R, ctrl);
         } else {
             k_set_origin<<<1, 1, 0, st>>>(ctrl, p->origin[0], p->origin[1], p->origin[2]);
         }
         k_ext_frame<<<1, 256, 0, st>>>(m->V, m->nv, ctrl);
-        k_tangent_ext<<<gr, tb, 0, st>>>(dm, rows->pos, rows->nrm, R, fr, ball, ctrl);
+        k_tangent_ext<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
+                                                                                 ball, ctrl);
         k_colfactor<<<gr, tb, 0, st>>>(rows->pos, R, ctrl, cf);
     } else {
-        k_tangent_int<<<gr, tb, 0, st>>>(dm, rows->pos, rows->nrm, R, fr, ball, ctrl);
+        k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
+                                                                                 ball, ctrl);
     }
     MCS_CUDA(cudaGetLastError());
     // walks

@@ -386,4 +386,157 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
     }
 }
 
+// --------------------------------------------------------------------------
+// warp-cooperative query: the 32 lanes of a warp answer ONE query together.
+// The top of the tree is expanded breadth-first into at most 32 subtrees
+// (one per lane), each lane then traverses its subtree depth-first; the
+// pruning bound is shared through warp reductions.
+//   kFull:  exact argmin of (d^2, id) over all triangles (as `closest`)
+//   kBelow: whether some triangle has sqrt(d^2) < thr (early exit), i.e. the
+//           negation of sqrt(min d^2) >= thr, decided on the same per-triangle
+//           values as the brute-force scan
+// Every lane must call it with the same point; `front` is 32 ints of shared
+// memory owned by the warp.
+// --------------------------------------------------------------------------
+constexpr int kFull = 0, kBelow = 1;
+constexpr int kNone = 0x7FFFFFFF;
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+template <typename T, int MODE>
+__device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &out, int *front, int *err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
+    T bound2;  // prune a box when its squared distance exceeds this
+    if (MODE == kBelow) {
+        const T r = thr + tau;
+        bound2 = r * r;
+    } else {
+        bound2 = (T)INFINITY;
+    }
+    Hit<T> best;
+    best.d2 = (T)INFINITY; best.id = 0x7FFFFFFF; best.slot = -1; best.b0 = best.b1 = best.b2 = (T)0;
+    bool hit = false;
+    auto test = [&](int s) {
+        T b[3];
+        int id;
+        const T d2 = Slot<T>::test(m, s, px, py, pz, b, id);
+        if (MODE == kBelow) {
+            if (rsq<T>(d2) < thr) hit = true;
+        } else if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
+            best.d2 = d2; best.id = id; best.slot = s; best.b0 = b[0]; best.b1 = b[1]; best.b2 = b[2];
+        }
+    };
+    auto refresh = [&]() {
+        if (MODE == kFull) {
+            const T r = rsq<T>(warp_min<T>(best.d2)) + tau;
+            bound2 = r * r;
+        }
+    };
+    // ---- breadth-first expansion of the top of the tree
+    int entry = kNone;  // >= 0 internal node, < 0 leaf (~slot)
+    if (lane == 0) entry = (m.nf == 1) ? ~0 : 0;
+    for (int round = 0; round < 8; round++) {
+        const bool internal = entry != kNone && entry >= 0;
+        int c0 = kNone, c1 = kNone;
+        if (internal) {
+            const Node nd = m.nodes[entry];
+            const T d0 = box_d2<T>(px, py, pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);
+            const T d1 = box_d2<T>(px, py, pz, nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w);
+            if (d0 <= bound2) c0 = nd.d.x;
+            if (d1 <= bound2) c1 = nd.d.y;
+        }
+        const int cnt = internal ? (c0 != kNone) + (c1 != kNone) : (entry != kNone);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (!__any_sync(FULL, internal) || total > 32) break;
+        __syncwarp();
+        int pos = incl - cnt;
+        if (internal) {
+            if (c0 != kNone) front[pos++] = c0;
+            if (c1 != kNone) front[pos++] = c1;
+        } else if (entry != kNone) {
+            front[pos] = entry;
+        }
+        __syncwarp();
+        entry = lane < total ? front[lane] : kNone;
+        __syncwarp();
+    }
+    // ---- depth-first traversal of each lane's subtree
+    int stack[kStackDepth];
+    float sdist[kStackDepth];
+    int sp = 0;
+    int node = kNone;
+    if (entry != kNone) {
+        if (entry < 0) test(~entry);
+        else node = entry;
+    }
+    int guard = 0;
+    while (true) {
+        refresh();
+        if (MODE == kBelow && __any_sync(FULL, hit)) { hit = true; break; }
+        const bool active = node != kNone;
+        if (!__any_sync(FULL, active)) break;
+        if (!active) continue;
+        if (++guard > 2 * m.nf + 64) { *err |= kErrTree; node = kNone; continue; }
+        const Node nd = m.nodes[node];
+        const T d0 = box_d2<T>(px, py, pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);
+        const T d1 = box_d2<T>(px, py, pz, nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w);
+        const int c0 = nd.d.x, c1 = nd.d.y;
+        bool h0 = d0 <= bound2, h1 = d1 <= bound2;
+        if (h0 && c0 < 0) { test(~c0); h0 = false; }
+        if (h1 && c1 < 0) { test(~c1); h1 = false; }
+        if (h0 && h1) {
+            const bool first0 = d0 <= d1;
+            if (sp < kStackDepth) {
+                stack[sp] = first0 ? c1 : c0;
+                sdist[sp] = store_down<T>(first0 ? d1 : d0);
+                sp++;
+            } else {
+                *err |= kErrStack;
+            }
+            node = first0 ? c0 : c1;
+        } else if (h0) {
+            node = c0;
+        } else if (h1) {
+            node = c1;
+        } else {
+            node = kNone;
+            while (sp > 0) {
+                sp--;
+                if ((T)sdist[sp] <= bound2) { node = stack[sp]; break; }
+            }
+        }
+    }
+    if (MODE == kBelow) return hit;
+    // ---- lexicographic warp argmin of (d^2, id)
+    T bd = best.d2;
+    int bi = best.id, bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T od = __shfl_xor_sync(FULL, bd, o);
+        const int oi = __shfl_xor_sync(FULL, bi, o);
+        const int ol = __shfl_xor_sync(FULL, bl, o);
+        if (od < bd || (od == bd && oi < bi)) { bd = od; bi = oi; bl = ol; }
+    }
+    out.d2 = bd;
+    out.id = bi;
+    out.slot = __shfl_sync(FULL, best.slot, bl);
+    out.b0 = __shfl_sync(FULL, best.b0, bl);
+    out.b1 = __shfl_sync(FULL, best.b1, bl);
+    out.b2 = __shfl_sync(FULL, best.b2, bl);
+    return false;
+}
+
 }  // namespace mcs
