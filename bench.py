@@ -120,15 +120,31 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     has_eig = hasattr(mcs, "steklov_modes")
 
+    eig_ws = mcs.Workspace()
+
     def step(V, F, keep=False):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         mesh = mcs.Mesh(V, F)
         rows = mcs.vertex_rows(mesh)
+        e1.record(stream)
         res = mcs.estimate_dtn(mesh, rows, params, workspace=ws)
         ev = None
+        e2.record(stream)
         if has_eig:
-            ev = mcs.steklov_modes(res["Lambda"], rows["area"], args.k)
+            ev = mcs.steklov_modes(res["Lambda"], rows["area"], args.k, vectors=True, workspace=eig_ws)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e3.record(stream)
+        e3.synchronize()
+        st = dict(res["stats"])
+        st["build_ms"] = e0.elapsed_time(e1)
+        st["eig_ms"] = e2.elapsed_time(e3)
+        if ev is not None:
+            st["eig"] = ev[2]
         out = (mesh, rows, res, ev)
-        return out if keep else (res["stats"], ev)
+        return out if keep else (st, ev)
 
     # warm-up
     for _ in range(args.warmup):
@@ -154,7 +170,7 @@ def run_ours(args, rank, world):
                 if ev is not None:
                     lam_h = ev[0].to("cpu", non_blocking=True)
                     d2h += lam_h.numel() * 8
-                st = res["stats"]
+                st = dict(res["stats"])
             else:
                 st, _ = step(V_d, F_d)
             s1.record(stream)
@@ -206,8 +222,10 @@ def run_ours(args, rank, world):
         "walks_per_s": (R * W + 64 * W) * world / (ms_max / 1e3),
         "closest_point_queries_per_s": value,
         "walk_steps_per_step": steps_total,
-        "phase_ms": {"rows_and_tangent_balls": phase[0], "walks": phase[1], "histogram": phase[2],
-                     "assembly": phase[3]},
+        "phase_ms": {"bvh_build_and_vertex_rows": float(np.mean([s["build_ms"] for s in stats])),
+                     "rows_and_tangent_balls": phase[0], "walks": phase[1], "histogram": phase[2],
+                     "assembly": phase[3], "steklov_modes": float(np.mean([s["eig_ms"] for s in stats]))},
+        "steklov": stats[-1].get("eig"),
         "e2e": {"value": steps_total * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": GPU_LAUNCHES_PER_STEP * args.steps,

@@ -181,7 +181,7 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
 typedef struct {
     int degree;             /* Chebyshev filter degree per iteration (10)        */
     int max_iters;          /* outer iterations (60)                             */
-    double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-6) */
+    double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-5) */
 } mcs_eig_params;
 typedef struct {
     int iterations, converged, block, tc_products;

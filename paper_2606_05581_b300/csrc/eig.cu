@@ -309,24 +309,48 @@ __global__ void k_combine(const float *P, int splits, int m, int n, int n_pad, d
     }
 }
 
-// G[a][b] = sum_i A[a][i] B[b][i] (FP64), one block per (a, b); sym: a <= b mirrored
-__global__ void k_gram(const double *A, const double *B, int m, int n_pad, double *G, int sym) {
-    const int a = blockIdx.y, b = blockIdx.x;
-    if (sym && a > b) return;
-    __shared__ double red[256];
-    const double *x = A + (size_t)a * n_pad, *y = B + (size_t)b * n_pad;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n_pad; i += blockDim.x) s += x[i] * y[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+// Gp[q][a][b] = sum_{i in chunk q} A[a][i] B[b][i] (FP64): 32 x 32 output
+// tiles per block, the n dimension split into chunks across blockIdx.z
+constexpr int kGramChunks = 16;
+__global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, double *Gp) {
+    __shared__ double sa[32][33], sb[32][33];
+    const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
+    const int chunk = (n_pad + kGramChunks - 1) / kGramChunks;
+    const int i0 = blockIdx.z * chunk, i1 = min(n_pad, i0 + chunk);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    double acc[4] = {0, 0, 0, 0};
+    for (int i = i0; i < i1; i += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int ii = i + tx;
+            sa[r][tx] = (a0 + r < m && ii < i1) ? A[(size_t)(a0 + r) * n_pad + ii] : 0.0;
+            sb[r][tx] = (b0 + r < m && ii < i1) ? B[(size_t)(b0 + r) * n_pad + ii] : 0.0;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; q++) {
+            const int r = ty + 8 * q;
+            double s = 0.0;
+            for (int t = 0; t < 32; t++) s += sa[r][t] * sb[tx][t];
+            acc[q] += s;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        G[a * m + b] = red[0];
-        if (sym) G[b * m + a] = red[0];
+    for (int q = 0; q < 4; q++) {
+        const int r = ty + 8 * q;
+        if (a0 + r < m && b0 + tx < m) Gp[((size_t)blockIdx.z * m + a0 + r) * m + b0 + tx] = acc[q];
     }
+}
+__global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    double s = 0.0;
+    for (int q = 0; q < kGramChunks; q++) s += Gp[(size_t)q * m * m + e];
+    if (sym) {
+        const int a = e / m, b = e % m;
+        double t = 0.0;
+        for (int q = 0; q < kGramChunks; q++) t += Gp[(size_t)q * m * m + b * m + a];
+        s = 0.5 * (s + t);
+    }
+    G[e] = s;
 }
 
 // upper Cholesky factor of G + shift I (FP64, one block, G in shared memory)
@@ -364,36 +388,48 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
     }
 }
 
-// X <- X R^-1 (rows of X = columns of Xt), R upper triangular in shared memory
-__global__ void k_trsm_right(double *Xt, const double *R, int m, int n, int n_pad) {
+// Rinv = R^-1 for upper-triangular R (one thread per column, back substitution)
+__global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
     extern __shared__ double sr[];
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) sr[e] = R[e];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double y[256];
-    for (int j = 0; j < m; j++) {
-        double s = Xt[(size_t)j * n_pad + i];
-        for (int k = 0; k < j; k++) s -= y[k] * sr[k * m + j];
-        y[j] = s / sr[j * m + j];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        for (int i = m - 1; i >= 0; i--) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; k++) s -= sr[i * m + k] * Rinv[k * m + c];
+            Rinv[i * m + c] = i > c ? 0.0 : s / sr[i * m + i];
+        }
     }
-    for (int j = 0; j < m; j++) Xt[(size_t)j * n_pad + i] = y[j];
+}
+__global__ void k_f32_to_f64(const float *a, int n, double *b) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = (double)a[e];
 }
 
-// Xt <- Q^T Xt (X <- X Q), Q m x m FP32 from the Jacobi solver
-__global__ void k_rotate(double *Xt, const float *Q, int m, int n, int n_pad) {
-    extern __shared__ float sq[];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sq[e] = Q[e];
+// Out[j][i] = sum_k C[k][j] In[k][i] (FP64): X <- X C for a block stored by
+// rows of X^T; eight output rows j per block, C's slice in shared memory
+constexpr int kJG = 8;
+__global__ void k_block_times(const double *C, const double *In, int m, int n_pad, double *Out) {
+    extern __shared__ double sc[];  // m x kJG
+    const int j0 = blockIdx.y * kJG;
+    for (int e = threadIdx.x; e < m * kJG; e += blockDim.x) {
+        const int k = e / kJG, jj = e % kJG;
+        sc[e] = (j0 + jj < m) ? C[k * m + j0 + jj] : 0.0;
+    }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x[256];
-    for (int k = 0; k < m; k++) x[k] = Xt[(size_t)k * n_pad + i];
-    for (int j = 0; j < m; j++) {
-        double s = 0.0;
-        for (int k = 0; k < m; k++) s += (double)sq[k * m + j] * x[k];
-        Xt[(size_t)j * n_pad + i] = s;
+    if (i >= n_pad) return;
+    double acc[kJG];
+#pragma unroll
+    for (int jj = 0; jj < kJG; jj++) acc[jj] = 0.0;
+    for (int k = 0; k < m; k++) {
+        const double x = In[(size_t)k * n_pad + i];
+#pragma unroll
+        for (int jj = 0; jj < kJG; jj++) acc[jj] += sc[k * kJG + jj] * x;
     }
+#pragma unroll
+    for (int jj = 0; jj < kJG; jj++)
+        if (j0 + jj < m) Out[(size_t)(j0 + jj) * n_pad + i] = acc[jj];
 }
 
 // Ritz values theta_j = x_j.z_j / x_j.x_j and residual norms |z_j - theta_j x_j|
@@ -443,7 +479,7 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
             off = o; nrm = t;
         }
         __syncthreads();
-        if (off <= 1e-14f * nrm) break;
+        if (off <= 1e-12f * nrm) break;
         for (int r = 0; r < m - 1; r++) {
             if (threadIdx.x < half) {
                 const int i = threadIdx.x;
@@ -565,7 +601,7 @@ static Plan plan_for(int n, int k, int guard) {
 struct Ws {
     float *Ahi, *Alo, *P;
     float *vh[4], *vl[4];   // tf32 parts of block vectors (m x n_pad)
-    double *Xt, *Zt, *G, *R, *theta, *res, *rowabs, *bound;
+    double *Xt, *Zt, *Xt2, *G, *Gp, *R, *Rinv, *Qd, *theta, *res, *rowabs, *bound;
     float *Q, *qev;
     int *err;
     size_t total;
@@ -584,8 +620,12 @@ static Ws ws_layout(const Plan &p, char *base) {
     for (int i = 0; i < 4; i++) { w.vh[i] = (float *)take(mv * 4); w.vl[i] = (float *)take(mv * 4); }
     w.Xt = (double *)take(mv * 8);
     w.Zt = (double *)take(mv * 8);
+    w.Xt2 = (double *)take(mv * 8);
     w.G = (double *)take((size_t)p.m * p.m * 8);
+    w.Gp = (double *)take((size_t)kGramChunks * p.m * p.m * 8);
     w.R = (double *)take((size_t)p.m * p.m * 8);
+    w.Rinv = (double *)take((size_t)p.m * p.m * 8);
+    w.Qd = (double *)take((size_t)p.m * p.m * 8);
     w.theta = (double *)take(p.m * 8);
     w.res = (double *)take(p.m * 8);
     w.rowabs = (double *)take((size_t)p.n * 8);
@@ -666,7 +706,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
     const size_t smm = (size_t)m * m * sizeof(double);
     MCS_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    MCS_CUDA(cudaFuncSetAttribute(k_trsm_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    MCS_CUDA(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
     MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * m * m * sizeof(float))));
     cudaStream_t st = c.st;
     const size_t mv = (size_t)m * p.n_pad;
@@ -681,13 +721,24 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     if (!(bound > 0.0)) bound = 1.0;
     const double ub = bound * 1.01;
 
-    // orthonormalise Xt: shifted CholeskyQR, then CholeskyQR2 (FP64)
+    // block buffers (m x n_pad FP64, by rows of X^T): X, Z and a spare, rotated by role
+    double *X = c.w.Xt, *Z = c.w.Zt, *T = c.w.Xt2;
+    const dim3 ggrid((m + 31) / 32, (m + 31) / 32, kGramChunks);
+    const dim3 bgrid(p.n_pad / 128, (m + kJG - 1) / kJG);
+    const size_t bsm = (size_t)m * kJG * sizeof(double);
+    auto gram = [&](const double *A, const double *B, int sym) {
+        k_gram_part<<<ggrid, 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp);
+        k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym);
+    };
+    // orthonormalise X: shifted CholeskyQR, then CholeskyQR2 (FP64)
     auto orth = [&]() -> cudaError_t {
         const double shifts[3] = {11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16, 0.0, 0.0};
         for (int pass = 0; pass < 3; pass++) {
-            k_gram<<<dim3(m, m), 256, 0, st>>>(c.w.Xt, c.w.Xt, m, p.n_pad, c.w.G, 1);
+            gram(X, X, 1);
             k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
-            k_trsm_right<<<(n + 127) / 128, 128, smm, st>>>(c.w.Xt, c.w.R, m, n, p.n_pad);
+            k_tri_inverse<<<1, 128, smm, st>>>(c.w.R, m, c.w.Rinv);
+            k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T);
+            std::swap(X, T);
         }
         return cudaGetLastError();
     };
@@ -697,7 +748,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     int iters = 0, converged = 0, gemms = 0;
     for (iters = 0; iters < prm.max_iters; iters++) {
         // ---- Chebyshev filter of degree d on [a_cut, ub] applied to X
-        k_split<<<g, 256, 0, st>>>(c.w.Xt, mv, c.w.vh[0], c.w.vl[0]);
+        k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[0], c.w.vl[0]);
         const double e = 0.5 * (ub - a_cut), cc = 0.5 * (ub + a_cut);
         double sigma = e / (a_low - cc);
         const double tau = 2.0 / sigma;
@@ -712,13 +763,13 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
                 const double alpha = sigma / e, beta = -cc * sigma / e;
                 k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, 0.0, c.w.vh[cur],
                                             c.w.vl[cur], nullptr, nullptr, last ? nullptr : c.w.vh[nxt],
-                                            last ? nullptr : c.w.vl[nxt], last ? c.w.Xt : nullptr);
+                                            last ? nullptr : c.w.vl[nxt], last ? X : nullptr);
             } else {
                 const double sig_new = 1.0 / (tau - sigma);
                 const double alpha = 2.0 * sig_new / e, beta = -2.0 * sig_new * cc / e, gamma = -sigma * sig_new;
                 k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, gamma, c.w.vh[cur],
                                             c.w.vl[cur], c.w.vh[prev], c.w.vl[prev], last ? nullptr : c.w.vh[nxt],
-                                            last ? nullptr : c.w.vl[nxt], last ? c.w.Xt : nullptr);
+                                            last ? nullptr : c.w.vl[nxt], last ? X : nullptr);
                 sigma = sig_new;
             }
             prev = cur;
@@ -726,16 +777,19 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         }
         MCS_CUDA(orth());
         // ---- Rayleigh-Ritz
-        k_split<<<g, 256, 0, st>>>(c.w.Xt, mv, c.w.vh[3], c.w.vl[3]);
+        k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[3], c.w.vl[3]);
         MCS_CUDA(tc_product(c, 3));
         gemms++;
         k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr,
-                                    nullptr, nullptr, c.w.Zt);
-        k_gram<<<dim3(m, m), 256, 0, st>>>(c.w.Xt, c.w.Zt, m, p.n_pad, c.w.G, 0);
+                                    nullptr, nullptr, Z);
+        gram(X, Z, 1);
         k_jacobi<<<1, 512, 2 * m * m * sizeof(float), st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
-        k_rotate<<<(n + 127) / 128, 128, (size_t)m * m * sizeof(float), st>>>(c.w.Xt, c.w.Q, m, n, p.n_pad);
-        k_rotate<<<(n + 127) / 128, 128, (size_t)m * m * sizeof(float), st>>>(c.w.Zt, c.w.Q, m, n, p.n_pad);
-        k_ritz<<<m, 256, 0, st>>>(c.w.Xt, c.w.Zt, p.n_pad, c.w.theta, c.w.res);
+        k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
+        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, X, m, p.n_pad, T);
+        std::swap(X, T);
+        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, Z, m, p.n_pad, T);
+        std::swap(Z, T);
+        k_ritz<<<m, 256, 0, st>>>(X, Z, p.n_pad, c.w.theta, c.w.res);
         MCS_CUDA(cudaGetLastError());
         MCS_CUDA(cudaMemcpyAsync(theta.data(), c.w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
         MCS_CUDA(cudaMemcpyAsync(res.data(), c.w.res, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -749,7 +803,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     int err = 0;
     MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaMemcpyAsync(evals, c.w.theta, k * sizeof(double), cudaMemcpyDefault, st));
-    if (evecs) k_output<<<grid_for((size_t)n * k), 256, 0, st>>>(c.w.Xt, mass, n, p.n_pad, k, evecs);
+    if (evecs) k_output<<<grid_for((size_t)n * k), 256, 0, st>>>(X, mass, n, p.n_pad, k, evecs);
     MCS_CUDA(cudaGetLastError());
     MCS_CUDA(cudaStreamSynchronize(st));
     if (stats) {
@@ -835,7 +889,7 @@ void mcs_default_eig_params(mcs_eig_params *p) {
     if (!p) return;
     p->degree = 10;
     p->max_iters = 60;
-    p->tol = 1e-6;
+    p->tol = 1e-5;
 }
 
 }  // extern "C"
