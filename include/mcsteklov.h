@@ -71,7 +71,8 @@ typedef struct {
     double rho_min_factor;  /* discard rows whose empty radius < factor * eps   */
     int prec;               /* MCS_FP32 (walks in float, FP64 eps-shell) or MCS_FP64 */
     int domain;             /* MCS_INTERIOR or MCS_EXTERIOR                     */
-    int origin_auto;        /* exterior: 1 = centre of the largest interior tangent ball */
+    int origin_auto;        /* exterior: 1 = centre of the largest interior tangent ball
+                               among rows 0, s, 2s, ... with s = ceil(n_rows / 256) */
     double origin[3];       /* exterior inversion centre when origin_auto == 0  */
     long long killing_walks;/* exterior: walks from the inverted origin (0 = killing off) */
     uint64_t seed;          /* Philox key                                       */
@@ -176,10 +177,10 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
  * Chebyshev-filtered subspace iteration on a block of m = k + 32 vectors
  * (rounded up to 16, at most 160): filter products A*Y on the tensor cores
  * (tcgen05 kind::tf32, operands split into tf32 high/low parts), FP64
- * shifted CholeskyQR + CholeskyQR2 orthonormalisation, Rayleigh-Ritz with a
+ * CholeskyQR2 orthonormalisation (shifted CholeskyQR first on the start block), Rayleigh-Ritz with a
  * parallel Jacobi on the block, Ritz values as FP64 Rayleigh quotients. */
 typedef struct {
-    int degree;             /* Chebyshev filter degree per iteration (10)        */
+    int degree;             /* Chebyshev filter degree per iteration (24)        */
     int max_iters;          /* outer iterations (60)                             */
     double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-5) */
 } mcs_eig_params;

@@ -222,11 +222,20 @@ def tangent_balls(V, F, rows, n_threads: int = 0, params=None):
     return r, c, rho
 
 
+def origin_stride(n_rows: int) -> int:
+    """Rows considered for the inversion centre: every s-th row, s = ceil(R / 256)."""
+    return (n_rows + 255) // 256
+
+
 def interior_origin(V, F, rows, n_threads: int = 0, params=None) -> np.ndarray:
     """Inversion centre for the exterior estimator: the centre of the largest
-    interior tangent ball (largest rho, lowest row on ties); it lies inside
-    Omega, as the Kelvin transform requires (Sec. 4.3, App. B.3)."""
-    r, c, rho = tangent_balls(V, F, rows, n_threads, params)
+    interior tangent ball (largest rho, lowest row on ties) among rows
+    0, s, 2s, ... (s = ceil(R/256)); it lies inside Omega, which is all the
+    Kelvin transform requires (Sec. 4.3, App. B.3)."""
+    st = origin_stride(len(rows["pos"]))
+    sub = dict(pos=np.ascontiguousarray(rows["pos"][::st]), nrm=np.ascontiguousarray(rows["nrm"][::st]),
+               tri2bin=rows.get("tri2bin"))
+    r, c, rho = tangent_balls(V, F, sub, n_threads, params)
     return c[int(np.argmax(rho))].copy()
 
 

@@ -353,32 +353,37 @@ __global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym) {
     G[e] = s;
 }
 
-// upper Cholesky factor of G + shift I (FP64, one block, G in shared memory)
+// upper Cholesky factor of G + shift I (FP64, one block, right-looking: after
+// row j of R is formed the trailing block is updated by all threads)
 __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, int *err) {
     extern __shared__ double sg[];
     __shared__ double tr;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) sg[e] = G[e];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double t = 0.0;
-        for (int j = 0; j < m; j++) t += sg[j * m + j];
-        tr = t;
+        for (int j = threadIdx.x; j < m; j += 32) t += sg[j * m + j];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        if (threadIdx.x == 0) tr = t;
     }
     __syncthreads();
     const double shift = shift_rel * tr;
+    for (int e = threadIdx.x; e < m; e += blockDim.x) sg[e * m + e] += shift;
+    __syncthreads();
     for (int j = 0; j < m; j++) {
-        if (threadIdx.x == 0) {
-            double s = sg[j * m + j] + shift;
-            for (int k = 0; k < j; k++) s -= sg[k * m + j] * sg[k * m + j];
-            if (!(s > 0.0)) { atomicOr(err, kErrChol); s = 1e-300; }
-            sg[j * m + j] = sqrt(s);
+        double d = sg[j * m + j];
+        if (!(d > 0.0)) {
+            if (threadIdx.x == 0) atomicOr(err, kErrChol);
+            d = 1e-300;
         }
+        d = sqrt(d);
         __syncthreads();
-        const double d = sg[j * m + j];
-        for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
-            double s = sg[j * m + c];
-            for (int k = 0; k < j; k++) s -= sg[k * m + j] * sg[k * m + c];
-            sg[j * m + c] = s / d;
+        for (int c = j + threadIdx.x; c < m; c += blockDim.x) sg[j * m + c] = c == j ? d : sg[j * m + c] / d;
+        __syncthreads();
+        const int w = m - j - 1;
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            const int a = j + 1 + e / w, b = j + 1 + e % w;
+            if (b >= a) sg[a * m + b] -= sg[j * m + a] * sg[j * m + b];
         }
         __syncthreads();
     }
@@ -388,17 +393,18 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
     }
 }
 
-// Rinv = R^-1 for upper-triangular R (one thread per column, back substitution)
+// Rinv = R^-1 for upper-triangular R: one warp per column c, back
+// substitution with the inner products reduced across the warp
 __global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
-    extern __shared__ double sr[];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sr[e] = R[e];
-    __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        for (int i = m - 1; i >= 0; i--) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= c; k++) s -= sr[i * m + k] * Rinv[k * m + c];
-            Rinv[i * m + c] = i > c ? 0.0 : s / sr[i * m + i];
-        }
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= m) return;
+    for (int i = m - 1; i >= 0; i--) {
+        double s = 0.0;
+        if (i < c)
+            for (int k = i + 1 + lane; k <= c; k += 32) s += R[i * m + k] * Rinv[k * m + c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) Rinv[i * m + c] = i > c ? 0.0 : ((i == c ? 1.0 : 0.0) - s) / R[i * m + i];
+        __syncwarp();
     }
 }
 __global__ void k_f32_to_f64(const float *a, int n, double *b) {
@@ -454,86 +460,96 @@ __global__ void k_ritz(const double *Xt, const double *Zt, int n_pad, double *th
 
 // symmetric eigendecomposition of H (m x m, m even <= 160) by parallel cyclic
 // Jacobi (round-robin pair schedule) in FP32, one block; eigenvalues ascending,
-// eigenvectors in the columns of Q
+// eigenvectors in the columns of Q.  Shared rows are padded to m + 1 floats so
+// that column sweeps hit distinct banks.
 __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int max_sweeps) {
     extern __shared__ float sj[];
-    float *H = sj, *V = sj + m * m;
+    const int ld = m + 1;
+    float *H = sj, *V = sj + m * ld;
     __shared__ float cs[80], sn[80];
     __shared__ int pp[80], qq[80];
-    __shared__ float off, nrm;
+    __shared__ float red_off[32], red_tot[32];
+    __shared__ int stop;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e / m, c = e % m;
-        H[e] = (float)(0.5 * (Hd[r * m + c] + Hd[c * m + r]));
-        V[e] = r == c ? 1.f : 0.f;
+        H[r * ld + c] = (float)(0.5 * (Hd[r * m + c] + Hd[c * m + r]));
+        V[r * ld + c] = r == c ? 1.f : 0.f;
     }
     __syncthreads();
     const int half = m / 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        float o = 0.f, t = 0.f;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e / m, c = e % m;
+            const float v = H[r * ld + c] * H[r * ld + c];
+            t += v;
+            if (r != c) o += v;
+        }
+        for (int of = 16; of > 0; of >>= 1) {
+            o += __shfl_xor_sync(0xFFFFFFFFu, o, of);
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, of);
+        }
+        if (lane == 0) { red_off[warp] = o; red_tot[warp] = t; }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            float o = 0.f, t = 0.f;
-            for (int e = 0; e < m * m; e++) {
-                const float v = H[e] * H[e];
-                t += v;
-                if (e / m != e % m) o += v;
-            }
-            off = o; nrm = t;
+            float so = 0.f, st = 0.f;
+            for (int w = 0; w < nwarps; w++) { so += red_off[w]; st += red_tot[w]; }
+            stop = so <= 1e-12f * st;
         }
         __syncthreads();
-        if (off <= 1e-12f * nrm) break;
+        if (stop) break;
         for (int r = 0; r < m - 1; r++) {
             if (threadIdx.x < half) {
                 const int i = threadIdx.x;
                 int p, q;
                 if (i == 0) { p = m - 1; q = r; }
                 else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
-                if (p > q) { const int t = p; p = q; q = t; }
+                if (p > q) { const int tt = p; p = q; q = tt; }
                 pp[i] = p; qq[i] = q;
-                const float apq = H[p * m + q];
-                float c = 1.f, s = 0.f;
+                const float apq = H[p * ld + q];
+                float c = 1.f, sv = 0.f;
                 if (fabsf(apq) > 1e-30f) {
-                    const float tau = (H[q * m + q] - H[p * m + p]) / (2.f * apq);
-                    const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                    c = 1.f / sqrtf(1.f + t * t);
-                    s = t * c;
+                    const float tau = (H[q * ld + q] - H[p * ld + p]) / (2.f * apq);
+                    const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+                    c = 1.f / sqrtf(1.f + tt * tt);
+                    sv = tt * c;
                 }
-                cs[i] = c; sn[i] = s;
+                cs[i] = c; sn[i] = sv;
             }
             __syncthreads();
-            // columns: H <- H J, V <- V J
             for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
                 const int i = e / m, row = e % m;
                 const int p = pp[i], q = qq[i];
-                const float c = cs[i], s = sn[i];
-                const float hp = H[row * m + p], hq = H[row * m + q];
-                H[row * m + p] = c * hp - s * hq;
-                H[row * m + q] = s * hp + c * hq;
-                const float vp = V[row * m + p], vq = V[row * m + q];
-                V[row * m + p] = c * vp - s * vq;
-                V[row * m + q] = s * vp + c * vq;
+                const float c = cs[i], sv = sn[i];
+                const float hp = H[row * ld + p], hq = H[row * ld + q];
+                H[row * ld + p] = c * hp - sv * hq;
+                H[row * ld + q] = sv * hp + c * hq;
+                const float vp = V[row * ld + p], vq = V[row * ld + q];
+                V[row * ld + p] = c * vp - sv * vq;
+                V[row * ld + q] = sv * vp + c * vq;
             }
             __syncthreads();
-            // rows: H <- J^T H
             for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
                 const int i = e / m, col = e % m;
                 const int p = pp[i], q = qq[i];
-                const float c = cs[i], s = sn[i];
-                const float hp = H[p * m + col], hq = H[q * m + col];
-                H[p * m + col] = c * hp - s * hq;
-                H[q * m + col] = s * hp + c * hq;
+                const float c = cs[i], sv = sn[i];
+                const float hp = H[p * ld + col], hq = H[q * ld + col];
+                H[p * ld + col] = c * hp - sv * hq;
+                H[q * ld + col] = sv * hp + c * hq;
             }
             __syncthreads();
         }
     }
-    // sort ascending (selection of ranks by one thread per column)
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const float d = H[j * m + j];
+        const float d = H[j * ld + j];
         int rank = 0;
         for (int k = 0; k < m; k++) {
-            const float e = H[k * m + k];
+            const float e = H[k * ld + k];
             rank += (e < d) || (e == d && k < j);
         }
         evals[rank] = d;
-        for (int r = 0; r < m; r++) Q[r * m + rank] = V[r * m + j];
+        for (int r = 0; r < m; r++) Q[r * m + rank] = V[r * ld + j];
     }
 }
 
@@ -706,8 +722,8 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
     const size_t smm = (size_t)m * m * sizeof(double);
     MCS_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    MCS_CUDA(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * m * m * sizeof(float))));
+    const size_t jsm = 2 * (size_t)m * (m + 1) * sizeof(float);
+    MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
     cudaStream_t st = c.st;
     const size_t mv = (size_t)m * p.n_pad;
     const int g = grid_for(mv);
@@ -731,18 +747,18 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym);
     };
     // orthonormalise X: shifted CholeskyQR, then CholeskyQR2 (FP64)
-    auto orth = [&]() -> cudaError_t {
+    auto orth = [&](bool shifted) -> cudaError_t {
         const double shifts[3] = {11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16, 0.0, 0.0};
-        for (int pass = 0; pass < 3; pass++) {
+        for (int pass = shifted ? 0 : 1; pass < 3; pass++) {
             gram(X, X, 1);
             k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
-            k_tri_inverse<<<1, 128, smm, st>>>(c.w.R, m, c.w.Rinv);
+            k_tri_inverse<<<(m + 7) / 8, 256, 0, st>>>(c.w.R, m, c.w.Rinv);
             k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T);
             std::swap(X, T);
         }
         return cudaGetLastError();
     };
-    MCS_CUDA(orth());
+    MCS_CUDA(orth(true));
     std::vector<double> theta(m), res(m);
     double a_cut = ub / 8.0, a_low = 0.0;
     int iters = 0, converged = 0, gemms = 0;
@@ -775,7 +791,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
             prev = cur;
             cur = nxt;
         }
-        MCS_CUDA(orth());
+        MCS_CUDA(orth(false));
         // ---- Rayleigh-Ritz
         k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[3], c.w.vl[3]);
         MCS_CUDA(tc_product(c, 3));
@@ -783,7 +799,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr,
                                     nullptr, nullptr, Z);
         gram(X, Z, 1);
-        k_jacobi<<<1, 512, 2 * m * m * sizeof(float), st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
+        k_jacobi<<<1, 512, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
         k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
         k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, X, m, p.n_pad, T);
         std::swap(X, T);
@@ -887,7 +903,7 @@ size_t mcs_tc_symm_product_workspace_size(int n, int m) {
 
 void mcs_default_eig_params(mcs_eig_params *p) {
     if (!p) return;
-    p->degree = 10;
+    p->degree = 24;
     p->max_iters = 60;
     p->tol = 1e-5;
 }

@@ -102,10 +102,11 @@ __device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, dou
     return !warp_query<double, kBelow>(m, x, y, z, thr, h, front, err);
 }
 
+// rows v = i * stride, i = 0, 1, ... (stride 1: every row)
 __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R,
-                                                                Frame fr, RowBall *ball, Ctrl *ctrl) {
+                                                                int stride, Frame fr, RowBall *ball, Ctrl *ctrl) {
     __shared__ int fronts[kTanWarps][32];
-    const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
+    const int v = (blockIdx.x * kTanWarps + (threadIdx.x >> 5)) * stride;
     if (v >= R) return;
     int *front = fronts[threadIdx.x >> 5];
     int err = 0;
@@ -143,13 +144,14 @@ __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const
     }
 }
 
-// largest empty radius, lowest row on ties -> inversion centre
-__global__ void k_origin_argmax(const RowBall *ball, int R, Ctrl *ctrl) {
+// largest empty radius over rows 0, stride, 2 stride, ..., lowest row on ties
+// -> inversion centre (any interior point serves; Sec. 4.3)
+__global__ void k_origin_argmax(const RowBall *ball, int R, int stride, Ctrl *ctrl) {
     __shared__ double sv[1024];
     __shared__ int si[1024];
     double best = -1.0;
     int bi = 0x7FFFFFFF;
-    for (int v = threadIdx.x; v < R; v += blockDim.x) {
+    for (int v = threadIdx.x * stride; v < R; v += blockDim.x * stride) {
         const double r = ball[v].rho;
         if (r > best) { best = r; bi = v; }
     }
@@ -744,9 +746,10 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     // tangent balls
     if (ext) {
         if (p->origin_auto) {
-            k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
-                                                                                     ball, ctrl);
-            k_origin_argmax<<<1, 1024, 0, st>>>(ball, R, ctrl);
+            const int ostride = (R + 255) / 256, nsub = (R + ostride - 1) / ostride;
+            k_tangent_int<<<(nsub + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R,
+                                                                                        ostride, fr, ball, ctrl);
+            k_origin_argmax<<<1, 1024, 0, st>>>(ball, R, ostride, ctrl);
         } else {
             k_set_origin<<<1, 1, 0, st>>>(ctrl, p->origin[0], p->origin[1], p->origin[2]);
         }
@@ -755,7 +758,7 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
                                                                                  ball, ctrl);
         k_colfactor<<<gr, tb, 0, st>>>(rows->pos, R, ctrl, cf);
     } else {
-        k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
+        k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, 1, fr,
                                                                                  ball, ctrl);
     }
     MCS_CUDA(cudaGetLastError());
