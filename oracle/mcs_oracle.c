@@ -376,6 +376,7 @@ static int walk_int64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
         int f; double bary[3];
         double d = sqrt(closest_brute64(cx, x, &f, bary));
         (*steps)++;
+        if (f < 0) { *capped = 1; ex->f = -1; return -1; }  /* non-finite point: lost */
         if (d < pb->eps || k == pb->max_steps) {
             *capped = !(d < pb->eps);
             ex->f = f; ex->b[0] = bary[0]; ex->b[1] = bary[1]; ex->b[2] = bary[2];
@@ -396,6 +397,7 @@ static int walk_int32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
         int f; float bary[3];
         float d = sqrtf(closest_brute32(cx, x, &f, bary));
         (*steps)++;
+        if (f < 0) { *capped = 1; ex->f = -1; return -1; }
         if (d < eps2 || k == pb->max_steps) {
             double xd[3] = {x[0], x[1], x[2]}, b64[3];
             double d64 = sqrt(recheck64(cx, f, xd, b64));
@@ -438,6 +440,7 @@ static int walk_ext64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
             for (int i = 0; i < 3; i++) { xp[i] = x[i] * inv; q[i] = xp[i] + o[i]; }
             double d = sqrt(closest_brute64(cx, q, &f, bary));
             (*steps)++;
+            if (f < 0) { *capped = 1; *lost = 1; ex->f = -1; return -1; }
             double nx = sqrt(xp[0] * xp[0] + xp[1] * xp[1] + xp[2] * xp[2]);
             double ri = d / (nx * (nx + d));
             double r0 = cx->rho0max - sqrt(r2);
@@ -474,6 +477,7 @@ static int walk_ext32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
             for (int i = 0; i < 3; i++) { xp[i] = x[i] * inv; q[i] = xp[i] + of[i]; }
             float d = sqrtf(closest_brute32(cx, q, &f, bary));
             (*steps)++;
+            if (f < 0) { *capped = 1; *lost = 1; ex->f = -1; return -1; }
             float nx = sqrtf(xp[0] * xp[0] + xp[1] * xp[1] + xp[2] * xp[2]);
             float ri = d / (nx * (nx + d));
             float r0 = r0max - sqrtf(r2);
@@ -546,8 +550,11 @@ static int inv_ball_ok(const orc_ctx *cx, const double st[3], const double nt[3]
     const orc_problem *pb = cx->pb;
     double ct[3];
     for (int i = 0; i < 3; i++) ct[i] = st[i] - r * nt[i];
-    double den = (ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2]) - r * r;
-    if (!(den > 0.0)) return 0;
+    double cc = ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2];
+    double den = cc - r * r;
+    /* the ball must stay clear of the inversion centre, and by a margin that
+     * keeps its primal image ball (centre ~ 1/den) within FP64 resolution */
+    if (!(den > 1e-6 * cc)) return 0;
     double inv = 1.0 / den, q[3];
     for (int i = 0; i < 3; i++) { C[i] = ct[i] * inv; q[i] = C[i] + pb->origin[i]; }
     *Rp = r * inv;
@@ -585,13 +592,16 @@ static void tangent_exterior(const orc_ctx *cx, const double s[3], const double 
     /* recompute C for the accepted r (the last test may have been a rejection) */
     double ct[3];
     for (int i = 0; i < 3; i++) ct[i] = st[i] - r * nt[i];
-    double den = (ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2]) - r * r;
-    if (!(den > 0.0)) return;
+    double cc = ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2];
+    double den = cc - r * r;
+    if (!(den > 1e-6 * cc)) return;
     double invd = 1.0 / den, q[3];
     for (int i = 0; i < 3; i++) { C[i] = ct[i] * invd; q[i] = C[i] + pb->origin[i]; }
     double D = dist64(cx, q);
-    double den2 = (C[0] * C[0] + C[1] * C[1] + C[2] * C[2]) - D * D;
-    if (!(den2 > 0.0)) return;
+    double CC = C[0] * C[0] + C[1] * C[1] + C[2] * C[2];
+    double den2 = CC - D * D;
+    /* |C|^2 - D^2 cancels when the empty ball nearly reaches the centre */
+    if (!(den2 > 1e-8 * CC)) return;
     double inv2 = 1.0 / den2;
     for (int i = 0; i < 3; i++) c_inv[i] = C[i] * inv2;
     *rho_inv = D * inv2;

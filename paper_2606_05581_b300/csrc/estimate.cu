@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 #include "mcs_internal.h"
 
@@ -39,6 +40,11 @@ struct Ctrl {
     unsigned long long queue, kqueue;
     unsigned long long steps, capped, lost, kill_steps, kill_capped, kill_lost;
     unsigned long long nodes, tris;
+    // first walk that met a query without a triangle: kind (1 interior,
+    // 2 exterior), killing flag, walk id, step and query point
+    int diag_set, diag_kind, diag_killing, diag_step;
+    unsigned long long diag_walk;
+    double diag_p[3];
     int err;
     int discarded;
     double origin[3];
@@ -229,8 +235,11 @@ __global__ void k_ext_frame(const double *V, int nv, Ctrl *ctrl) {
 __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double nt[3], double r, const double o[3],
                             double onemk, int *front, int *err) {
     const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
-    const double den = (ct0 * ct0 + ct1 * ct1 + ct2 * ct2) - r * r;
-    if (!(den > 0.0)) return false;
+    const double cc = ct0 * ct0 + ct1 * ct1 + ct2 * ct2;
+    const double den = cc - r * r;
+    // clear of the inversion centre by a margin that keeps the primal image
+    // ball (centre ~ 1/den) within FP64 resolution
+    if (!(den > 1e-6 * cc)) return false;
     const double inv = 1.0 / den;
     const double C0 = ct0 * inv, C1 = ct1 * inv, C2 = ct2 * inv;
     const double Rp = r * inv;
@@ -276,13 +285,16 @@ __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const
         b.r = r;
         if (r > 0.0) {
             const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
-            const double den = (ct0 * ct0 + ct1 * ct1 + ct2 * ct2) - r * r;
-            if (den > 0.0) {
+            const double cc = ct0 * ct0 + ct1 * ct1 + ct2 * ct2;
+            const double den = cc - r * r;
+            if (den > 1e-6 * cc) {
                 const double invd = 1.0 / den;
                 const double C0 = ct0 * invd, C1 = ct1 * invd, C2 = ct2 * invd;
                 const double D = wdist(m, C0 + o[0], C1 + o[1], C2 + o[2], front, &err);
-                const double den2 = (C0 * C0 + C1 * C1 + C2 * C2) - D * D;
-                if (den2 > 0.0) {
+                const double CC = C0 * C0 + C1 * C1 + C2 * C2;
+                const double den2 = CC - D * D;
+                // |C|^2 - D^2 cancels when the empty ball nearly reaches the centre
+                if (den2 > 1e-8 * CC) {
                     const double inv2 = 1.0 / den2;
                     b.c[0] = C0 * inv2; b.c[1] = C1 * inv2; b.c[2] = C2 * inv2;
                     b.rho = D * inv2;
@@ -334,6 +346,17 @@ __device__ __forceinline__ double recheck64(const DevMesh &m, int slot, double x
     const Tri32 t = m.t32[slot];
     return tri_closest<double>(x, y, z, (double)t.a.x, (double)t.a.y, (double)t.a.z, (double)t.ab.x, (double)t.ab.y,
                                (double)t.ab.z, (double)t.ac.x, (double)t.ac.y, (double)t.ac.z, b);
+}
+
+__device__ void record_nohit(Ctrl *c, int kind, int killing, unsigned long long g, int step, double x, double y,
+                             double z) {
+    if (atomicCAS(&c->diag_set, 0, 1) == 0) {
+        c->diag_kind = kind;
+        c->diag_killing = killing;
+        c->diag_walk = g;
+        c->diag_step = step;
+        c->diag_p[0] = x; c->diag_p[1] = y; c->diag_p[2] = z;
+    }
 }
 
 template <typename T> struct WalkState {
@@ -425,6 +448,12 @@ __global__ void __launch_bounds__(128) k_walks(WalkArgs a) {
             Hit<T> h;
             closest<T, COUNT>(a.m, s.x.x, s.x.y, s.x.z, s.prev, h, &err, &work);
             n_steps++;
+            if (h.slot < 0 || h.id < 0 || h.id >= a.m.nf) {
+                err |= kErrNoHit;
+                record_nohit(a.ctrl, 1, a.killing, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+                finish(-1, -1, true, true);
+                continue;
+            }
             const T d = rsq<T>(h.d2);
             if (d < epsT || s.k == a.max_steps) {
                 if (sizeof(T) == 8) {
@@ -451,6 +480,12 @@ __global__ void __launch_bounds__(128) k_walks(WalkArgs a) {
                 Hit<T> h;
                 closest<T, COUNT>(a.m, xp0 + oT[0], xp1 + oT[1], xp2 + oT[2], s.prev, h, &err, &work);
                 n_steps++;
+                if (h.slot < 0 || h.id < 0 || h.id >= a.m.nf) {
+                    err |= kErrNoHit;
+                    record_nohit(a.ctrl, 2, a.killing, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+                    finish(-1, -1, true, true);
+                    continue;
+                }
                 const T d = rsq<T>(h.d2);
                 const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
                 const T ri = d / (nx * (nx + d));
@@ -848,6 +883,15 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     if (hc.err & kErrNoOrigin) {
         set_error("mcs_estimate_dtn: no interior tangent ball to place the inversion centre");
         return MCS_ERR_NO_INTERIOR_POINT;
+    }
+    if (hc.err & kErrNoHit) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "mcs_estimate_dtn: a walk query found no triangle (kind %d, killing %d, walk %llu, step %d, "
+                 "x~ = (%.9g, %.9g, %.9g)); walk retired as lost",
+                 hc.diag_kind, hc.diag_killing, hc.diag_walk, hc.diag_step, hc.diag_p[0], hc.diag_p[1], hc.diag_p[2]);
+        set_error(buf);
+        return MCS_ERR_DEVICE;
     }
     if (hc.err) {
         set_error(hc.err & kErrBin ? "mcs_estimate_dtn: tri2bin maps a triangle outside [0, n_rows)"

@@ -22,6 +22,7 @@ constexpr int kErrStack = 1;       // traversal stack full (a far child was drop
 constexpr int kErrNoOrigin = 2;    // exterior: no interior tangent ball for the inversion centre
 constexpr int kErrTree = 4;        // traversal / refit exceeded its iteration bound
 constexpr int kErrBin = 8;         // an exit bin outside [0, n_rows)
+constexpr int kErrNoHit = 64;      // a walk query found no triangle (non-finite point); walk retired as lost
 
 // --------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -329,6 +330,7 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
     best.id = 0x7FFFFFFF;
     best.slot = -1;
     best.b0 = best.b1 = best.b2 = (T)0;
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) return;  // no triangle: caller checks slot < 0
     const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
     T thr2 = (T)INFINITY;
     auto test = [&](int s) {

@@ -394,3 +394,20 @@ def test_fp32_mode_agrees_statistically_with_fp64(oracle):
     l32, _ = oracle.steklov(oracle.assemble(e32, rows), rows["area"], 16)
     assert np.allclose(l32, l64, rtol=0.05, atol=1e-9)
     assert np.mean(e32["H"] == e64["H"]) > 0.9
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_exterior_walks_stay_in_the_exterior(oracle, prec):
+    """Every exterior walk ends on the surface within the step cap: the inverted tangent
+    balls stay inside the Kelvin image of the exterior, so no walk starts in (or leaks
+    into) the image of the interior, where inverted walks drift off to infinity."""
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    o = oracle.interior_origin(m.V, m.F, rows)
+    est = oracle.estimate(m.V, m.F, rows, 16, 1e-3, exterior=True, origin=o, seed=3, prec=prec,
+                          record_exits=True, killing_walks=512)
+    assert est["capped"].sum() == 0 and est["kill_stats"][1] == 0
+    assert np.all(est["exit_tri"][est["discarded"] == 0] >= 0)
+    # the inverted balls exclude the inversion centre: |c~| > rho~
+    ok = est["discarded"] == 0
+    assert np.all(np.linalg.norm(est["center"][ok], axis=1) > est["rho"][ok])
