@@ -816,6 +816,8 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         a_cut = theta[m - 1];
         a_low = std::min(0.0, theta[0]);
     }
+    // the last rotation used the FP32 Jacobi vectors: restore FP64 orthonormality
+    if (evecs) MCS_CUDA(orth(false));
     int err = 0;
     MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaMemcpyAsync(evals, c.w.theta, k * sizeof(double), cudaMemcpyDefault, st));
