@@ -172,6 +172,29 @@ size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, lo
 mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
                             void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream);
 
+/* Allocation-free estimate.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need an
+ * estimate -- code running inside a memory pool or arena it does not own, a
+ * custom allocator that forbids cudaMalloc in a critical section, or a
+ * process that must not change its allocator state while the device is full.
+ * It runs mcs_estimate_dtn with its scratch taken from a fixed 32 MiB array
+ * that the library reserves on every GPU where it is loaded (held until the
+ * process exits); it calls no cudaMalloc, cudaFree or allocating library
+ * routine, and creates no events (phase timing is off).  The caller still
+ * passes rows, parameters and outputs as for mcs_estimate_dtn.
+ *  - Estimates whose scratch (mcs_estimate_workspace_size) exceeds
+ *    mcs_estimate_dtn_noalloc_capacity() bytes are rejected with MCS_ERR_ARG.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before capturing a stream.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    every part the estimate reads is rewritten or cleared by the call itself.
+ *    Calls that overlap on the GPU (other streams, other threads) race on it:
+ *    serialise them. */
+size_t mcs_estimate_dtn_noalloc_capacity(void);
+mcs_status mcs_estimate_dtn_noalloc(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
+                                    mcs_stats *stats, void *stream);
+
 /* Steklov eigensolve (Eq. steklov-eigenproblem, Galerkin form Lambda psi =
  * lambda M psi with M = diag(mass); smallest k pairs, Sec. 4.4 / Sec. 5).
  * Chebyshev-filtered subspace iteration on a block of m = k + 32 vectors

@@ -87,6 +87,9 @@ def lib():
         L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
                                        C.POINTER(Stats), vp]
         L.mcs_philox_words.argtypes = [u64, u64, u32, u32, u32, u32, vp, vp]
+        L.mcs_estimate_dtn_noalloc_capacity.restype = C.c_size_t
+        L.mcs_estimate_dtn_noalloc.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs),
+                                               C.POINTER(Stats), vp]
         L.mcs_default_eig_params.argtypes = [C.POINTER(EigParams)]
         L.mcs_steklov_workspace_size.argtypes = [i32, i32]
         L.mcs_steklov_workspace_size.restype = C.c_size_t
@@ -287,3 +290,19 @@ def tc_symm_product(A: torch.Tensor, Xt: torch.Tensor) -> torch.Tensor:
     ws = torch.empty(nb + 256, dtype=torch.uint8, device=A.device)
     _check(lib().mcs_tc_symm_product(_ptr(A), _ptr(Xt), n, m, _ptr(Zt), C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
     return Zt
+
+
+def estimate_dtn_noalloc(mesh: Mesh, rows: dict, params: Params, outputs: dict):
+    """The estimate with the library's fixed device scratch (no allocation in
+    the call); ``outputs`` holds caller-allocated device tensors named as in
+    estimate_dtn.  Returns the stats dict."""
+    pos, nrm, area = rows["pos"], rows["nrm"], rows["area"]
+    t2b = rows.get("tri2bin")
+    R = int(pos.shape[0])
+    rs = Rows(R, pos.data_ptr(), nrm.data_ptr(), area.data_ptr(), None if t2b is None else t2b.data_ptr())
+    out = Outputs(*[None if outputs.get(k) is None else outputs[k].data_ptr()
+                    for k in ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")])
+    st = Stats()
+    _check(lib().mcs_estimate_dtn_noalloc(mesh.handle, C.byref(rs), C.byref(params), C.byref(out), C.byref(st),
+                                          _stream()))
+    return {k: (list(getattr(st, k)) if k in ("origin", "phase_ms") else getattr(st, k)) for k, _ in Stats._fields_}
