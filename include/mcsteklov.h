@@ -144,6 +144,21 @@ int mcs_mesh_nf(mcs_mesh m);
  * Device outputs nv x 3, nv x 3, nv. */
 mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, void *stream);
 
+/* Sample rows (point basis of Sec. 4.4; farthest-point sampling stands in
+ * for blue noise): n samples over face centroids by greedy farthest-point
+ * sampling from face 0 (FP64, ties -> lowest face id); each face is owned by
+ * its nearest sample (first selected on ties): tri2bin; a sample's area is
+ * the total area of the faces it owns; its normal is the unit normal of the
+ * sampled face, oriented (orient != 0) by the generalized winding number of
+ * the other faces at x -/+ delta n, delta = sqrt(face area)/4 (App. A item 1).
+ * Device outputs: sel n, pos n x 3, nrm n x 3, area n, tri2bin nf,
+ * orient_gap n (optional: GWN(x - delta n) - GWN(x + delta n)).  Needs a
+ * cooperative launch; synchronises `stream`. */
+size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n);
+mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,
+                           int32_t *tri2bin, float *orient_gap, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
 /* Closest point of n query points (device, n x 3 FP64) by BVH traversal in
  * FP64 (prec 64) or FP32 (prec 32, points rounded to float): squared
  * distance, triangle id (argmin of (d^2, id)), barycentrics.  Device outputs. */

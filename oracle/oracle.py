@@ -86,6 +86,8 @@ def lib():
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_gwn.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         _lib.orc_gwn.restype = C.c_double
+        _lib.orc_gwn_skip.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+        _lib.orc_gwn_skip.restype = C.c_double
         _lib.orc_num_threads.restype = C.c_int
     return _lib
 
@@ -138,11 +140,12 @@ def closest_points(V, F, P, prec: int = 64):
     return d2, f, b
 
 
-def gwn(V, F, q) -> float:
+def gwn(V, F, q, skip: int = -1) -> float:
+    """Generalized winding number at q (Jacobson et al. 2013), optionally without face `skip`."""
     V = np.ascontiguousarray(V, np.float64)
     F = np.ascontiguousarray(F, np.int32)
     q = np.ascontiguousarray(q, np.float64)
-    return float(lib().orc_gwn(_p(V), _p(F), F.shape[0], _p(q)))
+    return float(lib().orc_gwn_skip(_p(V), _p(F), F.shape[0], _p(q), skip))
 
 
 # ---------------------------------------------------------------------------

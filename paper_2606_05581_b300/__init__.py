@@ -87,6 +87,9 @@ def lib():
         L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
                                        C.POINTER(Stats), vp]
         L.mcs_philox_words.argtypes = [u64, u64, u32, u32, u32, u32, vp, vp]
+        L.mcs_sample_rows_workspace_size.argtypes = [vp, i32]
+        L.mcs_sample_rows_workspace_size.restype = C.c_size_t
+        L.mcs_sample_rows.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
         L.mcs_estimate_dtn_noalloc_capacity.restype = C.c_size_t
         L.mcs_estimate_dtn_noalloc.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs),
                                                C.POINTER(Stats), vp]
@@ -163,6 +166,22 @@ def vertex_rows(mesh: Mesh):
     area = torch.empty(mesh.nv, dtype=torch.float64, device=dev)
     _check(lib().mcs_vertex_rows(mesh.handle, _ptr(pos), _ptr(nrm), _ptr(area), _stream()))
     return dict(pos=pos, nrm=nrm, area=area, tri2bin=None)
+
+
+def sample_rows(mesh: Mesh, n: int, orient: bool = True, workspace: "Workspace | None" = None):
+    """Farthest-point sample rows with Voronoi areas and oriented face normals."""
+    dev = torch.device("cuda")
+    sel = torch.empty(n, dtype=torch.int32, device=dev)
+    pos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    nrm = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    area = torch.empty(n, dtype=torch.float64, device=dev)
+    t2b = torch.empty(mesh.nf, dtype=torch.int32, device=dev)
+    gap = torch.empty(n, dtype=torch.float32, device=dev)
+    nb = int(lib().mcs_sample_rows_workspace_size(mesh.handle, n))
+    ws = (workspace or Workspace()).get(nb)
+    _check(lib().mcs_sample_rows(mesh.handle, n, int(orient), _ptr(sel), _ptr(pos), _ptr(nrm), _ptr(area), _ptr(t2b),
+                                 _ptr(gap), C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return dict(pos=pos, nrm=nrm, area=area, tri2bin=t2b, sel=sel, gap=gap)
 
 
 def closest_points(mesh: Mesh, P: torch.Tensor, prec: int = 64):

@@ -168,3 +168,39 @@ def test_invalid_arguments_are_rejected():
         mcs.Mesh(bad, m.F)
     with pytest.raises(mcs.MCSError):
         mcs.Mesh(m.V, m.F + 1000)
+
+
+def test_sample_rows_match_oracle(oracle):
+    """FPS selections, owners (tri2bin), Voronoi areas and positions bit for bit; the
+    orientation sign agrees wherever the oracle's winding-number gap is not a near tie."""
+    m = meshgen.wild_union(8, 12000, seed=11)
+    mesh = mcs.Mesh(m.V, m.F)
+    g = mcs.sample_rows(mesh, 500, orient=True)
+    o = oracle.fps_rows(m.V, m.F, 500, orient=True)
+    assert np.array_equal(g["sel"].cpu().numpy(), o["sel"])
+    assert np.array_equal(g["tri2bin"].cpu().numpy(), o["tri2bin"])
+    assert np.array_equal(g["area"].cpu().numpy(), o["area"])
+    assert np.array_equal(g["pos"].cpu().numpy(), o["pos"])
+    gn, on = g["nrm"].cpu().numpy(), o["nrm"]
+    same = np.all(gn == on, axis=1)
+    flipped = np.all(gn == -on, axis=1)
+    assert np.all(same | flipped)
+    for i in np.flatnonzero(flipped):
+        f = o["sel"][i]
+        a, b, c = m.V[m.F[f]]
+        delta = 0.25 * np.sqrt(0.5 * np.linalg.norm(np.cross(b - a, c - a)))
+        gi = oracle.gwn(m.V, m.F, o["pos"][i] - delta * on[i], skip=f)
+        go = oracle.gwn(m.V, m.F, o["pos"][i] + delta * on[i], skip=f)
+        assert abs(gi - go) < 1e-3, (i, gi, go)
+    assert flipped.mean() < 0.01
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_sample_rows_estimate_bit_exact(oracle, prec):
+    """The estimate on GPU sample rows equals the oracle's on the same rows."""
+    m = meshgen.wild_union(6, 5000, seed=9)
+    mesh = mcs.Mesh(m.V, m.F)
+    g = mcs.sample_rows(mesh, 300, orient=True)
+    rows_np = dict(pos=g["pos"].cpu().numpy(), nrm=g["nrm"].cpu().numpy(), area=g["area"].cpu().numpy(),
+                   tri2bin=g["tri2bin"].cpu().numpy())
+    _compare(oracle, m, rows_np, 64, 1e-3, prec)
