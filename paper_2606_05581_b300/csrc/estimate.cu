@@ -369,7 +369,7 @@ template <typename T> struct WalkState {
 };
 
 template <typename T, bool EXT, bool COUNT>
-__global__ void __launch_bounds__(128) k_walks(WalkArgs a) {
+__global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const uint32_t k0 = a.k0, k1 = a.killing ? (a.k1 ^ kKillKeyXor) : a.k1;
