@@ -1,13 +1,26 @@
 """Benchmark of the Monte Carlo DtN hot path on B300.
 
-One step = the whole hot path on one synthetic workload: BVH build, rows,
-tangent balls, walks (+ killing walks), histograms, assembly of Lambda and
-the Steklov eigensolve.  Default workload: two icosphere-s4 spheres
-(R = 0.5, centres 1.5 apart; 5124 vertices, 10240 triangles), exterior
-estimator with killing walks (N0 = 64 W), FP32 walks, W = 1024 walks per
-vertex, eps = 1e-3, k = 64 Steklov pairs.
+One step = the whole hot path on one synthetic workload.  Workloads
+(--workload):
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  two_spheres_s4_exterior (default)  two icosphere-s4 spheres (R = 0.5,
+      centres 1.5 apart; 5124 vertices, 10240 triangles), exterior estimator
+      with killing walks (N0 = 64 W), FP32 walks, W = 1024 per vertex,
+      eps = 1e-3, k = 64 Steklov pairs.  Step: BVH build, vertex rows,
+      tangent balls, walks, histograms, assembly, Steklov eigensolve.
+  wild_2m   a ~2.0M-face union of 300 ellipsoids / tori (noise, flipped
+      faces, slivers), 10,000 farthest-point sample rows, W = 4096, FP32,
+      interior, k = 64.  Same step with sample rows instead of vertex rows.
+  batch     --meshes (512) unions with 5k-200k faces each (mesh i: seed
+      1000 + i, exterior when i is odd), 1024 sample rows x 512 walks each,
+      FP32, autotuned launch; step = one replay of the graph-captured batched
+      estimate (all meshes' setup, ONE persistent walk launch, histograms,
+      assembly).  BVH builds and sample rows are preprocessing, timed apart.
+  precision FP32 vs FP64 walks on the two-sphere mesh at W = 1024, 4096,
+      16384 (4 seeds each), k = 128, against an FP64 W = 65536 reference;
+      per-eigenvalue errors, their standard errors and walks/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 N > 1 (torchrun): every rank runs its own replica (seed = rank), no
 collective on the data path (weak scaling); the step time is the max over
@@ -38,15 +51,34 @@ OPS_PER_NODE = 36
 OPS_PER_TRI = 90
 
 
+WORKLOADS = ("two_spheres_s4_exterior", "wild_2m", "batch", "precision")
+
+
 def workload_config(args):
+    if args.workload == "wild_2m":
+        return dict(workload="wild_2m", mesh="union of 300 ellipsoids/tori, ~2.0M faces, seed 0 (noise 1e-3, "
+                    "5% flipped, 10% slivers)", rows="10000 farthest-point samples (face centroids, from face 0)",
+                    walks_per_row=args.walks or 4096, eps=1e-3, domain="interior", prec=f"fp{args.prec}",
+                    steklov_k=args.k, seed="rank + 1", l2="inputs larger than L2 (BVH + triangles ~170 MB) and "
+                    "flushed between steps (512 MiB write)")
+    if args.workload == "batch":
+        return dict(workload="batch", meshes=args.meshes, mesh="unions of U{1..50} primitives, faces "
+                    "log-uniform [5k, 200k], seed 1000 + i", rows="1024 farthest-point samples per mesh",
+                    walks_per_row=args.walks or 512, eps=1e-3, domain="exterior for odd i, interior for even i",
+                    killing_walks=64 * (args.walks or 512), prec=f"fp{args.prec}", seed="i",
+                    launch="one graph replay: per-mesh setup, one persistent walk launch, per-mesh histogram and "
+                           "assembly; autotuned launch shape and queue order",
+                    l2="inputs larger than L2 (all meshes' BVHs) and flushed between steps (512 MiB write)")
     return dict(workload="two_spheres_s4_exterior", mesh="two icospheres s4, R=0.5, centres 1.5 apart",
-                nv=5124, nf=10240, walks_per_row=args.walks, eps=1e-3, domain="exterior",
-                killing_walks=64 * args.walks, prec=f"fp{args.prec}", steklov_k=args.k, seed="rank",
+                nv=5124, nf=10240, walks_per_row=args.walks or 1024, eps=1e-3, domain="exterior",
+                killing_walks=64 * (args.walks or 1024), prec=f"fp{args.prec}", steklov_k=args.k, seed="rank",
                 rows="all vertices", l2="flushed between steps (512 MiB write)")
 
 
-def make_mesh():
+def make_mesh(args):
     import meshgen
+    if args.workload == "wild_2m":
+        return meshgen.wild_union(300, 2_000_000, seed=0)
     return meshgen.two_spheres(4, 0.5, 1.5)
 
 
@@ -102,51 +134,76 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- our arm
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def _alu_roofline(cst, walk_ms, kernel):
+    """FP32 ALU roofline of the walk kernel: algorithmic operations (node
+    visits and triangle tests of the same walks, counted in a separate
+    untimed run) over the kernel's event-timed duration."""
+    sm_max = _peaks().get("sm_max_mhz", 2032.0)
+    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x clock, T op/s
+    ops = OPS_PER_NODE * cst["nodes_visited"] + OPS_PER_TRI * cst["tris_tested"]
+    achieved = ops / (walk_ms / 1e3) / 1e12
+    q = max(1, cst["steps"] + cst["killing_steps"])
+    return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
+            "traffic": None, "kernel": kernel, "ops_per_node": OPS_PER_NODE, "ops_per_tri": OPS_PER_TRI,
+            "nodes_per_query": cst["nodes_visited"] / q, "tris_per_query": cst["tris_tested"] / q,
+            "peak_note": "148 SMs x 128 FP32 lanes x max SM clock (derived)"}
+
+
 def run_ours(args, rank, world):
+    """One mesh per step: the default two-sphere exterior workload or wild_2m."""
     import torch
     import paper_2606_05581_b300 as mcs
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    m = make_mesh()
+    wild = args.workload == "wild_2m"
+    m = make_mesh(args)
     V_h = torch.from_numpy(m.V).pin_memory()
     F_h = torch.from_numpy(m.F).pin_memory()
     V_d, F_d = V_h.to(dev), F_h.to(dev)
-    W = args.walks
-    params = mcs.default_params(walks_per_row=W, prec=args.prec, domain=1, killing_walks=64 * W, seed=rank,
-                                timing=1)
+    W = args.walks or (4096 if wild else 1024)
+    n_rows = 10_000 if wild else m.nv
+    kill = 0 if wild else 64 * W
+    pkw = dict(walks_per_row=W, prec=args.prec, domain=0 if wild else 1, killing_walks=kill,
+               seed=rank + (1 if wild else 0))
+    params = mcs.default_params(timing=1, **pkw)
     ws = mcs.Workspace()
+    rows_ws = mcs.Workspace()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    has_eig = hasattr(mcs, "steklov_modes")
-
     eig_ws = mcs.Workspace()
+
+    def make_rows(mesh):
+        if wild:
+            return mcs.sample_rows(mesh, n_rows, orient=True, workspace=rows_ws)
+        return mcs.vertex_rows(mesh)
 
     def step(V, F, keep=False):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         mesh = mcs.Mesh(V, F)
-        rows = mcs.vertex_rows(mesh)
+        rows = make_rows(mesh)
         e1.record(stream)
         res = mcs.estimate_dtn(mesh, rows, params, workspace=ws)
-        ev = None
         e2.record(stream)
-        if has_eig:
-            ev = mcs.steklov_modes(res["Lambda"], rows["area"], args.k, vectors=True, workspace=eig_ws)
-        e3 = torch.cuda.Event(enable_timing=True)
+        ev = mcs.steklov_modes(res["Lambda"], rows["area"], args.k, vectors=True, workspace=eig_ws)
         e3.record(stream)
         e3.synchronize()
         st = dict(res["stats"])
         st["build_ms"] = e0.elapsed_time(e1)
         st["eig_ms"] = e2.elapsed_time(e3)
-        if ev is not None:
-            st["eig"] = ev[2]
+        st["eig"] = ev[2]
         out = (mesh, rows, res, ev)
         return out if keep else (st, ev)
 
-    # warm-up
     for _ in range(args.warmup):
         step(V_d, F_d)
     torch.cuda.synchronize()
@@ -165,11 +222,9 @@ def run_ours(args, rank, world):
                 mesh, rows, res, ev = step(V, F, keep=True)
                 L_h = torch.empty(res["Lambda"].shape, dtype=torch.float64, pin_memory=True)
                 L_h.copy_(res["Lambda"], non_blocking=True)
+                lam_h = ev[0].to("cpu", non_blocking=True)
                 h2d = V_h.numel() * 8 + F_h.numel() * 4
-                d2h = L_h.numel() * 8
-                if ev is not None:
-                    lam_h = ev[0].to("cpu", non_blocking=True)
-                    d2h += lam_h.numel() * 8
+                d2h = L_h.numel() * 8 + lam_h.numel() * 8
                 st = dict(res["stats"])
             else:
                 st, _ = step(V_d, F_d)
@@ -184,57 +239,48 @@ def run_ours(args, rank, world):
     clk = ClockSampler(dev.index) if rank == 0 else None
     if clk:
         clk.start()
+    l0 = mcs.launch_count()
     times, stats, _, _ = timed(args.steps)
     torch.cuda.synchronize()
+    launches = mcs.launch_count() - l0
     barrier(world)
     clocks = clk.stop() if clk else None
     ms = float(np.sum(times)) / args.steps
     ms_max = allreduce_max(ms, world)
     steps_total = sum(s["steps"] + s["killing_steps"] for s in stats) / args.steps  # per replica per step
-    R = m.nv
     value = steps_total * world / (ms_max / 1e3)
-    # end to end: host buffers in, Lambda (+ eigenvalues) out
+    # end to end: host buffers in, Lambda and the eigenvalues out
     e2e_times, _, h2d, d2h = timed(max(1, min(args.steps, 3)), e2e=True)
     e2e_ms = allreduce_max(float(np.mean(e2e_times)), world)
     if rank != 0:
         return None
     # work counts of the same walks (identical seed -> identical walks), untimed
-    p2 = mcs.default_params(walks_per_row=W, prec=args.prec, domain=1, killing_walks=64 * W, seed=rank,
-                            timing=1, count_work=1)
     mesh = mcs.Mesh(V_d, F_d)
-    rows = mcs.vertex_rows(mesh)
-    cres = mcs.estimate_dtn(mesh, rows, p2, workspace=ws)
-    cst = cres["stats"]
+    rows = make_rows(mesh)
+    cst = mcs.estimate_dtn(mesh, rows, mcs.default_params(timing=1, count_work=1, **pkw), workspace=ws)["stats"]
     walk_ms = float(np.mean([s["phase_ms"][1] for s in stats]))
-    ops = OPS_PER_NODE * cst["nodes_visited"] + OPS_PER_TRI * cst["tris_tested"]
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    sm_max = peaks.get("sm_max_mhz", 2032.0)
-    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x clock, T op/s
-    achieved = ops / (walk_ms / 1e3) / 1e12
     phase = np.mean([s["phase_ms"] for s in stats], axis=0).tolist()
+    walks = n_rows * W + kill
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"f{args.prec}", "data": "synthetic",
         "config": dict(workload_config(args), parallelism=f"replicas{world}"),
-        "rows_per_s": R * world / (ms_max / 1e3),
-        "walks_per_s": (R * W + 64 * W) * world / (ms_max / 1e3),
+        "rows_per_s": n_rows * world / (ms_max / 1e3),
+        "walks_per_s": walks * world / (ms_max / 1e3),
         "closest_point_queries_per_s": value,
         "walk_steps_per_step": steps_total,
-        "phase_ms": {"bvh_build_and_vertex_rows": float(np.mean([s["build_ms"] for s in stats])),
-                     "rows_and_tangent_balls": phase[0], "walks": phase[1], "histogram": phase[2],
+        "capped_walks_per_step": float(np.mean([s["capped"] + s["killing_capped"] for s in stats])),
+        "discarded_rows": stats[-1]["discarded_rows"],
+        "phase_ms": {"bvh_build_and_rows": float(np.mean([s["build_ms"] for s in stats])),
+                     "row_setup_and_tangent_balls": phase[0], "walks": phase[1], "histogram": phase[2],
                      "assembly": phase[3], "steklov_modes": float(np.mean([s["eig_ms"] for s in stats]))},
         "steklov": stats[-1].get("eig"),
         "e2e": {"value": steps_total * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-        "gpu_launches": GPU_LAUNCHES_PER_STEP * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                     "frac": achieved / alu_peak, "traffic": None, "kernel": "k_walks (FP32, exterior)",
-                     "ops_per_node": OPS_PER_NODE, "ops_per_tri": OPS_PER_TRI,
-                     "nodes_per_query": cst["nodes_visited"] / max(1, cst["steps"] + cst["killing_steps"]),
-                     "tris_per_query": cst["tris_tested"] / max(1, cst["steps"] + cst["killing_steps"]),
-                     "peak_note": "148 SMs x 128 FP32 lanes x max SM clock (derived)"},
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "library kernels counted by the library (mcs_launch_count); CUB sort kernels excluded",
+        "roofline": _alu_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})"),
         "clocks": clocks,
     }
     if not args.no_cpu:
@@ -242,9 +288,220 @@ def run_ours(args, rank, world):
     return line
 
 
-# own kernels launched per step (BVH build 10, vertex rows 1, exterior
-# estimate with automatic origin and killing 14); CUB sort kernels not counted
-GPU_LAUNCHES_PER_STEP = 25
+def _batch_setup(args, dev, rank):
+    """Meshes, BVHs and sample rows of the batch workload (preprocessing)."""
+    import torch
+    import meshgen
+    import paper_2606_05581_b300 as mcs
+    t0 = time.time()
+    hosts = meshgen.batch_meshes(args.meshes, 1000)
+    t_gen = time.time() - t0
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    items = []
+    rows_ws = mcs.Workspace()
+    for i, h in enumerate(hosts):
+        mesh = mcs.Mesh(h.V, h.F)
+        rows = mcs.sample_rows(mesh, 1024, orient=True, workspace=rows_ws)
+        rows = {k: v for k, v in rows.items() if k in ("pos", "nrm", "area", "tri2bin")}
+        items.append(dict(mesh=mesh, rows=rows, domain=i % 2, seed=i + 1_000_000 * rank))
+    e1.record()
+    e1.synchronize()
+    return hosts, items, t_gen, e0.elapsed_time(e1)
+
+
+def run_batch(args, rank, world):
+    import torch
+    import paper_2606_05581_b300 as mcs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    W = args.walks or 512
+    hosts, items, t_gen, prep_ms = _batch_setup(args, dev, rank)
+    params = mcs.default_params(walks_per_row=W, prec=args.prec, killing_walks=64 * W)
+    b = mcs.Batch(items, params, assemble=True)
+    t0 = time.time()
+    tuned, trials = b.autotune(sample_fraction=1.0 / 64)
+    tune_s = time.time() - t0
+    t0 = time.time()
+    nodes = b.capture()
+    capture_s = time.time() - t0
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.launch()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = ClockSampler(dev.index) if rank == 0 else None
+    if clk:
+        clk.start()
+    l0 = mcs.launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        b.launch()
+        s1.record(stream)
+        s1.synchronize()
+        times.append(s0.elapsed_time(s1))
+    launches = mcs.launch_count() - l0
+    barrier(world)
+    clocks = clk.stop() if clk else None
+    status, tot, per = b.graph_stats()
+    ms_max = allreduce_max(float(np.mean(times)), world)
+    steps = tot["steps"] + tot["killing_steps"]
+    value = steps * world / (ms_max / 1e3)
+    n_rows = sum(int(it["rows"]["pos"].shape[0]) for it in items)
+    walks = tot["walks"] + sum(64 * W for it in items if it["domain"] == 1)
+    e2e = _batch_e2e(args, hosts, tuned, stream)
+    if rank != 0:
+        return None
+    # the walk kernel alone, event-timed, for the roofline (plain enqueue with phase timing)
+    tp = mcs.default_params(**{f: getattr(tuned, f) for f, _ in mcs.Params._fields_
+                               if f not in ("origin", "domain", "seed", "origin_auto")})
+    tp.timing = 1
+    _, tst, _ = b.run(tp)
+    tp.count_work = 1
+    _, cst, _ = b.run(tp)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"f{args.prec}", "data": "synthetic",
+        "config": dict(workload_config(args), parallelism=f"replicas{world}",
+                       total_faces=int(sum(h.nf for h in hosts))),
+        "rows_per_s": n_rows * world / (ms_max / 1e3),
+        "walks_per_s": walks * world / (ms_max / 1e3),
+        "walk_steps_per_step": steps, "capped_walks_per_step": tot["capped"] + tot["killing_capped"],
+        "discarded_rows": tot["discarded_rows"], "status": status,
+        "phase_ms": {"mesh_generation_host": t_gen * 1e3, "bvh_builds_and_sample_rows": prep_ms,
+                     "setup_and_tangent_balls": tst["phase_ms"][0], "walks": tst["phase_ms"][1],
+                     "histogram_and_assembly": tst["phase_ms"][2]},
+        "autotune": {"seconds": tune_s, "chosen": {"threads_per_block": tuned.threads_per_block,
+                                                   "blocks_per_sm": tuned.blocks_per_sm,
+                                                   "queue_order": tuned.queue_order}, "trials": trials},
+        "graph": {"nodes": nodes, "capture_and_instantiate_s": capture_s},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "library kernels per graph replay x steps (mcs_launch_count); CUB kernels excluded",
+        "roofline": _alu_roofline(cst, tst["phase_ms"][1], f"k_walks (FP{args.prec}, mixed batch)"),
+        "clocks": clocks,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args, samples=1, hosts=hosts)[0]
+    return line
+
+
+def _batch_e2e(args, hosts, params, stream):
+    """The batch end to end through the public API: every mesh's V, F copied
+    in from pinned host memory, BVH builds, sample rows, the batched estimate
+    (plain enqueue: a new mesh set means new device pointers), and every
+    mesh's Lambda copied out; timed on the stream."""
+    import torch
+    import paper_2606_05581_b300 as mcs
+    VF = [(torch.from_numpy(h.V).pin_memory(), torch.from_numpy(h.F).pin_memory()) for h in hosts]
+    rows_ws = mcs.Workspace()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    h2d = d2h = 0
+    items = []
+    for i, (V, F) in enumerate(VF):
+        mesh = mcs.Mesh(V.to("cuda", non_blocking=True), F.to("cuda", non_blocking=True))
+        h2d += V.numel() * 8 + F.numel() * 4
+        rows = mcs.sample_rows(mesh, 1024, orient=True, workspace=rows_ws)
+        items.append(dict(mesh=mesh, rows=rows, domain=i % 2, seed=i))
+    b = mcs.Batch(items, params, assemble=True)
+    _, tot, _ = b.run()
+    outs = []
+    for o in b.outputs:
+        hL = torch.empty(o["Lambda"].shape, dtype=torch.float64, pin_memory=True)
+        hL.copy_(o["Lambda"], non_blocking=True)
+        d2h += hL.numel() * 8
+        outs.append(hL)
+    s1.record(stream)
+    s1.synchronize()
+    ms = s0.elapsed_time(s1)
+    return {"value": (tot["steps"] + tot["killing_steps"]) / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+
+
+def run_precision(args, rank, world):
+    """FP32 vs FP64 walks on the same Philox counters: per-eigenvalue error
+    against an FP64 reference estimate with many more walks."""
+    import torch
+    import paper_2606_05581_b300 as mcs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    m = make_mesh(args)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    k = 128
+    ws, eig_ws = mcs.Workspace(), mcs.Workspace()
+
+    def spectrum(prec, W, seed):
+        p = mcs.default_params(walks_per_row=W, prec=prec, domain=1, killing_walks=64 * W, seed=seed, timing=1)
+        res = mcs.estimate_dtn(mesh, rows, p, workspace=ws)
+        ev, _, est = mcs.steklov_modes(res["Lambda"], rows["area"], k, vectors=False, workspace=eig_ws)
+        st = res["stats"]
+        return ev.cpu().numpy(), st["phase_ms"][1], st["steps"] + st["killing_steps"], est
+
+    Wref = args.ref_walks
+    t0 = time.time()
+    ref, ref_ms, _, ref_eig = spectrum(64, Wref, 999)
+    ref_s = time.time() - t0
+    table = []
+    for W in (1024, 4096, 16384):
+        for prec in (32, 64):
+            evs, ms, steps = [], [], []
+            for seed in range(args.seeds):
+                ev, wms, st, _ = spectrum(prec, W, seed)
+                evs.append(ev)
+                ms.append(wms)
+                steps.append(st)
+            evs = np.array(evs)
+            rel = np.abs(evs - ref[None, :]) / np.abs(ref[None, :])
+            se = evs.std(axis=0, ddof=1) / np.abs(ref) if args.seeds > 1 else np.zeros(k)
+            table.append({"prec": prec, "walks_per_row": W, "seeds": args.seeds,
+                          "mean_rel_err": float(rel.mean()), "median_rel_err": float(np.median(rel)),
+                          "max_rel_err": float(rel.max()),
+                          "rel_err_first16": rel.mean(axis=0)[:16].tolist(),
+                          "rel_se_single_run_mean": float(se.mean()),
+                          "walk_ms": float(np.mean(ms)), "walk_steps": float(np.mean(steps)),
+                          "walk_steps_per_s": float(np.mean(steps) / (np.mean(ms) / 1e3)),
+                          "fp32_fp64_spectrum_rel_diff": None})
+    # FP32 vs FP64 on identical counters: how far apart the two spectra are
+    for W in (1024, 4096, 16384):
+        e32 = spectrum(32, W, 0)[0]
+        e64 = spectrum(64, W, 0)[0]
+        for row in table:
+            if row["walks_per_row"] == W:
+                row["fp32_fp64_spectrum_rel_diff"] = float(np.max(np.abs(e32 - e64) / np.abs(e64)))
+    # equal error: W each precision needs for the FP32 error at W = 16384, by err ~ c / sqrt(W)
+    def need(prec, target):
+        rows_ = [r for r in table if r["prec"] == prec]
+        c = np.mean([r["mean_rel_err"] * math.sqrt(r["walks_per_row"]) for r in rows_])
+        return (c / target) ** 2, np.mean([r["walk_steps_per_s"] for r in rows_]), \
+            np.mean([r["walk_steps"] / r["walks_per_row"] for r in rows_])
+    target = [r for r in table if r["prec"] == 32 and r["walks_per_row"] == 16384][0]["mean_rel_err"]
+    w32, sps32, spw32 = need(32, target)
+    w64, sps64, spw64 = need(64, target)
+    t32 = w32 * spw32 / sps32
+    t64 = w64 * spw64 / sps64
+    fp32_best = max(r["walk_steps_per_s"] for r in table if r["prec"] == 32)
+    return {"metric": METRIC, "value": fp32_best, "unit": UNIT, "n_gpus": 1, "steps": None, "warmup": None,
+            "higher_is_better": True, "dtype": "f32 vs f64", "data": "synthetic",
+            "config": dict(workload="precision", mesh="two icospheres s4, R=0.5, centres 1.5 apart",
+                           domain="exterior", killing_walks="64 W", steklov_k=k, reference=f"FP64, W={Wref}",
+                           seeds=args.seeds),
+            "reference": {"walks_per_row": Wref, "walk_ms": ref_ms, "seconds": ref_s, "eig": ref_eig,
+                          "first8": ref[:8].tolist()},
+            "table": table,
+            "equal_error": {"target_mean_rel_err": target, "fp32_walks_per_row": w32, "fp64_walks_per_row": w64,
+                            "fp32_walk_seconds": t32, "fp64_walk_seconds": t64, "fp64_over_fp32_time": t64 / t32}}
 
 
 def barrier(world):
@@ -264,29 +521,73 @@ def allreduce_max(x, world):
 
 
 # ---------------------------------------------------------------- the oracle as baseline
-def cpu_baseline(args, samples=1):
-    """Oracle (plain C, brute force) on a bounded sample of the workload: a set of
-    rows of the same exterior estimate, W walks each, in the same precision."""
+def cpu_baseline(args, samples=1, hosts=None):
+    """Oracle (plain C, brute-force closest point over all triangles) on a
+    bounded sample of the workload, in the same precision."""
     from oracle import oracle as O
-    m = make_mesh()
-    rows = O.vertex_rows(m.V, m.F)
     nthr = O.num_threads()
-    origin = np.zeros(3)  # the inversion centre the estimate uses (sphere A's tangent-ball centre)
+    rng = np.random.default_rng(0)
+    out = []
+    if args.workload == "batch":
+        import meshgen
+        hosts = hosts or meshgen.batch_meshes(4, 1000)
+        W = args.walks or 512
+        for s in range(samples):
+            steps = 0
+            dt = 0.0
+            for i in range(2):  # mesh 0 (interior) and mesh 1 (exterior)
+                h = hosts[i]
+                rows = O.fps_rows(h.V, h.F, 1024, orient=True)
+                rl = np.sort(rng.choice(1024, max(2, nthr // 2), replace=False)).astype(np.int32)
+                origin = O.interior_origin(h.V, h.F, rows) if i % 2 else None
+                t0 = time.time()
+                est = O.estimate(h.V, h.F, rows, W // 8, 1e-3, exterior=bool(i % 2), origin=origin, seed=i,
+                                 prec=args.prec, row_list=rl)
+                dt += time.time() - t0
+                steps += int(est["steps"].sum())
+            out.append({"value": steps / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                        "sample": f"meshes 0 (interior, {hosts[0].nf} faces) and 1 (exterior, {hosts[1].nf} "
+                                  f"faces): {max(2, nthr // 2)} sample rows x {W // 8} walks each "
+                                  f"(fp{args.prec}); {steps} walk steps in {dt:.1f} s"})
+        return out
+    m = make_mesh(args)
+    if args.workload == "wild_2m":
+        # rows at random face centroids with their face normals (the oracle's
+        # farthest-point sampling over 2M faces alone takes minutes); every
+        # face mapped to row 0 -- the walks and their queries are the same work
+        n = max(2, nthr)
+        f = rng.choice(m.nf, n, replace=False)
+        a, b_, c = m.V[m.F[f, 0]], m.V[m.F[f, 1]], m.V[m.F[f, 2]]
+        nrm = np.cross(b_ - a, c - a)
+        area = 0.5 * np.linalg.norm(nrm, axis=1)
+        rows = dict(pos=(a + b_ + c) / 3.0, nrm=nrm / (2.0 * area[:, None]), area=area,
+                    tri2bin=np.zeros(m.nf, np.int32))
+        W = 4
+        for s in range(samples):
+            t0 = time.time()
+            est = O.estimate(m.V, m.F, rows, W, 1e-3, exterior=False, seed=s, prec=args.prec)
+            dt = time.time() - t0
+            steps = int(est["steps"].sum())
+            out.append({"value": steps / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                        "sample": f"{n} rows at random face centroids x {W} walks, interior, fp{args.prec}, "
+                                  f"brute-force closest point over {m.nf} triangles; {steps} walk steps in "
+                                  f"{dt:.1f} s"})
+        return out
+    rows = O.vertex_rows(m.V, m.F)
+    W = args.walks or 1024
     t0 = time.time()
     origin = O.interior_origin(m.V, m.F, rows)
     t_origin = time.time() - t0
     nrows = max(2, nthr)
-    rng = np.random.default_rng(0)
-    out = []
     for s in range(samples):
         rl = np.sort(rng.choice(m.nv, nrows, replace=False)).astype(np.int32)
         t0 = time.time()
-        est = O.estimate(m.V, m.F, rows, args.walks, 1e-3, exterior=True, origin=origin, seed=0, prec=args.prec,
+        est = O.estimate(m.V, m.F, rows, W, 1e-3, exterior=True, origin=origin, seed=0, prec=args.prec,
                          row_list=rl)
         dt = time.time() - t0
         steps = int(est["steps"].sum())
         out.append({"value": steps / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
-                    "sample": f"{nrows} rows x {args.walks} walks of the same exterior estimate "
+                    "sample": f"{nrows} rows x {W} walks of the same exterior estimate "
                               f"(fp{args.prec}, brute-force closest point over {m.nf} triangles); "
                               f"{steps} walk steps in {dt:.1f} s (+{t_origin:.1f} s interior pass for the origin)",
                     "rows_per_s": nrows / dt})
@@ -313,7 +614,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--walks", type=int, default=1024)
+    ap.add_argument("--workload", default="two_spheres_s4_exterior", choices=WORKLOADS)
+    ap.add_argument("--walks", type=int, default=0, help="walks per row (0: the workload's)")
+    ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
+    ap.add_argument("--seeds", type=int, default=4, help="precision workload: seeds per configuration")
+    ap.add_argument("--ref-walks", type=int, default=65536, help="precision workload: reference walks per row")
     ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -325,7 +630,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    line = run_ours(args, rank, world) if args.impl == "ours" else run_reference(args, rank, world)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    elif args.workload == "batch":
+        line = run_batch(args, rank, world)
+    elif args.workload == "precision":
+        line = run_precision(args, rank, world) if rank == 0 else None
+    else:
+        line = run_ours(args, rank, world)
     if line is not None:
         print(json.dumps(line))
     if world > 1 and args.impl == "ours":

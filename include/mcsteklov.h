@@ -81,6 +81,9 @@ typedef struct {
     int threads_per_block;  /* walk-kernel block size; 0 = library default      */
     int timing;             /* 1: time the phases with CUDA events (stats.phase_ms) */
     int count_work;         /* 1: count BVH nodes and triangles visited (slower; stats) */
+    int queue_order;        /* walk queue schedule, bit 0: rows in the caller's order instead of
+                               Z-order; bit 1 (batches): meshes by descending walk count.
+                               Results do not depend on it (counter-based walks). */
 } mcs_params;
 
 /* Rows of the estimate.  Vertex rows: n_rows = nv, tri2bin = NULL, a walk's
@@ -123,6 +126,10 @@ typedef struct {
 
 const char *mcs_last_error(void);
 const char *mcs_version(void);
+/* Instrumentation: kernels of this library enqueued on any stream since it
+ * was loaded (a graph replay counts its captured library kernels; kernels
+ * of the CUB sorts the library calls are not counted). */
+unsigned long long mcs_launch_count(void);
 void mcs_default_params(mcs_params *p);
 
 /* Build the mesh: copies V (nv x 3 FP64) and F (nf x 3 int32, 0-based), in
@@ -186,6 +193,72 @@ size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, lo
  * Returns MCS_WARN_CAPPED when stats are requested and some walk was capped. */
 mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
                             void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many meshes of uneven size and row count in one persistent walk launch
+ * (the paper estimates one shape at a time; its large-scale preprocessing
+ * runs shapes one after another, Sec. 6).  Each mesh gets its row setup and
+ * tangent balls; then ONE walk launch serves all meshes' walks from one
+ * global queue (meshes in table order, each mesh's row walks in its row
+ * order, then its killing walks); then each mesh's histogram and assembly.
+ * A mesh's results are bit-identical to mcs_estimate_dtn on that mesh with
+ * the same parameters, domain and seed.  The shared parameters (eps, W,
+ * precision, killing_walks, launch shape...) come from one mcs_params; its
+ * domain, origin and seed fields are ignored in favour of the item's. */
+typedef struct {
+    mcs_mesh mesh;
+    mcs_rows rows;
+    int domain;             /* MCS_INTERIOR or MCS_EXTERIOR                     */
+    int origin_auto;        /* exterior: 1 = automatic inversion centre         */
+    double origin[3];       /* exterior centre when origin_auto == 0            */
+    uint64_t seed;          /* Philox key of this mesh's walks                  */
+    mcs_outputs out;        /* as for mcs_estimate_dtn (device, caller-owned)   */
+} mcs_batch_item;
+
+/* Workspace bytes of a batch (device, 256-byte aligned). */
+size_t mcs_estimate_batched_workspace_size(const mcs_batch_item *items, int n, int walks_per_row);
+/* Enqueues the batch on `stream`.  total (host, optional): the launch's
+ * counters summed over meshes; per_item (host, optional, n entries): each
+ * mesh's counters and status fields.  When either is given the call
+ * synchronises `stream` and returns the worst status over the meshes
+ * (errors before warnings).  A traversal error is reported to the mesh it
+ * met and to the later meshes served by the same lane. */
+mcs_status mcs_estimate_batched(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                                size_t workspace_bytes, mcs_stats *total, mcs_stats *per_item, void *stream);
+
+/* The batch captured once into a CUDA graph (on a private stream, thread-
+ * local capture mode) and instantiated: mcs_graph_launch replays every
+ * kernel of mcs_estimate_batched with one host call.  The graph holds the
+ * device pointers of the items, outputs and workspace given here: they must
+ * stay valid, and the inputs may change in place between launches (not the
+ * sizes).  mcs_graph_stats synchronises `stream` and reads the counters of
+ * the last finished launch.  A graph may not be launched concurrently with
+ * itself or with another call that uses the same workspace. */
+typedef struct mcs_graph_s *mcs_graph;
+mcs_status mcs_graph_create(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                            size_t workspace_bytes, mcs_graph *out);
+mcs_status mcs_graph_launch(mcs_graph g, void *stream);
+mcs_status mcs_graph_stats(mcs_graph g, mcs_stats *total, mcs_stats *per_item, void *stream);
+size_t mcs_graph_nodes(mcs_graph g);
+void mcs_graph_destroy(mcs_graph g);
+
+/* Autotuner of the walk launch.  Runs the batch's row setup, then times the
+ * walk kernel on a sample (the first ceil(sample_fraction * n_rows) rows of
+ * every mesh, no killing walks) for candidate block sizes (64, 128 threads),
+ * resident blocks per SM (the three largest residencies the kernel allows)
+ * and queue orders (row order, mesh order), by coordinate search; the best
+ * two-run minimum wins.  tuned (host) = p with threads_per_block,
+ * blocks_per_sm and queue_order set.  trials (host, optional) receives up to
+ * max_trials entries, n_trials their count.  Synchronises `stream`.  The
+ * workspace and outputs are those of the batch; their contents are left
+ * undefined (the estimate rewrites them). */
+typedef struct {
+    int threads_per_block, blocks_per_sm, queue_order;
+    float ms;               /* walk-kernel time of the sample (best of 2)       */
+} mcs_tune_trial;
+mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                              size_t workspace_bytes, double sample_fraction, mcs_params *tuned,
+                              mcs_tune_trial *trials, int max_trials, int *n_trials, void *stream);
 
 /* Allocation-free estimate.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need an

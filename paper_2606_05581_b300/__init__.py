@@ -16,7 +16,8 @@ import torch
 from . import build as _build
 
 __all__ = ["lib", "Mesh", "default_params", "vertex_rows", "closest_points", "philox_words", "estimate_dtn",
-           "workspace_size", "steklov_modes", "tc_symm_product", "MCSError"]
+           "workspace_size", "steklov_modes", "tc_symm_product", "MCSError", "Batch", "sample_rows",
+           "estimate_dtn_noalloc", "dense_hist"]
 
 _LIB_PATH = _build.LIB
 
@@ -32,7 +33,8 @@ class Params(C.Structure):
                 ("max_steps", C.c_int), ("rho_min_factor", C.c_double), ("prec", C.c_int), ("domain", C.c_int),
                 ("origin_auto", C.c_int), ("origin", C.c_double * 3), ("killing_walks", C.c_longlong),
                 ("seed", C.c_uint64), ("walks_per_row", C.c_int), ("blocks_per_sm", C.c_int),
-                ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int)]
+                ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int),
+                ("queue_order", C.c_int)]
 
 
 class Rows(C.Structure):
@@ -51,6 +53,16 @@ class Stats(C.Structure):
                 ("killing_capped", C.c_longlong), ("origin", C.c_double * 3), ("rmax", C.c_double),
                 ("device_error", C.c_int), ("phase_ms", C.c_float * 4), ("nodes_visited", C.c_longlong),
                 ("tris_tested", C.c_longlong)]
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("rows", Rows), ("domain", C.c_int), ("origin_auto", C.c_int),
+                ("origin", C.c_double * 3), ("seed", C.c_uint64), ("out", Outputs)]
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("queue_order", C.c_int),
+                ("ms", C.c_float)]
 
 
 class EigParams(C.Structure):
@@ -75,6 +87,7 @@ def lib():
         vp, i32, i64, u64, u32, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_uint64, C.c_uint32, C.c_double
         L.mcs_last_error.restype = C.c_char_p
         L.mcs_version.restype = C.c_char_p
+        L.mcs_launch_count.restype = C.c_ulonglong
         L.mcs_default_params.argtypes = [C.POINTER(Params)]
         L.mcs_build_bvh.argtypes = [vp, i32, vp, i32, vp, C.POINTER(vp)]
         L.mcs_mesh_destroy.argtypes = [vp]
@@ -93,6 +106,18 @@ def lib():
         L.mcs_estimate_dtn_noalloc_capacity.restype = C.c_size_t
         L.mcs_estimate_dtn_noalloc.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs),
                                                C.POINTER(Stats), vp]
+        L.mcs_estimate_batched_workspace_size.argtypes = [C.POINTER(BatchItem), i32, i32]
+        L.mcs_estimate_batched_workspace_size.restype = C.c_size_t
+        L.mcs_estimate_batched.argtypes = [C.POINTER(BatchItem), i32, C.POINTER(Params), vp, C.c_size_t,
+                                           C.POINTER(Stats), C.POINTER(Stats), vp]
+        L.mcs_graph_create.argtypes = [C.POINTER(BatchItem), i32, C.POINTER(Params), vp, C.c_size_t, C.POINTER(vp)]
+        L.mcs_graph_launch.argtypes = [vp, vp]
+        L.mcs_graph_stats.argtypes = [vp, C.POINTER(Stats), C.POINTER(Stats), vp]
+        L.mcs_graph_nodes.argtypes = [vp]
+        L.mcs_graph_nodes.restype = C.c_size_t
+        L.mcs_graph_destroy.argtypes = [vp]
+        L.mcs_autotune_walks.argtypes = [C.POINTER(BatchItem), i32, C.POINTER(Params), vp, C.c_size_t, dbl,
+                                         C.POINTER(Params), C.POINTER(TuneTrial), i32, C.POINTER(i32), vp]
         L.mcs_default_eig_params.argtypes = [C.POINTER(EigParams)]
         L.mcs_steklov_workspace_size.argtypes = [i32, i32]
         L.mcs_steklov_workspace_size.restype = C.c_size_t
@@ -103,6 +128,11 @@ def lib():
         L.mcs_tc_symm_product.argtypes = [vp, vp, i32, i32, vp, vp, C.c_size_t, vp]
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Library kernels enqueued since load (instrumentation)."""
+    return int(lib().mcs_launch_count())
 
 
 def _check(status):
@@ -221,27 +251,44 @@ def _aligned_ptr(buf: torch.Tensor) -> int:
     return (p + 255) & ~255
 
 
+_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")
+
+
+def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool) -> dict:
+    cap = min(W, R)
+    return dict(hist_bin=torch.empty(R * cap, dtype=torch.int32, device=dev),
+                hist_cnt=torch.empty(R * cap, dtype=torch.int32, device=dev),
+                hist_nnz=torch.empty(R, dtype=torch.int32, device=dev),
+                omega=torch.empty(R, dtype=torch.float64, device=dev),
+                H0=torch.empty(R, dtype=torch.int32, device=dev),
+                Lambda=torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None,
+                exit_tri=torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None)
+
+
+def _rows_struct(rows: dict) -> Rows:
+    t2b = rows.get("tri2bin")
+    return Rows(int(rows["pos"].shape[0]), rows["pos"].data_ptr(), rows["nrm"].data_ptr(), rows["area"].data_ptr(),
+                None if t2b is None else t2b.data_ptr())
+
+
+def _outputs_struct(o: dict) -> Outputs:
+    return Outputs(*[None if o.get(k) is None else o[k].data_ptr() for k in _OUT_KEYS])
+
+
+def _stats_dict(st: Stats) -> dict:
+    return {k: (list(getattr(st, k)) if k in ("origin", "phase_ms") else getattr(st, k)) for k, _ in Stats._fields_}
+
+
 def estimate_dtn(mesh: Mesh, rows: dict, params: Params, assemble: bool = True, want_stats: bool = True,
                  record_exits: bool = False, workspace: Workspace | None = None, outputs: dict | None = None):
     """Run the DtN estimator; returns a dict of device tensors (+ stats)."""
-    pos, nrm, area = rows["pos"], rows["nrm"], rows["area"]
-    t2b = rows.get("tri2bin")
+    pos = rows["pos"]
     R = int(pos.shape[0])
     W = int(params.walks_per_row)
     cap = min(W, R)
-    dev = pos.device
-    o = outputs or {}
-    if not o:
-        o["hist_bin"] = torch.empty(R * cap, dtype=torch.int32, device=dev)
-        o["hist_cnt"] = torch.empty(R * cap, dtype=torch.int32, device=dev)
-        o["hist_nnz"] = torch.empty(R, dtype=torch.int32, device=dev)
-        o["omega"] = torch.empty(R, dtype=torch.float64, device=dev)
-        o["H0"] = torch.empty(R, dtype=torch.int32, device=dev)
-        o["Lambda"] = torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None
-        o["exit_tri"] = torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None
-    rs = Rows(R, pos.data_ptr(), nrm.data_ptr(), area.data_ptr(), None if t2b is None else t2b.data_ptr())
-    out = Outputs(*[None if o.get(k) is None else o[k].data_ptr()
-                    for k in ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")])
+    o = outputs or _alloc_outputs(R, W, pos.device, assemble, record_exits)
+    rs = _rows_struct(rows)
+    out = _outputs_struct(o)
     nbytes = workspace_size(mesh, R, W, params.killing_walks)
     ws = (workspace or Workspace()).get(nbytes)
     st = Stats()
@@ -254,9 +301,130 @@ def estimate_dtn(mesh: Mesh, rows: dict, params: Params, assemble: bool = True, 
     res["status"] = status
     res["_ws"] = ws
     if want_stats:
-        res["stats"] = {k: (list(getattr(st, k)) if k in ("origin", "phase_ms") else getattr(st, k))
-                        for k, _ in Stats._fields_}
+        res["stats"] = _stats_dict(st)
     return res
+
+
+class Batch:
+    """Many meshes in one persistent walk launch (mcs_estimate_batched).
+
+    ``items``: list of dicts with keys mesh (Mesh), rows (dict of device
+    tensors as for estimate_dtn), domain (0 interior, 1 exterior), seed and
+    optionally origin (exterior inversion centre; automatic otherwise).
+    Outputs are allocated per mesh (``self.outputs[i]``) unless given."""
+
+    def __init__(self, items: list, params: Params, assemble: bool = True, record_exits: bool = False,
+                 outputs: list | None = None):
+        self.params = params
+        self.items = items
+        W = int(params.walks_per_row)
+        self.outputs = outputs or [_alloc_outputs(int(it["rows"]["pos"].shape[0]), W, it["rows"]["pos"].device,
+                                                  assemble, record_exits) for it in items]
+        arr = (BatchItem * len(items))()
+        for i, it in enumerate(items):
+            b = arr[i]
+            b.mesh = it["mesh"].handle
+            b.rows = _rows_struct(it["rows"])
+            b.domain = int(it.get("domain", 0))
+            org = it.get("origin")
+            b.origin_auto = 1 if org is None else 0
+            if org is not None:
+                for k in range(3):
+                    b.origin[k] = float(org[k])
+            b.seed = int(it.get("seed", 0))
+            b.out = _outputs_struct(self.outputs[i])
+        self._arr = arr
+        self.nbytes = int(lib().mcs_estimate_batched_workspace_size(arr, len(items), W))
+        self._ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        self.ws_ptr = C.c_void_p(_aligned_ptr(self._ws))
+        self.graph = None
+
+    def __len__(self):
+        return len(self.items)
+
+    def run(self, params: Params | None = None, want_stats: bool = True, check: bool = True):
+        """Enqueue the batch; returns (status, total stats, per-mesh stats) when
+        want_stats (check=False: an error status is returned, not raised)."""
+        p = params or self.params
+        n = len(self.items)
+        tot = Stats()
+        per = (Stats * n)()
+        status = lib().mcs_estimate_batched(self._arr, n, C.byref(p), self.ws_ptr, self.nbytes,
+                                            C.byref(tot) if want_stats else None, per if want_stats else None,
+                                            _stream())
+        if check:
+            _check(status)
+        if not want_stats:
+            return status, None, None
+        t = _stats_dict(tot)
+        if status < 0:
+            t["error"] = lib().mcs_last_error().decode()
+        return status, t, [_stats_dict(per[i]) for i in range(n)]
+
+    def autotune(self, sample_fraction: float = 1.0 / 64, max_trials: int = 32):
+        """Time the walk launch on a sample for candidate launch shapes and queue orders;
+        sets and returns the tuned params and the trial list."""
+        n = len(self.items)
+        tuned = Params()
+        trials = (TuneTrial * max_trials)()
+        nt = C.c_int(0)
+        _check(lib().mcs_autotune_walks(self._arr, n, C.byref(self.params), self.ws_ptr, self.nbytes,
+                                        float(sample_fraction), C.byref(tuned), trials, max_trials, C.byref(nt),
+                                        _stream()))
+        self.params = tuned
+        self.close_graph()
+        out = [dict(threads_per_block=t.threads_per_block, blocks_per_sm=t.blocks_per_sm,
+                    queue_order=t.queue_order, ms=t.ms) for t in trials[:min(nt.value, max_trials)]]
+        return tuned, out
+
+    def capture(self):
+        """Capture the batch into a CUDA graph (mcs_graph_create)."""
+        self.close_graph()
+        h = C.c_void_p()
+        _check(lib().mcs_graph_create(self._arr, len(self.items), C.byref(self.params), self.ws_ptr, self.nbytes,
+                                      C.byref(h)))
+        self.graph = h
+        return int(lib().mcs_graph_nodes(h))
+
+    def launch(self):
+        if not self.graph:
+            self.capture()
+        _check(lib().mcs_graph_launch(self.graph, _stream()))
+
+    def graph_stats(self, check: bool = True):
+        """(status, total stats, per-mesh stats) of the last replay; check=False
+        returns an error status (and its message as 'error' in the totals)
+        instead of raising."""
+        n = len(self.items)
+        tot = Stats()
+        per = (Stats * n)()
+        status = lib().mcs_graph_stats(self.graph, C.byref(tot), per, _stream())
+        if check:
+            _check(status)
+        t = _stats_dict(tot)
+        if status < 0:
+            t["error"] = lib().mcs_last_error().decode()
+        return status, t, [_stats_dict(per[i]) for i in range(n)]
+
+    def close_graph(self):
+        if self.graph:
+            lib().mcs_graph_destroy(self.graph)
+            self.graph = None
+
+    def result(self, i: int) -> dict:
+        """Per-mesh outputs in the layout estimate_dtn returns."""
+        R = int(self.items[i]["rows"]["pos"].shape[0])
+        W = int(self.params.walks_per_row)
+        res = dict(self.outputs[i])
+        res["cap"] = min(W, R)
+        res["walks"] = W
+        return res
+
+    def __del__(self):
+        try:
+            self.close_graph()
+        except Exception:
+            pass
 
 
 def dense_hist(res: dict, R: int) -> torch.Tensor:
@@ -315,13 +483,9 @@ def estimate_dtn_noalloc(mesh: Mesh, rows: dict, params: Params, outputs: dict):
     """The estimate with the library's fixed device scratch (no allocation in
     the call); ``outputs`` holds caller-allocated device tensors named as in
     estimate_dtn.  Returns the stats dict."""
-    pos, nrm, area = rows["pos"], rows["nrm"], rows["area"]
-    t2b = rows.get("tri2bin")
-    R = int(pos.shape[0])
-    rs = Rows(R, pos.data_ptr(), nrm.data_ptr(), area.data_ptr(), None if t2b is None else t2b.data_ptr())
-    out = Outputs(*[None if outputs.get(k) is None else outputs[k].data_ptr()
-                    for k in ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")])
+    rs = _rows_struct(rows)
+    out = _outputs_struct(outputs)
     st = Stats()
     _check(lib().mcs_estimate_dtn_noalloc(mesh.handle, C.byref(rs), C.byref(params), C.byref(out), C.byref(st),
                                           _stream()))
-    return {k: (list(getattr(st, k)) if k in ("origin", "phase_ms") else getattr(st, k)) for k, _ in Stats._fields_}
+    return _stats_dict(st)

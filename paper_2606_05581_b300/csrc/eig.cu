@@ -672,6 +672,7 @@ static cudaError_t tc_product(Ctx &c, int b) {
     a.idesc = c.p.idesc;
     a.tmem_cols = c.p.tmem_cols;
     a.err = c.w.err;
+    note_launch();
     k_tc_gemm<<<dim3(c.p.n_pad / BM, c.p.splits), kTcThreads, c.p.smem, c.st>>>(c.mAh, c.mAl, c.mBh[b], c.mBl[b], a);
     return cudaGetLastError();
 }
@@ -728,8 +729,11 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     const size_t mv = (size_t)m * p.n_pad;
     const int g = grid_for(mv);
     MCS_CUDA(cudaMemsetAsync(c.w.err, 0, sizeof(int), st));
+    note_launch();
     k_prep_A<<<p.n_pad, 256, 0, st>>>(Lambda, mass, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.rowabs);
+    note_launch();
     k_max_reduce<<<1, 1024, 0, st>>>(c.w.rowabs, n, c.w.bound);
+    note_launch();
     k_random_block<<<g, 256, 0, st>>>(c.w.Xt, m, n, p.n_pad);
     double bound = 0.0;
     MCS_CUDA(cudaMemcpyAsync(&bound, c.w.bound, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -743,7 +747,9 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     const dim3 bgrid(p.n_pad / 128, (m + kJG - 1) / kJG);
     const size_t bsm = (size_t)m * kJG * sizeof(double);
     auto gram = [&](const double *A, const double *B, int sym) {
+        note_launch();
         k_gram_part<<<ggrid, 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp);
+        note_launch();
         k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym);
     };
     // orthonormalise X: shifted CholeskyQR, then CholeskyQR2 (FP64)
@@ -751,8 +757,11 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         const double shifts[3] = {11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16, 0.0, 0.0};
         for (int pass = shifted ? 0 : 1; pass < 3; pass++) {
             gram(X, X, 1);
+            note_launch();
             k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
+            note_launch();
             k_tri_inverse<<<(m + 7) / 8, 256, 0, st>>>(c.w.R, m, c.w.Rinv);
+            note_launch();
             k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T);
             std::swap(X, T);
         }
@@ -764,6 +773,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     int iters = 0, converged = 0, gemms = 0;
     for (iters = 0; iters < prm.max_iters; iters++) {
         // ---- Chebyshev filter of degree d on [a_cut, ub] applied to X
+        note_launch();
         k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[0], c.w.vl[0]);
         const double e = 0.5 * (ub - a_cut), cc = 0.5 * (ub + a_cut);
         double sigma = e / (a_low - cc);
@@ -777,12 +787,14 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
             const bool last = d == prm.degree;
             if (d == 1) {
                 const double alpha = sigma / e, beta = -cc * sigma / e;
+                note_launch();
                 k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, 0.0, c.w.vh[cur],
                                             c.w.vl[cur], nullptr, nullptr, last ? nullptr : c.w.vh[nxt],
                                             last ? nullptr : c.w.vl[nxt], last ? X : nullptr);
             } else {
                 const double sig_new = 1.0 / (tau - sigma);
                 const double alpha = 2.0 * sig_new / e, beta = -2.0 * sig_new * cc / e, gamma = -sigma * sig_new;
+                note_launch();
                 k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, alpha, beta, gamma, c.w.vh[cur],
                                             c.w.vl[cur], c.w.vh[prev], c.w.vl[prev], last ? nullptr : c.w.vh[nxt],
                                             last ? nullptr : c.w.vl[nxt], last ? X : nullptr);
@@ -793,18 +805,25 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         }
         MCS_CUDA(orth(false));
         // ---- Rayleigh-Ritz
+        note_launch();
         k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[3], c.w.vl[3]);
         MCS_CUDA(tc_product(c, 3));
         gemms++;
+        note_launch();
         k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr,
                                     nullptr, nullptr, Z);
         gram(X, Z, 1);
+        note_launch();
         k_jacobi<<<1, 512, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
+        note_launch();
         k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
+        note_launch();
         k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, X, m, p.n_pad, T);
         std::swap(X, T);
+        note_launch();
         k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, Z, m, p.n_pad, T);
         std::swap(Z, T);
+        note_launch();
         k_ritz<<<m, 256, 0, st>>>(X, Z, p.n_pad, c.w.theta, c.w.res);
         MCS_CUDA(cudaGetLastError());
         MCS_CUDA(cudaMemcpyAsync(theta.data(), c.w.theta, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -821,7 +840,10 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     int err = 0;
     MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaMemcpyAsync(evals, c.w.theta, k * sizeof(double), cudaMemcpyDefault, st));
-    if (evecs) k_output<<<grid_for((size_t)n * k), 256, 0, st>>>(X, mass, n, p.n_pad, k, evecs);
+    if (evecs) {
+        note_launch();
+        k_output<<<grid_for((size_t)n * k), 256, 0, st>>>(X, mass, n, p.n_pad, k, evecs);
+    }
     MCS_CUDA(cudaGetLastError());
     MCS_CUDA(cudaStreamSynchronize(st));
     if (stats) {
@@ -876,13 +898,16 @@ mcs_status mcs_tc_symm_product(const double *A, const double *Xt_in, int n, int 
     double *ones = c.w.rowabs;  // n doubles
     std::vector<double> h1(n, 1.0);
     MCS_CUDA(cudaMemcpyAsync(ones, h1.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    note_launch();
     k_prep_A<<<p.n_pad, 256, 0, st>>>(A, ones, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.Zt);
     const size_t mv = (size_t)p.m * p.n_pad;
     MCS_CUDA(cudaMemsetAsync(c.w.Xt, 0, mv * sizeof(double), st));
     MCS_CUDA(cudaMemcpy2DAsync(c.w.Xt, p.n_pad * sizeof(double), Xt_in, n * sizeof(double), n * sizeof(double), p.m,
                                cudaMemcpyDeviceToDevice, st));
+    note_launch();
     k_split<<<grid_for(mv), 256, 0, st>>>(c.w.Xt, mv, c.w.vh[0], c.w.vl[0]);
     MCS_CUDA(tc_product(c, 0));
+    note_launch();
     k_combine<<<grid_for(mv), 256, 0, st>>>(c.w.P, p.splits, p.m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr,
                                            nullptr, nullptr, nullptr, c.w.Zt);
     MCS_CUDA(cudaMemcpy2DAsync(Zt_out, n * sizeof(double), c.w.Zt, p.n_pad * sizeof(double), n * sizeof(double), p.m,

@@ -20,6 +20,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
 
 #include "mcs_internal.h"
 
@@ -312,7 +315,10 @@ __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const
 }
 
 // ---------------------------------------------------------------- walks
-struct WalkArgs {
+// One job = the walks of one mesh: its row walks (R x W, in Z-order row
+// position order) followed by its killing walks.  A launch serves a table of
+// jobs through one global queue; each lane looks its job up on refill.
+struct WalkJob {
     DevMesh m;
     const RowBall *ball;
     const int32_t *order;
@@ -320,19 +326,35 @@ struct WalkArgs {
     int32_t *exits;        // R x W, by sorted row position
     int32_t *exit_tri;     // optional, R x W by canonical row
     int32_t *H0;           // killing histogram
-    Ctrl *ctrl;
-    unsigned long long total;
+    Ctrl *ctrl;            // the mesh's control block (origin, Kelvin frame)
+    unsigned long long n_rows_walks;  // R * W
+    unsigned long long n_kill;        // killing walks after the row walks
     int R, W;
     uint32_t k0, k1;
+    int ext;
+    int pad;
+};
+
+struct MultiArgs {
+    const WalkJob *jobs;
+    const unsigned long long *offs;   // offs[j]: first queue index of job j; offs[n] = total
+    int n_jobs;
+    unsigned long long *queue;
+    Ctrl *stats;                      // counters of the whole launch (with one job: that job's block)
     double eps, iw0;
     float eps2f;
     int max_steps;
-    int killing;
+    WalkJob j0;                       // the job of a one-job launch (kernel parameter space)
 };
 
-__device__ __forceinline__ int exit_bin(const WalkArgs &a, int f, double b0, double b1, double b2) {
-    if (a.tri2bin) return a.tri2bin[f];
-    const int i0 = a.m.F[3 * f], i1 = a.m.F[3 * f + 1], i2 = a.m.F[3 * f + 2];
+template <bool MULTI> __device__ __forceinline__ const WalkJob &job_of(const MultiArgs &a, int i) {
+    if constexpr (MULTI) return a.jobs[i];
+    else return a.j0;
+}
+
+__device__ __forceinline__ int exit_bin(const WalkJob &J, int f, double b0, double b1, double b2) {
+    if (J.tri2bin) return J.tri2bin[f];
+    const int i0 = J.m.F[3 * f], i1 = J.m.F[3 * f + 1], i2 = J.m.F[3 * f + 2];
     int best = 0;
     double bm = b0;
     int im = i0;
@@ -362,42 +384,56 @@ __device__ void record_nohit(Ctrl *c, int kind, int killing, unsigned long long 
 template <typename T> struct WalkState {
     V3<T> x;
     unsigned long long g;   // walk id (Philox counter)
-    unsigned long long wi;  // queue index
+    unsigned long long li;  // index within the job
     int k;                  // next step number
     int prev;               // previous closest slot
     int v;                  // canonical row (-1: killing walk)
+    int job;
+    int kill;
+    uint32_t k1;            // Philox key word (killing walks use their own)
 };
 
-template <typename T, bool EXT, bool COUNT>
-__global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
+// MODE: 0 interior jobs only, 1 exterior jobs only, 2 both (the job decides)
+template <typename T, int MODE, bool COUNT, bool MULTI>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __grid_constant__ MultiArgs a) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
-    const uint32_t k0 = a.k0, k1 = a.killing ? (a.k1 ^ kKillKeyXor) : a.k1;
-    const double o64[3] = {EXT ? a.ctrl->origin[0] : 0.0, EXT ? a.ctrl->origin[1] : 0.0,
-                           EXT ? a.ctrl->origin[2] : 0.0};
-    const double r0max64 = EXT ? a.ctrl->rho0max : 0.0;
-    const T oT[3] = {(T)o64[0], (T)o64[1], (T)o64[2]};
-    const T r0maxT = (T)r0max64;
     const T epsT = sizeof(T) == 8 ? (T)a.eps : (T)a.eps2f;  // FP32: re-check below 2 eps
-    unsigned long long *queue = a.killing ? &a.ctrl->kqueue : &a.ctrl->queue;
     WalkState<T> s;
     s.x = V3<T>{(T)0, (T)0, (T)0};
-    s.g = 0; s.wi = 0; s.k = 1; s.prev = -1; s.v = -1;
+    s.g = 0; s.li = 0; s.k = 1; s.prev = -1; s.v = -1; s.job = 0; s.kill = 0; s.k1 = 0;
     bool active = false, more = true;
-    long long n_steps = 0, n_capped = 0, n_lost = 0;
+    // counters of the lane's current job since its last flush
+    long long n_steps = 0, n_ksteps = 0, n_capped = 0, n_kcapped = 0, n_lost = 0;
     int err = 0;
+    int cj = -1;
     Work work{0ull, 0ull};
+    const unsigned long long total = MULTI ? a.offs[a.n_jobs] : a.j0.n_rows_walks + a.j0.n_kill;
+    // with several jobs, a lane adds its counters to a job's block when it
+    // leaves that job; traversal errors are lane-cumulative, so a lane reports
+    // one to every job it served after meeting it
+    auto flush = [&]() {
+        if (cj < 0) return;
+        Ctrl *c = job_of<MULTI>(a, cj).ctrl;
+        if (n_steps) atomicAdd(&c->steps, (unsigned long long)n_steps);
+        if (n_ksteps) atomicAdd(&c->kill_steps, (unsigned long long)n_ksteps);
+        if (n_capped) atomicAdd(&c->capped, (unsigned long long)n_capped);
+        if (n_kcapped) atomicAdd(&c->kill_capped, (unsigned long long)n_kcapped);
+        if (n_lost) atomicAdd(&c->lost, (unsigned long long)n_lost);
+        if (err) atomicOr(&c->err, err);
+        n_steps = n_ksteps = n_capped = n_kcapped = n_lost = 0;
+    };
 
-    auto finish = [&](int bin, int f, bool capped, bool lost) {
-        n_capped += capped;
+    auto finish = [&](const WalkJob &J, int bin, int f, bool capped, bool lost) {
+        if (s.kill) n_kcapped += capped; else n_capped += capped;
         n_lost += lost;
-        if (bin >= a.R) { err |= kErrBin; bin = -1; }
-        if (a.killing) {
-            if (bin >= 0) atomicAdd(&a.H0[bin], 1);
+        if (bin >= J.R) { err |= kErrBin; bin = -1; }
+        if (s.kill) {
+            if (bin >= 0) atomicAdd(&J.H0[bin], 1);
         } else {
-            const int rp = (int)(s.wi / (unsigned long long)a.W), j = (int)(s.wi % (unsigned long long)a.W);
-            a.exits[(size_t)rp * a.W + j] = bin;
-            if (a.exit_tri) a.exit_tri[(size_t)s.v * a.W + j] = f;
+            const int rp = (int)(s.li / (unsigned long long)J.W), j = (int)(s.li % (unsigned long long)J.W);
+            J.exits[(size_t)rp * J.W + j] = bin;
+            if (J.exit_tri) J.exit_tri[(size_t)s.v * J.W + j] = f;
         }
         active = false;
     };
@@ -408,33 +444,52 @@ __global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
         if (nm) {
             const int leader = __ffs(nm) - 1;
             unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(queue, (unsigned long long)__popc(nm));
+            if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(nm));
             base = __shfl_sync(FULL, base, leader);
             if (need) {
                 const unsigned long long wi = base + __popc(nm & ((1u << lane) - 1u));
-                if (wi >= a.total) {
+                if (wi >= total) {
                     more = false;
-                } else if (a.killing) {
-                    s.wi = wi; s.g = wi; s.v = -1; s.k = 1; s.prev = -1;
-                    s.x = V3<T>{(T)0, (T)0, (T)0};
-                    active = true;
                 } else {
-                    const int rp = (int)(wi / (unsigned long long)a.W), j = (int)(wi % (unsigned long long)a.W);
-                    const int v = a.order[rp];
-                    const RowBall &b = a.ball[v];
-                    s.wi = wi;
-                    s.v = v;
-                    if (!b.valid) {
-                        a.exits[(size_t)rp * a.W + j] = -1;
-                        if (a.exit_tri) a.exit_tri[(size_t)v * a.W + j] = -1;
-                    } else {
-                        s.g = (unsigned long long)v * (unsigned long long)a.W + (unsigned long long)j;
-                        const unsigned long long gp = s.g - (unsigned long long)(j & 1);
-                        s.x = start_point<T>(k0, k1, gp, j & 1, (T)a.iw0, V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]},
-                                             (T)b.rho, V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]});
-                        s.k = 1;
-                        s.prev = -1;
+                    int lo = 0;
+                    if (MULTI) {
+                        int hi = a.n_jobs - 1;  // last job with offs <= wi
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (a.offs[mid] <= wi) lo = mid; else hi = mid - 1;
+                        }
+                    }
+                    const WalkJob &J = job_of<MULTI>(a, lo);
+                    if (MULTI && lo != cj) { flush(); cj = lo; }
+                    s.job = lo;
+                    s.li = MULTI ? wi - a.offs[lo] : wi;
+                    s.k = 1;
+                    s.prev = -1;
+                    if (s.li >= J.n_rows_walks) {
+                        s.kill = 1;
+                        s.k1 = J.k1 ^ kKillKeyXor;
+                        s.g = s.li - J.n_rows_walks;
+                        s.v = -1;
+                        s.x = V3<T>{(T)0, (T)0, (T)0};
                         active = true;
+                    } else {
+                        s.kill = 0;
+                        s.k1 = J.k1;
+                        const int rp = (int)(s.li / (unsigned long long)J.W), j = (int)(s.li % (unsigned long long)J.W);
+                        const int v = J.order[rp];
+                        const RowBall &b = J.ball[v];
+                        s.v = v;
+                        if (!b.valid) {
+                            J.exits[(size_t)rp * J.W + j] = -1;
+                            if (J.exit_tri) J.exit_tri[(size_t)v * J.W + j] = -1;
+                        } else {
+                            s.g = (unsigned long long)v * (unsigned long long)J.W + (unsigned long long)j;
+                            const unsigned long long gp = s.g - (unsigned long long)(j & 1);
+                            s.x = start_point<T>(J.k0, s.k1, gp, j & 1, (T)a.iw0,
+                                                 V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]}, (T)b.rho,
+                                                 V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]});
+                            active = true;
+                        }
                     }
                 }
             }
@@ -443,57 +498,61 @@ __global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
         if (!active) continue;
 
         // ---- one walk-on-spheres step
+        const WalkJob &J = job_of<MULTI>(a, s.job);
         T step;
-        if (!EXT) {
+        if (MODE == 0 || (MODE == 2 && !J.ext)) {
             Hit<T> h;
-            closest<T, COUNT>(a.m, s.x.x, s.x.y, s.x.z, s.prev, h, &err, &work);
-            n_steps++;
-            if (h.slot < 0 || h.id < 0 || h.id >= a.m.nf) {
+            closest<T, COUNT>(J.m, s.x.x, s.x.y, s.x.z, s.prev, h, &err, &work);
+            if (s.kill) n_ksteps++; else n_steps++;
+            if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
                 err |= kErrNoHit;
-                record_nohit(a.ctrl, 1, a.killing, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
-                finish(-1, -1, true, true);
+                record_nohit(J.ctrl, 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+                finish(J, -1, -1, true, true);
                 continue;
             }
             const T d = rsq<T>(h.d2);
             if (d < epsT || s.k == a.max_steps) {
                 if (sizeof(T) == 8) {
-                    finish(exit_bin(a, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false);
+                    finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false);
                     continue;
                 }
                 double b[3];
-                const double d64 = sqrt(recheck64(a.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
+                const double d64 = sqrt(recheck64(J.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
                 if (d64 < a.eps || s.k == a.max_steps) {
-                    finish(exit_bin(a, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false);
+                    finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false);
                     continue;
                 }
             }
             s.prev = h.slot;
             step = d;
         } else {
+            const double o64[3] = {J.ctrl->origin[0], J.ctrl->origin[1], J.ctrl->origin[2]};
+            const double r0max64 = J.ctrl->rho0max;
             const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
             if (r2 == (T)0) {
-                if (s.k == a.max_steps) { finish(-1, -1, true, true); continue; }
-                step = r0maxT;
+                if (s.k == a.max_steps) { finish(J, -1, -1, true, true); continue; }
+                step = (T)r0max64;
             } else {
                 const T inv = (T)1 / r2;
                 const T xp0 = s.x.x * inv, xp1 = s.x.y * inv, xp2 = s.x.z * inv;
                 Hit<T> h;
-                closest<T, COUNT>(a.m, xp0 + oT[0], xp1 + oT[1], xp2 + oT[2], s.prev, h, &err, &work);
-                n_steps++;
-                if (h.slot < 0 || h.id < 0 || h.id >= a.m.nf) {
+                closest<T, COUNT>(J.m, xp0 + (T)o64[0], xp1 + (T)o64[1], xp2 + (T)o64[2], s.prev, h, &err, &work);
+                if (s.kill) n_ksteps++; else n_steps++;
+                if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
                     err |= kErrNoHit;
-                    record_nohit(a.ctrl, 2, a.killing, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
-                    finish(-1, -1, true, true);
+                    record_nohit(J.ctrl, 2, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+                    finish(J, -1, -1, true, true);
                     continue;
                 }
                 const T d = rsq<T>(h.d2);
                 const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
                 const T ri = d / (nx * (nx + d));
-                const T r0 = r0maxT - rsq<T>(r2);
+                const T r0 = (T)r0max64 - rsq<T>(r2);
                 const T rho = ri > r0 ? ri : r0;
                 if (rho < epsT || s.k == a.max_steps) {
                     if (sizeof(T) == 8) {
-                        finish(exit_bin(a, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false);
+                        finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT),
+                               false);
                         continue;
                     }
                     const double xd0 = (double)s.x.x, xd1 = (double)s.x.y, xd2 = (double)s.x.z;
@@ -501,13 +560,13 @@ __global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
                     const double invd = 1.0 / r2d;
                     const double xpd0 = xd0 * invd, xpd1 = xd1 * invd, xpd2 = xd2 * invd;
                     double b[3];
-                    const double dd = sqrt(recheck64(a.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
+                    const double dd = sqrt(recheck64(J.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
                     const double nxd = sqrt(xpd0 * xpd0 + xpd1 * xpd1 + xpd2 * xpd2);
                     const double rid = dd / (nxd * (nxd + dd));
                     const double r0d = r0max64 - sqrt(r2d);
                     const double rhod = rid > r0d ? rid : r0d;
                     if (rhod < a.eps || s.k == a.max_steps) {
-                        finish(exit_bin(a, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false);
+                        finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false);
                         continue;
                     }
                 }
@@ -515,39 +574,66 @@ __global__ void __launch_bounds__(128, 6) k_walks(WalkArgs a) {
                 step = rho;
             }
         }
-        const V3<T> u = direction<T>(k0, k1, s.g, (uint32_t)s.k);
+        const V3<T> u = direction<T>(J.k0, s.k1, s.g, (uint32_t)s.k);
         s.x.x = s.x.x + step * u.x;
         s.x.y = s.x.y + step * u.y;
         s.x.z = s.x.z + step * u.z;
         s.k++;
     }
-    // per-warp reduction of the counters
-    for (int off = 16; off > 0; off >>= 1) {
-        n_steps += __shfl_down_sync(FULL, n_steps, off);
-        n_capped += __shfl_down_sync(FULL, n_capped, off);
-        n_lost += __shfl_down_sync(FULL, n_lost, off);
-        err |= __shfl_down_sync(FULL, err, off);
+    if constexpr (MULTI) {
+        flush();
         if (COUNT) {
-            work.nodes += __shfl_down_sync(FULL, work.nodes, off);
-            work.tris += __shfl_down_sync(FULL, work.tris, off);
+            for (int off = 16; off > 0; off >>= 1) {
+                work.nodes += __shfl_down_sync(FULL, work.nodes, off);
+                work.tris += __shfl_down_sync(FULL, work.tris, off);
+            }
+            if (lane == 0) {
+                atomicAdd(&a.stats->nodes, work.nodes);
+                atomicAdd(&a.stats->tris, work.tris);
+            }
+        }
+    } else {
+        // one job (a.stats is its block): per-warp reduction of the counters
+        for (int off = 16; off > 0; off >>= 1) {
+            n_steps += __shfl_down_sync(FULL, n_steps, off);
+            n_ksteps += __shfl_down_sync(FULL, n_ksteps, off);
+            n_capped += __shfl_down_sync(FULL, n_capped, off);
+            n_kcapped += __shfl_down_sync(FULL, n_kcapped, off);
+            n_lost += __shfl_down_sync(FULL, n_lost, off);
+            err |= __shfl_down_sync(FULL, err, off);
+            if (COUNT) {
+                work.nodes += __shfl_down_sync(FULL, work.nodes, off);
+                work.tris += __shfl_down_sync(FULL, work.tris, off);
+            }
+        }
+        if (lane == 0) {
+            if (COUNT) {
+                atomicAdd(&a.stats->nodes, work.nodes);
+                atomicAdd(&a.stats->tris, work.tris);
+            }
+            atomicAdd(&a.stats->steps, (unsigned long long)n_steps);
+            atomicAdd(&a.stats->kill_steps, (unsigned long long)n_ksteps);
+            atomicAdd(&a.stats->capped, (unsigned long long)n_capped);
+            atomicAdd(&a.stats->kill_capped, (unsigned long long)n_kcapped);
+            atomicAdd(&a.stats->lost, (unsigned long long)n_lost);
+            if (err) atomicOr(&a.stats->err, err);
         }
     }
-    if (lane == 0) {
-        if (COUNT) {
-            atomicAdd(&a.ctrl->nodes, work.nodes);
-            atomicAdd(&a.ctrl->tris, work.tris);
-        }
-        if (a.killing) {
-            atomicAdd(&a.ctrl->kill_steps, (unsigned long long)n_steps);
-            atomicAdd(&a.ctrl->kill_capped, (unsigned long long)n_capped);
-            atomicAdd(&a.ctrl->kill_lost, (unsigned long long)n_lost);
-        } else {
-            atomicAdd(&a.ctrl->steps, (unsigned long long)n_steps);
-            atomicAdd(&a.ctrl->capped, (unsigned long long)n_capped);
-            atomicAdd(&a.ctrl->lost, (unsigned long long)n_lost);
-        }
-        if (err) atomicOr(&a.ctrl->err, err);
+}
+
+// job tables are written by a kernel (capturable; kernel parameters are copied at launch)
+constexpr int kJobChunk = 96;
+struct JobChunk {
+    WalkJob j[kJobChunk];
+    unsigned long long offs[kJobChunk + 1];
+    int count, base, last;
+};
+__global__ void k_store_jobs(JobChunk c, WalkJob *jobs, unsigned long long *offs) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
+        jobs[c.base + i] = c.j[i];
+        offs[c.base + i] = c.offs[i];
     }
+    if (threadIdx.x == 0 && c.last) offs[c.base + c.count] = c.offs[c.count];
 }
 
 // ---------------------------------------------------------------- histogram + assembly
@@ -659,6 +745,12 @@ __global__ void k_diagonal(double *L, int R, const double *cf, const int32_t *H0
     }
 }
 
+// rows in the caller's order (queue-order option)
+__global__ void k_order_identity(int R, int32_t *order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < R) order[i] = i;
+}
+
 // ---------------------------------------------------------------- workspace
 struct Layout {
     size_t ball, keys, keys_s, order, exits, H0, cf, ctrl, sort, total;
@@ -667,7 +759,9 @@ struct Layout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Layout layout(int R, int W) {
+// per-mesh scratch; `own_ctrl` adds the control block of a single-mesh
+// estimate (a batch keeps its blocks in its header)
+static Layout layout(int R, int W, bool own_ctrl) {
     Layout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
@@ -678,7 +772,7 @@ static Layout layout(int R, int W) {
     L.exits = take(sizeof(int32_t) * (size_t)R * W);
     L.H0 = take(sizeof(int32_t) * R);
     L.cf = take(sizeof(double) * R);
-    L.ctrl = take(sizeof(Ctrl));
+    L.ctrl = own_ctrl ? take(sizeof(Ctrl)) : 0;
     size_t sb = 0;
     cub::DeviceRadixSort::SortKeys(nullptr, sb, (unsigned long long *)nullptr, (unsigned long long *)nullptr, R, 0, 62);
     L.sort_bytes = sb;
@@ -687,7 +781,484 @@ static Layout layout(int R, int W) {
     return L;
 }
 
+// one mesh of an estimate: its inputs, outputs and scratch
+struct Plan {
+    mcs_mesh m = nullptr;
+    mcs_rows rows{};
+    mcs_outputs out{};
+    Layout L{};
+    char *ws = nullptr;
+    Ctrl *ctrl = nullptr;
+    bool ext = false;
+    int W = 0;
+    double kappa = 0.0;
+    uint64_t seed = 0;
+    long long killing = 0;
+    int origin_auto = 1;
+    double origin[3] = {0.0, 0.0, 0.0};
+    Frame fr{};
+    RowBall *ball() const { return (RowBall *)(ws + L.ball); }
+    int32_t *order() const { return (int32_t *)(ws + L.order); }
+    int32_t *exits() const { return (int32_t *)(ws + L.exits); }
+    int32_t *H0() const { return out.H0 ? out.H0 : (int32_t *)(ws + L.H0); }
+    double *cf() const { return ext ? (double *)(ws + L.cf) : nullptr; }
+    unsigned long long walks() const { return (unsigned long long)rows.n_rows * (unsigned long long)W; }
+};
+
+static mcs_status check_common(const mcs_params *p, const std::string &f) {
+    MCS_ARG(p->walks_per_row > 0 && p->walks_per_row % 2 == 0, f + ": walks_per_row must be a positive even number");
+    MCS_ARG(p->eps > 0.0 && std::isfinite(p->eps), f + ": eps must be positive");
+    MCS_ARG(p->cap_deg > 0.0 && p->cap_deg < 180.0, f + ": cap_deg must be in (0, 180)");
+    MCS_ARG(p->bisect_iters >= 0 && p->bisect_iters <= 60, f + ": bisect_iters out of range");
+    MCS_ARG(p->max_steps >= 2, f + ": max_steps must be >= 2");
+    MCS_ARG(p->prec == MCS_FP32 || p->prec == MCS_FP64, f + ": prec must be 32 or 64");
+    MCS_ARG(p->killing_walks >= 0, f + ": killing_walks < 0");
+    MCS_ARG(p->kappa < 1.0, f + ": kappa must be < 1");
+    MCS_ARG(p->threads_per_block == 0 || (p->threads_per_block % 32 == 0 && p->threads_per_block <= 128 &&
+                                          p->threads_per_block > 0),
+            f + ": threads_per_block must be 0 or a multiple of 32 up to 128");
+    MCS_ARG(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 64, f + ": blocks_per_sm out of range");
+    MCS_ARG(p->queue_order >= 0 && p->queue_order <= 3, f + ": queue_order must be in [0, 3]");
+    return MCS_OK;
+}
+
+static mcs_status check_mesh_rows(mcs_mesh m, const mcs_rows *rows, const mcs_outputs *out, int domain, int W,
+                                  const std::string &f) {
+    MCS_ARG(m != nullptr, f + ": NULL mesh");
+    const int R = rows->n_rows;
+    MCS_ARG(R > 0, f + ": n_rows must be positive");
+    MCS_ARG(rows->pos && rows->nrm && rows->area, f + ": NULL row arrays");
+    MCS_ARG(rows->tri2bin != nullptr || R == m->nv, f + ": vertex rows need n_rows == nv");
+    MCS_ARG((long long)R * W < (1LL << 40), f + ": too many walks");
+    MCS_ARG(domain == MCS_INTERIOR || domain == MCS_EXTERIOR, f + ": bad domain");
+    MCS_ARG(out->hist_bin && out->hist_cnt && out->hist_nnz, f + ": NULL histogram outputs");
+    MCS_ARG((size_t)R * sizeof(int) <= 200 * 1024, f + ": more than 51200 rows per estimate");
+    return MCS_OK;
+}
+
+static Plan make_plan(mcs_mesh m, const mcs_rows &rows, const mcs_outputs &out, const mcs_params *p, int domain,
+                      uint64_t seed, int origin_auto, const double *origin, char *ws, Ctrl *ctrl, bool own_ctrl) {
+    Plan pl;
+    pl.m = m;
+    pl.rows = rows;
+    pl.out = out;
+    pl.W = p->walks_per_row;
+    pl.L = layout(rows.n_rows, pl.W, own_ctrl);
+    pl.ws = ws;
+    pl.ctrl = own_ctrl ? (Ctrl *)(ws + pl.L.ctrl) : ctrl;
+    pl.ext = domain == MCS_EXTERIOR;
+    pl.kappa = p->kappa >= 0.0 ? p->kappa : (rows.tri2bin ? 1e-6 : 0.05);
+    pl.seed = seed;
+    pl.killing = pl.ext ? p->killing_walks : 0;
+    pl.origin_auto = origin_auto;
+    for (int k = 0; k < 3; k++) pl.origin[k] = origin[k];
+    pl.fr.onemk = 1.0 - pl.kappa;
+    pl.fr.iw0 = 1.0 / sin(p->cap_deg * (M_PI / 360.0));
+    pl.fr.eps = p->eps;
+    pl.fr.rho_min_factor = p->rho_min_factor;
+    pl.fr.rmax = m->rmax;
+    pl.fr.bisect_iters = p->bisect_iters;
+    return pl;
+}
+
+// the row schedule: Z-order of the row points (Sec. 5), or the caller's order
+static mcs_status enqueue_order(const Plan &pl, int row_order, cudaStream_t st) {
+    const int R = pl.rows.n_rows, tb = 128, gr = (R + tb - 1) / tb;
+    if (row_order & 1) {
+        note_launch();
+        k_order_identity<<<gr, tb, 0, st>>>(R, pl.order());
+    } else {
+        double inv[3];
+        for (int k = 0; k < 3; k++) inv[k] = 1.0 / (pl.m->hi[k] - pl.m->lo[k]);
+        unsigned long long *keys = (unsigned long long *)(pl.ws + pl.L.keys);
+        unsigned long long *keys_s = (unsigned long long *)(pl.ws + pl.L.keys_s);
+        note_launch();
+        k_row_keys<<<gr, tb, 0, st>>>(pl.rows.pos, R, pl.m->lo[0], pl.m->lo[1], pl.m->lo[2], inv[0], inv[1], inv[2],
+                                      keys);
+        size_t sb = pl.L.sort_bytes;
+        MCS_CUDA(cub::DeviceRadixSort::SortKeys(pl.ws + pl.L.sort, sb, keys, keys_s, R, 0, 62, st));
+        note_launch();
+        k_order_from_keys<<<gr, tb, 0, st>>>(keys_s, R, pl.order());
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// control block, row schedule, tangent balls (and the exterior frame)
+static mcs_status enqueue_setup(const Plan &pl, int row_order, cudaStream_t st) {
+    const int R = pl.rows.n_rows;
+    const DevMesh dm = pl.m->dev();
+    MCS_CUDA(cudaMemsetAsync(pl.ctrl, 0, sizeof(Ctrl), st));
+    MCS_CUDA(cudaMemsetAsync(pl.H0(), 0, sizeof(int32_t) * R, st));
+    const mcs_status s = enqueue_order(pl, row_order, st);
+    if (s != MCS_OK) return s;
+    const int tb = 128, gr = (R + tb - 1) / tb;
+    const int tgrid = (R + kTanWarps - 1) / kTanWarps;
+    if (pl.ext) {
+        if (pl.origin_auto) {
+            const int ostride = (R + 255) / 256, nsub = (R + ostride - 1) / ostride;
+            note_launch();
+            k_tangent_int<<<(nsub + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(
+                dm, pl.rows.pos, pl.rows.nrm, R, ostride, pl.fr, pl.ball(), pl.ctrl);
+            note_launch();
+            k_origin_argmax<<<1, 1024, 0, st>>>(pl.ball(), R, ostride, pl.ctrl);
+        } else {
+            note_launch();
+            k_set_origin<<<1, 1, 0, st>>>(pl.ctrl, pl.origin[0], pl.origin[1], pl.origin[2]);
+        }
+        note_launch();
+        k_ext_frame<<<1, 256, 0, st>>>(pl.m->V, pl.m->nv, pl.ctrl);
+        note_launch();
+        k_tangent_ext<<<tgrid, 32 * kTanWarps, 0, st>>>(dm, pl.rows.pos, pl.rows.nrm, R, pl.fr, pl.ball(), pl.ctrl);
+        note_launch();
+        k_colfactor<<<gr, tb, 0, st>>>(pl.rows.pos, R, pl.ctrl, pl.cf());
+    } else {
+        note_launch();
+        k_tangent_int<<<tgrid, 32 * kTanWarps, 0, st>>>(dm, pl.rows.pos, pl.rows.nrm, R, 1, pl.fr, pl.ball(), pl.ctrl);
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// the job of a plan; n_row_walks < R*W truncates it to its first rows (autotuner samples)
+static WalkJob make_job(const Plan &pl, unsigned long long n_row_walks, unsigned long long n_kill) {
+    WalkJob J;
+    J.m = pl.m->dev();
+    J.ball = pl.ball();
+    J.order = pl.order();
+    J.tri2bin = pl.rows.tri2bin;
+    J.exits = pl.exits();
+    J.exit_tri = pl.out.exit_tri;
+    J.H0 = pl.H0();
+    J.ctrl = pl.ctrl;
+    J.n_rows_walks = n_row_walks;
+    J.n_kill = n_kill;
+    J.R = pl.rows.n_rows;
+    J.W = pl.W;
+    J.k0 = (uint32_t)pl.seed;
+    J.k1 = (uint32_t)(pl.seed >> 32);
+    J.ext = pl.ext;
+    J.pad = 0;
+    return J;
+}
+
+// writes the job table and its queue offsets on the stream
+static mcs_status store_jobs(const std::vector<WalkJob> &jobs, WalkJob *d_jobs, unsigned long long *d_offs,
+                             cudaStream_t st) {
+    unsigned long long off = 0;
+    for (size_t base = 0; base < jobs.size(); base += kJobChunk) {
+        JobChunk c;
+        c.count = (int)std::min<size_t>(kJobChunk, jobs.size() - base);
+        c.base = (int)base;
+        c.last = base + c.count == jobs.size();
+        for (int i = 0; i < c.count; i++) {
+            c.j[i] = jobs[base + i];
+            c.offs[i] = off;
+            off += jobs[base + i].n_rows_walks + jobs[base + i].n_kill;
+        }
+        c.offs[c.count] = off;
+        note_launch();
+        k_store_jobs<<<1, 128, 0, st>>>(c, d_jobs, d_offs);
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+typedef void (*WalkKernel)(MultiArgs);
+
+template <typename T, bool COUNT> static WalkKernel walk_kernel_mode(int mode, bool multi) {
+    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false> : k_walks<T, 1, COUNT, false>;
+    return mode == 0 ? k_walks<T, 0, COUNT, true> : (mode == 1 ? k_walks<T, 1, COUNT, true> : k_walks<T, 2, COUNT, true>);
+}
+
+// mode: 0 all jobs interior, 1 all exterior, 2 mixed; multi: several jobs
+static WalkKernel walk_kernel(const mcs_params *p, int mode, bool multi) {
+    if (p->count_work)
+        return p->prec == MCS_FP64 ? walk_kernel_mode<double, true>(mode, multi)
+                                   : walk_kernel_mode<float, true>(mode, multi);
+    return p->prec == MCS_FP64 ? walk_kernel_mode<double, false>(mode, multi)
+                               : walk_kernel_mode<float, false>(mode, multi);
+}
+
+// resident blocks per SM of the walk kernel for this block size
+static mcs_status walk_residency(const mcs_params *p, int mode, bool multi, int *tpb_out, int *bps_out) {
+    const int tpb = p->threads_per_block > 0 ? p->threads_per_block : 128;
+    int occ = 0;
+    MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel(p, mode, multi), tpb, 0));
+    occ = std::max(1, occ);
+    *tpb_out = tpb;
+    *bps_out = p->blocks_per_sm > 0 ? std::min(p->blocks_per_sm, occ) : occ;
+    return MCS_OK;
+}
+
+// the persistent walk launch over a job table
+// n_jobs == 1: `one` is the job (passed in the kernel parameters); else the
+// table at d_jobs / d_offs, written earlier on the stream
+static mcs_status launch_walks(const WalkJob *d_jobs, const unsigned long long *d_offs, int n_jobs, const WalkJob *one,
+                               Ctrl *stats, const mcs_params *p, int mode, int tpb, int bps, cudaStream_t st) {
+    MultiArgs a;
+    memset(&a, 0, sizeof a);
+    if (one) a.j0 = *one;
+    a.jobs = d_jobs;
+    a.offs = d_offs;
+    a.n_jobs = n_jobs;
+    a.queue = &stats->queue;
+    a.stats = stats;
+    a.eps = p->eps;
+    a.iw0 = 1.0 / sin(p->cap_deg * (M_PI / 360.0));
+    a.eps2f = (float)(2.0 * p->eps);
+    a.max_steps = p->max_steps;
+    note_launch();
+    walk_kernel(p, mode, n_jobs > 1)<<<num_sms() * bps, tpb, 0, st>>>(a);
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+static size_t hist_smem(int R) { return std::max<size_t>(sizeof(int) * (size_t)R, 1024); }
+
+static mcs_status prepare_histogram(size_t smem) {
+    MCS_CUDA(cudaFuncSetAttribute(k_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return MCS_OK;
+}
+
+// histogram + row normalisation, symmetrisation, Laplacian diagonal
+static mcs_status enqueue_hist(const Plan &pl, cudaStream_t st) {
+    const int R = pl.rows.n_rows, W = pl.W;
+    if (pl.out.Lambda) {
+        note_launch();
+        k_fill_zero<<<num_sms() * 8, 256, 0, st>>>(pl.out.Lambda, (size_t)R * R);
+    }
+    note_launch();
+    k_histogram<<<R, kHistThreads, sizeof(int) * (size_t)R, st>>>(
+        pl.exits(), pl.order(), pl.ball(), pl.rows.area, pl.cf(), R, W, std::min(W, R), pl.out.hist_bin,
+        pl.out.hist_cnt, pl.out.hist_nnz, pl.out.Lambda, pl.out.omega, pl.ctrl);
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+static mcs_status enqueue_assembly(const Plan &pl, cudaStream_t st) {
+    const int R = pl.rows.n_rows;
+    if (pl.out.Lambda) {
+        const int nt = (R + 31) / 32;
+        note_launch();
+        k_symmetrize<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(pl.out.Lambda, R);
+        const bool kill = pl.ext && pl.killing > 0;
+        note_launch();
+        k_diagonal<<<(R * 32 + 255) / 256, 256, 0, st>>>(pl.out.Lambda, R, pl.cf(), kill ? pl.H0() : nullptr,
+                                                        kill ? 1.0 / (double)pl.killing : 0.0);
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// host statistics of one control block; the status of that estimate
+static mcs_status read_stats(const Ctrl &hc, const Plan *pl, unsigned long long walks, mcs_stats *stats,
+                             const char *fn) {
+    if (stats) {
+        stats->nodes_visited = (long long)hc.nodes;
+        stats->tris_tested = (long long)hc.tris;
+        stats->walks = (long long)walks;
+        stats->steps = (long long)hc.steps;
+        stats->capped = (long long)hc.capped;
+        stats->lost = (long long)hc.lost;
+        stats->discarded_rows = hc.discarded;
+        stats->killing_steps = (long long)hc.kill_steps;
+        stats->killing_capped = (long long)hc.kill_capped;
+        const bool ext = pl && pl->ext;
+        for (int k = 0; k < 3; k++) stats->origin[k] = ext ? hc.origin[k] : 0.0;
+        stats->rmax = pl ? (ext ? hc.rmax_ext : pl->m->rmax) : 0.0;
+        stats->device_error = hc.err;
+    }
+    if (hc.err & kErrNoOrigin) {
+        set_error(std::string(fn) + ": no interior tangent ball to place the inversion centre");
+        return MCS_ERR_NO_INTERIOR_POINT;
+    }
+    if (hc.err & kErrNoHit) {
+        char buf[320];
+        snprintf(buf, sizeof buf,
+                 "%s: a walk query found no triangle (kind %d, killing %d, walk %llu, step %d, "
+                 "x~ = (%.9g, %.9g, %.9g)); walk retired as lost",
+                 fn, hc.diag_kind, hc.diag_killing, hc.diag_walk, hc.diag_step, hc.diag_p[0], hc.diag_p[1],
+                 hc.diag_p[2]);
+        set_error(buf);
+        return MCS_ERR_DEVICE;
+    }
+    if (hc.err) {
+        set_error(std::string(fn) + (hc.err & kErrBin ? ": tri2bin maps a triangle outside [0, n_rows)"
+                                                      : ": BVH traversal stack or iteration bound exceeded"));
+        return MCS_ERR_DEVICE;
+    }
+    return (hc.capped || hc.kill_capped) ? MCS_WARN_CAPPED : MCS_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// Batch workspace: header (job table, queue offsets, control blocks: one per
+// mesh and one for the launch), then each mesh's scratch.
+struct BatchLayout {
+    size_t jobs, offs, ctrl, total;
+    std::vector<size_t> item;
+};
+
+static BatchLayout batch_layout(const mcs_batch_item *items, int n, int W) {
+    BatchLayout B;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+    B.jobs = take(sizeof(WalkJob) * (size_t)n);
+    B.offs = take(sizeof(unsigned long long) * (size_t)(n + 1));
+    B.ctrl = take(sizeof(Ctrl) * (size_t)(n + 1));
+    B.item.resize(n);
+    for (int i = 0; i < n; i++) B.item[i] = take(layout(std::max(1, items[i].rows.n_rows), W, false).total);
+    B.total = o;
+    return B;
+}
+
+struct Batch {
+    std::vector<Plan> plans;
+    WalkJob *jobs = nullptr;
+    unsigned long long *offs = nullptr;
+    Ctrl *ctrl = nullptr;   // n + 1 blocks: per mesh, then the launch's
+    int n = 0;
+    int mode = 0;           // walk kernel: 0 all interior, 1 all exterior, 2 mixed
+    mcs_params p{};
+    Ctrl *launch_ctrl() const { return ctrl + n; }
+};
+
+static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                             size_t workspace_bytes, Batch &b, const char *fn) {
+    const std::string f(fn);
+    MCS_ARG(items != nullptr && p != nullptr, f + ": NULL items or params");
+    MCS_ARG(n > 0, f + ": the batch is empty");
+    mcs_status s = check_common(p, f);
+    if (s != MCS_OK) return s;
+    for (int i = 0; i < n; i++) {
+        s = check_mesh_rows(items[i].mesh, &items[i].rows, &items[i].out, items[i].domain, p->walks_per_row,
+                            f + " item " + std::to_string(i));
+        if (s != MCS_OK) return s;
+    }
+    const BatchLayout B = batch_layout(items, n, p->walks_per_row);
+    MCS_ARG(workspace != nullptr && workspace_bytes >= B.total, f + ": workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, f + ": workspace must be 256-byte aligned");
+    char *ws = (char *)workspace;
+    b.n = n;
+    b.p = *p;
+    b.jobs = (WalkJob *)(ws + B.jobs);
+    b.offs = (unsigned long long *)(ws + B.offs);
+    b.ctrl = (Ctrl *)(ws + B.ctrl);
+    b.plans.clear();
+    int n_ext = 0;
+    for (int i = 0; i < n; i++) n_ext += items[i].domain == MCS_EXTERIOR;
+    b.mode = n_ext == 0 ? 0 : (n_ext == n ? 1 : 2);
+    for (int i = 0; i < n; i++) {
+        const mcs_batch_item &it = items[i];
+        b.plans.push_back(make_plan(it.mesh, it.rows, it.out, p, it.domain, it.seed, it.origin_auto, it.origin,
+                                    ws + B.item[i], b.ctrl + i, false));
+    }
+    return MCS_OK;
+}
+
+// queue order of the jobs: as given, or by descending walk count (bit 2 of queue_order)
+static std::vector<int> job_order(const Batch &b) {
+    std::vector<int> ord(b.n);
+    for (int i = 0; i < b.n; i++) ord[i] = i;
+    if (b.p.queue_order & 2)
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+            const unsigned long long wx = b.plans[x].walks() + b.plans[x].killing;
+            const unsigned long long wy = b.plans[y].walks() + b.plans[y].killing;
+            return wx > wy;
+        });
+    return ord;
+}
+
+// everything a batched estimate launches, in stream order; `ev` (optional,
+// 4 events) marks setup | walks | histogram + assembly
+static mcs_status enqueue_batch(const Batch &b, cudaStream_t st, cudaEvent_t *ev) {
+    mcs_status s;
+    if (ev) cudaEventRecord(ev[0], st);
+    MCS_CUDA(cudaMemsetAsync(b.launch_ctrl(), 0, sizeof(Ctrl), st));
+    for (const Plan &pl : b.plans)
+        if ((s = enqueue_setup(pl, b.p.queue_order, st)) != MCS_OK) return s;
+    std::vector<WalkJob> jobs;
+    for (int i : job_order(b)) jobs.push_back(make_job(b.plans[i], b.plans[i].walks(), (unsigned long long)b.plans[i].killing));
+    if (b.n > 1 && (s = store_jobs(jobs, b.jobs, b.offs, st)) != MCS_OK) return s;
+    int tpb = 0, bps = 0;
+    if ((s = walk_residency(&b.p, b.mode, b.n > 1, &tpb, &bps)) != MCS_OK) return s;
+    if (ev) cudaEventRecord(ev[1], st);
+    // one mesh: the one-job kernel, counters straight into the mesh's block
+    if ((s = launch_walks(b.jobs, b.offs, b.n, b.n > 1 ? nullptr : &jobs[0], b.n > 1 ? b.launch_ctrl() : b.plans[0].ctrl,
+                          &b.p, b.mode, tpb, bps, st)) != MCS_OK)
+        return s;
+    if (ev) cudaEventRecord(ev[2], st);
+    for (const Plan &pl : b.plans) {
+        if ((s = enqueue_hist(pl, st)) != MCS_OK) return s;
+        if ((s = enqueue_assembly(pl, st)) != MCS_OK) return s;
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    return MCS_OK;
+}
+
+static mcs_status batch_hist_prepare(const Batch &b) {
+    int rmax = 1;
+    for (const Plan &pl : b.plans) rmax = std::max(rmax, pl.rows.n_rows);
+    return prepare_histogram(hist_smem(rmax));
+}
+
+// per-mesh and launch statistics of a finished batch (synchronises st)
+static mcs_status batch_stats(const Batch &b, mcs_stats *total, mcs_stats *per_item, cudaStream_t st,
+                              const char *fn) {
+    std::vector<Ctrl> hc(b.n + 1);
+    MCS_CUDA(cudaMemcpyAsync(hc.data(), b.ctrl, sizeof(Ctrl) * (b.n + 1), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaStreamSynchronize(st));
+    mcs_status worst = MCS_OK;
+    // the launch block holds the work counters; the rest is summed over meshes
+    Ctrl sum = hc[b.n];
+    sum.discarded = 0;
+    sum.steps = sum.capped = sum.lost = sum.kill_steps = sum.kill_capped = 0;
+    if (b.n == 1) {  // the one-job kernel counted its work in the mesh's block
+        sum.nodes = hc[0].nodes;
+        sum.tris = hc[0].tris;
+    }
+    unsigned long long walks = 0;
+    std::string msgs;
+    int n_bad = 0;
+    for (int i = 0; i < b.n; i++) {
+        sum.steps += hc[i].steps;
+        sum.capped += hc[i].capped;
+        sum.lost += hc[i].lost;
+        sum.kill_steps += hc[i].kill_steps;
+        sum.kill_capped += hc[i].kill_capped;
+        const std::string name = std::string(fn) + " item " + std::to_string(i);
+        const mcs_status s = read_stats(hc[i], &b.plans[i], b.plans[i].walks(), per_item ? per_item + i : nullptr,
+                                        name.c_str());
+        if (s < 0) {
+            if (n_bad < 3) msgs += (msgs.empty() ? "" : "; ") + get_error();
+            n_bad++;
+        }
+        if (s < 0 && worst >= 0) worst = s;
+        else if (s > 0 && worst == MCS_OK) worst = s;
+        sum.discarded += hc[i].discarded;
+        sum.err |= hc[i].err;
+        walks += b.plans[i].walks();
+    }
+    if (total) {
+        read_stats(sum, nullptr, walks, total, fn);
+        for (int k = 0; k < 4; k++) total->phase_ms[k] = 0.f;
+    }
+    if (worst < 0) {
+        if (n_bad > 3) msgs += "; ... (" + std::to_string(n_bad) + " meshes reported errors)";
+        set_error(msgs);
+        return worst;
+    }
+    return worst;
+}
+
 }  // namespace mcs
+
+struct mcs_graph_s {
+    mcs::Batch b;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;  // library kernels per replay
+};
 
 using namespace mcs;
 
@@ -710,195 +1281,260 @@ void mcs_default_params(mcs_params *p) {
     p->walks_per_row = 1024;
     p->blocks_per_sm = 0;
     p->threads_per_block = 0;
+    p->timing = 0;
+    p->count_work = 0;
+    p->queue_order = 0;
 }
 
 size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, long long killing_walks) {
     (void)m; (void)killing_walks;
     if (n_rows <= 0 || walks_per_row <= 0) return 0;
-    return layout(n_rows, walks_per_row).total;
+    return layout(n_rows, walks_per_row, true).total;
 }
 
 mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
                             void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream_) {
-    MCS_ARG(m && rows && p && out, "mcs_estimate_dtn: NULL mesh, rows, params or outputs");
-    const int R = rows->n_rows, W = p->walks_per_row;
-    MCS_ARG(R > 0, "mcs_estimate_dtn: n_rows must be positive");
-    MCS_ARG(rows->pos && rows->nrm && rows->area, "mcs_estimate_dtn: NULL row arrays");
-    MCS_ARG(rows->tri2bin != nullptr || R == m->nv, "mcs_estimate_dtn: vertex rows need n_rows == nv");
-    MCS_ARG(W > 0 && W % 2 == 0, "mcs_estimate_dtn: walks_per_row must be a positive even number");
-    MCS_ARG((long long)R * W < (1LL << 40), "mcs_estimate_dtn: too many walks");
-    MCS_ARG(p->eps > 0.0 && std::isfinite(p->eps), "mcs_estimate_dtn: eps must be positive");
-    MCS_ARG(p->cap_deg > 0.0 && p->cap_deg < 180.0, "mcs_estimate_dtn: cap_deg must be in (0, 180)");
-    MCS_ARG(p->bisect_iters >= 0 && p->bisect_iters <= 60, "mcs_estimate_dtn: bisect_iters out of range");
-    MCS_ARG(p->max_steps >= 2, "mcs_estimate_dtn: max_steps must be >= 2");
-    MCS_ARG(p->prec == MCS_FP32 || p->prec == MCS_FP64, "mcs_estimate_dtn: prec must be 32 or 64");
-    MCS_ARG(p->domain == MCS_INTERIOR || p->domain == MCS_EXTERIOR, "mcs_estimate_dtn: bad domain");
-    MCS_ARG(p->killing_walks >= 0, "mcs_estimate_dtn: killing_walks < 0");
-    MCS_ARG(out->hist_bin && out->hist_cnt && out->hist_nnz, "mcs_estimate_dtn: NULL histogram outputs");
-    MCS_ARG((size_t)R * sizeof(int) <= 200 * 1024, "mcs_estimate_dtn: more than 51200 rows per estimate");
-    const Layout L = layout(R, W);
-    MCS_ARG(workspace != nullptr && workspace_bytes >= L.total, "mcs_estimate_dtn: workspace too small");
-    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_estimate_dtn: workspace must be 256-byte aligned");
-    const bool ext = p->domain == MCS_EXTERIOR;
-    const double kappa = p->kappa >= 0.0 ? p->kappa : (rows->tri2bin ? 1e-6 : 0.05);
-    MCS_ARG(kappa < 1.0, "mcs_estimate_dtn: kappa must be < 1");
-
+    const std::string f = "mcs_estimate_dtn";
+    MCS_ARG(m && rows && p && out, f + ": NULL mesh, rows, params or outputs");
+    mcs_status s = check_common(p, f);
+    if (s != MCS_OK) return s;
+    if ((s = check_mesh_rows(m, rows, out, p->domain, p->walks_per_row, f)) != MCS_OK) return s;
+    const Layout L = layout(rows->n_rows, p->walks_per_row, true);
+    MCS_ARG(workspace != nullptr && workspace_bytes >= L.total, f + ": workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, f + ": workspace must be 256-byte aligned");
     cudaStream_t st = as_stream(stream_);
     char *ws = (char *)workspace;
-    RowBall *ball = (RowBall *)(ws + L.ball);
-    unsigned long long *keys = (unsigned long long *)(ws + L.keys), *keys_s = (unsigned long long *)(ws + L.keys_s);
-    int32_t *order = (int32_t *)(ws + L.order);
-    int32_t *exits = (int32_t *)(ws + L.exits);
-    int32_t *H0 = out->H0 ? out->H0 : (int32_t *)(ws + L.H0);
-    double *cf = ext ? (double *)(ws + L.cf) : nullptr;
-    Ctrl *ctrl = (Ctrl *)(ws + L.ctrl);
-    const DevMesh dm = m->dev();
-
-    Frame fr;
-    fr.onemk = 1.0 - kappa;
-    fr.iw0 = 1.0 / sin(p->cap_deg * (M_PI / 360.0));
-    fr.eps = p->eps;
-    fr.rho_min_factor = p->rho_min_factor;
-    fr.rmax = m->rmax;
-    fr.bisect_iters = p->bisect_iters;
+    const Plan pl = make_plan(m, *rows, *out, p, p->domain, p->seed, p->origin_auto, p->origin, ws, nullptr, true);
 
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     const bool timing = stats && p->timing;
     if (timing)
         for (auto &e : ev) MCS_CUDA(cudaEventCreate(&e));
     auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], st); };
+    auto release = [&]() { if (timing) for (auto &e : ev) cudaEventDestroy(e); };
     mark(0);
-    MCS_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-    MCS_CUDA(cudaMemsetAsync(H0, 0, sizeof(int32_t) * R, st));
-    const int tb = 128, gr = (R + tb - 1) / tb;
-    // Z-order row schedule
-    double inv[3];
-    for (int k = 0; k < 3; k++) inv[k] = 1.0 / (m->hi[k] - m->lo[k]);
-    k_row_keys<<<gr, tb, 0, st>>>(rows->pos, R, m->lo[0], m->lo[1], m->lo[2], inv[0], inv[1], inv[2], keys);
-    size_t sb = L.sort_bytes;
-    MCS_CUDA(cub::DeviceRadixSort::SortKeys(ws + L.sort, sb, keys, keys_s, R, 0, 62, st));
-    k_order_from_keys<<<gr, tb, 0, st>>>(keys_s, R, order);
-    // tangent balls
-    if (ext) {
-        if (p->origin_auto) {
-            const int ostride = (R + 255) / 256, nsub = (R + ostride - 1) / ostride;
-            k_tangent_int<<<(nsub + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R,
-                                                                                        ostride, fr, ball, ctrl);
-            k_origin_argmax<<<1, 1024, 0, st>>>(ball, R, ostride, ctrl);
-        } else {
-            k_set_origin<<<1, 1, 0, st>>>(ctrl, p->origin[0], p->origin[1], p->origin[2]);
-        }
-        k_ext_frame<<<1, 256, 0, st>>>(m->V, m->nv, ctrl);
-        k_tangent_ext<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, fr,
-                                                                                 ball, ctrl);
-        k_colfactor<<<gr, tb, 0, st>>>(rows->pos, R, ctrl, cf);
-    } else {
-        k_tangent_int<<<(R + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(dm, rows->pos, rows->nrm, R, 1, fr,
-                                                                                 ball, ctrl);
-    }
-    MCS_CUDA(cudaGetLastError());
-    // walks
-    WalkArgs a;
-    a.m = dm;
-    a.ball = ball;
-    a.order = order;
-    a.tri2bin = rows->tri2bin;
-    a.exits = exits;
-    a.exit_tri = out->exit_tri;
-    a.H0 = H0;
-    a.ctrl = ctrl;
-    a.total = (unsigned long long)R * (unsigned long long)W;
-    a.R = R;
-    a.W = W;
-    a.k0 = (uint32_t)p->seed;
-    a.k1 = (uint32_t)(p->seed >> 32);
-    a.eps = p->eps;
-    a.iw0 = fr.iw0;
-    a.eps2f = (float)(2.0 * p->eps);
-    a.max_steps = p->max_steps;
-    a.killing = 0;
-    void (*kern)(WalkArgs) = nullptr;
-    if (p->count_work) {
-        if (p->prec == MCS_FP64) kern = ext ? k_walks<double, true, true> : k_walks<double, false, true>;
-        else kern = ext ? k_walks<float, true, true> : k_walks<float, false, true>;
-    } else {
-        if (p->prec == MCS_FP64) kern = ext ? k_walks<double, true, false> : k_walks<double, false, false>;
-        else kern = ext ? k_walks<float, true, false> : k_walks<float, false, false>;
-    }
-    const int tpb = 128;
-    int occ = 0;
-    MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tpb, 0));
-    const int bps = p->blocks_per_sm > 0 ? p->blocks_per_sm : std::max(1, occ);
-    const int grid = num_sms() * bps;
+    if ((s = enqueue_setup(pl, p->queue_order, st)) != MCS_OK) { release(); return s; }
+    const WalkJob job = make_job(pl, pl.walks(), (unsigned long long)pl.killing);
+    int tpb = 0, bps = 0;
+    const int mode = pl.ext ? 1 : 0;
+    if ((s = walk_residency(p, mode, false, &tpb, &bps)) != MCS_OK) { release(); return s; }
+    if ((s = prepare_histogram(hist_smem(rows->n_rows))) != MCS_OK) { release(); return s; }
     mark(1);
-    kern<<<grid, tpb, 0, st>>>(a);
-    if (ext && p->killing_walks > 0) {
-        a.killing = 1;
-        a.total = (unsigned long long)p->killing_walks;
-        kern<<<grid, tpb, 0, st>>>(a);
-    }
-    MCS_CUDA(cudaGetLastError());
-    // histogram, row normalisation, assembly
+    if ((s = launch_walks(nullptr, nullptr, 1, &job, pl.ctrl, p, mode, tpb, bps, st)) != MCS_OK) { release(); return s; }
     mark(2);
-    if (out->Lambda) {
-        const size_t nn = (size_t)R * R;
-        k_fill_zero<<<num_sms() * 8, 256, 0, st>>>(out->Lambda, nn);
-    }
-    const size_t smem = sizeof(int) * (size_t)R;
-    MCS_CUDA(cudaFuncSetAttribute(k_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1024)));
-    k_histogram<<<R, kHistThreads, smem, st>>>(exits, order, ball, rows->area, cf, R, W, std::min(W, R), out->hist_bin,
-                                             out->hist_cnt, out->hist_nnz, out->Lambda, out->omega, ctrl);
+    if ((s = enqueue_hist(pl, st)) != MCS_OK) { release(); return s; }
     mark(3);
-    if (out->Lambda) {
-        const int nt = (R + 31) / 32;
-        k_symmetrize<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(out->Lambda, R);
-        const bool kill = ext && p->killing_walks > 0;
-        k_diagonal<<<(R * 32 + 255) / 256, 256, 0, st>>>(out->Lambda, R, cf, kill ? H0 : nullptr,
-                                                        kill ? 1.0 / (double)p->killing_walks : 0.0);
-    }
+    if ((s = enqueue_assembly(pl, st)) != MCS_OK) { release(); return s; }
     mark(4);
-    MCS_CUDA(cudaGetLastError());
-    if (!stats) return MCS_OK;
+    if (!stats) { release(); return MCS_OK; }
     Ctrl hc;
-    MCS_CUDA(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    MCS_CUDA(cudaStreamSynchronize(st));
+    cudaError_t e = cudaMemcpyAsync(&hc, pl.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { release(); return cuda_fail(e, "mcs_estimate_dtn: reading the control block"); }
     for (int i = 0; i < 4; i++) {
         stats->phase_ms[i] = 0.f;
         if (timing) cudaEventElapsedTime(&stats->phase_ms[i], ev[i], ev[i + 1]);
     }
+    release();
+    return read_stats(hc, &pl, pl.walks(), stats, "mcs_estimate_dtn");
+}
+
+size_t mcs_estimate_batched_workspace_size(const mcs_batch_item *items, int n, int walks_per_row) {
+    if (!items || n <= 0 || walks_per_row <= 0) return 0;
+    return batch_layout(items, n, walks_per_row).total;
+}
+
+mcs_status mcs_estimate_batched(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                                size_t workspace_bytes, mcs_stats *total, mcs_stats *per_item, void *stream_) {
+    Batch b;
+    mcs_status s = make_batch(items, n, p, workspace, workspace_bytes, b, "mcs_estimate_batched");
+    if (s != MCS_OK) return s;
+    cudaStream_t st = as_stream(stream_);
+    if ((s = batch_hist_prepare(b)) != MCS_OK) return s;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    const bool timing = total && p->timing;
+    if (timing)
+        for (auto &e : ev) MCS_CUDA(cudaEventCreate(&e));
+    s = enqueue_batch(b, st, timing ? ev : nullptr);
+    if (s == MCS_OK && (total || per_item)) {
+        s = batch_stats(b, total, per_item, st, "mcs_estimate_batched");
+        if (timing)
+            for (int i = 0; i < 3; i++) cudaEventElapsedTime(&total->phase_ms[i], ev[i], ev[i + 1]);
+    }
     if (timing)
         for (auto &e : ev) cudaEventDestroy(e);
-    stats->nodes_visited = (long long)hc.nodes;
-    stats->tris_tested = (long long)hc.tris;
-    stats->walks = (long long)R * W;
-    stats->steps = (long long)hc.steps;
-    stats->capped = (long long)hc.capped;
-    stats->lost = (long long)hc.lost;
-    stats->discarded_rows = hc.discarded;
-    stats->killing_steps = (long long)hc.kill_steps;
-    stats->killing_capped = (long long)hc.kill_capped;
-    for (int k = 0; k < 3; k++) stats->origin[k] = ext ? hc.origin[k] : 0.0;
-    stats->rmax = ext ? hc.rmax_ext : m->rmax;
-    stats->device_error = hc.err;
-    if (hc.err & kErrNoOrigin) {
-        set_error("mcs_estimate_dtn: no interior tangent ball to place the inversion centre");
-        return MCS_ERR_NO_INTERIOR_POINT;
+    return s;
+}
+
+mcs_status mcs_graph_create(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                            size_t workspace_bytes, mcs_graph *out) {
+    MCS_ARG(out != nullptr, "mcs_graph_create: NULL output handle");
+    *out = nullptr;
+    mcs_graph g = new (std::nothrow) mcs_graph_s;
+    if (!g) { set_error("mcs_graph_create: host allocation failed"); return MCS_ERR_OOM; }
+    mcs_status s = make_batch(items, n, p, workspace, workspace_bytes, g->b, "mcs_graph_create");
+    if (s == MCS_OK) s = batch_hist_prepare(g->b);
+    int tpb = 0, bps = 0;
+    if (s == MCS_OK) s = walk_residency(p, g->b.mode, n > 1, &tpb, &bps);  // occupancy queried before capture
+    if (s != MCS_OK) { delete g; return s; }
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "mcs_graph_create: cudaStreamCreateWithFlags"); }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        delete g;
+        return cuda_fail(e, "mcs_graph_create: cudaStreamBeginCapture");
     }
-    if (hc.err & kErrNoHit) {
-        char buf[256];
-        snprintf(buf, sizeof buf,
-                 "mcs_estimate_dtn: a walk query found no triangle (kind %d, killing %d, walk %llu, step %d, "
-                 "x~ = (%.9g, %.9g, %.9g)); walk retired as lost",
-                 hc.diag_kind, hc.diag_killing, hc.diag_walk, hc.diag_step, hc.diag_p[0], hc.diag_p[1], hc.diag_p[2]);
-        set_error(buf);
-        return MCS_ERR_DEVICE;
+    const unsigned long long before = g_launches.load();
+    s = enqueue_batch(g->b, cs, nullptr);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    // captured kernels run at each replay, not here
+    g->launches = g_launches.load() - before;
+    g_launches.fetch_sub(g->launches);
+    cudaStreamDestroy(cs);
+    if (s != MCS_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete g;
+        return s != MCS_OK ? s : cuda_fail(e, "mcs_graph_create: cudaStreamEndCapture");
     }
-    if (hc.err) {
-        set_error(hc.err & kErrBin ? "mcs_estimate_dtn: tri2bin maps a triangle outside [0, n_rows)"
-                                   : "mcs_estimate_dtn: BVH traversal stack or iteration bound exceeded");
-        return MCS_ERR_DEVICE;
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete g;
+        return cuda_fail(e, "mcs_graph_create: cudaGraphInstantiate");
     }
-    return (hc.capped || hc.kill_capped) ? MCS_WARN_CAPPED : MCS_OK;
+    *out = g;
+    return MCS_OK;
+}
+
+mcs_status mcs_graph_launch(mcs_graph g, void *stream) {
+    MCS_ARG(g != nullptr, "mcs_graph_launch: NULL graph");
+    MCS_CUDA(cudaGraphLaunch(g->exec, as_stream(stream)));
+    note_launch(g->launches);
+    return MCS_OK;
+}
+
+mcs_status mcs_graph_stats(mcs_graph g, mcs_stats *total, mcs_stats *per_item, void *stream) {
+    MCS_ARG(g != nullptr, "mcs_graph_stats: NULL graph");
+    return batch_stats(g->b, total, per_item, as_stream(stream), "mcs_graph_stats");
+}
+
+size_t mcs_graph_nodes(mcs_graph g) {
+    if (!g || !g->graph) return 0;
+    size_t k = 0;
+    if (cudaGraphGetNodes(g->graph, nullptr, &k) != cudaSuccess) return 0;
+    return k;
+}
+
+void mcs_graph_destroy(mcs_graph g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
+                              size_t workspace_bytes, double sample_fraction, mcs_params *tuned,
+                              mcs_tune_trial *trials, int max_trials, int *n_trials, void *stream_) {
+    const std::string f = "mcs_autotune_walks";
+    MCS_ARG(tuned != nullptr, f + ": NULL tuned params");
+    MCS_ARG(sample_fraction > 0.0 && sample_fraction <= 1.0, f + ": sample_fraction must be in (0, 1]");
+    MCS_ARG(max_trials >= 0 && (max_trials == 0 || trials != nullptr), f + ": NULL trials");
+    Batch b;
+    mcs_status s = make_batch(items, n, p, workspace, workspace_bytes, b, f.c_str());
+    if (s != MCS_OK) return s;
+    cudaStream_t st = as_stream(stream_);
+    int count = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MCS_CUDA(cudaEventCreate(&e0));
+    MCS_CUDA(cudaEventCreate(&e1));
+    auto cleanup = [&]() { cudaEventDestroy(e0); cudaEventDestroy(e1); };
+    int cur_rows = -1;
+    // sample: the first rows of every mesh (in the candidate's row order), no killing walks
+    auto trial = [&](const mcs_params &q, float *ms) -> mcs_status {
+        mcs_status r;
+        if ((q.queue_order & 1) != cur_rows) {
+            for (const Plan &pl : b.plans)
+                if ((r = (cur_rows < 0 ? enqueue_setup(pl, q.queue_order, st) : enqueue_order(pl, q.queue_order, st))) !=
+                    MCS_OK)
+                    return r;
+            cur_rows = q.queue_order & 1;
+        }
+        Batch bq = b;
+        bq.p = q;
+        std::vector<WalkJob> jobs;
+        for (int i : job_order(bq)) {
+            const Plan &pl = b.plans[i];
+            const unsigned long long rows =
+                std::max<unsigned long long>(1, (unsigned long long)std::ceil(sample_fraction * pl.rows.n_rows));
+            jobs.push_back(make_job(pl, std::min<unsigned long long>(rows, pl.rows.n_rows) * pl.W, 0));
+        }
+        if (b.n > 1 && (r = store_jobs(jobs, b.jobs, b.offs, st)) != MCS_OK) return r;
+        int tpb = 0, bps = 0;
+        if ((r = walk_residency(&q, b.mode, b.n > 1, &tpb, &bps)) != MCS_OK) return r;
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            MCS_CUDA(cudaMemsetAsync(b.launch_ctrl(), 0, sizeof(Ctrl), st));
+            MCS_CUDA(cudaEventRecord(e0, st));
+            if ((r = launch_walks(b.jobs, b.offs, b.n, b.n > 1 ? nullptr : &jobs[0], b.launch_ctrl(), &q, b.mode, tpb,
+                                  bps, st)) != MCS_OK)
+                return r;
+            MCS_CUDA(cudaEventRecord(e1, st));
+            MCS_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            MCS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best = std::min(best, ms);
+        }
+        Ctrl hc;
+        MCS_CUDA(cudaMemcpy(&hc, b.launch_ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        if (hc.err) {
+            set_error(f + ": a device error during a tuning launch");
+            return MCS_ERR_DEVICE;
+        }
+        if (count < max_trials) {
+            trials[count].threads_per_block = tpb;
+            trials[count].blocks_per_sm = bps;
+            trials[count].queue_order = q.queue_order;
+            trials[count].ms = best;
+        }
+        count++;
+        *ms = best;
+        return MCS_OK;
+    };
+    // coordinate search: residency (block size x blocks per SM), then queue order
+    mcs_params best = *p;
+    best.queue_order = 0;
+    float best_ms = 1e30f;
+    for (int tpb : {64, 128}) {
+        mcs_params q = best;
+        q.threads_per_block = tpb;
+        q.blocks_per_sm = 0;
+        int t = 0, occ = 0;
+        if ((s = walk_residency(&q, b.mode, n > 1, &t, &occ)) != MCS_OK) { cleanup(); return s; }
+        for (int bps = std::max(1, occ - 2 * (128 / tpb)); bps <= occ; bps += 128 / tpb) {
+            q.blocks_per_sm = bps;
+            float ms = 0.f;
+            if ((s = trial(q, &ms)) != MCS_OK) { cleanup(); return s; }
+            if (ms < best_ms) { best_ms = ms; best.threads_per_block = tpb; best.blocks_per_sm = bps; }
+        }
+    }
+    mcs_params base = best;
+    for (int qo : {1, 2, 3}) {
+        if (qo == 2 && n == 1) continue;
+        if (qo == 3 && n == 1) continue;
+        mcs_params q = base;
+        q.queue_order = qo;
+        float ms = 0.f;
+        if ((s = trial(q, &ms)) != MCS_OK) { cleanup(); return s; }
+        if (ms < best_ms) { best_ms = ms; best.queue_order = qo; }
+    }
+    cleanup();
+    *tuned = best;
+    if (n_trials) *n_trials = count;
+    return MCS_OK;
 }
 
 }  // extern "C"

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 
 #include "../../include/mcsteklov.h"
@@ -33,9 +35,13 @@ struct mcs_mesh_s {
 
 namespace mcs {
 void set_error(const std::string &msg);
+std::string get_error();
 mcs_status cuda_fail(cudaError_t e, const char *what);
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 int num_sms();
+// kernels of this library enqueued since it was loaded (mcs_launch_count)
+extern std::atomic<unsigned long long> g_launches;
+inline void note_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace mcs
 
 #define MCS_CUDA(call)                                                      \

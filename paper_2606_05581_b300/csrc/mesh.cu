@@ -21,10 +21,13 @@ namespace mcs {
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
+std::string get_error() { return g_err; }
 mcs_status cuda_fail(cudaError_t e, const char *what) {
     g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? MCS_ERR_OOM : MCS_ERR_CUDA;
 }
+std::atomic<unsigned long long> g_launches{0};
+
 int num_sms() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -302,6 +305,8 @@ extern "C" {
 const char *mcs_last_error(void) { return g_err.c_str(); }
 const char *mcs_version(void) { return "mcsteklov 0.1 (sm_103a)"; }
 
+unsigned long long mcs_launch_count(void) { return mcs::g_launches.load(std::memory_order_relaxed); }
+
 void mcs_mesh_destroy(mcs_mesh m) { mesh_free(m); }
 int mcs_mesh_nv(mcs_mesh m) { return m ? m->nv : 0; }
 int mcs_mesh_nf(mcs_mesh m) { return m ? m->nf : 0; }
@@ -348,8 +353,11 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     double *d_box = (double *)talloc(sizeof(double) * 6);
     if (!d_bad || !d_part || !d_box) return fail(MCS_ERR_OOM);
     MB_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
+    note_launch();
     k_validate<<<num_sms() * 4, 256, 0, st>>>(m->V, nv, m->F, nf, d_bad);
+    note_launch();
     k_bounds_partial<<<nbp, 256, 0, st>>>(m->V, nv, d_part);
+    note_launch();
     k_bounds_final<<<1, 32, 0, st>>>(d_part, nbp, d_box);
     int bad = 0;
     double box[6];
@@ -383,6 +391,7 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     unsigned long long *keys_s = (unsigned long long *)talloc(sizeof(unsigned long long) * nf);
     if (!keys || !keys_s) return fail(MCS_ERR_OOM);
     const int tb = 256;
+    note_launch();
     k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, fr, keys);
     size_t sort_bytes = 0, sort_bytes2 = 0;
     cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes, keys, keys_s, nf, 0, 62, st);
@@ -399,6 +408,7 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     MB_CUDA(cudaMalloc(&m->t64, sizeof(Tri64) * nf));
     float *slotbox = (float *)talloc(sizeof(float) * 6 * nf);
     if (!slotbox) return fail(MCS_ERR_OOM);
+    note_launch();
     k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, m->t32, m->t64, slotbox);
     if (nf > 1) {
         int *child = (int *)talloc(sizeof(int) * 2 * (nf - 1));
@@ -410,17 +420,22 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
         MB_CUDA(cudaMemsetAsync(par_i, 0xFF, sizeof(int) * (nf - 1), st));
         MB_CUDA(cudaMemsetAsync(par_l, 0xFF, sizeof(int) * nf, st));
+        note_launch();
         k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, child, par_i, par_l);
+        note_launch();
         k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, child, par_i, par_l, slotbox, nodebox, arrive, d_bad + 1);
         MB_CUDA(cudaMalloc(&m->nodes, sizeof(Node) * (nf - 1)));
+        note_launch();
         k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, child, nodebox, m->nodes);
     }
     // vertex -> incident faces, ascending
     MB_CUDA(cudaMalloc(&m->inc_f, sizeof(int32_t) * 3 * nf));
     MB_CUDA(cudaMalloc(&m->vstart, sizeof(int32_t) * (nv + 1)));
+    note_launch();
     k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
     MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
     MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
+    note_launch();
     k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, m->inc_f, m->vstart);
     MB_CUDA(cudaGetLastError());
     int tree_err = 0;
@@ -441,6 +456,7 @@ mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, v
     MCS_ARG(m != nullptr, "mcs_vertex_rows: mesh is NULL");
     MCS_ARG(pos && nrm && area, "mcs_vertex_rows: NULL output");
     cudaStream_t st = as_stream(stream_);
+    note_launch();
     k_vertex_rows<<<(m->nv + 255) / 256, 256, 0, st>>>(m->V, m->F, m->inc_f, m->vstart, m->nv, pos, nrm, area);
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
@@ -456,6 +472,7 @@ mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, doub
     cudaStream_t st = as_stream(stream_);
     int *d_err = m->err;
     MCS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    note_launch();
     if (prec == 64)
         k_closest_points<double><<<(n + 127) / 128, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
     else
@@ -474,6 +491,7 @@ mcs_status mcs_philox_words(uint64_t start, uint64_t n, uint32_t c2, uint32_t c3
                             uint32_t *out, void *stream_) {
     MCS_ARG(out != nullptr || n == 0, "mcs_philox_words: out is NULL");
     if (n == 0) return MCS_OK;
+    note_launch();
     k_philox<<<num_sms() * 4, 256, 0, as_stream(stream_)>>>(start, n, c2, c3, k0, k1, out);
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;

@@ -326,28 +326,36 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
     const int nf = m->nf, tb = 256;
     MCS_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
     MCS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    note_launch();
     k_centroids<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, cen, farea, mind, owner);
     FpsArgs a;
     a.cen = cen; a.mind = mind; a.owner = owner; a.sel = sel;
     a.cand_v = (double *)(w + L.cand_v); a.cand_i = (int *)(w + L.cand_i);
     a.bar = bar; a.err = err; a.nf = nf; a.ns = n;
     void *args[] = {&a};
+    note_launch();
     MCS_CUDA(cudaLaunchCooperativeKernel((void *)k_fps, dim3(nb), dim3(256), args, 0, st));
     // quadrature areas: faces sorted (stably) by owner, summed in ascending face order
     int32_t *keys = (int32_t *)(w + L.keys), *vals = (int32_t *)(w + L.vals);
     int32_t *skeys = (int32_t *)(w + L.skeys), *svals = (int32_t *)(w + L.svals);
     int32_t *start = (int32_t *)(w + L.start);
+    note_launch();
     k_owner_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(owner, nf, keys, vals);
     size_t sb = L.sort_bytes;
     MCS_CUDA(cub::DeviceRadixSort::SortPairs(w + L.sort, sb, keys, skeys, vals, svals, nf, 0, 32, st));
     MCS_CUDA(cudaMemsetAsync(start, 0, sizeof(int32_t) * (n + 1), st));
+    note_launch();
     k_segments<<<(nf + tb - 1) / tb, tb, 0, st>>>(skeys, nf, n, start);
+    note_launch();
     k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, sel, svals, start, n, pos, nrm, area);
     if (orient) {
         float4 *q = (float4 *)(w + L.q);
         float *partial = (float *)(w + L.partial);
+        note_launch();
         k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(pos, nrm, farea, sel, n, q);
+        note_launch();
         k_gwn<<<dim3((2 * n + 255) / 256, kGwnChunks), 256, 0, st>>>(m->V, m->F, nf, q, 2 * n, partial);
+        note_launch();
         k_orient<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, n, nrm, orient_gap);
     }
     MCS_CUDA(cudaGetLastError());

@@ -1,0 +1,170 @@
+"""Batched estimates: many meshes in one persistent walk launch, plain and
+graph-captured, and the walk-launch autotuner.
+
+Every mesh of a batch must give exactly the outputs of a single-mesh estimate
+with the same parameters, domain and seed (the single-mesh path is itself
+compared with the oracle in test_gpu_parity.py, and one batch item is
+compared with the oracle here directly).
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_05581_b300 as mcs  # noqa: E402
+
+KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "omega", "H0", "Lambda", "exit_tri")
+
+
+def _items():
+    """Uneven meshes and row kinds, interior and exterior (two with killing walks)."""
+    specs = [
+        (meshgen.icosphere(2), "vertex", 0, 11),
+        (meshgen.two_spheres(2, 0.5, 1.5), "vertex", 1, 12),
+        (meshgen.wild_union(6, 5000, seed=9), 300, 0, 13),
+        (meshgen.wild_union(4, 3000, seed=5), 200, 1, 14),
+        (meshgen.icosphere(3, 0.7), "vertex", 1, 15),
+    ]
+    items = []
+    for m, rows, dom, seed in specs:
+        mesh = mcs.Mesh(m.V, m.F)
+        r = mcs.vertex_rows(mesh) if rows == "vertex" else mcs.sample_rows(mesh, rows, orient=True)
+        items.append(dict(mesh=mesh, rows=r, domain=dom, seed=seed, host=m))
+    return items
+
+
+def _single(it, p):
+    q = mcs.default_params(**{f: getattr(p, f) for f, _ in mcs.Params._fields_
+                              if f not in ("domain", "seed", "origin", "origin_auto")})
+    q.domain = it["domain"]
+    q.seed = it["seed"]
+    return mcs.estimate_dtn(it["mesh"], it["rows"], q, assemble=True, record_exits=True)
+
+
+def _assert_same(a, b, ctx):
+    for k in KEYS:
+        x, y = a.get(k), b.get(k)
+        if x is None and y is None:
+            continue
+        if k == "hist_bin" or k == "hist_cnt":
+            # padded CSR: compare the filled part of every row
+            R = a["hist_nnz"].numel()
+            cap = a["cap"]
+            nnz = a["hist_nnz"].cpu().numpy()
+            xa, ya = x.view(R, cap).cpu().numpy(), y.view(R, cap).cpu().numpy()
+            for v in range(R):
+                assert np.array_equal(xa[v, :nnz[v]], ya[v, :nnz[v]]), (ctx, k, v)
+            continue
+        if k == "H0":
+            continue  # compared below for exterior items only
+        assert torch.equal(x, y), (ctx, k)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_batch_equals_single_estimates(prec):
+    items = _items()
+    p = mcs.default_params(walks_per_row=64, prec=prec, killing_walks=1024)
+    b = mcs.Batch(items, p, assemble=True, record_exits=True)
+    status, tot, per = b.run()
+    torch.cuda.synchronize()
+    assert status >= 0
+    steps = 0
+    for i, it in enumerate(items):
+        single = _single(it, p)
+        got = b.result(i)
+        _assert_same(got, single, i)
+        if it["domain"] == 1:
+            assert torch.equal(got["H0"], single["H0"]), i
+        st = single["stats"]
+        for k in ("steps", "capped", "lost", "discarded_rows", "killing_steps", "killing_capped", "walks"):
+            assert per[i][k] == st[k], (i, k)
+        assert per[i]["origin"] == st["origin"]
+        steps += st["steps"]
+    assert tot["steps"] == steps
+    assert tot["walks"] == sum(int(it["rows"]["pos"].shape[0]) * 64 for it in items)
+
+
+def test_batch_item_matches_oracle(oracle):
+    """The interior icosphere of the batch against the oracle directly."""
+    items = _items()
+    p = mcs.default_params(walks_per_row=64, prec=64)
+    b = mcs.Batch(items, p, assemble=False, record_exits=True)
+    b.run()
+    m = items[0]["host"]
+    rows_np = oracle.vertex_rows(m.V, m.F)
+    est = oracle.estimate(m.V, m.F, rows_np, 64, 1e-3, seed=11, prec=64, record_exits=True)
+    res = b.result(0)
+    H = mcs.dense_hist(res, m.nv).cpu().numpy()
+    assert np.array_equal(H, est["H"])
+    assert np.array_equal(res["exit_tri"].cpu().numpy(), est["exit_tri"])
+
+
+def test_graph_launch_repeats_the_batch():
+    items = _items()
+    p = mcs.default_params(walks_per_row=32, prec=32, killing_walks=512)
+    b = mcs.Batch(items, p, assemble=True, record_exits=True)
+    b.run()
+    torch.cuda.synchronize()
+    ref = [{k: (None if v is None else v.clone()) for k, v in b.result(i).items() if isinstance(v, torch.Tensor)}
+           for i in range(len(items))]
+    for i in range(len(items)):
+        for k in ("Lambda", "hist_nnz", "exit_tri", "omega"):
+            b.outputs[i][k].zero_()
+    nodes = b.capture()
+    assert nodes > len(items)
+    for _ in range(2):
+        b.launch()
+    status, tot, per = b.graph_stats()
+    assert status >= 0 and tot["device_error"] == 0
+    for i in range(len(items)):
+        got = b.result(i)
+        for k in ("Lambda", "hist_nnz", "exit_tri", "omega"):
+            assert torch.equal(got[k], ref[i][k]), (i, k)
+
+
+def test_queue_orders_and_launch_shapes_do_not_change_results():
+    items = _items()[:4]
+    p = mcs.default_params(walks_per_row=32, prec=32, killing_walks=256)
+    b = mcs.Batch(items, p, assemble=False, record_exits=True)
+    b.run()
+    ref = [b.result(i)["exit_tri"].clone() for i in range(len(items))]
+    for qo, tpb, bps in ((1, 64, 3), (2, 128, 2), (3, 96, 1)):
+        q = mcs.default_params(walks_per_row=32, prec=32, killing_walks=256, queue_order=qo,
+                               threads_per_block=tpb, blocks_per_sm=bps)
+        status, tot, per = b.run(q)
+        for i in range(len(items)):
+            assert torch.equal(b.result(i)["exit_tri"], ref[i]), (qo, i)
+
+
+def test_autotuner_returns_a_valid_shape_and_same_results():
+    items = _items()
+    p = mcs.default_params(walks_per_row=64, prec=32, killing_walks=512)
+    b = mcs.Batch(items, p, assemble=False, record_exits=True)
+    b.run()
+    ref = [b.result(i)["exit_tri"].clone() for i in range(len(items))]
+    tuned, trials = b.autotune(sample_fraction=0.25)
+    assert len(trials) >= 4
+    assert all(t["ms"] > 0 for t in trials)
+    assert tuned.threads_per_block in (64, 128) and tuned.blocks_per_sm >= 1
+    assert 0 <= tuned.queue_order <= 3
+    best = min(trials, key=lambda t: t["ms"])
+    assert (best["threads_per_block"], best["blocks_per_sm"], best["queue_order"]) == \
+        (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order)
+    b.run()
+    for i in range(len(items)):
+        assert torch.equal(b.result(i)["exit_tri"], ref[i]), i
+
+
+def test_batch_argument_errors():
+    items = _items()[:2]
+    with pytest.raises(mcs.MCSError):
+        mcs.Batch(items, mcs.default_params(walks_per_row=7)).run()
+    bad = [dict(items[0], domain=5)]
+    with pytest.raises(mcs.MCSError):
+        mcs.Batch(bad, mcs.default_params(walks_per_row=8)).run()
