@@ -125,6 +125,7 @@ typedef struct {
     double  *center;     /* n_list x 3: ball centre (inverted for exterior)   */
     int64_t *steps;      /* n_list: closest-point queries                     */
     int64_t *capped;     /* n_list                                            */
+    int64_t *lost;       /* n_list: walks retired without a hit (exterior)    */
     int32_t *H0;         /* n_rows: killing-walk hits                         */
     int64_t *kill_stats; /* [steps, capped, lost]                             */
     int32_t *exit_tri;   /* optional n_list x W: exit triangle                */
@@ -153,6 +154,7 @@ typedef struct {
     double iw0;      /* 1 / sin(theta0/2) */
     double rmax;     /* tangent ball radius clamp */
     double rho0max;  /* exterior: radius of the empty ball at the inverted origin */
+    double esc2;     /* exterior: |x~|^2 beyond which a walk has left the exterior's image */
 } orc_ctx;
 
 static void build_tris(orc_ctx *cx)
@@ -430,6 +432,7 @@ static int walk_ext64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
     for (int k = 1;; k++) {
         double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
         double rho;
+        if (r2 > cx->esc2) { *lost = 1; ex->f = -1; return -1; }  /* escaped (reading R17) */
         if (r2 == 0.0) {
             rho = cx->rho0max;
             if (k == pb->max_steps) { *capped = 1; *lost = 1; return -1; }
@@ -463,10 +466,12 @@ static int walk_ext32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
     const float of[3] = {(float)pb->origin[0], (float)pb->origin[1], (float)pb->origin[2]};
     const float eps2 = (float)(2.0 * pb->eps);
     const float r0max = (float)cx->rho0max;
+    const float esc2 = (float)cx->esc2;
     float x[3] = {z[0], z[1], z[2]};
     for (int k = 1;; k++) {
         float r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
         float rho;
+        if (r2 > esc2) { *lost = 1; ex->f = -1; return -1; }  /* escaped (reading R17) */
         if (r2 == 0.0f) {
             rho = r0max;
             if (k == pb->max_steps) { *capped = 1; *lost = 1; return -1; }
@@ -649,6 +654,21 @@ static double rho0max_of(const orc_problem *pb)
     return 1.0 / m;
 }
 
+/* Exterior walks live in the Kelvin image of the unbounded component of the
+ * complement of the surface.  The inversion centre o lies in a bounded
+ * component, and the ball B(o, dist(o)) holds no surface point, so it lies in
+ * o's component too: no point of the exterior is closer to o than dist(o),
+ * and the exterior's image satisfies |x~| <= 1/dist(o).  A walk found at
+ * |x~| > 2/dist(o) is in o's own component (it started in a pocket of a
+ * self-overlapping surface that contains o, or crossed the surface); it can
+ * never reach the eps-shell of the exterior's boundary and would run off to
+ * |x~| = infinity, so it is retired without a hit (reading R17). */
+static double esc2_of(const orc_ctx *cx)
+{
+    const double d = dist64(cx, cx->pb->origin);
+    return d > 0.0 ? 4.0 / (d * d) : INFINITY;
+}
+
 static void ctx_init(orc_ctx *cx, const orc_problem *pb)
 {
     cx->pb = pb;
@@ -656,6 +676,7 @@ static void ctx_init(orc_ctx *cx, const orc_problem *pb)
     cx->iw0 = 1.0 / sin(pb->cap_deg * (M_PI / 360.0));
     cx->rmax = rmax_of(pb);
     cx->rho0max = pb->exterior ? rho0max_of(pb) : 0.0;
+    cx->esc2 = pb->exterior ? esc2_of(cx) : INFINITY;
 }
 static void ctx_free(orc_ctx *cx)
 {
@@ -700,6 +721,7 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
         res->discarded[li] = disc;
         res->steps[li] = 0;
         res->capped[li] = 0;
+        if (res->lost) res->lost[li] = 0;
         if (disc) {
             res->Mjump[li] = 0.0;
             if (res->exit_tri)
@@ -729,6 +751,7 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
                                    : walk_int64(&cx, k0, k1, g, z, &res->steps[li], &capped, &ex);
             }
             res->capped[li] += capped;
+            if (res->lost) res->lost[li] += lost;
             if (bin >= 0) Hrow[bin] += 1;
             if (res->exit_tri) {
                 size_t e = (size_t)li * pb->walks + j;

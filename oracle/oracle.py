@@ -61,7 +61,8 @@ class _Problem(C.Structure):
 
 class _Result(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("H", "Mjump", "kfac", "discarded", "r_t", "rho", "center",
-                                          "steps", "capped", "H0", "kill_stats", "exit_tri", "exit_bary")]
+                                          "steps", "capped", "lost", "H0", "kill_stats", "exit_tri",
+                                          "exit_bary")]
 
 
 def lib():
@@ -249,8 +250,10 @@ def estimate(V, F, rows, walks: int, eps: float, exterior: bool = False, origin=
 
     Returns a dict with the hit histogram H (len(row_list) x n_rows, int32),
     per-row jump mass M, exterior factor |s~|^3, discard flags, tangent-ball
-    data, query counts, and (exterior, killing_walks > 0) the killing
-    histogram H0 over all n_rows bins."""
+    data, query counts, capped and lost (retired without a hit: exterior
+    walks that left the image of the exterior, reading R17) walk counts, and
+    (exterior, killing_walks > 0) the killing histogram H0 over all n_rows
+    bins and kill_stats = [steps, capped, lost] of the killing walks."""
     if walks <= 0 or walks % 2:
         raise ValueError("walks per row must be a positive even number (antithetic pairs)")
     pb, keep = _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, row_list, n_threads,
@@ -259,7 +262,7 @@ def estimate(V, F, rows, walks: int, eps: float, exterior: bool = False, origin=
     out = dict(H=np.zeros((nl, nr), np.int32), M=np.zeros(nl), kfac=np.zeros(nl),
                discarded=np.zeros(nl, np.int32), r_t=np.zeros(nl), rho=np.zeros(nl),
                center=np.zeros((nl, 3)), steps=np.zeros(nl, np.int64), capped=np.zeros(nl, np.int64),
-               H0=np.zeros(nr, np.int32), kill_stats=np.zeros(3, np.int64))
+               lost=np.zeros(nl, np.int64), H0=np.zeros(nr, np.int32), kill_stats=np.zeros(3, np.int64))
     if record_exits:
         out["exit_tri"] = np.zeros((nl, walks), np.int32)
         out["exit_bary"] = np.zeros((nl, walks, 3))
@@ -268,7 +271,7 @@ def estimate(V, F, rows, walks: int, eps: float, exterior: bool = False, origin=
         res.exit_tri, res.exit_bary = _p(out["exit_tri"]), _p(out["exit_bary"])
     for name, key in (("H", "H"), ("Mjump", "M"), ("kfac", "kfac"), ("discarded", "discarded"),
                       ("r_t", "r_t"), ("rho", "rho"), ("center", "center"), ("steps", "steps"),
-                      ("capped", "capped"), ("H0", "H0"), ("kill_stats", "kill_stats")):
+                      ("capped", "capped"), ("lost", "lost"), ("H0", "H0"), ("kill_stats", "kill_stats")):
         setattr(res, name, _p(out[key]))
     lib().orc_estimate(C.byref(pb), C.byref(res))
     out["row_list"] = np.arange(nr, dtype=np.int32) if row_list is None else np.asarray(row_list, np.int32)

@@ -411,3 +411,29 @@ def test_exterior_walks_stay_in_the_exterior(oracle, prec):
     # the inverted balls exclude the inversion centre: |c~| > rho~
     ok = est["discarded"] == 0
     assert np.all(np.linalg.norm(est["center"][ok], axis=1) > est["rho"][ok])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_exterior_walks_in_the_origin_component_escape(oracle, prec):
+    """Reading R17.  Nested spheres A (R = 1) and B (R = 0.3), both outward,
+    inversion centre in the gap between them.  Exterior walks of A's rows live
+    in the true exterior: none is retired.  B's rows face the gap, a bounded
+    component that contains the centre: its Kelvin image is unbounded, and
+    walks that wander towards the centre are retired as escaped instead of
+    running to the step cap (FP64) or overflowing (FP32).  Every walk ends:
+    with a hit or escaped, none capped."""
+    A = meshgen.icosphere(3, 1.0)
+    B = meshgen.icosphere(3, 0.3)
+    V = np.concatenate([A.V, B.V])
+    F = np.concatenate([A.F, B.F + A.nv])
+    rows = oracle.vertex_rows(V, F)
+    W = 16
+    est = oracle.estimate(V, F, rows, W, 1e-3, exterior=True, origin=np.array([0.65, 0.0, 0.0]), seed=5,
+                          prec=prec)
+    nA = A.nv
+    lost, capped, disc = est["lost"], est["capped"], est["discarded"].astype(bool)
+    assert capped.sum() == 0
+    assert lost[:nA].sum() == 0
+    assert lost[nA:].sum() > 0
+    kept = ~disc
+    assert np.array_equal(est["H"].sum(1)[kept] + lost[kept], np.full(kept.sum(), W))
