@@ -155,6 +155,8 @@ typedef struct {
     double rmax;     /* tangent ball radius clamp */
     double rho0max;  /* exterior: radius of the empty ball at the inverted origin */
     double esc2;     /* exterior: |x~|^2 beyond which a walk has left the exterior's image */
+    double cb[3];    /* interior: centre of the vertices' bounding box */
+    double esc_int2; /* interior: squared box diagonal; a walk farther than this from cb has left the box */
 } orc_ctx;
 
 static void build_tris(orc_ctx *cx)
@@ -370,11 +372,13 @@ static void start32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t gp, in
 /* max_steps queries exits at its current closest point and is counted.      */
 /* ------------------------------------------------------------------------- */
 static int walk_int64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
-                      const double z[3], int64_t *steps, int *capped, orc_exit *ex)
+                      const double z[3], int64_t *steps, int *capped, int *lost, orc_exit *ex)
 {
     const orc_problem *pb = cx->pb;
     double x[3] = {z[0], z[1], z[2]};
     for (int k = 1;; k++) {
+        const double e0 = x[0] - cx->cb[0], e1 = x[1] - cx->cb[1], e2 = x[2] - cx->cb[2];
+        if (e0 * e0 + e1 * e1 + e2 * e2 > cx->esc_int2) { *lost = 1; ex->f = -1; return -1; }  /* R18 */
         int f; double bary[3];
         double d = sqrt(closest_brute64(cx, x, &f, bary));
         (*steps)++;
@@ -390,12 +394,16 @@ static int walk_int64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
     }
 }
 static int walk_int32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t g,
-                      const float z[3], int64_t *steps, int *capped, orc_exit *ex)
+                      const float z[3], int64_t *steps, int *capped, int *lost, orc_exit *ex)
 {
     const orc_problem *pb = cx->pb;
     const float eps2 = (float)(2.0 * pb->eps);
+    const float cb[3] = {(float)cx->cb[0], (float)cx->cb[1], (float)cx->cb[2]};
+    const float esc = (float)cx->esc_int2;
     float x[3] = {z[0], z[1], z[2]};
     for (int k = 1;; k++) {
+        const float e0 = x[0] - cb[0], e1 = x[1] - cb[1], e2 = x[2] - cb[2];
+        if (e0 * e0 + e1 * e1 + e2 * e2 > esc) { *lost = 1; ex->f = -1; return -1; }  /* R18 */
         int f; float bary[3];
         float d = sqrtf(closest_brute32(cx, x, &f, bary));
         (*steps)++;
@@ -669,9 +677,30 @@ static double esc2_of(const orc_ctx *cx)
     return d > 0.0 ? 4.0 / (d * d) : INFINITY;
 }
 
+/* Interior walks live in bounded components of the complement of the
+ * surface, all inside the bounding box of the vertices.  A walk farther from
+ * the box centre than the box diagonal (twice the box's circumradius) is in
+ * the unbounded component -- its row's inward side faces outward (a face
+ * whose orientation repair failed) -- and could only come back by chance; it
+ * is retired without a hit (reading R18). */
+static void interior_bound(orc_ctx *cx)
+{
+    const orc_problem *pb = cx->pb;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < pb->nv; v++)
+        for (int i = 0; i < 3; i++) {
+            if (pb->V[3 * v + i] < lo[i]) lo[i] = pb->V[3 * v + i];
+            if (pb->V[3 * v + i] > hi[i]) hi[i] = pb->V[3 * v + i];
+        }
+    for (int i = 0; i < 3; i++) cx->cb[i] = 0.5 * (lo[i] + hi[i]);
+    const double s0 = hi[0] - lo[0], s1 = hi[1] - lo[1], s2 = hi[2] - lo[2];
+    cx->esc_int2 = s0 * s0 + s1 * s1 + s2 * s2;
+}
+
 static void ctx_init(orc_ctx *cx, const orc_problem *pb)
 {
     cx->pb = pb;
+    interior_bound(cx);
     build_tris(cx);
     cx->iw0 = 1.0 / sin(pb->cap_deg * (M_PI / 360.0));
     cx->rmax = rmax_of(pb);
@@ -743,12 +772,12 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
                 float z[3];
                 start32(&cx, k0, k1, gp, j & 1, cf, rf, nf3, z);
                 bin = pb->exterior ? walk_ext32(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex)
-                                   : walk_int32(&cx, k0, k1, g, z, &res->steps[li], &capped, &ex);
+                                   : walk_int32(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex);
             } else {
                 double z[3];
                 start64(&cx, k0, k1, gp, j & 1, c, rho, nb, z);
                 bin = pb->exterior ? walk_ext64(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex)
-                                   : walk_int64(&cx, k0, k1, g, z, &res->steps[li], &capped, &ex);
+                                   : walk_int64(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex);
             }
             res->capped[li] += capped;
             if (res->lost) res->lost[li] += lost;
@@ -824,10 +853,10 @@ int orc_walk_from_points(const orc_problem *pb, const double *X, int npts,
             if (pb->prec == 32) {
                 float zf[3] = {(float)z[0], (float)z[1], (float)z[2]};
                 if (pb->exterior) walk_ext32(&cx, k0, k1, g, zf, &s1, &capped, &lost, &ex);
-                else walk_int32(&cx, k0, k1, g, zf, &s1, &capped, &ex);
+                else walk_int32(&cx, k0, k1, g, zf, &s1, &capped, &lost, &ex);
             } else {
                 if (pb->exterior) walk_ext64(&cx, k0, k1, g, z, &s1, &capped, &lost, &ex);
-                else walk_int64(&cx, k0, k1, g, z, &s1, &capped, &ex);
+                else walk_int64(&cx, k0, k1, g, z, &s1, &capped, &lost, &ex);
             }
             size_t e = (size_t)i * pb->walks + j;
             exit_tri[e] = ex.f;

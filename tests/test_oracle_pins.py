@@ -437,3 +437,24 @@ def test_exterior_walks_in_the_origin_component_escape(oracle, prec):
     assert lost[nA:].sum() > 0
     kept = ~disc
     assert np.array_equal(est["H"].sum(1)[kept] + lost[kept], np.full(kept.sum(), W))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_interior_walks_in_the_unbounded_component_are_retired(oracle, prec):
+    """Reading R18.  An inside-out sphere: every row's inward normal points out,
+    so the interior walks start in the unbounded component.  3-D Brownian
+    motion is transient; the walks that wander off are retired once they are
+    farther from the box centre than the box diagonal, instead of running to
+    the step cap (FP64) or overflowing (FP32).  Every walk ends: hit or
+    retired, none capped; a right-side-out sphere retires none."""
+    m = meshgen.icosphere(3, 1.0)
+    flipped = m.F[:, ::-1].copy()
+    W = 16
+    for F, inside_out in ((flipped, True), (m.F, False)):
+        rows = oracle.vertex_rows(m.V, F)
+        est = oracle.estimate(m.V, F, rows, W, 1e-3, seed=3, prec=prec)
+        lost, capped = est["lost"], est["capped"]
+        assert capped.sum() == 0
+        assert (lost.sum() > 0) == inside_out
+        kept = ~est["discarded"].astype(bool)
+        assert np.array_equal(est["H"].sum(1)[kept] + lost[kept], np.full(kept.sum(), W))
