@@ -1045,7 +1045,8 @@ void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int
 {
     (void)nv;
     double *cen = (double *)malloc(sizeof(double) * 3 * (size_t)nf);
-    double *mind = (double *)malloc(sizeof(double) * (size_t)nf);
+    float *cenf = (float *)malloc(sizeof(float) * 3 * (size_t)nf);
+    float *mind = (float *)malloc(sizeof(float) * (size_t)nf);
     double *far_ = (double *)malloc(sizeof(double) * (size_t)nf);
     for (int f = 0; f < nf; f++) {
         const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
@@ -1056,17 +1057,22 @@ void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int
         N[1] = ab[2] * ac[0] - ab[0] * ac[2];
         N[2] = ab[0] * ac[1] - ab[1] * ac[0];
         far_[f] = 0.5 * sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        for (int i = 0; i < 3; i++) cenf[3 * f + i] = (float)cen[3 * f + i];
         mind[f] = INFINITY;
         tri2bin[f] = -1;
     }
+    /* greedy farthest points in single precision on the float-rounded
+     * centroids (reading R16): the squared distance is ((dx dx + dy dy) + dz dz)
+     * in float; a face's owner is the first sample strictly nearest; the next
+     * sample is the face with the largest distance, lowest face id on ties */
     sel[0] = 0;
     for (int i = 0; i < ns; i++) {
-        const double *q = cen + 3 * sel[i];
+        const float *q = cenf + 3 * sel[i];
         int arg = 0;
-        double best = -1.0;
+        float best = -1.0f;
         for (int f = 0; f < nf; f++) {
-            double d[3] = {cen[3 * f] - q[0], cen[3 * f + 1] - q[1], cen[3 * f + 2] - q[2]};
-            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            float d[3] = {cenf[3 * f] - q[0], cenf[3 * f + 1] - q[1], cenf[3 * f + 2] - q[2]};
+            float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (d2 < mind[f]) { mind[f] = d2; tri2bin[f] = i; }
             if (mind[f] > best) { best = mind[f]; arg = f; }
         }
@@ -1096,6 +1102,7 @@ void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int
         for (int k = 0; k < 3; k++) nrm[3 * i + k] = n[k];
     }
     free(cen);
+    free(cenf);
     free(mind);
     free(far_);
 }

@@ -176,9 +176,11 @@ def test_fps_rows_are_greedy_farthest_points(oracle):
     cen = m.V[m.F].mean(1)
     sel = r["sel"]
     assert sel[0] == 0 and len(set(sel.tolist())) == 64
+    # each choice is the farthest face up to single-precision rounding of the
+    # squared distances (the sampling runs in float)
     for i in range(1, 64):
         dmin = np.min(np.sum((cen[:, None, :] - cen[sel[:i]][None]) ** 2, -1), 1)
-        assert np.isclose(dmin[sel[i]], dmin.max(), rtol=1e-12, atol=0)
+        assert dmin[sel[i]] >= dmin.max() * (1 - 1e-5)
     owner = np.argmin(np.sum((cen[:, None, :] - cen[sel][None]) ** 2, -1), 1)
     assert np.mean(owner == r["tri2bin"]) > 0.999
     a, b, c = (m.V[m.F[:, k]] for k in range(3))
