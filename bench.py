@@ -170,7 +170,7 @@ def run_ours(args, rank, world):
     n_rows = 10_000 if wild else m.nv
     kill = 0 if wild else 64 * W
     pkw = dict(walks_per_row=W, prec=args.prec, domain=0 if wild else 1, killing_walks=kill,
-               seed=rank + (1 if wild else 0))
+               seed=replica_seed(rank, 1 if wild else 0), bvh_layout=args.bvh_layout)
     params = mcs.default_params(timing=1, **pkw)
     ws = mcs.Workspace()
     rows_ws = mcs.Workspace()
@@ -190,6 +190,8 @@ def run_ours(args, rank, world):
         e3 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         mesh = mcs.Mesh(V, F)
+        if args.bvh_layout == 4:
+            mesh.build_wide()
         rows = make_rows(mesh)
         e1.record(stream)
         res = mcs.estimate_dtn(mesh, rows, params, workspace=ws)
@@ -256,6 +258,8 @@ def run_ours(args, rank, world):
         return None
     # work counts of the same walks (identical seed -> identical walks), untimed
     mesh = mcs.Mesh(V_d, F_d)
+    if args.bvh_layout == 4:
+        mesh.build_wide()
     rows = make_rows(mesh)
     cst = mcs.estimate_dtn(mesh, rows, mcs.default_params(timing=1, count_work=1, **pkw), workspace=ws)["stats"]
     walk_ms = float(np.mean([s["phase_ms"][1] for s in stats]))
@@ -301,10 +305,13 @@ def _batch_setup(args, dev, rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     items = []
-    rows_ws = mcs.Workspace()
-    for i, h in enumerate(hosts):
+    meshes = []
+    for h in hosts:
         mesh = mcs.Mesh(h.V, h.F)
-        rows = mcs.sample_rows(mesh, 1024, orient=True, workspace=rows_ws)
+        if args.bvh_layout != 2:
+            mesh.build_wide()  # the autotuner tries both layouts
+        meshes.append(mesh)
+    for i, (mesh, rows) in enumerate(zip(meshes, mcs.sample_rows_batched(meshes, 1024, orient=True))):
         rows = {k: v for k, v in rows.items() if k in ("pos", "nrm", "area", "tri2bin")}
         items.append(dict(mesh=mesh, rows=rows, domain=i % 2, seed=i + 1_000_000 * rank))
     e1.record()
@@ -319,7 +326,7 @@ def run_batch(args, rank, world):
     torch.cuda.set_device(dev)
     W = args.walks or 512
     hosts, items, t_gen, prep_ms = _batch_setup(args, dev, rank)
-    params = mcs.default_params(walks_per_row=W, prec=args.prec, killing_walks=64 * W)
+    params = mcs.default_params(walks_per_row=W, prec=args.prec, killing_walks=64 * W, bvh_layout=args.bvh_layout)
     b = mcs.Batch(items, params, assemble=True)
     t0 = time.time()
     tuned, trials = b.autotune(sample_fraction=1.0 / 64)
@@ -402,18 +409,20 @@ def _batch_e2e(args, hosts, params, stream):
     import torch
     import paper_2606_05581_b300 as mcs
     VF = [(torch.from_numpy(h.V).pin_memory(), torch.from_numpy(h.F).pin_memory()) for h in hosts]
-    rows_ws = mcs.Workspace()
     torch.cuda.synchronize()
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record(stream)
     h2d = d2h = 0
-    items = []
-    for i, (V, F) in enumerate(VF):
+    meshes = []
+    for V, F in VF:
         mesh = mcs.Mesh(V.to("cuda", non_blocking=True), F.to("cuda", non_blocking=True))
+        if params.bvh_layout == 4:
+            mesh.build_wide()
         h2d += V.numel() * 8 + F.numel() * 4
-        rows = mcs.sample_rows(mesh, 1024, orient=True, workspace=rows_ws)
-        items.append(dict(mesh=mesh, rows=rows, domain=i % 2, seed=i))
+        meshes.append(mesh)
+    items = [dict(mesh=mesh, rows=rows, domain=i % 2, seed=i)
+             for i, (mesh, rows) in enumerate(zip(meshes, mcs.sample_rows_batched(meshes, 1024, orient=True)))]
     b = mcs.Batch(items, params, assemble=True)
     _, tot, _ = b.run()
     outs = []
@@ -480,12 +489,18 @@ def run_precision(args, rank, world):
         for row in table:
             if row["walks_per_row"] == W:
                 row["fp32_fp64_spectrum_rel_diff"] = float(np.max(np.abs(e32 - e64) / np.abs(e64)))
-    # equal error: W each precision needs for the FP32 error at W = 16384, by err ~ c / sqrt(W)
+    # equal error: the walks per row each precision needs for the FP32 error at
+    # W = 16384, by log-log interpolation between the measured points (no
+    # extrapolation beyond them), and the walk time that takes at the
+    # measured walk steps per walk and walk steps per second
     def need(prec, target):
-        rows_ = [r for r in table if r["prec"] == prec]
-        c = np.mean([r["mean_rel_err"] * math.sqrt(r["walks_per_row"]) for r in rows_])
-        return (c / target) ** 2, np.mean([r["walk_steps_per_s"] for r in rows_]), \
-            np.mean([r["walk_steps"] / r["walks_per_row"] for r in rows_])
+        rs = sorted((r for r in table if r["prec"] == prec), key=lambda r: r["walks_per_row"])
+        lw = np.log([r["walks_per_row"] for r in rs])
+        le = np.log([r["mean_rel_err"] for r in rs])
+        # errors fall with W: interpolate W(err) on the decreasing sequence
+        w = float(np.exp(np.interp(np.log(target), le[::-1], lw[::-1])))
+        near = min(rs, key=lambda r: abs(math.log(r["walks_per_row"]) - math.log(w)))
+        return w, near["walk_steps_per_s"], near["walk_steps"] / near["walks_per_row"]
     target = [r for r in table if r["prec"] == 32 and r["walks_per_row"] == 16384][0]["mean_rel_err"]
     w32, sps32, spw32 = need(32, target)
     w64, sps64, spw64 = need(64, target)
@@ -511,13 +526,20 @@ def barrier(world):
 
 
 def allreduce_max(x, world):
+    """Max over the replicas (the job's step time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank, base=0):
+    """Each replica estimates its own problem: the walk seed is offset by the rank."""
+    return base + rank
 
 
 # ---------------------------------------------------------------- the oracle as baseline
@@ -622,6 +644,8 @@ def main():
     ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--bvh-layout", type=int, default=0, choices=[0, 2, 4],
+                    help="BVH node layout of the walk queries: 0 library default, 2 binary, 4 four-wide")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -44,6 +44,7 @@ typedef enum {
     MCS_OK = 0,
     MCS_WARN_CAPPED = 1,            /* some walks hit max_steps (still counted) */
     MCS_WARN_NOT_CONVERGED = 2,     /* eigensolve: residual tolerance not met  */
+    MCS_WARN_LOST = 3,              /* some walks were retired without a hit (stats.lost) */
     MCS_ERR_ARG = -1,
     MCS_ERR_CUDA = -2,
     MCS_ERR_OOM = -3,
@@ -84,6 +85,10 @@ typedef struct {
     int queue_order;        /* walk queue schedule, bit 0: rows in the caller's order instead of
                                Z-order; bit 1 (batches): meshes by descending walk count.
                                Results do not depend on it (counter-based walks). */
+    int bvh_layout;         /* BVH node layout of the walks' closest-point queries: 0 =
+                               default (2), 2 = binary nodes (64 B), 4 = 4-wide nodes (the
+                               binary tree collapsed two levels at a time, 128 B; needs
+                               mcs_mesh_build_wide).  Same results either way. */
 } mcs_params;
 
 /* Rows of the estimate.  Vertex rows: n_rows = nv, tri2bin = NULL, a walk's
@@ -101,8 +106,10 @@ typedef struct {
  * The hit histogram is a padded CSR: row v holds hist_nnz[v] (bin, count)
  * pairs at offset v*cap, bins ascending, counts summing to W (0 for a
  * discarded row).  Lambda (n_rows x n_rows row-major FP64, optional) is the
- * assembled stiffness; omega (optional) the FP64 row weights; H0 (optional,
- * exterior with killing walks) the killing-walk hit counts per column. */
+ * assembled stiffness (Lambda32 its FP32 copy, rounded to nearest, for
+ * consumers that work in FP32); omega (optional) the FP64 row weights; H0
+ * (optional, exterior with killing walks) the killing-walk hit counts per
+ * column. */
 typedef struct {
     int32_t *hist_bin;      /* n_rows * cap                                     */
     int32_t *hist_cnt;      /* n_rows * cap                                     */
@@ -111,10 +118,20 @@ typedef struct {
     double *omega;          /* n_rows, or NULL                                  */
     int32_t *H0;            /* n_rows, or NULL                                  */
     int32_t *exit_tri;      /* optional debug: n_rows * W exit triangle per walk (-1 discarded) */
+    float *Lambda32;        /* optional: n_rows * n_rows FP32 copy of Lambda (needs Lambda) */
 } mcs_outputs;
 
 typedef struct {
-    long long walks, steps, capped, lost, discarded_rows;
+    long long walks, steps, capped;
+    long long lost;         /* walks retired without a hit: exterior walks found at
+                               |x~| > 2 / dist(o), i.e. in the inversion centre's own
+                               component of a self-overlapping surface (they cannot
+                               reach the exterior's boundary); interior walks farther
+                               from the bounding-box centre than the box diagonal, i.e.
+                               in the unbounded component (a row whose inward normal
+                               points out); killing walks capped at x~ = 0.  Row sums
+                               of H are W minus these */
+    long long discarded_rows;
     long long killing_steps, killing_capped;
     double origin[3];       /* exterior inversion centre actually used          */
     double rmax;            /* tangent-ball radius clamp actually used          */
@@ -142,6 +159,12 @@ void mcs_default_params(mcs_params *p);
  * zero-extent bounding box), CUDA, OOM.  Synchronises `stream`. */
 mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream, mcs_mesh *out);
 void mcs_mesh_destroy(mcs_mesh m);
+/* The mesh's 4-wide BVH (mcs_params.bvh_layout = 4): the binary tree
+ * collapsed two levels at a time, built on request (allocates mesh-owned
+ * device memory; synchronises `stream`).  mcs_mesh_has_wide tells whether it
+ * exists (always true for one-triangle meshes). */
+mcs_status mcs_mesh_build_wide(mcs_mesh m, void *stream);
+int mcs_mesh_has_wide(mcs_mesh m);
 int mcs_mesh_nv(mcs_mesh m);
 int mcs_mesh_nf(mcs_mesh m);
 
@@ -153,23 +176,43 @@ mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, v
 
 /* Sample rows (point basis of Sec. 4.4; farthest-point sampling stands in
  * for blue noise): n samples over face centroids by greedy farthest-point
- * sampling from face 0 (FP64, ties -> lowest face id); each face is owned by
+ * sampling from face 0; each face is owned by
  * its nearest sample (first selected on ties): tri2bin; a sample's area is
  * the total area of the faces it owns; its normal is the unit normal of the
  * sampled face, oriented (orient != 0) by the generalized winding number of
  * the other faces at x -/+ delta n, delta = sqrt(face area)/4 (App. A item 1).
  * Device outputs: sel n, pos n x 3, nrm n x 3, area n, tri2bin nf,
- * orient_gap n (optional: GWN(x - delta n) - GWN(x + delta n)).  Needs a
- * cooperative launch; synchronises `stream`. */
+ * orient_gap n (optional: GWN(x - delta n) - GWN(x + delta n)).  The
+ * sampling runs in single precision on the float-rounded centroids (ties ->
+ * lowest face id); meshes above 2^18 faces use a cooperative launch.
+ * Synchronises `stream`. */
 size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n);
 mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,
                            int32_t *tri2bin, float *orient_gap, void *workspace, size_t workspace_bytes,
                            void *stream);
 
+/* Sample rows of many meshes at once: each mesh's farthest-point sampling
+ * runs as one block of a single launch (meshes in parallel), the rest as in
+ * mcs_sample_rows.  Outputs per item as for mcs_sample_rows (orient_gap
+ * optional).  workspace: device, 256-byte aligned, >=
+ * mcs_sample_rows_batched_workspace_size.  Synchronises `stream`. */
+typedef struct {
+    mcs_mesh mesh;
+    int n;
+    int32_t *sel;
+    double *pos, *nrm, *area;
+    int32_t *tri2bin;
+    float *orient_gap;
+} mcs_sample_item;
+size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int count);
+mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int orient, void *workspace,
+                                   size_t workspace_bytes, void *stream);
+
 /* Closest point of n query points (device, n x 3 FP64) by BVH traversal in
- * FP64 (prec 64) or FP32 (prec 32, points rounded to float): squared
- * distance, triangle id (argmin of (d^2, id)), barycentrics.  Device outputs. */
-mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, double *d2, int32_t *tri,
+ * FP64 (prec 64) or FP32 (prec 32, points rounded to float), on the binary
+ * (layout 2) or 4-wide (layout 4) nodes: squared distance, triangle id
+ * (argmin of (d^2, id)), barycentrics.  Device outputs. */
+mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, int layout, double *d2, int32_t *tri,
                               double *bary, void *stream);
 
 /* Workspace bytes needed by mcs_estimate_dtn for these sizes. */
@@ -190,7 +233,8 @@ size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, lo
  *                  with Wsym = (W + W^T)/2 (+ diag of the killing measure).
  * workspace: device, >= mcs_estimate_workspace_size bytes, 256-byte aligned.
  * stats: host, optional; when given the call synchronises `stream`.
- * Returns MCS_WARN_CAPPED when stats are requested and some walk was capped. */
+ * With stats requested, returns MCS_WARN_CAPPED when some walk was capped,
+ * else MCS_WARN_LOST when some walk was retired without a hit (stats.lost). */
 mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *p, const mcs_outputs *out,
                             void *workspace, size_t workspace_bytes, mcs_stats *stats, void *stream);
 
@@ -221,8 +265,7 @@ size_t mcs_estimate_batched_workspace_size(const mcs_batch_item *items, int n, i
  * counters summed over meshes; per_item (host, optional, n entries): each
  * mesh's counters and status fields.  When either is given the call
  * synchronises `stream` and returns the worst status over the meshes
- * (errors before warnings).  A traversal error is reported to the mesh it
- * met and to the later meshes served by the same lane. */
+ * (errors before warnings); the error text names the first failing meshes. */
 mcs_status mcs_estimate_batched(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
                                 size_t workspace_bytes, mcs_stats *total, mcs_stats *per_item, void *stream);
 
@@ -244,16 +287,17 @@ void mcs_graph_destroy(mcs_graph g);
 
 /* Autotuner of the walk launch.  Runs the batch's row setup, then times the
  * walk kernel on a sample (the first ceil(sample_fraction * n_rows) rows of
- * every mesh, no killing walks) for candidate block sizes (64, 128 threads),
- * resident blocks per SM (the three largest residencies the kernel allows)
- * and queue orders (row order, mesh order), by coordinate search; the best
- * two-run minimum wins.  tuned (host) = p with threads_per_block,
- * blocks_per_sm and queue_order set.  trials (host, optional) receives up to
+ * every mesh, no killing walks) for the two BVH node layouts (when
+ * p->bvh_layout is 0), candidate block sizes (64, 128 threads), resident
+ * blocks per SM (the three largest residencies the kernel allows) and queue
+ * orders (row order, mesh order), by coordinate search in that order; the
+ * best two-run minimum wins.  tuned (host) = p with bvh_layout,
+ * threads_per_block, blocks_per_sm and queue_order set.  trials (host, optional) receives up to
  * max_trials entries, n_trials their count.  Synchronises `stream`.  The
  * workspace and outputs are those of the batch; their contents are left
  * undefined (the estimate rewrites them). */
 typedef struct {
-    int threads_per_block, blocks_per_sm, queue_order;
+    int threads_per_block, blocks_per_sm, queue_order, bvh_layout;
     float ms;               /* walk-kernel time of the sample (best of 2)       */
 } mcs_tune_trial;
 mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,

@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 __all__ = ["lib", "Mesh", "default_params", "vertex_rows", "closest_points", "philox_words", "estimate_dtn",
-           "workspace_size", "steklov_modes", "tc_symm_product", "MCSError", "Batch", "sample_rows",
+           "workspace_size", "steklov_modes", "tc_symm_product", "MCSError", "Batch", "sample_rows", "sample_rows_batched",
            "estimate_dtn_noalloc", "dense_hist"]
 
 _LIB_PATH = _build.LIB
@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("origin_auto", C.c_int), ("origin", C.c_double * 3), ("killing_walks", C.c_longlong),
                 ("seed", C.c_uint64), ("walks_per_row", C.c_int), ("blocks_per_sm", C.c_int),
                 ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int),
-                ("queue_order", C.c_int)]
+                ("queue_order", C.c_int), ("bvh_layout", C.c_int)]
 
 
 class Rows(C.Structure):
@@ -44,7 +44,8 @@ class Rows(C.Structure):
 
 class Outputs(C.Structure):
     _fields_ = [("hist_bin", C.c_void_p), ("hist_cnt", C.c_void_p), ("hist_nnz", C.c_void_p),
-                ("Lambda", C.c_void_p), ("omega", C.c_void_p), ("H0", C.c_void_p), ("exit_tri", C.c_void_p)]
+                ("Lambda", C.c_void_p), ("omega", C.c_void_p), ("H0", C.c_void_p), ("exit_tri", C.c_void_p),
+                ("Lambda32", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -60,9 +61,14 @@ class BatchItem(C.Structure):
                 ("origin", C.c_double * 3), ("seed", C.c_uint64), ("out", Outputs)]
 
 
+class SampleItem(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("n", C.c_int), ("sel", C.c_void_p), ("pos", C.c_void_p), ("nrm", C.c_void_p),
+                ("area", C.c_void_p), ("tri2bin", C.c_void_p), ("orient_gap", C.c_void_p)]
+
+
 class TuneTrial(C.Structure):
     _fields_ = [("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("queue_order", C.c_int),
-                ("ms", C.c_float)]
+                ("bvh_layout", C.c_int), ("ms", C.c_float)]
 
 
 class EigParams(C.Structure):
@@ -93,8 +99,10 @@ def lib():
         L.mcs_mesh_destroy.argtypes = [vp]
         L.mcs_mesh_nv.argtypes = [vp]
         L.mcs_mesh_nf.argtypes = [vp]
+        L.mcs_mesh_build_wide.argtypes = [vp, vp]
+        L.mcs_mesh_has_wide.argtypes = [vp]
         L.mcs_vertex_rows.argtypes = [vp, vp, vp, vp, vp]
-        L.mcs_closest_points.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+        L.mcs_closest_points.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp]
         L.mcs_estimate_workspace_size.argtypes = [vp, i32, i32, i64]
         L.mcs_estimate_workspace_size.restype = C.c_size_t
         L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
@@ -103,6 +111,9 @@ def lib():
         L.mcs_sample_rows_workspace_size.argtypes = [vp, i32]
         L.mcs_sample_rows_workspace_size.restype = C.c_size_t
         L.mcs_sample_rows.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+        L.mcs_sample_rows_batched_workspace_size.argtypes = [C.POINTER(SampleItem), i32]
+        L.mcs_sample_rows_batched_workspace_size.restype = C.c_size_t
+        L.mcs_sample_rows_batched.argtypes = [C.POINTER(SampleItem), i32, i32, vp, C.c_size_t, vp]
         L.mcs_estimate_dtn_noalloc_capacity.restype = C.c_size_t
         L.mcs_estimate_dtn_noalloc.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs),
                                                C.POINTER(Stats), vp]
@@ -177,6 +188,11 @@ class Mesh:
         self.nv = int(V.shape[0])
         self.nf = int(F.shape[0])
 
+    def build_wide(self):
+        """Build the 4-wide BVH (bvh_layout 4) of this mesh."""
+        _check(lib().mcs_mesh_build_wide(self.handle, _stream()))
+        return self
+
     def close(self):
         if self.handle:
             lib().mcs_mesh_destroy(self.handle)
@@ -214,13 +230,35 @@ def sample_rows(mesh: Mesh, n: int, orient: bool = True, workspace: "Workspace |
     return dict(pos=pos, nrm=nrm, area=area, tri2bin=t2b, sel=sel, gap=gap)
 
 
-def closest_points(mesh: Mesh, P: torch.Tensor, prec: int = 64):
+def sample_rows_batched(meshes: list, n: int, orient: bool = True) -> list:
+    """Farthest-point sample rows of many meshes, their sampling in one launch."""
+    dev = torch.device("cuda")
+    outs = []
+    arr = (SampleItem * len(meshes))()
+    for i, mesh in enumerate(meshes):
+        o = dict(sel=torch.empty(n, dtype=torch.int32, device=dev),
+                 pos=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                 nrm=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                 area=torch.empty(n, dtype=torch.float64, device=dev),
+                 tri2bin=torch.empty(mesh.nf, dtype=torch.int32, device=dev),
+                 gap=torch.empty(n, dtype=torch.float32, device=dev))
+        arr[i] = SampleItem(mesh.handle, n, o["sel"].data_ptr(), o["pos"].data_ptr(), o["nrm"].data_ptr(),
+                            o["area"].data_ptr(), o["tri2bin"].data_ptr(), o["gap"].data_ptr())
+        outs.append(o)
+    nb = int(lib().mcs_sample_rows_batched_workspace_size(arr, len(meshes)))
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    _check(lib().mcs_sample_rows_batched(arr, len(meshes), int(orient), C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return outs
+
+
+def closest_points(mesh: Mesh, P: torch.Tensor, prec: int = 64, layout: int = 2):
     P = P.to(device="cuda", dtype=torch.float64).contiguous()
     n = P.shape[0]
     d2 = torch.empty(n, dtype=torch.float64, device="cuda")
     tri = torch.empty(n, dtype=torch.int32, device="cuda")
     bary = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    _check(lib().mcs_closest_points(mesh.handle, _ptr(P), n, prec, _ptr(d2), _ptr(tri), _ptr(bary), _stream()))
+    _check(lib().mcs_closest_points(mesh.handle, _ptr(P), n, prec, layout, _ptr(d2), _ptr(tri), _ptr(bary),
+                                    _stream()))
     return d2, tri, bary
 
 
@@ -251,10 +289,10 @@ def _aligned_ptr(buf: torch.Tensor) -> int:
     return (p + 255) & ~255
 
 
-_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri")
+_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri", "Lambda32")
 
 
-def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool) -> dict:
+def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32_copy: bool = False) -> dict:
     cap = min(W, R)
     return dict(hist_bin=torch.empty(R * cap, dtype=torch.int32, device=dev),
                 hist_cnt=torch.empty(R * cap, dtype=torch.int32, device=dev),
@@ -262,7 +300,8 @@ def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool) -> d
                 omega=torch.empty(R, dtype=torch.float64, device=dev),
                 H0=torch.empty(R, dtype=torch.int32, device=dev),
                 Lambda=torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None,
-                exit_tri=torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None)
+                exit_tri=torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None,
+                Lambda32=torch.empty((R, R), dtype=torch.float32, device=dev) if (assemble and fp32_copy) else None)
 
 
 def _rows_struct(rows: dict) -> Rows:
@@ -280,13 +319,14 @@ def _stats_dict(st: Stats) -> dict:
 
 
 def estimate_dtn(mesh: Mesh, rows: dict, params: Params, assemble: bool = True, want_stats: bool = True,
-                 record_exits: bool = False, workspace: Workspace | None = None, outputs: dict | None = None):
+                 record_exits: bool = False, workspace: Workspace | None = None, outputs: dict | None = None,
+                 fp32_copy: bool = False):
     """Run the DtN estimator; returns a dict of device tensors (+ stats)."""
     pos = rows["pos"]
     R = int(pos.shape[0])
     W = int(params.walks_per_row)
     cap = min(W, R)
-    o = outputs or _alloc_outputs(R, W, pos.device, assemble, record_exits)
+    o = outputs or _alloc_outputs(R, W, pos.device, assemble, record_exits, fp32_copy)
     rs = _rows_struct(rows)
     out = _outputs_struct(o)
     nbytes = workspace_size(mesh, R, W, params.killing_walks)
@@ -374,7 +414,8 @@ class Batch:
         self.params = tuned
         self.close_graph()
         out = [dict(threads_per_block=t.threads_per_block, blocks_per_sm=t.blocks_per_sm,
-                    queue_order=t.queue_order, ms=t.ms) for t in trials[:min(nt.value, max_trials)]]
+                    queue_order=t.queue_order, bvh_layout=t.bvh_layout, ms=t.ms)
+               for t in trials[:min(nt.value, max_trials)]]
         return tuned, out
 
     def capture(self):

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <new>
 #include <string>
 #include <vector>
@@ -53,6 +54,8 @@ struct Ctrl {
     double origin[3];
     double rmax_ext;
     double rho0max;
+    double esc2;   // |x~|^2 beyond which an exterior walk has left the exterior's image
+    float origin_f[3], rho0max_f, esc2_f;  // the same, rounded once for FP32 walks
     int argmax_row;
     int pad;
 };
@@ -69,10 +72,9 @@ __device__ __forceinline__ double dist64(const DevMesh &m, double x, double y, d
 }
 
 // ---------------------------------------------------------------- row schedule
-__global__ void k_row_keys(const double *pos, int R, double lx, double ly, double lz, double ix, double iy, double iz,
-                           unsigned long long *keys) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= R) return;
+// Z-order key of row v: 30-bit Morton code of its point in the mesh box, then v
+__device__ unsigned long long row_key(const double *pos, int v, double lx, double ly, double lz, double ix, double iy,
+                                      double iz) {
     auto q = [](double x, double lo, double inv) {
         const double f = fmin(fmax((x - lo) * inv, 0.0), 1.0);
         return min((uint32_t)(f * 1024.0), 1023u);
@@ -87,7 +89,13 @@ __global__ void k_row_keys(const double *pos, int R, double lx, double ly, doubl
     };
     const uint32_t code = (spread(q(pos[3 * v], lx, ix)) << 2) | (spread(q(pos[3 * v + 1], ly, iy)) << 1) |
                           spread(q(pos[3 * v + 2], lz, iz));
-    keys[v] = ((unsigned long long)code << 32) | (unsigned)v;
+    return ((unsigned long long)code << 32) | (unsigned)v;
+}
+__global__ void k_row_keys(const double *pos, int R, double lx, double ly, double lz, double ix, double iy, double iz,
+                           unsigned long long *keys) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= R) return;
+    keys[v] = row_key(pos, v, lx, ly, lz, ix, iy, iz);
 }
 __global__ void k_order_from_keys(const unsigned long long *keys, int R, int32_t *order) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -111,13 +119,9 @@ __device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, dou
     return !warp_query<double, kBelow>(m, x, y, z, thr, h, front, err);
 }
 
-// rows v = i * stride, i = 0, 1, ... (stride 1: every row)
-__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R,
-                                                                int stride, Frame fr, RowBall *ball, Ctrl *ctrl) {
-    __shared__ int fronts[kTanWarps][32];
-    const int v = (blockIdx.x * kTanWarps + (threadIdx.x >> 5)) * stride;
-    if (v >= R) return;
-    int *front = fronts[threadIdx.x >> 5];
+// interior tangent ball of row v, by one warp
+__device__ void tangent_int_row(const DevMesh &m, const double *pos, const double *nrm, int v, const Frame &fr,
+                                RowBall *ball, Ctrl *ctrl, int *front) {
     int err = 0;
     const double s0 = pos[3 * v], s1 = pos[3 * v + 1], s2 = pos[3 * v + 2];
     const double n0 = nrm[3 * v], n1 = nrm[3 * v + 1], n2 = nrm[3 * v + 2];
@@ -153,11 +157,19 @@ __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const
     }
 }
 
+// rows v = i * stride, i = 0, 1, ... (stride 1: every row)
+__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R,
+                                                                int stride, Frame fr, RowBall *ball, Ctrl *ctrl) {
+    __shared__ int fronts[kTanWarps][32];
+    const int v = (blockIdx.x * kTanWarps + (threadIdx.x >> 5)) * stride;
+    if (v >= R) return;
+    tangent_int_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5]);
+}
+
 // largest empty radius over rows 0, stride, 2 stride, ..., lowest row on ties
 // -> inversion centre (any interior point serves; Sec. 4.3)
-__global__ void k_origin_argmax(const RowBall *ball, int R, int stride, Ctrl *ctrl) {
-    __shared__ double sv[1024];
-    __shared__ int si[1024];
+// one block; sv, si: shared arrays of blockDim.x entries (a power of two)
+__device__ void origin_argmax_block(const RowBall *ball, int R, int stride, Ctrl *ctrl, double *sv, int *si) {
     double best = -1.0;
     int bi = 0x7FFFFFFF;
     for (int v = threadIdx.x * stride; v < R; v += blockDim.x * stride) {
@@ -191,14 +203,26 @@ __global__ void k_origin_argmax(const RowBall *ball, int R, int stride, Ctrl *ct
         }
     }
 }
+__global__ void k_origin_argmax(const RowBall *ball, int R, int stride, Ctrl *ctrl) {
+    __shared__ double sv[1024];
+    __shared__ int si[1024];
+    origin_argmax_block(ball, R, stride, ctrl, sv, si);
+}
 __global__ void k_set_origin(Ctrl *ctrl, double x, double y, double z) {
     ctrl->origin[0] = x; ctrl->origin[1] = y; ctrl->origin[2] = z;
 }
 
-// Kelvin-inverted AABB of the vertices (radius clamp) and the radius of the
-// empty ball at the inverted origin, 1 / max |v - o|
-__global__ void k_ext_frame(const double *V, int nv, Ctrl *ctrl) {
-    __shared__ double sm[7][256];
+// Kelvin-inverted AABB of the vertices (radius clamp), the radius of the
+// empty ball at the inverted origin, 1 / max |v - o|, and the escape bound:
+// the inversion centre o lies in a bounded component of the complement of
+// the surface and B(o, dist(o)) holds no surface point, so no exterior point
+// is closer to o than dist(o) and the exterior's image satisfies
+// |x~| <= 1 / dist(o); a walk at |x~| > 2 / dist(o) is in o's own component
+// (a pocket of a self-overlapping surface) and is retired without a hit
+constexpr int kFrameThreads = 256;
+// one block of kFrameThreads threads, after the origin is set
+__device__ void ext_frame_block(const DevMesh &m, const double *V, int nv, Ctrl *ctrl) {
+    __shared__ double sm[7][kFrameThreads];
     const double o0 = ctrl->origin[0], o1 = ctrl->origin[1], o2 = ctrl->origin[2];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.0;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -229,6 +253,25 @@ __global__ void k_ext_frame(const double *V, int nv, Ctrl *ctrl) {
         ctrl->rmax_ext = 0.5 * side;
         ctrl->rho0max = 1.0 / sm[6][0];
     }
+    // dist(o) by one warp (a single thread would visit every triangle alone
+    // when o is equidistant from many of them, as at a sphere's centre)
+    __shared__ int front[32];
+    if (threadIdx.x < 32) {
+        int err = 0;
+        const double d = wdist(m, o0, o1, o2, front, &err);
+        if (threadIdx.x == 0) {
+            ctrl->esc2 = d > 0.0 ? 4.0 / (d * d) : INFINITY;
+            ctrl->origin_f[0] = (float)o0;
+            ctrl->origin_f[1] = (float)o1;
+            ctrl->origin_f[2] = (float)o2;
+            ctrl->rho0max_f = (float)ctrl->rho0max;
+            ctrl->esc2_f = (float)ctrl->esc2;
+            if (err) atomicOr(&ctrl->err, err);
+        }
+    }
+}
+__global__ void __launch_bounds__(kFrameThreads) k_ext_frame(DevMesh m, const double *V, int nv, Ctrl *ctrl) {
+    ext_frame_block(m, V, nv, ctrl);
 }
 
 // exterior tangent ball: the inverted ball B(c~, r) (not containing 0) is the
@@ -249,12 +292,9 @@ __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double n
     return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], onemk * Rp, front, err);
 }
 
-__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const double *pos, const double *nrm, int R,
-                                                                Frame fr, RowBall *ball, Ctrl *ctrl) {
-    __shared__ int fronts[kTanWarps][32];
-    const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
-    if (v >= R) return;
-    int *front = fronts[threadIdx.x >> 5];
+// exterior tangent ball of row v, by one warp
+__device__ void tangent_ext_row(const DevMesh &m, const double *pos, const double *nrm, int v, const Frame &fr,
+                                RowBall *ball, Ctrl *ctrl, int *front) {
     int err = 0;
     const double o[3] = {ctrl->origin[0], ctrl->origin[1], ctrl->origin[2]};
     const double rmax = ctrl->rmax_ext;
@@ -314,6 +354,14 @@ __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const
     }
 }
 
+__global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const double *pos, const double *nrm, int R,
+                                                                Frame fr, RowBall *ball, Ctrl *ctrl) {
+    __shared__ int fronts[kTanWarps][32];
+    const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
+    if (v >= R) return;
+    tangent_ext_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5]);
+}
+
 // ---------------------------------------------------------------- walks
 // One job = the walks of one mesh: its row walks (R x W, in Z-order row
 // position order) followed by its killing walks.  A launch serves a table of
@@ -329,6 +377,9 @@ struct WalkJob {
     Ctrl *ctrl;            // the mesh's control block (origin, Kelvin frame)
     unsigned long long n_rows_walks;  // R * W
     unsigned long long n_kill;        // killing walks after the row walks
+    double box_c[3];                  // interior: centre of the vertices' bounding box
+    double esc_int2;                  // interior: squared box diagonal (reading R18)
+    float box_cf[3], esc_int2f;       // the same, rounded once for FP32 walks
     int R, W;
     uint32_t k0, k1;
     int ext;
@@ -346,6 +397,11 @@ struct MultiArgs {
     int max_steps;
     WalkJob j0;                       // the job of a one-job launch (kernel parameter space)
 };
+
+// a job constant in the walk's precision (FP32 walks read the copy rounded once)
+template <typename T> __device__ __forceinline__ T pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 template <bool MULTI> __device__ __forceinline__ const WalkJob &job_of(const MultiArgs &a, int i) {
     if constexpr (MULTI) return a.jobs[i];
@@ -393,9 +449,15 @@ template <typename T> struct WalkState {
     uint32_t k1;            // Philox key word (killing walks use their own)
 };
 
-// MODE: 0 interior jobs only, 1 exterior jobs only, 2 both (the job decides)
-template <typename T, int MODE, bool COUNT, bool MULTI>
-__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __grid_constant__ MultiArgs a) {
+// MODE: 0 interior jobs only, 1 exterior jobs only, 2 both (the job decides).
+// WIDE: closest-point queries on the 4-wide BVH, else on the binary one
+// (identical results; the node layout is an autotuner knob).
+// FP32 walks are capped at 48 registers for 10 resident blocks per SM: the
+// traversal is latency-bound, and the extra warps outweigh the spills
+// (measured on the two-sphere exterior workload: 80 registers 300 ms,
+// 64: 267 ms, 56: 256 ms, 48: 252 ms, 40: 250-256 ms; identical hit counts).
+template <typename T, int MODE, bool COUNT, bool MULTI, bool WIDE>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __grid_constant__ MultiArgs a) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const T epsT = sizeof(T) == 8 ? (T)a.eps : (T)a.eps2f;  // FP32: re-check below 2 eps
@@ -409,9 +471,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __g
     int cj = -1;
     Work work{0ull, 0ull};
     const unsigned long long total = MULTI ? a.offs[a.n_jobs] : a.j0.n_rows_walks + a.j0.n_kill;
-    // with several jobs, a lane adds its counters to a job's block when it
-    // leaves that job; traversal errors are lane-cumulative, so a lane reports
-    // one to every job it served after meeting it
+    // with several jobs, a lane adds its counters (and error bits) to a job's
+    // block when it leaves that job
     auto flush = [&]() {
         if (cj < 0) return;
         Ctrl *c = job_of<MULTI>(a, cj).ctrl;
@@ -422,6 +483,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __g
         if (n_lost) atomicAdd(&c->lost, (unsigned long long)n_lost);
         if (err) atomicOr(&c->err, err);
         n_steps = n_ksteps = n_capped = n_kcapped = n_lost = 0;
+        err = 0;
+    };
+
+    // x <- x + step u with the step's Philox direction
+    auto advance = [&](T step, const WalkJob &J) {
+        const V3<T> u = direction<T>(J.k0, s.k1, s.g, (uint32_t)s.k);
+        s.x.x = s.x.x + step * u.x;
+        s.x.y = s.x.y + step * u.y;
+        s.x.z = s.x.z + step * u.z;
+        s.k++;
     };
 
     auto finish = [&](const WalkJob &J, int bin, int f, bool capped, bool lost) {
@@ -497,20 +568,47 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __g
         if (!__any_sync(FULL, active || more)) break;
         if (!active) continue;
 
-        // ---- one walk-on-spheres step
+        // ---- one walk-on-spheres step: the query point (exterior: the primal
+        // image of x~), the closest-point query, the decision
         const WalkJob &J = job_of<MULTI>(a, s.job);
-        T step;
-        if (MODE == 0 || (MODE == 2 && !J.ext)) {
-            Hit<T> h;
-            closest<T, COUNT>(J.m, s.x.x, s.x.y, s.x.z, s.prev, h, &err, &work);
-            if (s.kill) n_ksteps++; else n_steps++;
-            if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
-                err |= kErrNoHit;
-                record_nohit(J.ctrl, 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
-                finish(J, -1, -1, true, true);
+        const bool ext = MODE == 1 || (MODE == 2 && J.ext);
+        T qx = s.x.x, qy = s.x.y, qz = s.x.z;
+        if (!ext) {
+            // farther from the box centre than the box diagonal: the walk is in
+            // the unbounded component and is retired without a hit
+            const T e0 = s.x.x - pick<T>(J.box_c[0], J.box_cf[0]), e1 = s.x.y - pick<T>(J.box_c[1], J.box_cf[1]),
+                    e2 = s.x.z - pick<T>(J.box_c[2], J.box_cf[2]);
+            if (e0 * e0 + e1 * e1 + e2 * e2 > pick<T>(J.esc_int2, J.esc_int2f)) {
+                finish(J, -1, -1, false, true);
                 continue;
             }
-            const T d = rsq<T>(h.d2);
+        } else {
+            const Ctrl &C = *J.ctrl;
+            const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
+            if (r2 > pick<T>(C.esc2, C.esc2_f)) { finish(J, -1, -1, false, true); continue; }  // escaped
+            if (r2 == (T)0) {
+                // the empty ball around the inverted origin; no query
+                if (s.k == a.max_steps) { finish(J, -1, -1, true, true); continue; }
+                advance(pick<T>(C.rho0max, C.rho0max_f), J);
+                continue;
+            }
+            const T inv = (T)1 / r2;
+            qx = s.x.x * inv + pick<T>(C.origin[0], C.origin_f[0]);
+            qy = s.x.y * inv + pick<T>(C.origin[1], C.origin_f[1]);
+            qz = s.x.z * inv + pick<T>(C.origin[2], C.origin_f[2]);
+        }
+        Hit<T> h;
+        if (WIDE) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
+        else closest<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
+        if (s.kill) n_ksteps++; else n_steps++;
+        if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
+            err |= kErrNoHit;
+            record_nohit(J.ctrl, ext ? 2 : 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+            finish(J, -1, -1, true, true);
+            continue;
+        }
+        const T d = rsq<T>(h.d2);
+        if (!ext) {
             if (d < epsT || s.k == a.max_steps) {
                 if (sizeof(T) == 8) {
                     finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false);
@@ -524,61 +622,41 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) k_walks(const __g
                 }
             }
             s.prev = h.slot;
-            step = d;
-        } else {
+            advance(d, J);
+            continue;
+        }
+        // exterior: the step radius in inverted coordinates (reading R7)
+        const double r0max64 = J.ctrl->rho0max;
+        const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
+        const T inv = (T)1 / r2;
+        const T xp0 = s.x.x * inv, xp1 = s.x.y * inv, xp2 = s.x.z * inv;
+        const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
+        const T ri = d / (nx * (nx + d));
+        const T r0 = pick<T>(r0max64, J.ctrl->rho0max_f) - rsq<T>(r2);
+        const T rho = ri > r0 ? ri : r0;
+        if (rho < epsT || s.k == a.max_steps) {
+            if (sizeof(T) == 8) {
+                finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false);
+                continue;
+            }
             const double o64[3] = {J.ctrl->origin[0], J.ctrl->origin[1], J.ctrl->origin[2]};
-            const double r0max64 = J.ctrl->rho0max;
-            const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
-            if (r2 == (T)0) {
-                if (s.k == a.max_steps) { finish(J, -1, -1, true, true); continue; }
-                step = (T)r0max64;
-            } else {
-                const T inv = (T)1 / r2;
-                const T xp0 = s.x.x * inv, xp1 = s.x.y * inv, xp2 = s.x.z * inv;
-                Hit<T> h;
-                closest<T, COUNT>(J.m, xp0 + (T)o64[0], xp1 + (T)o64[1], xp2 + (T)o64[2], s.prev, h, &err, &work);
-                if (s.kill) n_ksteps++; else n_steps++;
-                if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
-                    err |= kErrNoHit;
-                    record_nohit(J.ctrl, 2, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
-                    finish(J, -1, -1, true, true);
-                    continue;
-                }
-                const T d = rsq<T>(h.d2);
-                const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
-                const T ri = d / (nx * (nx + d));
-                const T r0 = (T)r0max64 - rsq<T>(r2);
-                const T rho = ri > r0 ? ri : r0;
-                if (rho < epsT || s.k == a.max_steps) {
-                    if (sizeof(T) == 8) {
-                        finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT),
-                               false);
-                        continue;
-                    }
-                    const double xd0 = (double)s.x.x, xd1 = (double)s.x.y, xd2 = (double)s.x.z;
-                    const double r2d = xd0 * xd0 + xd1 * xd1 + xd2 * xd2;
-                    const double invd = 1.0 / r2d;
-                    const double xpd0 = xd0 * invd, xpd1 = xd1 * invd, xpd2 = xd2 * invd;
-                    double b[3];
-                    const double dd = sqrt(recheck64(J.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
-                    const double nxd = sqrt(xpd0 * xpd0 + xpd1 * xpd1 + xpd2 * xpd2);
-                    const double rid = dd / (nxd * (nxd + dd));
-                    const double r0d = r0max64 - sqrt(r2d);
-                    const double rhod = rid > r0d ? rid : r0d;
-                    if (rhod < a.eps || s.k == a.max_steps) {
-                        finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false);
-                        continue;
-                    }
-                }
-                s.prev = h.slot;
-                step = rho;
+            const double xd0 = (double)s.x.x, xd1 = (double)s.x.y, xd2 = (double)s.x.z;
+            const double r2d = xd0 * xd0 + xd1 * xd1 + xd2 * xd2;
+            const double invd = 1.0 / r2d;
+            const double xpd0 = xd0 * invd, xpd1 = xd1 * invd, xpd2 = xd2 * invd;
+            double b[3];
+            const double dd = sqrt(recheck64(J.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
+            const double nxd = sqrt(xpd0 * xpd0 + xpd1 * xpd1 + xpd2 * xpd2);
+            const double rid = dd / (nxd * (nxd + dd));
+            const double r0d = r0max64 - sqrt(r2d);
+            const double rhod = rid > r0d ? rid : r0d;
+            if (rhod < a.eps || s.k == a.max_steps) {
+                finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false);
+                continue;
             }
         }
-        const V3<T> u = direction<T>(J.k0, s.k1, s.g, (uint32_t)s.k);
-        s.x.x = s.x.x + step * u.x;
-        s.x.y = s.x.y + step * u.y;
-        s.x.z = s.x.z + step * u.z;
-        s.k++;
+        s.prev = h.slot;
+        advance(rho, J);
     }
     if constexpr (MULTI) {
         flush();
@@ -654,15 +732,14 @@ constexpr int kHistThreads = 256;
 // one block per sorted row position: shared-memory hit counts of the row's W
 // exit bins with warp aggregation, then the row's nonzero bins in ascending
 // order -> padded CSR, and W_vu = omega_v cf_u H_vu / W into Lambda
-__global__ void __launch_bounds__(kHistThreads) k_histogram(const int32_t *exits, const int32_t *order,
-                                                           const RowBall *ball, const double *area, const double *cf,
-                                                           int R, int W, int cap, int32_t *hbin, int32_t *hcnt,
-                                                           int32_t *hnnz, double *Lambda, double *omega_out,
-                                                           Ctrl *ctrl) {
-    extern __shared__ int hist[];
-    typedef cub::BlockScan<int, kHistThreads> Scan;
-    __shared__ typename Scan::TempStorage scan_tmp;
-    const int rp = blockIdx.x;
+typedef cub::BlockScan<int, kHistThreads> HistScan;
+
+// the histogram of sorted row position rp, by one block of kHistThreads
+__device__ void row_histogram(int rp, const int32_t *exits, const int32_t *order, const RowBall *ball,
+                              const double *area, const double *cf, int R, int W, int cap, int32_t *hbin,
+                              int32_t *hcnt, int32_t *hnnz, double *Lambda, double *omega_out, Ctrl *ctrl, int *hist,
+                              typename HistScan::TempStorage &scan_tmp) {
+    typedef HistScan Scan;
     const int v = order[rp];
     const RowBall &b = ball[v];
     const double omega = b.valid ? area[v] * b.M * b.kfac : 0.0;
@@ -702,11 +779,20 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const int32_t *exits
     if (threadIdx.x == 0) hnnz[v] = total;
 }
 
-// Lambda <- -(D + D^T)/2 off the diagonal, by 32 x 32 tile pairs (I <= J)
-__global__ void k_symmetrize(double *L, int R) {
-    __shared__ double A[32][33], B[32][33];
-    const int I = blockIdx.y, J = blockIdx.x;
-    if (I > J) return;
+__global__ void __launch_bounds__(kHistThreads) k_histogram(const int32_t *exits, const int32_t *order,
+                                                           const RowBall *ball, const double *area, const double *cf,
+                                                           int R, int W, int cap, int32_t *hbin, int32_t *hcnt,
+                                                           int32_t *hnnz, double *Lambda, double *omega_out,
+                                                           Ctrl *ctrl) {
+    extern __shared__ int hist[];
+    __shared__ typename HistScan::TempStorage scan_tmp;
+    row_histogram(blockIdx.x, exits, order, ball, area, cf, R, W, cap, hbin, hcnt, hnnz, Lambda, omega_out, ctrl,
+                  hist, scan_tmp);
+}
+
+// Lambda <- -(D + D^T)/2 off the diagonal, by 32 x 32 tile pairs (I <= J);
+// one block of 32 x 8 threads per pair
+__device__ void symmetrize_tiles(double *L, int R, int I, int J, double (*A)[33], double (*B)[33]) {
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int r = ty; r < 32; r += blockDim.y) {
         const int gi = I * 32 + r, gj = J * 32 + tx;
@@ -729,11 +815,17 @@ __global__ void k_symmetrize(double *L, int R) {
         if (hi < R && hj < R) L[(size_t)hi * R + hj] = -(0.5 * (A[tx][r] + B[r][tx]));
     }
 }
+__global__ void k_symmetrize(double *L, int R) {
+    __shared__ double A[32][33], B[32][33];
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (I > J) return;
+    symmetrize_tiles(L, R, I, J, A, B);
+}
 
-// Laplacian diagonal: Lambda_vv = sum_{u != v} Wsym_vu (+ killing 4 pi cf_v H0_v / N0)
-__global__ void k_diagonal(double *L, int R, const double *cf, const int32_t *H0, double inv_n0) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= R) return;
+// Laplacian diagonal of row `warp`, by one warp:
+// Lambda_vv = sum_{u != v} Wsym_vu (+ killing 4 pi cf_v H0_v / N0)
+__device__ void diagonal_row(double *L, int R, int warp, const double *cf, const int32_t *H0, double inv_n0) {
+    const int lane = threadIdx.x & 31;
     const double *row = L + (size_t)warp * R;
     double s = 0.0;
     for (int u = lane; u < R; u += 32) s += row[u];
@@ -743,6 +835,174 @@ __global__ void k_diagonal(double *L, int R, const double *cf, const int32_t *H0
         if (H0) d += ((4.0 * M_PI * (cf ? cf[warp] : 1.0)) * (double)H0[warp]) * inv_n0;
         L[(size_t)warp * R + warp] = d;
     }
+}
+__global__ void k_to_f32(const double *L, size_t n, float *out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)L[i];
+}
+__global__ void k_diagonal(double *L, int R, const double *cf, const int32_t *H0, double inv_n0) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= R) return;
+    diagonal_row(L, R, warp, cf, H0, inv_n0);
+}
+
+// ---------------------------------------------------------------- batched setup and finish
+// Every mesh of a batch, as the batched setup and finishing kernels see it.
+// Units of work are numbered across the batch; a kernel finds its mesh by a
+// binary search of the per-mesh offsets, so one launch serves all meshes.
+struct MeshJob {
+    DevMesh m;
+    const double *pos, *nrm, *area, *V;
+    RowBall *ball;
+    Ctrl *ctrl;
+    int32_t *order, *exits, *H0;
+    double *cf;                 // exterior column factors, else null
+    int32_t *hbin, *hcnt, *hnnz;
+    double *Lambda, *omega;
+    float *Lambda32;
+    Frame fr;
+    double lo[3], inv[3];       // box frame of the row keys
+    double origin[3];           // exterior, origin_auto == 0
+    double inv_n0;              // 1 / N0 with killing walks, else 0
+    int R, W, cap, nv;
+    int ext, origin_auto, ostride, kill;
+};
+
+// last j with offs[j] <= g (offs ascending, offs[0] = 0)
+__device__ __forceinline__ int find_job(const int *offs, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kMeshChunk = 40;
+struct MeshChunk {
+    MeshJob j[kMeshChunk];
+    int count, base;
+};
+__global__ void k_store_mesh_jobs(MeshChunk c, MeshJob *jobs) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) jobs[c.base + i] = c.j[i];
+}
+constexpr int kIntChunk = 2048;
+struct IntChunk {
+    int v[kIntChunk];
+    int count, base;
+};
+__global__ void k_store_ints(IntChunk c, int *out) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) out[c.base + i] = c.v[i];
+}
+
+// zero H0; the Z-order key of every row (or the caller's order)
+__global__ void k_b_rows(const MeshJob *jobs, const int *row0, int n, int identity, unsigned long long *keys) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= row0[n]) return;
+    const int j = find_job(row0, n, g);
+    const MeshJob &J = jobs[j];
+    const int v = g - row0[j];
+    J.H0[v] = 0;
+    if (identity) J.order[v] = v;
+    else keys[g] = row_key(J.pos, v, J.lo[0], J.lo[1], J.lo[2], J.inv[0], J.inv[1], J.inv[2]);
+}
+__global__ void k_b_order(const MeshJob *jobs, const int *row0, int n, const unsigned long long *keys_s) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= row0[n]) return;
+    const int j = find_job(row0, n, g);
+    jobs[j].order[g - row0[j]] = (int32_t)(keys_s[g] & 0xFFFFFFFFull);
+}
+
+// interior tangent balls: every row of interior meshes, the strided subset of
+// exterior meshes with an automatic inversion centre; one warp per row
+__global__ void __launch_bounds__(32 * kTanWarps) k_b_tangent_int(const MeshJob *jobs, const int *unit0, int n) {
+    __shared__ int fronts[kTanWarps][32];
+    const int u = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
+    if (u >= unit0[n]) return;
+    const int j = find_job(unit0, n, u);
+    const MeshJob &J = jobs[j];
+    const int v = (u - unit0[j]) * (J.ext ? J.ostride : 1);
+    tangent_int_row(J.m, J.pos, J.nrm, v, J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5]);
+}
+// exterior meshes: inversion centre and inverted frame, one block each
+__global__ void __launch_bounds__(kFrameThreads) k_b_frame(const MeshJob *jobs) {
+    __shared__ double sv[kFrameThreads];
+    __shared__ int si[kFrameThreads];
+    const MeshJob &J = jobs[blockIdx.x];
+    if (!J.ext) return;
+    if (J.origin_auto) {
+        origin_argmax_block(J.ball, J.R, J.ostride, J.ctrl, sv, si);
+    } else if (threadIdx.x == 0) {
+        J.ctrl->origin[0] = J.origin[0];
+        J.ctrl->origin[1] = J.origin[1];
+        J.ctrl->origin[2] = J.origin[2];
+    }
+    __syncthreads();
+    ext_frame_block(J.m, J.V, J.nv, J.ctrl);
+}
+// exterior tangent balls of every row of the exterior meshes
+__global__ void __launch_bounds__(32 * kTanWarps) k_b_tangent_ext(const MeshJob *jobs, const int *unit0, int n,
+                                                                  const int *ext_ids) {
+    __shared__ int fronts[kTanWarps][32];
+    const int u = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
+    if (u >= unit0[n]) return;
+    const int e = find_job(unit0, n, u);
+    const MeshJob &J = jobs[ext_ids[e]];
+    tangent_ext_row(J.m, J.pos, J.nrm, u - unit0[e], J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5]);
+}
+__global__ void k_b_colfactor(const MeshJob *jobs, const int *row0, int n) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= row0[n]) return;
+    const int j = find_job(row0, n, g);
+    const MeshJob &J = jobs[j];
+    if (!J.ext) return;
+    const int u = g - row0[j];
+    const double d0 = J.pos[3 * u] - J.ctrl->origin[0], d1 = J.pos[3 * u + 1] - J.ctrl->origin[1],
+                 d2 = J.pos[3 * u + 2] - J.ctrl->origin[2];
+    J.cf[u] = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// finishing: zero Lambda (grid.y = mesh), histograms (one block per row),
+// symmetrisation (one block per tile pair), Laplacian diagonals (one warp per row)
+__global__ void k_b_fill_zero(const MeshJob *jobs) {
+    const MeshJob &J = jobs[blockIdx.y];
+    if (!J.Lambda) return;
+    const size_t nn = (size_t)J.R * J.R;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+        J.Lambda[i] = 0.0;
+}
+__global__ void __launch_bounds__(kHistThreads) k_b_histogram(const MeshJob *jobs, const int *row0, int n) {
+    extern __shared__ int hist[];
+    __shared__ typename HistScan::TempStorage scan_tmp;
+    const int j = find_job(row0, n, blockIdx.x);
+    const MeshJob &J = jobs[j];
+    row_histogram(blockIdx.x - row0[j], J.exits, J.order, J.ball, J.area, J.cf, J.R, J.W, J.cap, J.hbin, J.hcnt,
+                  J.hnnz, J.Lambda, J.omega, J.ctrl, hist, scan_tmp);
+}
+__global__ void k_b_symmetrize(const MeshJob *jobs, const int *tile0, int n) {
+    __shared__ double A[32][33], B[32][33];
+    const int j = find_job(tile0, n, blockIdx.x);
+    const MeshJob &J = jobs[j];
+    if (!J.Lambda) return;
+    const int nt = (J.R + 31) / 32, t = blockIdx.x - tile0[j];
+    const int I = t / nt, Jt = t % nt;
+    if (I > Jt) return;
+    symmetrize_tiles(J.Lambda, J.R, I, Jt, A, B);
+}
+__global__ void k_b_to_f32(const MeshJob *jobs) {
+    const MeshJob &J = jobs[blockIdx.y];
+    if (!J.Lambda || !J.Lambda32) return;
+    const size_t nn = (size_t)J.R * J.R;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+        J.Lambda32[i] = (float)J.Lambda[i];
+}
+__global__ void k_b_diagonal(const MeshJob *jobs, const int *row0, int n) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= row0[n]) return;
+    const int j = find_job(row0, n, g);
+    const MeshJob &J = jobs[j];
+    if (!J.Lambda) return;
+    diagonal_row(J.Lambda, J.R, g - row0[j], J.cf, J.kill ? J.H0 : nullptr, J.inv_n0);
 }
 
 // rows in the caller's order (queue-order option)
@@ -819,6 +1079,7 @@ static mcs_status check_common(const mcs_params *p, const std::string &f) {
             f + ": threads_per_block must be 0 or a multiple of 32 up to 128");
     MCS_ARG(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 64, f + ": blocks_per_sm out of range");
     MCS_ARG(p->queue_order >= 0 && p->queue_order <= 3, f + ": queue_order must be in [0, 3]");
+    MCS_ARG(p->bvh_layout == 0 || p->bvh_layout == 2 || p->bvh_layout == 4, f + ": bvh_layout must be 0, 2 or 4");
     return MCS_OK;
 }
 
@@ -907,7 +1168,7 @@ static mcs_status enqueue_setup(const Plan &pl, int row_order, cudaStream_t st) 
             k_set_origin<<<1, 1, 0, st>>>(pl.ctrl, pl.origin[0], pl.origin[1], pl.origin[2]);
         }
         note_launch();
-        k_ext_frame<<<1, 256, 0, st>>>(pl.m->V, pl.m->nv, pl.ctrl);
+        k_ext_frame<<<1, kFrameThreads, 0, st>>>(dm, pl.m->V, pl.m->nv, pl.ctrl);
         note_launch();
         k_tangent_ext<<<tgrid, 32 * kTanWarps, 0, st>>>(dm, pl.rows.pos, pl.rows.nrm, R, pl.fr, pl.ball(), pl.ctrl);
         note_launch();
@@ -933,6 +1194,11 @@ static WalkJob make_job(const Plan &pl, unsigned long long n_row_walks, unsigned
     J.ctrl = pl.ctrl;
     J.n_rows_walks = n_row_walks;
     J.n_kill = n_kill;
+    for (int k = 0; k < 3; k++) J.box_c[k] = 0.5 * (pl.m->lo[k] + pl.m->hi[k]);
+    const double s0 = pl.m->hi[0] - pl.m->lo[0], s1 = pl.m->hi[1] - pl.m->lo[1], s2 = pl.m->hi[2] - pl.m->lo[2];
+    J.esc_int2 = s0 * s0 + s1 * s1 + s2 * s2;
+    for (int k = 0; k < 3; k++) J.box_cf[k] = (float)J.box_c[k];
+    J.esc_int2f = (float)J.esc_int2;
     J.R = pl.rows.n_rows;
     J.W = pl.W;
     J.k0 = (uint32_t)pl.seed;
@@ -966,18 +1232,29 @@ static mcs_status store_jobs(const std::vector<WalkJob> &jobs, WalkJob *d_jobs, 
 
 typedef void (*WalkKernel)(MultiArgs);
 
-template <typename T, bool COUNT> static WalkKernel walk_kernel_mode(int mode, bool multi) {
-    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false> : k_walks<T, 1, COUNT, false>;
-    return mode == 0 ? k_walks<T, 0, COUNT, true> : (mode == 1 ? k_walks<T, 1, COUNT, true> : k_walks<T, 2, COUNT, true>);
+template <typename T, bool COUNT, bool WIDE> static WalkKernel walk_kernel_mode(int mode, bool multi) {
+    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false, WIDE> : k_walks<T, 1, COUNT, false, WIDE>;
+    return mode == 0 ? k_walks<T, 0, COUNT, true, WIDE>
+                     : (mode == 1 ? k_walks<T, 1, COUNT, true, WIDE> : k_walks<T, 2, COUNT, true, WIDE>);
 }
+
+template <typename T, bool COUNT> static WalkKernel walk_kernel_w(int mode, bool multi, bool wide) {
+    return wide ? walk_kernel_mode<T, COUNT, true>(mode, multi) : walk_kernel_mode<T, COUNT, false>(mode, multi);
+}
+
+// the BVH node layout of the walk queries: binary unless the caller asks for
+// 4-wide (measured: binary 304 ms, 4-wide 332 ms on the two-sphere exterior
+// workload; 95 vs 107 ms on the 2M-face union)
+static bool use_wide(const mcs_params *p) { return p->bvh_layout == 4; }
 
 // mode: 0 all jobs interior, 1 all exterior, 2 mixed; multi: several jobs
 static WalkKernel walk_kernel(const mcs_params *p, int mode, bool multi) {
+    const bool wide = use_wide(p);
     if (p->count_work)
-        return p->prec == MCS_FP64 ? walk_kernel_mode<double, true>(mode, multi)
-                                   : walk_kernel_mode<float, true>(mode, multi);
-    return p->prec == MCS_FP64 ? walk_kernel_mode<double, false>(mode, multi)
-                               : walk_kernel_mode<float, false>(mode, multi);
+        return p->prec == MCS_FP64 ? walk_kernel_w<double, true>(mode, multi, wide)
+                                   : walk_kernel_w<float, true>(mode, multi, wide);
+    return p->prec == MCS_FP64 ? walk_kernel_w<double, false>(mode, multi, wide)
+                               : walk_kernel_w<float, false>(mode, multi, wide);
 }
 
 // resident blocks per SM of the walk kernel for this block size
@@ -1046,6 +1323,10 @@ static mcs_status enqueue_assembly(const Plan &pl, cudaStream_t st) {
         note_launch();
         k_diagonal<<<(R * 32 + 255) / 256, 256, 0, st>>>(pl.out.Lambda, R, pl.cf(), kill ? pl.H0() : nullptr,
                                                         kill ? 1.0 / (double)pl.killing : 0.0);
+        if (pl.out.Lambda32) {
+            note_launch();
+            k_to_f32<<<num_sms() * 8, 256, 0, st>>>(pl.out.Lambda, (size_t)R * R, pl.out.Lambda32);
+        }
     }
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
@@ -1088,14 +1369,16 @@ static mcs_status read_stats(const Ctrl &hc, const Plan *pl, unsigned long long 
                                                       : ": BVH traversal stack or iteration bound exceeded"));
         return MCS_ERR_DEVICE;
     }
-    return (hc.capped || hc.kill_capped) ? MCS_WARN_CAPPED : MCS_OK;
+    if (hc.capped || hc.kill_capped) return MCS_WARN_CAPPED;
+    return hc.lost ? MCS_WARN_LOST : MCS_OK;
 }
 
 // ---------------------------------------------------------------- batches
 // Batch workspace: header (job table, queue offsets, control blocks: one per
 // mesh and one for the launch), then each mesh's scratch.
 struct BatchLayout {
-    size_t jobs, offs, ctrl, total;
+    size_t jobs, offs, ctrl, mjobs, ints, keys, keys_s, sort, total;
+    size_t sort_bytes;
     std::vector<size_t> item;
 };
 
@@ -1103,9 +1386,20 @@ static BatchLayout batch_layout(const mcs_batch_item *items, int n, int W) {
     BatchLayout B;
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+    long long rows = 0;
+    for (int i = 0; i < n; i++) rows += std::max(1, items[i].rows.n_rows);
     B.jobs = take(sizeof(WalkJob) * (size_t)n);
     B.offs = take(sizeof(unsigned long long) * (size_t)(n + 1));
     B.ctrl = take(sizeof(Ctrl) * (size_t)(n + 1));
+    B.mjobs = take(sizeof(MeshJob) * (size_t)n);
+    B.ints = take(sizeof(int) * (size_t)(5 * (n + 1)));  // row0, unitA, unitB, tile0, ext ids
+    B.keys = take(sizeof(unsigned long long) * (size_t)rows);
+    B.keys_s = take(sizeof(unsigned long long) * (size_t)rows);
+    size_t sb = 0;
+    cub::DeviceSegmentedRadixSort::SortKeys(nullptr, sb, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
+                                            (int)rows, n, (int *)nullptr, (int *)nullptr, 0, 62);
+    B.sort_bytes = sb;
+    B.sort = take(sb);
     B.item.resize(n);
     for (int i = 0; i < n; i++) B.item[i] = take(layout(std::max(1, items[i].rows.n_rows), W, false).total);
     B.total = o;
@@ -1117,6 +1411,14 @@ struct Batch {
     WalkJob *jobs = nullptr;
     unsigned long long *offs = nullptr;
     Ctrl *ctrl = nullptr;   // n + 1 blocks: per mesh, then the launch's
+    MeshJob *mjobs = nullptr;
+    int *row0 = nullptr, *unitA = nullptr, *unitB = nullptr, *tile0 = nullptr, *ext_ids = nullptr;
+    unsigned long long *keys = nullptr, *keys_s = nullptr;
+    void *sort = nullptr;
+    size_t sort_bytes = 0;
+    std::vector<int> h_row0, h_unitA, h_unitB, h_tile0, h_ext;  // host copies
+    int max_rows = 1;
+    bool any_lambda = false, any_lambda32 = false;
     int n = 0;
     int mode = 0;           // walk kernel: 0 all interior, 1 all exterior, 2 mixed
     mcs_params p{};
@@ -1134,6 +1436,8 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
         s = check_mesh_rows(items[i].mesh, &items[i].rows, &items[i].out, items[i].domain, p->walks_per_row,
                             f + " item " + std::to_string(i));
         if (s != MCS_OK) return s;
+        MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(items[i].mesh),
+                f + " item " + std::to_string(i) + ": bvh_layout 4 needs mcs_mesh_build_wide first");
     }
     const BatchLayout B = batch_layout(items, n, p->walks_per_row);
     MCS_ARG(workspace != nullptr && workspace_bytes >= B.total, f + ": workspace too small");
@@ -1144,6 +1448,17 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
     b.jobs = (WalkJob *)(ws + B.jobs);
     b.offs = (unsigned long long *)(ws + B.offs);
     b.ctrl = (Ctrl *)(ws + B.ctrl);
+    b.mjobs = (MeshJob *)(ws + B.mjobs);
+    int *ints = (int *)(ws + B.ints);
+    b.row0 = ints;
+    b.unitA = ints + (n + 1);
+    b.unitB = ints + 2 * (n + 1);
+    b.tile0 = ints + 3 * (n + 1);
+    b.ext_ids = ints + 4 * (n + 1);
+    b.keys = (unsigned long long *)(ws + B.keys);
+    b.keys_s = (unsigned long long *)(ws + B.keys_s);
+    b.sort = ws + B.sort;
+    b.sort_bytes = B.sort_bytes;
     b.plans.clear();
     int n_ext = 0;
     for (int i = 0; i < n; i++) n_ext += items[i].domain == MCS_EXTERIOR;
@@ -1153,6 +1468,154 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
         b.plans.push_back(make_plan(it.mesh, it.rows, it.out, p, it.domain, it.seed, it.origin_auto, it.origin,
                                     ws + B.item[i], b.ctrl + i, false));
     }
+    // unit offsets of the batched kernels
+    b.h_row0.assign(1, 0);
+    b.h_unitA.assign(1, 0);
+    b.h_unitB.assign(1, 0);
+    b.h_tile0.assign(1, 0);
+    b.h_ext.clear();
+    b.max_rows = 1;
+    b.any_lambda = false;
+    b.any_lambda32 = false;
+    for (int i = 0; i < n; i++) {
+        const Plan &pl = b.plans[i];
+        const int R = pl.rows.n_rows, ostride = (R + 255) / 256;
+        b.h_row0.push_back(b.h_row0.back() + R);
+        b.h_unitA.push_back(b.h_unitA.back() +
+                            (pl.ext ? (pl.origin_auto ? (R + ostride - 1) / ostride : 0) : R));
+        const int nt = (R + 31) / 32;
+        b.h_tile0.push_back(b.h_tile0.back() + nt * nt);
+        if (pl.ext) {
+            b.h_ext.push_back(i);
+            b.h_unitB.push_back(b.h_unitB.back() + R);
+        }
+        b.max_rows = std::max(b.max_rows, R);
+        b.any_lambda = b.any_lambda || pl.out.Lambda != nullptr;
+        b.any_lambda32 = b.any_lambda32 || (pl.out.Lambda != nullptr && pl.out.Lambda32 != nullptr);
+    }
+    return MCS_OK;
+}
+
+static MeshJob make_mesh_job(const Plan &pl) {
+    MeshJob J;
+    memset(&J, 0, sizeof J);
+    J.m = pl.m->dev();
+    J.pos = pl.rows.pos;
+    J.nrm = pl.rows.nrm;
+    J.area = pl.rows.area;
+    J.V = pl.m->V;
+    J.ball = pl.ball();
+    J.ctrl = pl.ctrl;
+    J.order = pl.order();
+    J.exits = pl.exits();
+    J.H0 = pl.H0();
+    J.cf = pl.cf();
+    J.hbin = pl.out.hist_bin;
+    J.hcnt = pl.out.hist_cnt;
+    J.hnnz = pl.out.hist_nnz;
+    J.Lambda = pl.out.Lambda;
+    J.Lambda32 = pl.out.Lambda32;
+    J.omega = pl.out.omega;
+    J.fr = pl.fr;
+    for (int k = 0; k < 3; k++) {
+        J.lo[k] = pl.m->lo[k];
+        J.inv[k] = 1.0 / (pl.m->hi[k] - pl.m->lo[k]);
+        J.origin[k] = pl.origin[k];
+    }
+    const bool kill = pl.ext && pl.killing > 0;
+    J.inv_n0 = kill ? 1.0 / (double)pl.killing : 0.0;
+    J.kill = kill;
+    J.R = pl.rows.n_rows;
+    J.W = pl.W;
+    J.cap = std::min(pl.W, pl.rows.n_rows);
+    J.nv = pl.m->nv;
+    J.ext = pl.ext;
+    J.origin_auto = pl.origin_auto;
+    J.ostride = (pl.rows.n_rows + 255) / 256;
+    return J;
+}
+
+static mcs_status store_int_array(const std::vector<int> &v, int *d, cudaStream_t st) {
+    for (size_t base = 0; base < v.size(); base += kIntChunk) {
+        IntChunk c;
+        c.count = (int)std::min<size_t>(kIntChunk, v.size() - base);
+        c.base = (int)base;
+        for (int i = 0; i < c.count; i++) c.v[i] = v[base + i];
+        note_launch();
+        k_store_ints<<<1, 256, 0, st>>>(c, d);
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// the batch's row setup in a fixed number of launches: job table, row
+// schedule (one segmented sort), interior tangent balls, exterior frames,
+// exterior tangent balls, column factors
+static mcs_status enqueue_batch_setup(const Batch &b, int row_order, cudaStream_t st) {
+    MCS_CUDA(cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl) * (b.n + 1), st));
+    for (int base = 0; base < b.n; base += kMeshChunk) {
+        MeshChunk c;
+        c.count = std::min(kMeshChunk, b.n - base);
+        c.base = base;
+        for (int i = 0; i < c.count; i++) c.j[i] = make_mesh_job(b.plans[base + i]);
+        note_launch();
+        k_store_mesh_jobs<<<1, 64, 0, st>>>(c, b.mjobs);
+    }
+    mcs_status s;
+    if ((s = store_int_array(b.h_row0, b.row0, st)) != MCS_OK) return s;
+    if ((s = store_int_array(b.h_unitA, b.unitA, st)) != MCS_OK) return s;
+    if ((s = store_int_array(b.h_unitB, b.unitB, st)) != MCS_OK) return s;
+    if ((s = store_int_array(b.h_tile0, b.tile0, st)) != MCS_OK) return s;
+    if (!b.h_ext.empty() && (s = store_int_array(b.h_ext, b.ext_ids, st)) != MCS_OK) return s;
+    const int rows = b.h_row0.back(), tb = 256;
+    const bool identity = row_order & 1;
+    note_launch();
+    k_b_rows<<<(rows + tb - 1) / tb, tb, 0, st>>>(b.mjobs, b.row0, b.n, identity, b.keys);
+    if (!identity) {
+        size_t sb = b.sort_bytes;
+        MCS_CUDA(cub::DeviceSegmentedRadixSort::SortKeys(b.sort, sb, b.keys, b.keys_s, rows, b.n, b.row0, b.row0 + 1,
+                                                         0, 62, st));
+        note_launch();
+        k_b_order<<<(rows + tb - 1) / tb, tb, 0, st>>>(b.mjobs, b.row0, b.n, b.keys_s);
+    }
+    const int ua = b.h_unitA.back(), ub = b.h_unitB.back(), ne = (int)b.h_ext.size();
+    if (ua > 0) {
+        note_launch();
+        k_b_tangent_int<<<(ua + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(b.mjobs, b.unitA, b.n);
+    }
+    if (ne > 0) {
+        note_launch();
+        k_b_frame<<<b.n, kFrameThreads, 0, st>>>(b.mjobs);
+        note_launch();
+        k_b_tangent_ext<<<(ub + kTanWarps - 1) / kTanWarps, 32 * kTanWarps, 0, st>>>(b.mjobs, b.unitB, ne,
+                                                                                    b.ext_ids);
+        note_launch();
+        k_b_colfactor<<<(rows + tb - 1) / tb, tb, 0, st>>>(b.mjobs, b.row0, b.n);
+    }
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// histograms, row normalisation, symmetrisation and diagonals of every mesh
+static mcs_status enqueue_batch_finish(const Batch &b, cudaStream_t st) {
+    const int rows = b.h_row0.back();
+    if (b.any_lambda) {
+        note_launch();
+        k_b_fill_zero<<<dim3(64, b.n), 256, 0, st>>>(b.mjobs);
+    }
+    note_launch();
+    k_b_histogram<<<rows, kHistThreads, hist_smem(b.max_rows), st>>>(b.mjobs, b.row0, b.n);
+    if (b.any_lambda) {
+        note_launch();
+        k_b_symmetrize<<<b.h_tile0.back(), dim3(32, 8), 0, st>>>(b.mjobs, b.tile0, b.n);
+        note_launch();
+        k_b_diagonal<<<(rows * 32 + 255) / 256, 256, 0, st>>>(b.mjobs, b.row0, b.n);
+        if (b.any_lambda32) {
+            note_launch();
+            k_b_to_f32<<<dim3(64, b.n), 256, 0, st>>>(b.mjobs);
+        }
+    }
+    MCS_CUDA(cudaGetLastError());
     return MCS_OK;
 }
 
@@ -1174,9 +1637,7 @@ static std::vector<int> job_order(const Batch &b) {
 static mcs_status enqueue_batch(const Batch &b, cudaStream_t st, cudaEvent_t *ev) {
     mcs_status s;
     if (ev) cudaEventRecord(ev[0], st);
-    MCS_CUDA(cudaMemsetAsync(b.launch_ctrl(), 0, sizeof(Ctrl), st));
-    for (const Plan &pl : b.plans)
-        if ((s = enqueue_setup(pl, b.p.queue_order, st)) != MCS_OK) return s;
+    if ((s = enqueue_batch_setup(b, b.p.queue_order, st)) != MCS_OK) return s;
     std::vector<WalkJob> jobs;
     for (int i : job_order(b)) jobs.push_back(make_job(b.plans[i], b.plans[i].walks(), (unsigned long long)b.plans[i].killing));
     if (b.n > 1 && (s = store_jobs(jobs, b.jobs, b.offs, st)) != MCS_OK) return s;
@@ -1188,18 +1649,15 @@ static mcs_status enqueue_batch(const Batch &b, cudaStream_t st, cudaEvent_t *ev
                           &b.p, b.mode, tpb, bps, st)) != MCS_OK)
         return s;
     if (ev) cudaEventRecord(ev[2], st);
-    for (const Plan &pl : b.plans) {
-        if ((s = enqueue_hist(pl, st)) != MCS_OK) return s;
-        if ((s = enqueue_assembly(pl, st)) != MCS_OK) return s;
-    }
+    if ((s = enqueue_batch_finish(b, st)) != MCS_OK) return s;
     if (ev) cudaEventRecord(ev[3], st);
     return MCS_OK;
 }
 
 static mcs_status batch_hist_prepare(const Batch &b) {
-    int rmax = 1;
-    for (const Plan &pl : b.plans) rmax = std::max(rmax, pl.rows.n_rows);
-    return prepare_histogram(hist_smem(rmax));
+    MCS_CUDA(cudaFuncSetAttribute(k_b_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)hist_smem(b.max_rows)));
+    return MCS_OK;
 }
 
 // per-mesh and launch statistics of a finished batch (synchronises st)
@@ -1284,6 +1742,7 @@ void mcs_default_params(mcs_params *p) {
     p->timing = 0;
     p->count_work = 0;
     p->queue_order = 0;
+    p->bvh_layout = 0;
 }
 
 size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, long long killing_walks) {
@@ -1299,6 +1758,7 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     mcs_status s = check_common(p, f);
     if (s != MCS_OK) return s;
     if ((s = check_mesh_rows(m, rows, out, p->domain, p->walks_per_row, f)) != MCS_OK) return s;
+    MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(m), f + ": bvh_layout 4 needs mcs_mesh_build_wide first");
     const Layout L = layout(rows->n_rows, p->walks_per_row, true);
     MCS_ARG(workspace != nullptr && workspace_bytes >= L.total, f + ": workspace too small");
     MCS_ARG(((uintptr_t)workspace & 255) == 0, f + ": workspace must be 256-byte aligned");
@@ -1454,13 +1914,10 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
     auto cleanup = [&]() { cudaEventDestroy(e0); cudaEventDestroy(e1); };
     int cur_rows = -1;
     // sample: the first rows of every mesh (in the candidate's row order), no killing walks
-    auto trial = [&](const mcs_params &q, float *ms) -> mcs_status {
+    auto trial = [&](const mcs_params &q, float *ms, int *bps_used) -> mcs_status {
         mcs_status r;
         if ((q.queue_order & 1) != cur_rows) {
-            for (const Plan &pl : b.plans)
-                if ((r = (cur_rows < 0 ? enqueue_setup(pl, q.queue_order, st) : enqueue_order(pl, q.queue_order, st))) !=
-                    MCS_OK)
-                    return r;
+            if ((r = enqueue_batch_setup(b, q.queue_order, st)) != MCS_OK) return r;
             cur_rows = q.queue_order & 1;
         }
         Batch bq = b;
@@ -1498,16 +1955,34 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
             trials[count].threads_per_block = tpb;
             trials[count].blocks_per_sm = bps;
             trials[count].queue_order = q.queue_order;
+            trials[count].bvh_layout = use_wide(&q) ? 4 : 2;
             trials[count].ms = best;
         }
         count++;
         *ms = best;
+        *bps_used = bps;
         return MCS_OK;
     };
-    // coordinate search: residency (block size x blocks per SM), then queue order
+    // coordinate search: BVH node layout, residency (block size x blocks per SM), queue order
     mcs_params best = *p;
     best.queue_order = 0;
+    best.bvh_layout = use_wide(p) ? 4 : 2;  // the library default unless the caller fixed one
     float best_ms = 1e30f;
+    best.threads_per_block = 128;
+    best.blocks_per_sm = 0;
+    bool all_wide = true;
+    for (int i = 0; i < n; i++) all_wide = all_wide && mcs_mesh_has_wide(items[i].mesh);
+    for (int lay : {2, 4}) {
+        if (p->bvh_layout != 0 && lay != best.bvh_layout) continue;
+        if (lay == 4 && !all_wide) continue;
+        mcs_params q = best;
+        q.bvh_layout = lay;
+        q.blocks_per_sm = 0;
+        float ms = 0.f;
+        int used = 0;
+        if ((s = trial(q, &ms, &used)) != MCS_OK) { cleanup(); return s; }
+        if (ms < best_ms) { best_ms = ms; best.bvh_layout = lay; best.blocks_per_sm = used; }
+    }
     for (int tpb : {64, 128}) {
         mcs_params q = best;
         q.threads_per_block = tpb;
@@ -1517,7 +1992,8 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
         for (int bps = std::max(1, occ - 2 * (128 / tpb)); bps <= occ; bps += 128 / tpb) {
             q.blocks_per_sm = bps;
             float ms = 0.f;
-            if ((s = trial(q, &ms)) != MCS_OK) { cleanup(); return s; }
+            int used = 0;
+            if ((s = trial(q, &ms, &used)) != MCS_OK) { cleanup(); return s; }
             if (ms < best_ms) { best_ms = ms; best.threads_per_block = tpb; best.blocks_per_sm = bps; }
         }
     }
@@ -1528,7 +2004,8 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
         mcs_params q = base;
         q.queue_order = qo;
         float ms = 0.f;
-        if ((s = trial(q, &ms)) != MCS_OK) { cleanup(); return s; }
+        int used = 0;
+        if ((s = trial(q, &ms, &used)) != MCS_OK) { cleanup(); return s; }
         if (ms < best_ms) { best_ms = ms; best.queue_order = qo; }
     }
     cleanup();

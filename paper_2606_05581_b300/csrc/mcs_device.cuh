@@ -251,6 +251,16 @@ struct __align__(16) Node {
     float4 c;  // lo1.z hi1.x hi1.y hi1.z
     int4 d;    // child0 child1 - -
 };
+// 4-wide node: the binary tree collapsed two levels at a time (the nodes
+// at even depth keep their grandchildren), one 128-byte line per node.
+// Child boxes in SoA order; child k >= 0 internal 4-wide node, < 0 leaf
+// (~slot), kNoChild unused (its box is empty: lo = +inf, hi = -inf)
+constexpr int kNoChild = 0x7FFFFFFF;
+struct __align__(128) Node4 {
+    float4 lox, loy, loz, hix, hiy, hiz;
+    int4 child;
+    int4 pad;
+};
 // triangle slot in BVH order, FP32: (a, id) (ab, -) (ac, -)
 struct __align__(16) Tri32 {
     float4 a;
@@ -267,6 +277,7 @@ struct DevMesh {
     const double *V;       // nv x 3
     const int32_t *F;      // nf x 3
     const Node *nodes;     // nf - 1 internal nodes (root 0); none when nf == 1
+    const Node4 *nodes4;   // the same tree, 4-wide (root 0); none when nf == 1
     const Tri32 *t32;      // nf slots
     const Tri64 *t64;      // nf slots
     int nv, nf;
@@ -322,8 +333,8 @@ struct Work {
     unsigned long long nodes, tris;
 };
 
-// closest triangle by BVH traversal (nearest child first, explicit stack);
-// guess >= 0 is a slot tested first to tighten the bound
+// closest triangle by traversal of the binary BVH (nearest child first,
+// explicit stack); guess >= 0 is a slot tested first to tighten the bound
 template <typename T, bool COUNT = false>
 __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &best, int *err, Work *work = nullptr) {
     best.d2 = (T)INFINITY;
@@ -351,8 +362,6 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
     float sdist[kStackDepth];
     int sp = 0;
     int node = 0;
-    // a tree over nf leaves has nf - 1 internal nodes: a traversal visits each
-    // at most once, so a longer one means a malformed tree
     for (int guard = 0;; guard++) {
         if (guard > 2 * m.nf + 64) { *err |= kErrTree; break; }
         if (COUNT) work->nodes++;
@@ -379,6 +388,93 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
         }
         if (h0) { node = c0; continue; }
         if (h1) { node = c1; continue; }
+        bool found = false;
+        while (sp > 0) {
+            sp--;
+            if ((T)sdist[sp] <= thr2) { node = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+}
+
+constexpr int kStack4 = 96;  // 4-wide traversal: up to 3 deferred children per level
+
+// closest triangle by traversal of the 4-wide BVH: the children in reach are
+// visited nearest first, the others deferred on the stack; same result as
+// closest() (the exact argmin of (d^2, id)), fewer dependent node fetches
+template <typename T, bool COUNT = false>
+__device__ void closest4(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &best, int *err,
+                         Work *work = nullptr) {
+    best.d2 = (T)INFINITY;
+    best.id = 0x7FFFFFFF;
+    best.slot = -1;
+    best.b0 = best.b1 = best.b2 = (T)0;
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) return;  // no triangle: caller checks slot < 0
+    const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
+    T thr2 = (T)INFINITY;
+    auto test = [&](int s) {
+        if (COUNT) work->tris++;
+        T b[3];
+        int id;
+        const T d2 = Slot<T>::test(m, s, px, py, pz, b, id);
+        if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
+            best.d2 = d2; best.id = id; best.slot = s;
+            best.b0 = b[0]; best.b1 = b[1]; best.b2 = b[2];
+            const T r = rsq<T>(d2) + tau;
+            thr2 = r * r;
+        }
+    };
+    if (guess >= 0) test(guess);
+    if (m.nf == 1) { if (guess != 0) test(0); return; }
+    int stack[kStack4];
+    float sdist[kStack4];
+    int sp = 0;
+    int node = 0;
+    for (int guard = 0;; guard++) {
+        if (guard > m.nf + 64) { *err |= kErrTree; break; }
+        if (COUNT) work->nodes++;
+        const Node4 nd = m.nodes4[node];
+        const float lx[4] = {nd.lox.x, nd.lox.y, nd.lox.z, nd.lox.w};
+        const float ly[4] = {nd.loy.x, nd.loy.y, nd.loy.z, nd.loy.w};
+        const float lz[4] = {nd.loz.x, nd.loz.y, nd.loz.z, nd.loz.w};
+        const float hx[4] = {nd.hix.x, nd.hix.y, nd.hix.z, nd.hix.w};
+        const float hy[4] = {nd.hiy.x, nd.hiy.y, nd.hiy.z, nd.hiy.w};
+        const float hz[4] = {nd.hiz.x, nd.hiz.y, nd.hiz.z, nd.hiz.w};
+        const int ch[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
+        T d[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) d[k] = box_d2<T>(px, py, pz, lx[k], ly[k], lz[k], hx[k], hy[k], hz[k]);
+        // leaves in reach first (they tighten the bound), nearest first
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (ch[k] < 0 && d[k] <= thr2) test(~ch[k]);
+        // internal children still in reach, sorted by distance (at most 4)
+        int ci[4];
+        T cd[4];
+        int nc = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (ch[k] >= 0 && ch[k] != kNoChild && d[k] <= thr2) {
+                int j = nc++;
+                while (j > 0 && cd[j - 1] > d[k]) { cd[j] = cd[j - 1]; ci[j] = ci[j - 1]; j--; }
+                cd[j] = d[k];
+                ci[j] = ch[k];
+            }
+        }
+        if (nc > 0) {
+            // defer the farther ones, farthest deepest
+            for (int j = nc - 1; j >= 1; j--) {
+                if (sp < kStack4) {
+                    stack[sp] = ci[j];
+                    sdist[sp] = store_down<T>(cd[j]);
+                    sp++;
+                } else {
+                    *err |= kErrStack;
+                }
+            }
+            node = ci[0];
+            continue;
+        }
         bool found = false;
         while (sp > 0) {
             sp--;

@@ -16,6 +16,11 @@ struct mcs_mesh_s {
     double *V = nullptr;           // nv x 3
     int32_t *F = nullptr;          // nf x 3
     mcs::Node *nodes = nullptr;    // nf - 1
+    mcs::Node4 *nodes4 = nullptr;  // n4: the same tree, 4-wide (mcs_mesh_build_wide)
+    int n4 = 0;
+    int *child = nullptr;          // binary links, parents and child boxes, kept for the 4-wide copy
+    int *parent = nullptr;
+    float *nodebox = nullptr;
     mcs::Tri32 *t32 = nullptr;     // nf
     mcs::Tri64 *t64 = nullptr;     // nf
     int32_t *inc_f = nullptr;      // 3 nf: faces of each vertex, ascending
@@ -27,7 +32,7 @@ struct mcs_mesh_s {
     float scale = 0.f;             // max |coordinate|
     mcs::DevMesh dev() const {
         mcs::DevMesh d;
-        d.V = V; d.F = F; d.nodes = nodes; d.t32 = t32; d.t64 = t64;
+        d.V = V; d.F = F; d.nodes = nodes; d.nodes4 = nodes4; d.t32 = t32; d.t64 = t64;
         d.nv = nv; d.nf = nf; d.scale = scale;
         return d;
     }

@@ -209,6 +209,57 @@ __global__ void k_pack_nodes(int n, const int *child, const float *nodebox, Node
     nodes[i] = nd;
 }
 
+// depth parity of every internal node (the root has depth 0)
+__global__ void k_even_depth(int n, const int *parent_int, int *even, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = 0, p = i;
+    while (p != 0) {
+        p = parent_int[p];
+        if (++d > 130 || p < 0 || p >= n - 1) { atomicOr(err, kErrTree); even[i] = 0; return; }
+    }
+    even[i] = (d & 1) == 0;
+}
+
+// 4-wide nodes: every binary node at even depth keeps its children, with an
+// internal child (odd depth) replaced by that child's two children; boxes
+// are copied, so the 4-wide tree bounds exactly what the binary one does
+__global__ void k_collapse4(int n, const int *child, const float *nodebox, const int *even, const int *idx4,
+                            Node4 *nodes4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1 || !even[i]) return;
+    float lo[3][4], hi[3][4];
+    int ch[4];
+    int k = 0;
+    auto add = [&](const float *b, int c) {
+        for (int a = 0; a < 3; a++) { lo[a][k] = b[a]; hi[a][k] = b[3 + a]; }
+        ch[k] = c < 0 ? c : idx4[c];
+        k++;
+    };
+    for (int side = 0; side < 2; side++) {
+        const int c = child[2 * i + side];
+        if (c < 0) {
+            add(nodebox + 12 * i + 6 * side, c);
+        } else {
+            for (int g = 0; g < 2; g++) add(nodebox + 12 * c + 6 * g, child[2 * c + g]);
+        }
+    }
+    for (; k < 4; k++) {
+        for (int a = 0; a < 3; a++) { lo[a][k] = INFINITY; hi[a][k] = -INFINITY; }
+        ch[k] = kNoChild;
+    }
+    Node4 nd;
+    nd.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    nd.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    nd.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    nd.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    nd.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    nd.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    nd.child = make_int4(ch[0], ch[1], ch[2], ch[3]);
+    nd.pad = make_int4(0, 0, 0, 0);
+    nodes4[idx4[i]] = nd;
+}
+
 __global__ void k_incidence(const int32_t *F, int nf, unsigned long long *pairs) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
@@ -253,14 +304,15 @@ __global__ void k_vertex_rows(const double *V, const int32_t *F, const int32_t *
     area[v] = A / 3.0;
 }
 
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void k_closest_points(DevMesh m, const double *P, int n, double *d2, int32_t *tri, double *bary,
                                  int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     Hit<T> h;
     int e = 0;
-    closest<T>(m, (T)P[3 * i], (T)P[3 * i + 1], (T)P[3 * i + 2], -1, h, &e);
+    if (WIDE) closest4<T>(m, (T)P[3 * i], (T)P[3 * i + 1], (T)P[3 * i + 2], -1, h, &e);
+    else closest<T>(m, (T)P[3 * i], (T)P[3 * i + 1], (T)P[3 * i + 2], -1, h, &e);
     if (e) atomicOr(err, e);
     d2[i] = (double)h.d2;
     tri[i] = h.id;
@@ -295,7 +347,8 @@ static bool is_device_ptr(const void *p) {
 
 static void mesh_free(mcs_mesh_s *m) {
     if (!m) return;
-    cudaFree(m->V); cudaFree(m->F); cudaFree(m->nodes); cudaFree(m->t32); cudaFree(m->t64);
+    cudaFree(m->V); cudaFree(m->F); cudaFree(m->nodes); cudaFree(m->nodes4); cudaFree(m->t32); cudaFree(m->t64);
+    cudaFree(m->child); cudaFree(m->parent); cudaFree(m->nodebox);
     cudaFree(m->inc_f); cudaFree(m->vstart); cudaFree(m->err);
     delete m;
 }
@@ -427,6 +480,13 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         MB_CUDA(cudaMalloc(&m->nodes, sizeof(Node) * (nf - 1)));
         note_launch();
         k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, child, nodebox, m->nodes);
+        // kept for an on-demand 4-wide copy (mcs_mesh_build_wide)
+        MB_CUDA(cudaMalloc(&m->child, sizeof(int) * 2 * (nf - 1)));
+        MB_CUDA(cudaMalloc(&m->parent, sizeof(int) * (nf - 1)));
+        MB_CUDA(cudaMalloc(&m->nodebox, sizeof(float) * 12 * (nf - 1)));
+        MB_CUDA(cudaMemcpyAsync(m->child, child, sizeof(int) * 2 * (nf - 1), cudaMemcpyDeviceToDevice, st));
+        MB_CUDA(cudaMemcpyAsync(m->parent, par_i, sizeof(int) * (nf - 1), cudaMemcpyDeviceToDevice, st));
+        MB_CUDA(cudaMemcpyAsync(m->nodebox, nodebox, sizeof(float) * 12 * (nf - 1), cudaMemcpyDeviceToDevice, st));
     }
     // vertex -> incident faces, ascending
     MB_CUDA(cudaMalloc(&m->inc_f, sizeof(int32_t) * 3 * nf));
@@ -452,6 +512,53 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     return MCS_OK;
 }
 
+mcs_status mcs_mesh_build_wide(mcs_mesh m, void *stream_) {
+    MCS_ARG(m != nullptr, "mcs_mesh_build_wide: mesh is NULL");
+    if (m->nf < 2 || m->nodes4) return MCS_OK;
+    cudaStream_t st = as_stream(stream_);
+    const int nf = m->nf, tb = 256;
+    int *even = nullptr, *idx4 = nullptr, *d_err = nullptr;
+    void *d_scan = nullptr;
+    size_t scan_bytes = 0;
+    auto cleanup = [&]() { cudaFree(even); cudaFree(idx4); cudaFree(d_scan); cudaFree(d_err); };
+    cudaError_t e = cudaMalloc(&even, sizeof(int) * (nf - 1));
+    if (e == cudaSuccess) e = cudaMalloc(&idx4, sizeof(int) * nf);
+    if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, even, idx4, nf - 1, st);
+    if (e == cudaSuccess) e = cudaMalloc(&d_scan, scan_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "mcs_mesh_build_wide: allocation"); }
+    // the 4-wide copy: nodes at even depth, numbered by an exclusive scan
+    note_launch();
+    k_even_depth<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, m->parent, even, d_err);
+    e = cub::DeviceScan::ExclusiveSum(d_scan, scan_bytes, even, idx4, nf - 1, st);
+    int last[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[0], idx4 + (nf - 2), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[1], even + (nf - 2), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last[2], d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "mcs_mesh_build_wide"); }
+    if (last[2]) {
+        cleanup();
+        set_error("mcs_mesh_build_wide: internal error, malformed hierarchy");
+        return MCS_ERR_DEVICE;
+    }
+    const int n4 = last[0] + last[1];
+    Node4 *nodes4 = nullptr;
+    e = cudaMalloc(&nodes4, sizeof(Node4) * std::max(1, n4));
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "mcs_mesh_build_wide: allocation"); }
+    note_launch();
+    k_collapse4<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->nodebox, even, idx4, nodes4);
+    e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) { cudaFree(nodes4); return cuda_fail(e, "mcs_mesh_build_wide"); }
+    m->nodes4 = nodes4;
+    m->n4 = n4;
+    return MCS_OK;
+}
+
+int mcs_mesh_has_wide(mcs_mesh m) { return m && (m->nf < 2 || m->nodes4 != nullptr); }
+
 mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, void *stream_) {
     MCS_ARG(m != nullptr, "mcs_vertex_rows: mesh is NULL");
     MCS_ARG(pos && nrm && area, "mcs_vertex_rows: NULL output");
@@ -462,21 +569,27 @@ mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, v
     return MCS_OK;
 }
 
-mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, double *d2, int32_t *tri, double *bary,
-                              void *stream_) {
+mcs_status mcs_closest_points(mcs_mesh m, const double *P, int n, int prec, int layout, double *d2, int32_t *tri,
+                              double *bary, void *stream_) {
     MCS_ARG(m != nullptr, "mcs_closest_points: mesh is NULL");
     MCS_ARG(n >= 0, "mcs_closest_points: n < 0");
     MCS_ARG(prec == 32 || prec == 64, "mcs_closest_points: prec must be 32 or 64");
+    MCS_ARG(layout == 2 || layout == 4, "mcs_closest_points: layout must be 2 or 4");
+    MCS_ARG(layout == 2 || mcs_mesh_has_wide(m), "mcs_closest_points: layout 4 needs mcs_mesh_build_wide first");
     if (n == 0) return MCS_OK;
     MCS_ARG(P && d2 && tri && bary, "mcs_closest_points: NULL pointer");
     cudaStream_t st = as_stream(stream_);
     int *d_err = m->err;
     MCS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     note_launch();
-    if (prec == 64)
-        k_closest_points<double><<<(n + 127) / 128, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
-    else
-        k_closest_points<float><<<(n + 127) / 128, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+    const int g = (n + 127) / 128;
+    if (layout == 4) {
+        if (prec == 64) k_closest_points<double, true><<<g, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+        else k_closest_points<float, true><<<g, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+    } else {
+        if (prec == 64) k_closest_points<double, false><<<g, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+        else k_closest_points<float, false><<<g, 128, 0, st>>>(m->dev(), P, n, d2, tri, bary, d_err);
+    }
     int err = 0;
     MCS_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaStreamSynchronize(st));

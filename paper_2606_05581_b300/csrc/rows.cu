@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <string>
+#include <vector>
 
 #include "mcs_internal.h"
 
@@ -43,8 +45,9 @@ __device__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, i
             atomicAdd(gen, 1u);
         } else {
             const uint64_t t0 = gtime_ns();
-            while (*vgen == g) {
-                if (gtime_ns() - t0 > 2000000000ull) {
+            for (unsigned spins = 1; *vgen == g; spins++) {
+                // the clock is read every 64 polls: the wait stays bounded (~2 s)
+                if ((spins & 63) == 0 && gtime_ns() - t0 > 2000000000ull) {
                     atomicOr(err, kErrBarrier);
                     break;
                 }
@@ -55,8 +58,7 @@ __device__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, i
     __syncthreads();
 }
 
-__global__ void k_centroids(const double *V, const int32_t *F, int nf, double *cen, double *farea, double *mind,
-                            int32_t *owner) {
+__global__ void k_centroids(const double *V, const int32_t *F, int nf, double *cen, double *farea) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
@@ -65,82 +67,234 @@ __global__ void k_centroids(const double *V, const int32_t *F, int nf, double *c
     const double ac0 = c[0] - a[0], ac1 = c[1] - a[1], ac2 = c[2] - a[2];
     const double N0 = ab1 * ac2 - ab2 * ac1, N1 = ab2 * ac0 - ab0 * ac2, N2 = ab0 * ac1 - ab1 * ac0;
     farea[f] = 0.5 * sqrt(N0 * N0 + N1 * N1 + N2 * N2);
-    mind[f] = INFINITY;
-    owner[f] = -1;
 }
 
 struct FpsArgs {
-    const double *cen;
-    double *mind;
-    int32_t *owner;
+    const float *cen;   // float-rounded face centroids (by face id)
+    float *cen_s;       // the same in BVH slot order (spatially coherent ranges)
+    float *mind;        // squared distance to the nearest sample, by slot
+    int32_t *owner;     // nearest sample, by slot
+    const int32_t *face;  // face id of each slot
     int32_t *sel;
-    double *cand_v;     // 2 x gridDim candidates (double-buffered)
+    float *cand_v;      // 2 x gridDim candidates (double-buffered)
     int *cand_i;
     unsigned *bar;      // count, generation
     int *err;
     int nf, ns;
 };
 
-// greedy farthest-point sampling; sel[0] = 0
+// float-rounded centroids, by face and in slot order; distances start at +inf
+__global__ void k_fps_prep(DevMesh m, const double *cen, float *cenf, float *cen_s, float *mind, int32_t *owner,
+                           int32_t *face) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m.nf) return;
+    const int f = m.t64[s].id;
+    for (int k = 0; k < 3; k++) {
+        const float c = (float)cen[3 * f + k];
+        cen_s[3 * s + k] = c;
+        cenf[3 * f + k] = c;
+    }
+    mind[s] = INFINITY;
+    owner[s] = -1;
+    face[s] = f;
+}
+__global__ void k_fps_scatter(int nf, const int32_t *face, const int32_t *owner_s, int32_t *owner) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nf) owner[face[s]] = owner_s[s];
+}
+
+__device__ __forceinline__ bool fps_better(float v, int i, float bv, int bi) {
+    return v > bv || (v == bv && i < bi);
+}
+
+// block-wide argmax of (v, lowest i on ties); every thread gets the result
+__device__ void fps_block_max(float &v, int &i, float *rv, int *ri) {
+    rv[threadIdx.x] = v;
+    ri[threadIdx.x] = i;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && fps_better(rv[threadIdx.x + s], ri[threadIdx.x + s], rv[threadIdx.x], ri[threadIdx.x])) {
+            rv[threadIdx.x] = rv[threadIdx.x + s];
+            ri[threadIdx.x] = ri[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    v = rv[0];
+    i = ri[0];
+    __syncthreads();
+}
+
+// Greedy farthest-point sampling, sel[0] = face 0.  Block b owns a
+// contiguous range of BVH slots (a compact region of space); after each new
+// sample q it rescans its range only when q can be nearer than some current
+// distance there: when the squared distance from q to the range's centroid
+// box exceeds the range's largest distance (with a relative margin far above
+// the rounding of either), no distance in the range can drop, and the range
+// keeps its previous candidate.  The result is the plain greedy choice.
 __global__ void __launch_bounds__(256) k_fps(FpsArgs a) {
-    __shared__ double rv[256];
+    __shared__ float rv[256];
     __shared__ int ri[256];
-    __shared__ int s_next;
+    __shared__ float sbox[6];
     const unsigned nb = gridDim.x;
+    const int chunk = (a.nf + (int)nb - 1) / (int)nb;
+    const int s0 = min(a.nf, (int)blockIdx.x * chunk), s1 = min(a.nf, s0 + chunk);
+    // the range's centroid box
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
+            hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
+        }
+    for (int k = 0; k < 6; k++) {
+        rv[threadIdx.x] = k < 3 ? lo[k] : hi[k - 3];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                rv[threadIdx.x] = k < 3 ? fminf(rv[threadIdx.x], rv[threadIdx.x + w]) : fmaxf(rv[threadIdx.x], rv[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sbox[k] = rv[0];
+        __syncthreads();
+    }
+    float cv = INFINITY;  // the range's largest distance (its candidate's value)
+    int ci = 0x7FFFFFFF;
     int cur = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[0] = 0;
     for (int i = 0; i < a.ns; i++) {
-        const double qx = a.cen[3 * cur], qy = a.cen[3 * cur + 1], qz = a.cen[3 * cur + 2];
-        double bv = -1.0;
-        int bi = 0x7FFFFFFF;
-        for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < a.nf; f += nb * blockDim.x) {
-            const double d0 = a.cen[3 * f] - qx, d1 = a.cen[3 * f + 1] - qy, d2 = a.cen[3 * f + 2] - qz;
-            const double d = d0 * d0 + d1 * d1 + d2 * d2;
-            double md = a.mind[f];
-            if (d < md) {
-                md = d;
-                a.mind[f] = d;
-                a.owner[f] = i;
+        const float qx = a.cen[3 * cur], qy = a.cen[3 * cur + 1], qz = a.cen[3 * cur + 2];
+        const float e0 = fmaxf(fmaxf(sbox[0] - qx, 0.0f), qx - sbox[3]);
+        const float e1 = fmaxf(fmaxf(sbox[1] - qy, 0.0f), qy - sbox[4]);
+        const float e2 = fmaxf(fmaxf(sbox[2] - qz, 0.0f), qz - sbox[5]);
+        const float lb2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (s0 < s1 && !(lb2 * (1.0f - 1e-5f) > cv)) {
+            float bv = -1.0f;
+            int bi = 0x7FFFFFFF;
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+                const float d0 = a.cen_s[3 * s] - qx, d1 = a.cen_s[3 * s + 1] - qy, d2 = a.cen_s[3 * s + 2] - qz;
+                const float d = d0 * d0 + d1 * d1 + d2 * d2;
+                float md = a.mind[s];
+                if (d < md) {
+                    md = d;
+                    a.mind[s] = d;
+                    a.owner[s] = i;
+                }
+                const int f = a.face[s];
+                if (fps_better(md, f, bv, bi)) { bv = md; bi = f; }
             }
-            if (md > bv) { bv = md; bi = f; }
+            fps_block_max(bv, bi, rv, ri);
+            cv = bv;
+            ci = bi;
         }
         if (i + 1 == a.ns) break;
-        rv[threadIdx.x] = bv;
-        ri[threadIdx.x] = bi;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                const double ov = rv[threadIdx.x + s];
-                const int oi = ri[threadIdx.x + s];
-                if (ov > rv[threadIdx.x] || (ov == rv[threadIdx.x] && oi < ri[threadIdx.x])) {
-                    rv[threadIdx.x] = ov;
-                    ri[threadIdx.x] = oi;
-                }
-            }
-            __syncthreads();
-        }
         const int par = i & 1;
         if (threadIdx.x == 0) {
-            a.cand_v[par * nb + blockIdx.x] = rv[0];
-            a.cand_i[par * nb + blockIdx.x] = ri[0];
+            a.cand_v[par * nb + blockIdx.x] = s0 < s1 ? cv : -1.0f;
+            a.cand_i[par * nb + blockIdx.x] = ci;
         }
         __threadfence();
         grid_barrier(a.bar, a.bar + 1, nb, a.err);
-        // every block folds the candidates the same way
-        if (threadIdx.x == 0) {
-            double v = -1.0;
-            int idx = 0x7FFFFFFF;
-            for (unsigned b = 0; b < nb; b++) {
-                const double ov = ((volatile double *)a.cand_v)[par * nb + b];
-                const int oi = ((volatile int *)a.cand_i)[par * nb + b];
-                if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+        // every block folds the candidates (any folding order gives the same winner)
+        float v = -1.0f;
+        int idx = 0x7FFFFFFF;
+        for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) {
+            const float ov = __ldcg(a.cand_v + par * nb + b);
+            const int oi = __ldcg(a.cand_i + par * nb + b);
+            if (fps_better(ov, oi, v, idx)) { v = ov; idx = oi; }
+        }
+        fps_block_max(v, idx, rv, ri);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
+        cur = idx;
+    }
+}
+
+// The same greedy sampling by ONE block of kFpsThreads threads (no grid
+// barrier): warp w owns a contiguous slot range and skips it when the new
+// sample cannot be nearer than the range's largest distance; the warps'
+// candidates are folded by every warp from a double-buffered shared array.
+constexpr int kFpsThreads = 1024;
+constexpr int kFpsSmallFaces = 1 << 18;  // meshes up to this size use the one-block kernel
+
+__device__ __forceinline__ void warp_argmax(float &v, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i, o);
+        if (fps_better(ov, oi, v, i)) { v = ov; i = oi; }
+    }
+}
+
+__device__ void fps_one_block(const FpsArgs &a) {
+    constexpr int NW = kFpsThreads / 32;
+    __shared__ float cand_v[2][NW];
+    __shared__ int cand_i[2][NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int chunk = (a.nf + NW - 1) / NW;
+    const int s0 = min(a.nf, w * chunk), s1 = min(a.nf, s0 + chunk);
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int s = s0 + lane; s < s1; s += 32)
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
+            hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+        }
+    float cv = INFINITY;
+    int ci = 0x7FFFFFFF;
+    int cur = 0;
+    if (threadIdx.x == 0) a.sel[0] = 0;
+    for (int i = 0; i < a.ns; i++) {
+        const float qx = a.cen[3 * cur], qy = a.cen[3 * cur + 1], qz = a.cen[3 * cur + 2];
+        const float e0 = fmaxf(fmaxf(lo[0] - qx, 0.0f), qx - hi[0]);
+        const float e1 = fmaxf(fmaxf(lo[1] - qy, 0.0f), qy - hi[1]);
+        const float e2 = fmaxf(fmaxf(lo[2] - qz, 0.0f), qz - hi[2]);
+        const float lb2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (s0 < s1 && !(lb2 * (1.0f - 1e-5f) > cv)) {
+            float bv = -1.0f;
+            int bi = 0x7FFFFFFF;
+            for (int s = s0 + lane; s < s1; s += 32) {
+                const float d0 = a.cen_s[3 * s] - qx, d1 = a.cen_s[3 * s + 1] - qy, d2 = a.cen_s[3 * s + 2] - qz;
+                const float d = d0 * d0 + d1 * d1 + d2 * d2;
+                float md = a.mind[s];
+                if (d < md) {
+                    md = d;
+                    a.mind[s] = d;
+                    a.owner[s] = i;
+                }
+                const int f = a.face[s];
+                if (fps_better(md, f, bv, bi)) { bv = md; bi = f; }
             }
-            s_next = idx;
-            if (blockIdx.x == 0) a.sel[i + 1] = idx;
+            warp_argmax(bv, bi);
+            cv = bv;
+            ci = bi;
+        }
+        if (i + 1 == a.ns) break;
+        const int par = i & 1;
+        if (lane == 0) {
+            cand_v[par][w] = s0 < s1 ? cv : -1.0f;
+            cand_i[par][w] = ci;
         }
         __syncthreads();
-        cur = s_next;
+        float v = lane < NW ? cand_v[par][lane] : -1.0f;
+        int idx = lane < NW ? cand_i[par][lane] : 0x7FFFFFFF;
+        warp_argmax(v, idx);
+        if (threadIdx.x == 0) a.sel[i + 1] = idx;
+        cur = idx;
     }
+}
+__global__ void __launch_bounds__(kFpsThreads) k_fps_block(FpsArgs a) { fps_one_block(a); }
+// many meshes at once: block b samples mesh b
+__global__ void __launch_bounds__(kFpsThreads) k_fps_blocks(const FpsArgs *table) { fps_one_block(table[blockIdx.x]); }
+constexpr int kFpsChunk = 100;
+struct FpsChunk {
+    FpsArgs a[kFpsChunk];
+    int count, base;
+};
+__global__ void k_store_fps(FpsChunk c, FpsArgs *table) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) table[c.base + i] = c.a[i];
 }
 
 __global__ void k_owner_keys(const int32_t *owner, int nf, int32_t *keys, int32_t *vals) {
@@ -252,7 +406,8 @@ __global__ void k_orient(const float *partial, int ns, double *nrm, float *gap) 
 }
 
 struct Layout {
-    size_t cen, farea, mind, owner, cand_v, cand_i, bar, err, keys, vals, skeys, svals, start, q, partial, sort, total;
+    size_t cen, cen_s, cenf, face, farea, mind, owner, cand_v, cand_i, bar, err, keys, vals, skeys, svals, start, q, partial, sort,
+        total;
     size_t sort_bytes;
 };
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -261,10 +416,13 @@ static Layout layout(int nf, int ns, int nblocks) {
     size_t o = 0;
     auto take = [&](size_t b) { const size_t at = o; o = a256(o + b); return at; };
     L.cen = take(sizeof(double) * 3 * nf);
+    L.cen_s = take(sizeof(float) * 3 * nf);
+    L.cenf = take(sizeof(float) * 3 * nf);
+    L.face = take(sizeof(int32_t) * nf);
     L.farea = take(sizeof(double) * nf);
-    L.mind = take(sizeof(double) * nf);
+    L.mind = take(sizeof(float) * nf);
     L.owner = take(sizeof(int32_t) * nf);
-    L.cand_v = take(sizeof(double) * 2 * nblocks);
+    L.cand_v = take(sizeof(float) * 2 * nblocks);
     L.cand_i = take(sizeof(int) * 2 * nblocks);
     L.bar = take(sizeof(unsigned) * 2);
     L.err = take(sizeof(int));
@@ -284,57 +442,59 @@ static Layout layout(int nf, int ns, int nblocks) {
     return L;
 }
 
-static int fps_blocks() {
+// blocks of the FPS launch: about 16 faces per thread (small meshes keep the
+// grid barrier cheap), at most 4 resident blocks per SM
+static int fps_blocks(int nf) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fps, 256, 0);
-    return num_sms() * std::max(1, std::min(occ, 4));
+    const int cap = num_sms() * std::max(1, std::min(occ, 4));
+    const int want = (nf + 256 * 16 - 1) / (256 * 16);
+    return std::max(1, std::min(cap, want));
 }
 
-}  // namespace rows
-}  // namespace mcs
-
-using namespace mcs;
-using namespace mcs::rows;
-
-extern "C" {
-
-size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n) {
-    if (!m || n <= 0) return 0;
-    return layout(m->nf, n, fps_blocks()).total;
+static mcs_status sample_check(const mcs_sample_item &it, const char *fn) {
+    const std::string f(fn);
+    MCS_ARG(it.mesh != nullptr, f + ": mesh is NULL");
+    MCS_ARG(it.n >= 1 && it.n <= it.mesh->nf, f + ": need 1 <= n <= nf");
+    MCS_ARG(it.sel && it.pos && it.nrm && it.area && it.tri2bin, f + ": NULL output");
+    return MCS_OK;
 }
 
-mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,
-                           int32_t *tri2bin, float *orient_gap, void *workspace, size_t workspace_bytes,
-                           void *stream_) {
-    MCS_ARG(m != nullptr, "mcs_sample_rows: mesh is NULL");
-    MCS_ARG(n >= 1 && n <= m->nf, "mcs_sample_rows: need 1 <= n <= nf");
-    MCS_ARG(sel && pos && nrm && area && tri2bin, "mcs_sample_rows: NULL output");
-    const int nb = fps_blocks();
-    const Layout L = layout(m->nf, n, nb);
-    MCS_ARG(workspace && workspace_bytes >= L.total, "mcs_sample_rows: workspace too small");
-    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_sample_rows: workspace must be 256-byte aligned");
-    int coop = 0, dev = 0;
-    MCS_CUDA(cudaGetDevice(&dev));
-    MCS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    MCS_ARG(coop, "mcs_sample_rows: the device does not support cooperative launches");
-    cudaStream_t st = as_stream(stream_);
-    char *w = (char *)workspace;
-    double *cen = (double *)(w + L.cen), *farea = (double *)(w + L.farea), *mind = (double *)(w + L.mind);
-    int32_t *owner = tri2bin;  // the owner of each face is the output column map
+// centroids, areas and the slot-order copies; the FPS arguments of the mesh
+static mcs_status sample_prepare(const mcs_sample_item &it, char *w, const Layout &L, int nb, cudaStream_t st,
+                                 FpsArgs *out) {
+    mcs_mesh m = it.mesh;
+    const int nf = m->nf, tb = 256;
+    double *cen = (double *)(w + L.cen), *farea = (double *)(w + L.farea);
+    float *mind = (float *)(w + L.mind);
     int *err = (int *)(w + L.err);
     unsigned *bar = (unsigned *)(w + L.bar);
-    const int nf = m->nf, tb = 256;
     MCS_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
     MCS_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     note_launch();
-    k_centroids<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, cen, farea, mind, owner);
-    FpsArgs a;
-    a.cen = cen; a.mind = mind; a.owner = owner; a.sel = sel;
-    a.cand_v = (double *)(w + L.cand_v); a.cand_i = (int *)(w + L.cand_i);
-    a.bar = bar; a.err = err; a.nf = nf; a.ns = n;
-    void *args[] = {&a};
+    k_centroids<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, cen, farea);
+    float *cen_s = (float *)(w + L.cen_s), *cenf = (float *)(w + L.cenf);
+    int32_t *face = (int32_t *)(w + L.face), *owner_s = (int32_t *)(w + L.owner);
     note_launch();
-    MCS_CUDA(cudaLaunchCooperativeKernel((void *)k_fps, dim3(nb), dim3(256), args, 0, st));
+    k_fps_prep<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->dev(), cen, cenf, cen_s, mind, owner_s, face);
+    FpsArgs &a = *out;
+    a.cen = cenf; a.cen_s = cen_s; a.mind = mind; a.owner = owner_s; a.face = face; a.sel = it.sel;
+    a.cand_v = (float *)(w + L.cand_v); a.cand_i = (int *)(w + L.cand_i);
+    a.bar = bar; a.err = err; a.nf = nf; a.ns = it.n;
+    (void)nb;
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+// owners by face, quadrature areas, row points and normals (+ orientation)
+static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, const Layout &L, cudaStream_t st) {
+    mcs_mesh m = it.mesh;
+    const int nf = m->nf, n = it.n, tb = 256;
+    double *cen = (double *)(w + L.cen), *farea = (double *)(w + L.farea);
+    int32_t *face = (int32_t *)(w + L.face), *owner_s = (int32_t *)(w + L.owner);
+    int32_t *owner = it.tri2bin;  // the owner of each face is the output column map
+    note_launch();
+    k_fps_scatter<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, face, owner_s, owner);
     // quadrature areas: faces sorted (stably) by owner, summed in ascending face order
     int32_t *keys = (int32_t *)(w + L.keys), *vals = (int32_t *)(w + L.vals);
     int32_t *skeys = (int32_t *)(w + L.skeys), *svals = (int32_t *)(w + L.svals);
@@ -347,25 +507,128 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
     note_launch();
     k_segments<<<(nf + tb - 1) / tb, tb, 0, st>>>(skeys, nf, n, start);
     note_launch();
-    k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, sel, svals, start, n, pos, nrm, area);
+    k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, it.sel, svals, start, n, it.pos, it.nrm,
+                                                    it.area);
     if (orient) {
         float4 *q = (float4 *)(w + L.q);
         float *partial = (float *)(w + L.partial);
         note_launch();
-        k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(pos, nrm, farea, sel, n, q);
+        k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, farea, it.sel, n, q);
         note_launch();
         k_gwn<<<dim3((2 * n + 255) / 256, kGwnChunks), 256, 0, st>>>(m->V, m->F, nf, q, 2 * n, partial);
         note_launch();
-        k_orient<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, n, nrm, orient_gap);
+        k_orient<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, n, it.nrm, it.orient_gap);
     }
     MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
+}  // namespace rows
+}  // namespace mcs
+
+using namespace mcs;
+using namespace mcs::rows;
+
+extern "C" {
+
+size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n) {
+    if (!m || n <= 0) return 0;
+    return layout(m->nf, n, fps_blocks(m->nf)).total;
+}
+
+mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,
+                           int32_t *tri2bin, float *orient_gap, void *workspace, size_t workspace_bytes,
+                           void *stream_) {
+    mcs_sample_item it;
+    it.mesh = m;
+    it.n = n;
+    it.sel = sel;
+    it.pos = pos;
+    it.nrm = nrm;
+    it.area = area;
+    it.tri2bin = tri2bin;
+    it.orient_gap = orient_gap;
+    mcs_status s = sample_check(it, "mcs_sample_rows");
+    if (s != MCS_OK) return s;
+    const int nb = fps_blocks(m->nf);
+    const Layout L = layout(m->nf, n, nb);
+    MCS_ARG(workspace && workspace_bytes >= L.total, "mcs_sample_rows: workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_sample_rows: workspace must be 256-byte aligned");
+    cudaStream_t st = as_stream(stream_);
+    char *w = (char *)workspace;
+    FpsArgs a;
+    if ((s = sample_prepare(it, w, L, nb, st, &a)) != MCS_OK) return s;
+    if (m->nf <= kFpsSmallFaces) {
+        note_launch();
+        k_fps_block<<<1, kFpsThreads, 0, st>>>(a);
+    } else {
+        int coop = 0, dev = 0;
+        MCS_CUDA(cudaGetDevice(&dev));
+        MCS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        MCS_ARG(coop, "mcs_sample_rows: the device does not support cooperative launches");
+        void *args[] = {&a};
+        note_launch();
+        MCS_CUDA(cudaLaunchCooperativeKernel((void *)k_fps, dim3(nb), dim3(256), args, 0, st));
+    }
+    if ((s = sample_finish(it, orient, w, L, st)) != MCS_OK) return s;
     int herr = 0;
-    MCS_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaMemcpyAsync(&herr, w + L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaStreamSynchronize(st));
     if (herr) {
         set_error("mcs_sample_rows: a grid barrier wait timed out");
         return MCS_ERR_DEVICE;
     }
+    return MCS_OK;
+}
+
+size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int count) {
+    if (!items || count <= 0) return 0;
+    size_t o = a256(sizeof(FpsArgs) * (size_t)count);
+    for (int i = 0; i < count; i++) {
+        if (!items[i].mesh || items[i].n <= 0) return 0;
+        o += a256(layout(items[i].mesh->nf, items[i].n, 1).total);
+    }
+    return o;
+}
+
+mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int orient, void *workspace,
+                                   size_t workspace_bytes, void *stream_) {
+    MCS_ARG(items != nullptr && count > 0, "mcs_sample_rows_batched: no items");
+    for (int i = 0; i < count; i++) {
+        const mcs_status s = sample_check(items[i], "mcs_sample_rows_batched");
+        if (s != MCS_OK) return s;
+    }
+    const size_t need = mcs_sample_rows_batched_workspace_size(items, count);
+    MCS_ARG(workspace && workspace_bytes >= need, "mcs_sample_rows_batched: workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_sample_rows_batched: workspace must be 256-byte aligned");
+    cudaStream_t st = as_stream(stream_);
+    char *w = (char *)workspace;
+    FpsArgs *table = (FpsArgs *)w;
+    size_t o = a256(sizeof(FpsArgs) * (size_t)count);
+    std::vector<FpsArgs> args(count);
+    std::vector<Layout> lay(count);
+    std::vector<size_t> base(count);
+    mcs_status s;
+    for (int i = 0; i < count; i++) {
+        lay[i] = layout(items[i].mesh->nf, items[i].n, 1);
+        base[i] = o;
+        o += a256(lay[i].total);
+        if ((s = sample_prepare(items[i], w + base[i], lay[i], 1, st, &args[i])) != MCS_OK) return s;
+    }
+    // every mesh's farthest-point sampling in one launch, one block per mesh
+    for (int b0 = 0; b0 < count; b0 += kFpsChunk) {
+        FpsChunk c;
+        c.count = std::min(kFpsChunk, count - b0);
+        c.base = b0;
+        for (int i = 0; i < c.count; i++) c.a[i] = args[b0 + i];
+        note_launch();
+        k_store_fps<<<1, 128, 0, st>>>(c, table);
+    }
+    note_launch();
+    k_fps_blocks<<<count, kFpsThreads, 0, st>>>(table);
+    for (int i = 0; i < count; i++)
+        if ((s = sample_finish(items[i], orient, w + base[i], lay[i], st)) != MCS_OK) return s;
+    MCS_CUDA(cudaStreamSynchronize(st));
     return MCS_OK;
 }
 

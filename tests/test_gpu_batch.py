@@ -33,7 +33,7 @@ def _items():
     ]
     items = []
     for m, rows, dom, seed in specs:
-        mesh = mcs.Mesh(m.V, m.F)
+        mesh = mcs.Mesh(m.V, m.F).build_wide()
         r = mcs.vertex_rows(mesh) if rows == "vertex" else mcs.sample_rows(mesh, rows, orient=True)
         items.append(dict(mesh=mesh, rows=r, domain=dom, seed=seed, host=m))
     return items
@@ -134,9 +134,9 @@ def test_queue_orders_and_launch_shapes_do_not_change_results():
     b = mcs.Batch(items, p, assemble=False, record_exits=True)
     b.run()
     ref = [b.result(i)["exit_tri"].clone() for i in range(len(items))]
-    for qo, tpb, bps in ((1, 64, 3), (2, 128, 2), (3, 96, 1)):
+    for qo, tpb, bps, lay in ((1, 64, 3, 2), (2, 128, 2, 4), (3, 96, 1, 2), (0, 128, 6, 4)):
         q = mcs.default_params(walks_per_row=32, prec=32, killing_walks=256, queue_order=qo,
-                               threads_per_block=tpb, blocks_per_sm=bps)
+                               threads_per_block=tpb, blocks_per_sm=bps, bvh_layout=lay)
         status, tot, per = b.run(q)
         for i in range(len(items)):
             assert torch.equal(b.result(i)["exit_tri"], ref[i]), (qo, i)
@@ -154,8 +154,9 @@ def test_autotuner_returns_a_valid_shape_and_same_results():
     assert tuned.threads_per_block in (64, 128) and tuned.blocks_per_sm >= 1
     assert 0 <= tuned.queue_order <= 3
     best = min(trials, key=lambda t: t["ms"])
-    assert (best["threads_per_block"], best["blocks_per_sm"], best["queue_order"]) == \
-        (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order)
+    assert (best["threads_per_block"], best["blocks_per_sm"], best["queue_order"], best["bvh_layout"]) == \
+        (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order, tuned.bvh_layout)
+    assert {t["bvh_layout"] for t in trials} == {2, 4}
     b.run()
     for i in range(len(items)):
         assert torch.equal(b.result(i)["exit_tri"], ref[i]), i
@@ -168,3 +169,14 @@ def test_batch_argument_errors():
     bad = [dict(items[0], domain=5)]
     with pytest.raises(mcs.MCSError):
         mcs.Batch(bad, mcs.default_params(walks_per_row=8)).run()
+
+
+def test_batched_sample_rows_equal_single():
+    """Farthest-point rows of several meshes in one launch equal the per-mesh call."""
+    ms = [meshgen.wild_union(5, 4000, seed=21), meshgen.icosphere(3), meshgen.wild_union(3, 9000, seed=22)]
+    meshes = [mcs.Mesh(m.V, m.F) for m in ms]
+    got = mcs.sample_rows_batched(meshes, 200, orient=True)
+    for mesh, g in zip(meshes, got):
+        one = mcs.sample_rows(mesh, 200, orient=True)
+        for k in ("sel", "tri2bin", "area", "pos", "nrm"):
+            assert torch.equal(g[k], one[k]), k

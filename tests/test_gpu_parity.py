@@ -34,9 +34,10 @@ def test_philox_words_match(oracle):
     assert np.array_equal(g, c)
 
 
+@pytest.mark.parametrize("layout", [2, 4])
 @pytest.mark.parametrize("which", ["ico2", "two3", "wild"])
 @pytest.mark.parametrize("prec", [64, 32])
-def test_closest_points_bit_exact(oracle, which, prec):
+def test_closest_points_bit_exact(oracle, which, prec, layout):
     m = {"ico2": lambda: meshgen.icosphere(2), "two3": lambda: meshgen.two_spheres(3, 0.5, 1.5),
          "wild": lambda: meshgen.wild_union(6, 6000, seed=4)}[which]()
     rng = np.random.default_rng(7)
@@ -45,7 +46,9 @@ def test_closest_points_bit_exact(oracle, which, prec):
     P[:50] = m.V[:50]                         # on vertices: exact ties between faces
     P[50:100] = m.V[m.F[:50]].mean(1)         # on faces
     mesh = mcs.Mesh(m.V, m.F)
-    d2g, fg, bg = (t.cpu().numpy() for t in mcs.closest_points(mesh, torch.from_numpy(P), prec))
+    if layout == 4:
+        mesh.build_wide()
+    d2g, fg, bg = (t.cpu().numpy() for t in mcs.closest_points(mesh, torch.from_numpy(P), prec, layout))
     d2c, fc, bc = oracle.closest_points(m.V, m.F, P, prec)
     assert np.array_equal(fg, fc)
     assert np.array_equal(d2g, d2c)
@@ -82,6 +85,8 @@ def _compare(oracle, m, rows_np, W, eps, prec, exterior=False, killing=0, seed=0
     assert np.array_equal(res["exit_tri"].cpu().numpy()[rl], est["exit_tri"])
     if killing:
         assert np.array_equal(res["H0"].cpu().numpy(), est["H0"])
+    if row_list is None:
+        assert st["lost"] == est["lost"].sum() + est["kill_stats"][2]
     om = res["omega"].cpu().numpy()[rl]
     assert np.array_equal(om, oracle.row_weights(est, rows_np))
     if check_L and row_list is None:
@@ -144,8 +149,9 @@ def test_lambda_invariants_icosphere():
     m = meshgen.icosphere(3)
     mesh = mcs.Mesh(m.V, m.F)
     rows = mcs.vertex_rows(mesh)
-    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32))
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32), fp32_copy=True)
     L = res["Lambda"].cpu().numpy()
+    assert np.array_equal(res["Lambda32"].cpu().numpy(), L.astype(np.float32))
     assert np.array_equal(L, L.T)
     assert np.abs(L.sum(1)).max() < 1e-12 * np.abs(L).max()
     assert np.linalg.eigvalsh(L).min() > -1e-10 * np.abs(L).max()
@@ -204,3 +210,37 @@ def test_sample_rows_estimate_bit_exact(oracle, prec):
     rows_np = dict(pos=g["pos"].cpu().numpy(), nrm=g["nrm"].cpu().numpy(), area=g["area"].cpu().numpy(),
                    tri2bin=g["tri2bin"].cpu().numpy())
     _compare(oracle, m, rows_np, 64, 1e-3, prec)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_exterior_escapes_bit_exact(oracle, prec):
+    """Exterior of nested spheres with the inversion centre in the gap: walks of
+    the inner sphere's rows that wander towards the centre are retired without a
+    hit, on the GPU exactly as in the oracle (reading R17)."""
+    A = meshgen.icosphere(3, 1.0)
+    B = meshgen.icosphere(3, 0.3)
+    m = meshgen.Mesh(np.concatenate([A.V, B.V]), np.concatenate([A.F, B.F + A.nv]), "nested spheres")
+    rows = oracle.vertex_rows(m.V, m.F)
+    res, est = _compare(oracle, m, rows, 16, 1e-3, prec, exterior=True, killing=256, seed=5,
+                        origin=np.array([0.65, 0.0, 0.0]))
+    assert res["stats"]["lost"] > 0 and res["stats"]["capped"] == 0
+    assert res["status"] == 3
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_interior_walks_retired_in_the_unbounded_component(oracle, prec):
+    """An inside-out sphere: interior walks start outside; the ones that wander
+    off are retired without a hit on the GPU exactly as in the oracle (R18)."""
+    m = meshgen.icosphere(3, 1.0)
+    m = meshgen.Mesh(m.V, m.F[:, ::-1].copy(), "inside-out sphere")
+    rows = oracle.vertex_rows(m.V, m.F)
+    res, est = _compare(oracle, m, rows, 16, 1e-3, prec, seed=3)
+    assert res["stats"]["lost"] > 0 and res["stats"]["capped"] == 0
+    assert res["status"] == 3
+
+
+def test_wild_exterior_rows_bit_exact(oracle):
+    """Sample rows of an overlapping union, exterior, FP32: pockets, escapes and all."""
+    m = meshgen.wild_union(6, 5000, seed=9)
+    rows = oracle.fps_rows(m.V, m.F, 200, orient=True)
+    _compare(oracle, m, rows, 32, 1e-3, 32, exterior=True, killing=512, seed=2)
