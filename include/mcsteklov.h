@@ -286,8 +286,8 @@ size_t mcs_graph_nodes(mcs_graph g);
 void mcs_graph_destroy(mcs_graph g);
 
 /* Autotuner of the walk launch.  Runs the batch's row setup, then times the
- * walk kernel on a sample (the first ceil(sample_fraction * n_rows) rows of
- * every mesh, no killing walks) for the two BVH node layouts (when
+ * walk kernel on a sample (every s-th row of every mesh's row schedule,
+ * s = floor(1 / sample_fraction), no killing walks) for the two BVH node layouts (when
  * p->bvh_layout is 0), candidate block sizes (64, 128 threads), resident
  * blocks per SM (the three largest residencies the kernel allows) and queue
  * orders (row order, mesh order), by coordinate search in that order; the

@@ -108,13 +108,43 @@ __global__ void k_order_from_keys(const unsigned long long *keys, int R, int32_t
 // than (1 - kappa) r, which is the oracle's dist >= (1 - kappa) r decision.
 constexpr int kTanWarps = 4;
 
+// Tangent-ball queries are FP64 decisions (the oracle's); an FP32 query on
+// the float triangles answers them first whenever it is clear of a band of
+// half-width E = 2^-16 (scale + |p|inf) around the threshold -- E bounds the
+// float rounding of the point, of the triangle vertices and of the distance
+// arithmetic many times over -- and the FP64 query decides the rest.
+__device__ __forceinline__ double fp32_band(const DevMesh &m, double x, double y, double z) {
+    return 1.52587890625e-05 * ((double)m.scale + fmax(fabs(x), fmax(fabs(y), fabs(z))));
+}
+
+// dist(p) in FP64 (the exact argmin distance): an FP32 query bounds it, then
+// the FP64 query searches only the triangles within that bound
 __device__ __forceinline__ double wdist(const DevMesh &m, double x, double y, double z, int *front, int *err) {
     Hit<double> h;
-    warp_query<double, kFull>(m, x, y, z, 0.0, h, front, err);
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    double bound = 0.0;
+    if (isfinite(xf) && isfinite(yf) && isfinite(zf)) {
+        Hit<float> hf;
+        warp_query<float, kFull>(m, xf, yf, zf, 0.0f, hf, front, err);
+        if (hf.slot >= 0 && isfinite(hf.d2)) bound = sqrt((double)hf.d2) + 2.0 * fp32_band(m, x, y, z);
+    }
+    warp_query<double, kFull>(m, x, y, z, bound, h, front, err);
+    if (h.slot < 0 && bound > 0.0) warp_query<double, kFull>(m, x, y, z, 0.0, h, front, err);
     return sqrt(h.d2);
 }
+// dist(p) >= thr, decided as the FP64 query would
 __device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, double z, double thr, int *front,
                                        int *err) {
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    const double E = fp32_band(m, x, y, z);
+    if (isfinite(xf) && isfinite(yf) && isfinite(zf) && thr > 2.0 * E) {
+        // the float distances below thr + E (if any): none -> clear; one below thr - E -> not clear
+        Hit<float> hf;
+        warp_query<float, kFull>(m, xf, yf, zf, (float)(thr + 2.0 * E), hf, front, err);
+        const double df = hf.slot >= 0 ? sqrt((double)hf.d2) : INFINITY;
+        if (df >= thr + E) return true;
+        if (df < thr - E) return false;
+    }
     Hit<double> h;
     return !warp_query<double, kBelow>(m, x, y, z, thr, h, front, err);
 }
@@ -192,7 +222,7 @@ __device__ void origin_argmax_block(const RowBall *ball, int R, int stride, Ctrl
     }
     if (threadIdx.x == 0) {
         const int v = si[0];
-        ctrl->argmax_row = v;
+        ctrl->argmax_row = sv[0] > 0.0 ? v : -1;
         if (!(sv[0] > 0.0)) {
             ctrl->err |= kErrNoOrigin;
             ctrl->origin[0] = ctrl->origin[1] = ctrl->origin[2] = 0.0;
@@ -221,7 +251,9 @@ __global__ void k_set_origin(Ctrl *ctrl, double x, double y, double z) {
 // (a pocket of a self-overlapping surface) and is retired without a hit
 constexpr int kFrameThreads = 256;
 // one block of kFrameThreads threads, after the origin is set
-__device__ void ext_frame_block(const DevMesh &m, const double *V, int nv, Ctrl *ctrl) {
+// auto_ball: the rows' interior balls when the origin is the centre of the
+// ball of ctrl->argmax_row (its empty radius is dist(o)); null otherwise
+__device__ void ext_frame_block(const DevMesh &m, const double *V, int nv, Ctrl *ctrl, const RowBall *auto_ball) {
     __shared__ double sm[7][kFrameThreads];
     const double o0 = ctrl->origin[0], o1 = ctrl->origin[1], o2 = ctrl->origin[2];
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mr = 0.0;
@@ -253,12 +285,14 @@ __device__ void ext_frame_block(const DevMesh &m, const double *V, int nv, Ctrl 
         ctrl->rmax_ext = 0.5 * side;
         ctrl->rho0max = 1.0 / sm[6][0];
     }
-    // dist(o) by one warp (a single thread would visit every triangle alone
-    // when o is equidistant from many of them, as at a sphere's centre)
+    // dist(o): the origin ball's empty radius, else by one warp (a single
+    // thread would visit every triangle alone when o is equidistant from many
+    // of them, as at a sphere's centre)
     __shared__ int front[32];
     if (threadIdx.x < 32) {
         int err = 0;
-        const double d = wdist(m, o0, o1, o2, front, &err);
+        const int am = ctrl->argmax_row;
+        const double d = auto_ball ? (am >= 0 ? auto_ball[am].rho : 0.0) : wdist(m, o0, o1, o2, front, &err);
         if (threadIdx.x == 0) {
             ctrl->esc2 = d > 0.0 ? 4.0 / (d * d) : INFINITY;
             ctrl->origin_f[0] = (float)o0;
@@ -270,8 +304,9 @@ __device__ void ext_frame_block(const DevMesh &m, const double *V, int nv, Ctrl 
         }
     }
 }
-__global__ void __launch_bounds__(kFrameThreads) k_ext_frame(DevMesh m, const double *V, int nv, Ctrl *ctrl) {
-    ext_frame_block(m, V, nv, ctrl);
+__global__ void __launch_bounds__(kFrameThreads) k_ext_frame(DevMesh m, const double *V, int nv, Ctrl *ctrl,
+                                                            const RowBall *auto_ball) {
+    ext_frame_block(m, V, nv, ctrl, auto_ball);
 }
 
 // exterior tangent ball: the inverted ball B(c~, r) (not containing 0) is the
@@ -383,7 +418,7 @@ struct WalkJob {
     int R, W;
     uint32_t k0, k1;
     int ext;
-    int pad;
+    int row_stride;                   // sorted row positions 0, s, 2s, ... (autotuner samples; else 1)
 };
 
 struct MultiArgs {
@@ -502,7 +537,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         if (s.kill) {
             if (bin >= 0) atomicAdd(&J.H0[bin], 1);
         } else {
-            const int rp = (int)(s.li / (unsigned long long)J.W), j = (int)(s.li % (unsigned long long)J.W);
+            const int rp = (int)(s.li / (unsigned long long)J.W) * J.row_stride, j = (int)(s.li % (unsigned long long)J.W);
             J.exits[(size_t)rp * J.W + j] = bin;
             if (J.exit_tri) J.exit_tri[(size_t)s.v * J.W + j] = f;
         }
@@ -546,7 +581,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                     } else {
                         s.kill = 0;
                         s.k1 = J.k1;
-                        const int rp = (int)(s.li / (unsigned long long)J.W), j = (int)(s.li % (unsigned long long)J.W);
+                        const int rp = (int)(s.li / (unsigned long long)J.W) * J.row_stride,
+                                  j = (int)(s.li % (unsigned long long)J.W);
                         const int v = J.order[rp];
                         const RowBall &b = J.ball[v];
                         s.v = v;
@@ -938,7 +974,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_b_frame(const MeshJob *jobs) 
         J.ctrl->origin[2] = J.origin[2];
     }
     __syncthreads();
-    ext_frame_block(J.m, J.V, J.nv, J.ctrl);
+    ext_frame_block(J.m, J.V, J.nv, J.ctrl, J.origin_auto ? J.ball : nullptr);
 }
 // exterior tangent balls of every row of the exterior meshes
 __global__ void __launch_bounds__(32 * kTanWarps) k_b_tangent_ext(const MeshJob *jobs, const int *unit0, int n,
@@ -1168,7 +1204,7 @@ static mcs_status enqueue_setup(const Plan &pl, int row_order, cudaStream_t st) 
             k_set_origin<<<1, 1, 0, st>>>(pl.ctrl, pl.origin[0], pl.origin[1], pl.origin[2]);
         }
         note_launch();
-        k_ext_frame<<<1, kFrameThreads, 0, st>>>(dm, pl.m->V, pl.m->nv, pl.ctrl);
+        k_ext_frame<<<1, kFrameThreads, 0, st>>>(dm, pl.m->V, pl.m->nv, pl.ctrl, pl.origin_auto ? pl.ball() : nullptr);
         note_launch();
         k_tangent_ext<<<tgrid, 32 * kTanWarps, 0, st>>>(dm, pl.rows.pos, pl.rows.nrm, R, pl.fr, pl.ball(), pl.ctrl);
         note_launch();
@@ -1204,7 +1240,7 @@ static WalkJob make_job(const Plan &pl, unsigned long long n_row_walks, unsigned
     J.k0 = (uint32_t)pl.seed;
     J.k1 = (uint32_t)(pl.seed >> 32);
     J.ext = pl.ext;
-    J.pad = 0;
+    J.row_stride = 1;
     return J;
 }
 
@@ -1924,10 +1960,14 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
         bq.p = q;
         std::vector<WalkJob> jobs;
         for (int i : job_order(bq)) {
+            // every stride-th row of the mesh's schedule: a sample spread over the whole mesh
             const Plan &pl = b.plans[i];
-            const unsigned long long rows =
-                std::max<unsigned long long>(1, (unsigned long long)std::ceil(sample_fraction * pl.rows.n_rows));
-            jobs.push_back(make_job(pl, std::min<unsigned long long>(rows, pl.rows.n_rows) * pl.W, 0));
+            const int R = pl.rows.n_rows;
+            const int stride = std::max(1, (int)std::floor(1.0 / sample_fraction));
+            const unsigned long long rows = (unsigned long long)((R + stride - 1) / stride);
+            WalkJob J = make_job(pl, rows * pl.W, 0);
+            J.row_stride = stride;
+            jobs.push_back(J);
         }
         if (b.n > 1 && (r = store_jobs(jobs, b.jobs, b.offs, st)) != MCS_OK) return r;
         int tpb = 0, bps = 0;

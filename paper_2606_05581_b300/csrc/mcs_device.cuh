@@ -489,7 +489,8 @@ __device__ void closest4(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &
 // The top of the tree is expanded breadth-first into at most 32 subtrees
 // (one per lane), each lane then traverses its subtree depth-first; the
 // pruning bound is shared through warp reductions.
-//   kFull:  exact argmin of (d^2, id) over all triangles (as `closest`)
+//   kFull:  exact argmin of (d^2, id) over all triangles (as `closest`);
+//           with thr > 0, over the triangles nearer than thr (none: slot < 0)
 //   kBelow: whether some triangle has sqrt(d^2) < thr (early exit), i.e. the
 //           negation of sqrt(min d^2) >= thr, decided on the same per-triangle
 //           values as the brute-force scan
@@ -512,7 +513,9 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
     const int lane = threadIdx.x & 31;
     const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
     T bound2;  // prune a box when its squared distance exceeds this
-    if (MODE == kBelow) {
+    if (MODE == kBelow || thr > (T)0) {
+        // kFull with thr > 0: only triangles nearer than thr are searched
+        // (out.slot < 0 when there is none)
         const T r = thr + tau;
         bound2 = r * r;
     } else {
@@ -534,7 +537,7 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
     auto refresh = [&]() {
         if (MODE == kFull) {
             const T r = rsq<T>(warp_min<T>(best.d2)) + tau;
-            bound2 = r * r;
+            bound2 = fmin(bound2, r * r);
         }
     };
     // ---- breadth-first expansion of the top of the tree

@@ -124,93 +124,6 @@ __device__ void fps_block_max(float &v, int &i, float *rv, int *ri) {
     __syncthreads();
 }
 
-// Greedy farthest-point sampling, sel[0] = face 0.  Block b owns a
-// contiguous range of BVH slots (a compact region of space); after each new
-// sample q it rescans its range only when q can be nearer than some current
-// distance there: when the squared distance from q to the range's centroid
-// box exceeds the range's largest distance (with a relative margin far above
-// the rounding of either), no distance in the range can drop, and the range
-// keeps its previous candidate.  The result is the plain greedy choice.
-__global__ void __launch_bounds__(256) k_fps(FpsArgs a) {
-    __shared__ float rv[256];
-    __shared__ int ri[256];
-    __shared__ float sbox[6];
-    const unsigned nb = gridDim.x;
-    const int chunk = (a.nf + (int)nb - 1) / (int)nb;
-    const int s0 = min(a.nf, (int)blockIdx.x * chunk), s1 = min(a.nf, s0 + chunk);
-    // the range's centroid box
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-        for (int k = 0; k < 3; k++) {
-            lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
-            hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
-        }
-    for (int k = 0; k < 6; k++) {
-        rv[threadIdx.x] = k < 3 ? lo[k] : hi[k - 3];
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w)
-                rv[threadIdx.x] = k < 3 ? fminf(rv[threadIdx.x], rv[threadIdx.x + w]) : fmaxf(rv[threadIdx.x], rv[threadIdx.x + w]);
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) sbox[k] = rv[0];
-        __syncthreads();
-    }
-    float cv = INFINITY;  // the range's largest distance (its candidate's value)
-    int ci = 0x7FFFFFFF;
-    int cur = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[0] = 0;
-    for (int i = 0; i < a.ns; i++) {
-        const float qx = a.cen[3 * cur], qy = a.cen[3 * cur + 1], qz = a.cen[3 * cur + 2];
-        const float e0 = fmaxf(fmaxf(sbox[0] - qx, 0.0f), qx - sbox[3]);
-        const float e1 = fmaxf(fmaxf(sbox[1] - qy, 0.0f), qy - sbox[4]);
-        const float e2 = fmaxf(fmaxf(sbox[2] - qz, 0.0f), qz - sbox[5]);
-        const float lb2 = e0 * e0 + e1 * e1 + e2 * e2;
-        if (s0 < s1 && !(lb2 * (1.0f - 1e-5f) > cv)) {
-            float bv = -1.0f;
-            int bi = 0x7FFFFFFF;
-            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-                const float d0 = a.cen_s[3 * s] - qx, d1 = a.cen_s[3 * s + 1] - qy, d2 = a.cen_s[3 * s + 2] - qz;
-                const float d = d0 * d0 + d1 * d1 + d2 * d2;
-                float md = a.mind[s];
-                if (d < md) {
-                    md = d;
-                    a.mind[s] = d;
-                    a.owner[s] = i;
-                }
-                const int f = a.face[s];
-                if (fps_better(md, f, bv, bi)) { bv = md; bi = f; }
-            }
-            fps_block_max(bv, bi, rv, ri);
-            cv = bv;
-            ci = bi;
-        }
-        if (i + 1 == a.ns) break;
-        const int par = i & 1;
-        if (threadIdx.x == 0) {
-            a.cand_v[par * nb + blockIdx.x] = s0 < s1 ? cv : -1.0f;
-            a.cand_i[par * nb + blockIdx.x] = ci;
-        }
-        __threadfence();
-        grid_barrier(a.bar, a.bar + 1, nb, a.err);
-        // every block folds the candidates (any folding order gives the same winner)
-        float v = -1.0f;
-        int idx = 0x7FFFFFFF;
-        for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) {
-            const float ov = __ldcg(a.cand_v + par * nb + b);
-            const int oi = __ldcg(a.cand_i + par * nb + b);
-            if (fps_better(ov, oi, v, idx)) { v = ov; idx = oi; }
-        }
-        fps_block_max(v, idx, rv, ri);
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
-        cur = idx;
-    }
-}
-
-// The same greedy sampling by ONE block of kFpsThreads threads (no grid
-// barrier): warp w owns a contiguous slot range and skips it when the new
-// sample cannot be nearer than the range's largest distance; the warps'
-// candidates are folded by every warp from a double-buffered shared array.
 constexpr int kFpsThreads = 1024;
 constexpr int kFpsSmallFaces = 1 << 18;  // meshes up to this size use the one-block kernel
 
@@ -223,6 +136,102 @@ __device__ __forceinline__ void warp_argmax(float &v, int &i) {
     }
 }
 
+// Greedy farthest-point sampling, sel[0] = face 0, by a cooperative grid of
+// kFpsThreads-thread blocks (one per SM at most).  Every warp of the grid
+// owns a contiguous range of BVH slots (a compact region of space); after
+// each new sample q a warp rescans its range only when q can be nearer than
+// the range's largest distance: when the squared distance from q to the
+// range's centroid box exceeds that distance (with a relative margin far
+// above the float rounding of either), no distance in the range can drop and
+// the range keeps its candidate.  The warps' candidates are folded per block,
+// the blocks' across the grid after a grid barrier.  The result is the plain
+// greedy choice.
+__global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
+    constexpr int NW = kFpsThreads / 32;
+    __shared__ float wv[2][NW];
+    __shared__ int wi[2][NW];
+    const unsigned nb = gridDim.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * NW + w, nw = (int)nb * NW;
+    const int chunk = (a.nf + nw - 1) / nw;
+    const int s0 = min(a.nf, gw * chunk), s1 = min(a.nf, s0 + chunk);
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int s = s0 + lane; s < s1; s += 32)
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
+            hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+        }
+    float cv = INFINITY;  // the range's largest distance (its candidate's value)
+    int ci = 0x7FFFFFFF;
+    int cur = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[0] = 0;
+    for (int i = 0; i < a.ns; i++) {
+        const float qx = a.cen[3 * cur], qy = a.cen[3 * cur + 1], qz = a.cen[3 * cur + 2];
+        const float e0 = fmaxf(fmaxf(lo[0] - qx, 0.0f), qx - hi[0]);
+        const float e1 = fmaxf(fmaxf(lo[1] - qy, 0.0f), qy - hi[1]);
+        const float e2 = fmaxf(fmaxf(lo[2] - qz, 0.0f), qz - hi[2]);
+        const float lb2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (s0 < s1 && !(lb2 * (1.0f - 1e-5f) > cv)) {
+            float bv = -1.0f;
+            int bi = 0x7FFFFFFF;
+            for (int s = s0 + lane; s < s1; s += 32) {
+                const float d0 = a.cen_s[3 * s] - qx, d1 = a.cen_s[3 * s + 1] - qy, d2 = a.cen_s[3 * s + 2] - qz;
+                const float d = d0 * d0 + d1 * d1 + d2 * d2;
+                float md = a.mind[s];
+                if (d < md) {
+                    md = d;
+                    a.mind[s] = d;
+                    a.owner[s] = i;
+                }
+                const int f = a.face[s];
+                if (fps_better(md, f, bv, bi)) { bv = md; bi = f; }
+            }
+            warp_argmax(bv, bi);
+            cv = bv;
+            ci = bi;
+        }
+        if (i + 1 == a.ns) break;
+        const int par = i & 1;
+        if (lane == 0) {
+            wv[par][w] = s0 < s1 ? cv : -1.0f;
+            wi[par][w] = ci;
+        }
+        __syncthreads();
+        if (w == 0) {
+            float v = lane < NW ? wv[par][lane] : -1.0f;
+            int idx = lane < NW ? wi[par][lane] : 0x7FFFFFFF;
+            warp_argmax(v, idx);
+            if (lane == 0) {
+                a.cand_v[par * nb + blockIdx.x] = v;
+                a.cand_i[par * nb + blockIdx.x] = idx;
+            }
+        }
+        __threadfence();
+        grid_barrier(a.bar, a.bar + 1, nb, a.err);
+        // every warp folds the blocks' candidates (any order gives the same winner)
+        float v = -1.0f;
+        int idx = 0x7FFFFFFF;
+        for (unsigned b = lane; b < nb; b += 32) {
+            const float ov = __ldcg(a.cand_v + par * nb + b);
+            const int oi = __ldcg(a.cand_i + par * nb + b);
+            if (fps_better(ov, oi, v, idx)) { v = ov; idx = oi; }
+        }
+        warp_argmax(v, idx);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
+        cur = idx;
+    }
+}
+
+// The same greedy sampling by ONE block of kFpsThreads threads (no grid
+// barrier): warp w owns a contiguous slot range and skips it when the new
+// sample cannot be nearer than the range's largest distance; the warps'
+// candidates are folded by every warp from a double-buffered shared array.
 __device__ void fps_one_block(const FpsArgs &a) {
     constexpr int NW = kFpsThreads / 32;
     __shared__ float cand_v[2][NW];
@@ -445,11 +454,8 @@ static Layout layout(int nf, int ns, int nblocks) {
 // blocks of the FPS launch: about 16 faces per thread (small meshes keep the
 // grid barrier cheap), at most 4 resident blocks per SM
 static int fps_blocks(int nf) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fps, 256, 0);
-    const int cap = num_sms() * std::max(1, std::min(occ, 4));
-    const int want = (nf + 256 * 16 - 1) / (256 * 16);
-    return std::max(1, std::min(cap, want));
+    const int want = (nf + kFpsThreads * 16 - 1) / (kFpsThreads * 16);
+    return std::max(1, std::min(num_sms(), want));
 }
 
 static mcs_status sample_check(const mcs_sample_item &it, const char *fn) {
@@ -568,7 +574,7 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
         MCS_ARG(coop, "mcs_sample_rows: the device does not support cooperative launches");
         void *args[] = {&a};
         note_launch();
-        MCS_CUDA(cudaLaunchCooperativeKernel((void *)k_fps, dim3(nb), dim3(256), args, 0, st));
+        MCS_CUDA(cudaLaunchCooperativeKernel((void *)k_fps, dim3(nb), dim3(kFpsThreads), args, 0, st));
     }
     if ((s = sample_finish(it, orient, w, L, st)) != MCS_OK) return s;
     int herr = 0;
