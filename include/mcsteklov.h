@@ -89,6 +89,8 @@ typedef struct {
                                default (2), 2 = binary nodes (64 B), 4 = 4-wide nodes (the
                                binary tree collapsed two levels at a time, 128 B; needs
                                mcs_mesh_build_wide).  Same results either way. */
+    int lanes_per_query;    /* with bvh_layout 4: 4 = a group of four lanes runs each walk,
+                               lane r testing child r of each node; 0/1 = one lane per walk */
 } mcs_params;
 
 /* Rows of the estimate.  Vertex rows: n_rows = nv, tri2bin = NULL, a walk's
@@ -291,13 +293,13 @@ void mcs_graph_destroy(mcs_graph g);
  * p->bvh_layout is 0), candidate block sizes (64, 128 threads), resident
  * blocks per SM (the three largest residencies the kernel allows) and queue
  * orders (row order, mesh order), by coordinate search in that order; the
- * best two-run minimum wins.  tuned (host) = p with bvh_layout,
+ * best two-run minimum wins.  tuned (host) = p with bvh_layout, lanes_per_query,
  * threads_per_block, blocks_per_sm and queue_order set.  trials (host, optional) receives up to
  * max_trials entries, n_trials their count.  Synchronises `stream`.  The
  * workspace and outputs are those of the batch; their contents are left
  * undefined (the estimate rewrites them). */
 typedef struct {
-    int threads_per_block, blocks_per_sm, queue_order, bvh_layout;
+    int threads_per_block, blocks_per_sm, queue_order, bvh_layout, lanes_per_query;
     float ms;               /* walk-kernel time of the sample (best of 2)       */
 } mcs_tune_trial;
 mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,

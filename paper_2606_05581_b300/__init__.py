@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("origin_auto", C.c_int), ("origin", C.c_double * 3), ("killing_walks", C.c_longlong),
                 ("seed", C.c_uint64), ("walks_per_row", C.c_int), ("blocks_per_sm", C.c_int),
                 ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int),
-                ("queue_order", C.c_int), ("bvh_layout", C.c_int)]
+                ("queue_order", C.c_int), ("bvh_layout", C.c_int), ("lanes_per_query", C.c_int)]
 
 
 class Rows(C.Structure):
@@ -68,7 +68,7 @@ class SampleItem(C.Structure):
 
 class TuneTrial(C.Structure):
     _fields_ = [("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int), ("queue_order", C.c_int),
-                ("bvh_layout", C.c_int), ("ms", C.c_float)]
+                ("bvh_layout", C.c_int), ("lanes_per_query", C.c_int), ("ms", C.c_float)]
 
 
 class EigParams(C.Structure):
@@ -414,7 +414,8 @@ class Batch:
         self.params = tuned
         self.close_graph()
         out = [dict(threads_per_block=t.threads_per_block, blocks_per_sm=t.blocks_per_sm,
-                    queue_order=t.queue_order, bvh_layout=t.bvh_layout, ms=t.ms)
+                    queue_order=t.queue_order, bvh_layout=t.bvh_layout, lanes_per_query=t.lanes_per_query,
+                    ms=t.ms)
                for t in trials[:min(nt.value, max_trials)]]
         return tuned, out
 

@@ -491,10 +491,17 @@ template <typename T> struct WalkState {
 // traversal is latency-bound, and the extra warps outweigh the spills
 // (measured on the two-sphere exterior workload: 80 registers 300 ms,
 // 64: 267 ms, 56: 256 ms, 48: 252 ms, 40: 250-256 ms; identical hit counts).
-template <typename T, int MODE, bool COUNT, bool MULTI, bool WIDE>
+// TRAV: 0 binary BVH, one lane per query; 1 4-wide BVH, one lane per query;
+// 2 4-wide BVH, a group of 4 lanes per query (the group runs one walk, every
+// lane holding its state; lane 0 of the group writes results and counters)
+template <typename T, int MODE, bool COUNT, bool MULTI, int TRAV>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __grid_constant__ MultiArgs a) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
+    constexpr bool GROUP = TRAV == 2;
+    const int gr = GROUP ? (lane & 3) : 0;                         // lane within its group
+    const unsigned gmask = GROUP ? (0xFu << (lane & ~3)) : (1u << lane);
+    const bool writer = gr == 0;                                   // writes results and counts
     const T epsT = sizeof(T) == 8 ? (T)a.eps : (T)a.eps2f;  // FP32: re-check below 2 eps
     WalkState<T> s;
     s.x = V3<T>{(T)0, (T)0, (T)0};
@@ -531,6 +538,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
     };
 
     auto finish = [&](const WalkJob &J, int bin, int f, bool capped, bool lost) {
+        active = false;
+        if (!writer) return;
         if (s.kill) n_kcapped += capped; else n_capped += capped;
         n_lost += lost;
         if (bin >= J.R) { err |= kErrBin; bin = -1; }
@@ -541,19 +550,20 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
             J.exits[(size_t)rp * J.W + j] = bin;
             if (J.exit_tri) J.exit_tri[(size_t)s.v * J.W + j] = f;
         }
-        active = false;
     };
 
     while (true) {
         const bool need = !active && more;
-        const unsigned nm = __ballot_sync(FULL, need);
+        // groups: one queue entry per group, taken by its lane 0
+        const unsigned nm = __ballot_sync(FULL, need && writer);
         if (nm) {
             const int leader = __ffs(nm) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(nm));
             base = __shfl_sync(FULL, base, leader);
+            unsigned long long wi = base + __popc(nm & ((1u << (lane & ~(GROUP ? 3 : 0))) - 1u));
+            if (GROUP) wi = __shfl_sync(FULL, wi, lane & ~3);
             if (need) {
-                const unsigned long long wi = base + __popc(nm & ((1u << lane) - 1u));
                 if (wi >= total) {
                     more = false;
                 } else {
@@ -634,12 +644,15 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
             qz = s.x.z * inv + pick<T>(C.origin[2], C.origin_f[2]);
         }
         Hit<T> h;
-        if (WIDE) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
+        if (TRAV == 2) closest_g4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work, gmask, gr);
+        else if (TRAV == 1) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
         else closest<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
-        if (s.kill) n_ksteps++; else n_steps++;
+        if (writer) {
+            if (s.kill) n_ksteps++; else n_steps++;
+        }
         if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
             err |= kErrNoHit;
-            record_nohit(J.ctrl, ext ? 2 : 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+            if (writer) record_nohit(J.ctrl, ext ? 2 : 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
             finish(J, -1, -1, true, true);
             continue;
         }
@@ -1116,6 +1129,8 @@ static mcs_status check_common(const mcs_params *p, const std::string &f) {
     MCS_ARG(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 64, f + ": blocks_per_sm out of range");
     MCS_ARG(p->queue_order >= 0 && p->queue_order <= 3, f + ": queue_order must be in [0, 3]");
     MCS_ARG(p->bvh_layout == 0 || p->bvh_layout == 2 || p->bvh_layout == 4, f + ": bvh_layout must be 0, 2 or 4");
+    MCS_ARG(p->lanes_per_query == 0 || p->lanes_per_query == 1 || (p->lanes_per_query == 4 && p->bvh_layout == 4),
+            f + ": lanes_per_query must be 0, 1, or 4 (with bvh_layout 4)");
     return MCS_OK;
 }
 
@@ -1268,14 +1283,21 @@ static mcs_status store_jobs(const std::vector<WalkJob> &jobs, WalkJob *d_jobs, 
 
 typedef void (*WalkKernel)(MultiArgs);
 
-template <typename T, bool COUNT, bool WIDE> static WalkKernel walk_kernel_mode(int mode, bool multi) {
-    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false, WIDE> : k_walks<T, 1, COUNT, false, WIDE>;
-    return mode == 0 ? k_walks<T, 0, COUNT, true, WIDE>
-                     : (mode == 1 ? k_walks<T, 1, COUNT, true, WIDE> : k_walks<T, 2, COUNT, true, WIDE>);
+template <typename T, bool COUNT, int TRAV> static WalkKernel walk_kernel_mode(int mode, bool multi) {
+    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false, TRAV> : k_walks<T, 1, COUNT, false, TRAV>;
+    return mode == 0 ? k_walks<T, 0, COUNT, true, TRAV>
+                     : (mode == 1 ? k_walks<T, 1, COUNT, true, TRAV> : k_walks<T, 2, COUNT, true, TRAV>);
 }
 
-template <typename T, bool COUNT> static WalkKernel walk_kernel_w(int mode, bool multi, bool wide) {
-    return wide ? walk_kernel_mode<T, COUNT, true>(mode, multi) : walk_kernel_mode<T, COUNT, false>(mode, multi);
+template <typename T, bool COUNT> static WalkKernel walk_kernel_w(int mode, bool multi, int trav) {
+    if (trav == 2) return walk_kernel_mode<T, COUNT, 2>(mode, multi);
+    return trav == 1 ? walk_kernel_mode<T, COUNT, 1>(mode, multi) : walk_kernel_mode<T, COUNT, 0>(mode, multi);
+}
+
+// traversal: 0 binary, 1 4-wide one lane per query, 2 4-wide four lanes per query
+static int trav_of(const mcs_params *p) {
+    if (p->bvh_layout != 4) return 0;
+    return p->lanes_per_query == 4 ? 2 : 1;
 }
 
 // the BVH node layout of the walk queries: binary unless the caller asks for
@@ -1285,12 +1307,12 @@ static bool use_wide(const mcs_params *p) { return p->bvh_layout == 4; }
 
 // mode: 0 all jobs interior, 1 all exterior, 2 mixed; multi: several jobs
 static WalkKernel walk_kernel(const mcs_params *p, int mode, bool multi) {
-    const bool wide = use_wide(p);
+    const int trav = trav_of(p);
     if (p->count_work)
-        return p->prec == MCS_FP64 ? walk_kernel_w<double, true>(mode, multi, wide)
-                                   : walk_kernel_w<float, true>(mode, multi, wide);
-    return p->prec == MCS_FP64 ? walk_kernel_w<double, false>(mode, multi, wide)
-                               : walk_kernel_w<float, false>(mode, multi, wide);
+        return p->prec == MCS_FP64 ? walk_kernel_w<double, true>(mode, multi, trav)
+                                   : walk_kernel_w<float, true>(mode, multi, trav);
+    return p->prec == MCS_FP64 ? walk_kernel_w<double, false>(mode, multi, trav)
+                               : walk_kernel_w<float, false>(mode, multi, trav);
 }
 
 // resident blocks per SM of the walk kernel for this block size
@@ -1779,6 +1801,7 @@ void mcs_default_params(mcs_params *p) {
     p->count_work = 0;
     p->queue_order = 0;
     p->bvh_layout = 0;
+    p->lanes_per_query = 0;
 }
 
 size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, long long killing_walks) {
@@ -1996,6 +2019,7 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
             trials[count].blocks_per_sm = bps;
             trials[count].queue_order = q.queue_order;
             trials[count].bvh_layout = use_wide(&q) ? 4 : 2;
+            trials[count].lanes_per_query = trav_of(&q) == 2 ? 4 : 1;
             trials[count].ms = best;
         }
         count++;
@@ -2012,16 +2036,25 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
     best.blocks_per_sm = 0;
     bool all_wide = true;
     for (int i = 0; i < n; i++) all_wide = all_wide && mcs_mesh_has_wide(items[i].mesh);
-    for (int lay : {2, 4}) {
-        if (p->bvh_layout != 0 && lay != best.bvh_layout) continue;
-        if (lay == 4 && !all_wide) continue;
+    best.lanes_per_query = trav_of(p) == 2 ? 4 : 1;
+    const int layouts[3][2] = {{2, 1}, {4, 1}, {4, 4}};
+    for (const auto &lq : layouts) {
+        if (p->bvh_layout != 0 && lq[0] != best.bvh_layout) continue;
+        if (p->lanes_per_query != 0 && lq[1] != best.lanes_per_query) continue;
+        if (lq[0] == 4 && !all_wide) continue;
         mcs_params q = best;
-        q.bvh_layout = lay;
+        q.bvh_layout = lq[0];
+        q.lanes_per_query = lq[1];
         q.blocks_per_sm = 0;
         float ms = 0.f;
         int used = 0;
         if ((s = trial(q, &ms, &used)) != MCS_OK) { cleanup(); return s; }
-        if (ms < best_ms) { best_ms = ms; best.bvh_layout = lay; best.blocks_per_sm = used; }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.bvh_layout = lq[0];
+            best.lanes_per_query = lq[1];
+            best.blocks_per_sm = used;
+        }
     }
     for (int tpb : {64, 128}) {
         mcs_params q = best;

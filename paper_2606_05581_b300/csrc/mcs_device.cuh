@@ -484,6 +484,125 @@ __device__ void closest4(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &
     }
 }
 
+// closest triangle on the 4-wide BVH by a group of 4 consecutive lanes (the
+// same query in all four; `r` = lane & 3, `gm` = the group's lane mask):
+// lane r tests child box r of the current node and, when that child is a
+// leaf in reach, its triangle; the group takes the lexicographic minimum of
+// (d^2, id), sorts the internal children in reach by distance, visits the
+// nearest and defers the others on a stack that every lane of the group
+// holds a copy of.  Same result as closest(); every lane returns it.
+template <typename T, bool COUNT = false>
+__device__ void closest_g4(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &best, int *err, Work *work,
+                           unsigned gm, int r) {
+    best.d2 = (T)INFINITY;
+    best.id = 0x7FFFFFFF;
+    best.slot = -1;
+    best.b0 = best.b1 = best.b2 = (T)0;
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) return;
+    const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
+    T thr2 = (T)INFINITY;
+    const int base = (threadIdx.x & 31) & ~3;
+    auto take = [&](T d2, int id, int slot, T b0, T b1, T b2) {
+        if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
+            best.d2 = d2; best.id = id; best.slot = slot;
+            best.b0 = b0; best.b1 = b1; best.b2 = b2;
+            const T rr = rsq<T>(d2) + tau;
+            thr2 = rr * rr;
+        }
+    };
+    if (guess >= 0) {
+        T b[3];
+        int id;
+        const T d2 = Slot<T>::test(m, guess, px, py, pz, b, id);
+        if (COUNT && r == 0) work->tris++;
+        take(d2, id, guess, b[0], b[1], b[2]);
+    }
+    if (m.nf == 1) {
+        if (guess != 0) {
+            T b[3];
+            int id;
+            const T d2 = Slot<T>::test(m, 0, px, py, pz, b, id);
+            if (COUNT && r == 0) work->tris++;
+            take(d2, id, 0, b[0], b[1], b[2]);
+        }
+        return;
+    }
+    int stack[kStack4];
+    float sdist[kStack4];
+    int sp = 0;
+    int node = 0;
+    for (int guard = 0;; guard++) {
+        if (guard > m.nf + 64) { *err |= kErrTree; break; }
+        if (COUNT && r == 0) work->nodes++;
+        const float *nf4 = reinterpret_cast<const float *>(m.nodes4 + node);
+        const int ch = reinterpret_cast<const int *>(nf4)[24 + r];
+        T d = (T)INFINITY;
+        if (ch != kNoChild) d = box_d2<T>(px, py, pz, nf4[r], nf4[4 + r], nf4[8 + r], nf4[12 + r], nf4[16 + r], nf4[20 + r]);
+        // leaf children in reach: one triangle per lane, then the group minimum
+        T ld = (T)INFINITY, lb0 = (T)0, lb1 = (T)0, lb2 = (T)0;
+        int lid = 0x7FFFFFFF, lslot = -1;
+        if (ch < 0 && d <= thr2) {
+            T b[3];
+            lslot = ~ch;
+            ld = Slot<T>::test(m, lslot, px, py, pz, b, lid);
+            lb0 = b[0]; lb1 = b[1]; lb2 = b[2];
+            if (COUNT) work->tris++;
+        }
+        int wl = r;  // lane holding the group minimum
+        {
+            T md = ld;
+            int mid = lid;
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                const T od = __shfl_xor_sync(gm, md, o);
+                const int oi = __shfl_xor_sync(gm, mid, o);
+                const int ol = __shfl_xor_sync(gm, wl, o);
+                if (od < md || (od == md && oi < mid)) { md = od; mid = oi; wl = ol; }
+            }
+            const T w0 = __shfl_sync(gm, lb0, base + wl), w1 = __shfl_sync(gm, lb1, base + wl),
+                    w2 = __shfl_sync(gm, lb2, base + wl);
+            const int ws = __shfl_sync(gm, lslot, base + wl);
+            if (ws >= 0) take(md, mid, ws, w0, w1, w2);
+        }
+        // internal children still in reach, nearest first (every lane builds the same list)
+        const bool cand = ch >= 0 && ch != kNoChild && d <= thr2;
+        int ci[4];
+        T cd[4];
+        int nc = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const T dk = __shfl_sync(gm, d, base + k);
+            const int chk = __shfl_sync(gm, ch, base + k);
+            const bool ck = __shfl_sync(gm, (int)cand, base + k) != 0;
+            if (ck) {
+                int j = nc++;
+                while (j > 0 && cd[j - 1] > dk) { cd[j] = cd[j - 1]; ci[j] = ci[j - 1]; j--; }
+                cd[j] = dk;
+                ci[j] = chk;
+            }
+        }
+        if (nc > 0) {
+            for (int j = nc - 1; j >= 1; j--) {
+                if (sp < kStack4) {
+                    stack[sp] = ci[j];
+                    sdist[sp] = store_down<T>(cd[j]);
+                    sp++;
+                } else {
+                    *err |= kErrStack;
+                }
+            }
+            node = ci[0];
+            continue;
+        }
+        bool found = false;
+        while (sp > 0) {
+            sp--;
+            if ((T)sdist[sp] <= thr2) { node = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+}
+
 // --------------------------------------------------------------------------
 // warp-cooperative query: the 32 lanes of a warp answer ONE query together.
 // The top of the tree is expanded breadth-first into at most 32 subtrees

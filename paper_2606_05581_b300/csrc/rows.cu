@@ -31,26 +31,22 @@ __device__ __forceinline__ uint64_t gtime_ns() {
     return t;
 }
 
-// grid-wide barrier for a cooperative launch; every wait is bounded (~2 s),
-// after which the error word is set and the block carries on
-__device__ void grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, int *err) {
+// grid-wide barrier for a cooperative launch: `count` only grows (it starts
+// at zero); arrival number a belongs to barrier a / nblocks, which opens once
+// the count reaches the end of that barrier's arrivals.  Every wait is
+// bounded (~2 s), after which the error word is set and the block carries on.
+__device__ void grid_barrier(unsigned *count, unsigned nblocks, int *err) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = gen;
-        const unsigned g = *vgen;
         __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const uint64_t t0 = gtime_ns();
-            for (unsigned spins = 1; *vgen == g; spins++) {
-                // the clock is read every 64 polls: the wait stays bounded (~2 s)
-                if ((spins & 63) == 0 && gtime_ns() - t0 > 2000000000ull) {
-                    atomicOr(err, kErrBarrier);
-                    break;
-                }
+        const unsigned target = (atomicAdd(count, 1u) / nblocks + 1u) * nblocks;
+        volatile unsigned *vc = count;
+        const uint64_t t0 = gtime_ns();
+        for (unsigned spins = 1; *vc < target; spins++) {
+            // the clock is read every 64 polls
+            if ((spins & 63) == 0 && gtime_ns() - t0 > 2000000000ull) {
+                atomicOr(err, kErrBarrier);
+                break;
             }
         }
         __threadfence();
@@ -78,7 +74,7 @@ struct FpsArgs {
     int32_t *sel;
     float *cand_v;      // 2 x gridDim candidates (double-buffered)
     int *cand_i;
-    unsigned *bar;      // count, generation
+    unsigned *bar;      // barrier arrivals (monotonic)
     int *err;
     int nf, ns;
 };
@@ -213,7 +209,7 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
             }
         }
         __threadfence();
-        grid_barrier(a.bar, a.bar + 1, nb, a.err);
+        grid_barrier(a.bar, nb, a.err);
         // every warp folds the blocks' candidates (any order gives the same winner)
         float v = -1.0f;
         int idx = 0x7FFFFFFF;

@@ -134,9 +134,10 @@ def test_queue_orders_and_launch_shapes_do_not_change_results():
     b = mcs.Batch(items, p, assemble=False, record_exits=True)
     b.run()
     ref = [b.result(i)["exit_tri"].clone() for i in range(len(items))]
-    for qo, tpb, bps, lay in ((1, 64, 3, 2), (2, 128, 2, 4), (3, 96, 1, 2), (0, 128, 6, 4)):
+    for qo, tpb, bps, lay, lq in ((1, 64, 3, 2, 1), (2, 128, 2, 4, 1), (3, 96, 1, 2, 1), (0, 128, 6, 4, 4),
+                                  (1, 64, 8, 4, 4)):
         q = mcs.default_params(walks_per_row=32, prec=32, killing_walks=256, queue_order=qo,
-                               threads_per_block=tpb, blocks_per_sm=bps, bvh_layout=lay)
+                               threads_per_block=tpb, blocks_per_sm=bps, bvh_layout=lay, lanes_per_query=lq)
         status, tot, per = b.run(q)
         for i in range(len(items)):
             assert torch.equal(b.result(i)["exit_tri"], ref[i]), (qo, i)
@@ -154,9 +155,10 @@ def test_autotuner_returns_a_valid_shape_and_same_results():
     assert tuned.threads_per_block in (64, 128) and tuned.blocks_per_sm >= 1
     assert 0 <= tuned.queue_order <= 3
     best = min(trials, key=lambda t: t["ms"])
-    assert (best["threads_per_block"], best["blocks_per_sm"], best["queue_order"], best["bvh_layout"]) == \
-        (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order, tuned.bvh_layout)
-    assert {t["bvh_layout"] for t in trials} == {2, 4}
+    assert (best["threads_per_block"], best["blocks_per_sm"], best["queue_order"], best["bvh_layout"],
+            best["lanes_per_query"]) == (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order,
+                                         tuned.bvh_layout, tuned.lanes_per_query)
+    assert {(t["bvh_layout"], t["lanes_per_query"]) for t in trials} >= {(2, 1), (4, 1), (4, 4)}
     b.run()
     for i in range(len(items)):
         assert torch.equal(b.result(i)["exit_tri"], ref[i]), i

@@ -244,3 +244,22 @@ def test_wild_exterior_rows_bit_exact(oracle):
     m = meshgen.wild_union(6, 5000, seed=9)
     rows = oracle.fps_rows(m.V, m.F, 200, orient=True)
     _compare(oracle, m, rows, 32, 1e-3, 32, exterior=True, killing=512, seed=2)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_group_traversal_bit_exact(oracle, prec):
+    """Four lanes per walk on the 4-wide BVH: the same hit counts as the oracle."""
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    mesh = mcs.Mesh(m.V, m.F).build_wide()
+    r = _rows_to_torch(rows)
+    p = mcs.default_params(walks_per_row=64, prec=prec, seed=3, domain=1, killing_walks=1024, bvh_layout=4,
+                           lanes_per_query=4)
+    res = mcs.estimate_dtn(mesh, r, p, assemble=False, record_exits=True)
+    st = res["stats"]
+    est = oracle.estimate(m.V, m.F, rows, 64, 1e-3, exterior=True, origin=np.array(st["origin"]), seed=3, prec=prec,
+                          killing_walks=1024, record_exits=True)
+    assert np.array_equal(mcs.dense_hist(res, m.nv).cpu().numpy(), est["H"])
+    assert np.array_equal(res["exit_tri"].cpu().numpy(), est["exit_tri"])
+    assert np.array_equal(res["H0"].cpu().numpy(), est["H0"])
+    assert st["steps"] == est["steps"].sum()
