@@ -132,18 +132,37 @@ __device__ __forceinline__ double wdist(const DevMesh &m, double x, double y, do
     if (h.slot < 0 && bound > 0.0) warp_query<double, kFull>(m, x, y, z, 0.0, h, front, err);
     return sqrt(h.d2);
 }
-// dist(p) >= thr, decided as the FP64 query would
+// dist(p) >= thr, decided as the FP64 query would: an FP32 query stops at the
+// first triangle nearer than thr - E (not clear) and otherwise collects the
+// triangles whose float distance lies in [thr - E, thr + E); only those can
+// be nearer than thr in FP64, and they are tested in FP64, one per lane
 __device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, double z, double thr, int *front,
-                                       int *err) {
+                                       int *cand, int *err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
     const float xf = (float)x, yf = (float)y, zf = (float)z;
     const double E = fp32_band(m, x, y, z);
     if (isfinite(xf) && isfinite(yf) && isfinite(zf) && thr > 2.0 * E) {
-        // the float distances below thr + E (if any): none -> clear; one below thr - E -> not clear
+        int *ncand = cand + kCandMax;
+        if (lane == 0) *ncand = 0;
+        __syncwarp();
         Hit<float> hf;
-        warp_query<float, kFull>(m, xf, yf, zf, (float)(thr + 2.0 * E), hf, front, err);
-        const double df = hf.slot >= 0 ? sqrt((double)hf.d2) : INFINITY;
-        if (df >= thr + E) return true;
-        if (df < thr - E) return false;
+        if (warp_query<float, kCollect>(m, xf, yf, zf, (float)(thr + E), hf, front, err, (float)(thr - E), cand,
+                                        ncand))
+            return false;
+        __syncwarp();
+        const int nc = *ncand;
+        if (nc <= kCandMax) {
+            bool below = false;
+            for (int k = lane; k < nc; k += 32) {
+                double b[3];
+                int id;
+                below = below || sqrt(Slot<double>::test(m, cand[k], x, y, z, b, id)) < thr;
+            }
+            const bool any = __any_sync(FULL, below);
+            __syncwarp();
+            return !any;
+        }
     }
     Hit<double> h;
     return !warp_query<double, kBelow>(m, x, y, z, thr, h, front, err);
@@ -151,7 +170,7 @@ __device__ __forceinline__ bool wclear(const DevMesh &m, double x, double y, dou
 
 // interior tangent ball of row v, by one warp
 __device__ void tangent_int_row(const DevMesh &m, const double *pos, const double *nrm, int v, const Frame &fr,
-                                RowBall *ball, Ctrl *ctrl, int *front) {
+                                RowBall *ball, Ctrl *ctrl, int *front, int *cand) {
     int err = 0;
     const double s0 = pos[3 * v], s1 = pos[3 * v + 1], s2 = pos[3 * v + 2];
     const double n0 = nrm[3 * v], n1 = nrm[3 * v + 1], n2 = nrm[3 * v + 2];
@@ -163,13 +182,13 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
     if (nz) {
         const double rmax = fr.rmax;
         double r;
-        if (wclear(m, s0 - rmax * n0, s1 - rmax * n1, s2 - rmax * n2, fr.onemk * rmax, front, &err)) {
+        if (wclear(m, s0 - rmax * n0, s1 - rmax * n1, s2 - rmax * n2, fr.onemk * rmax, front, cand, &err)) {
             r = rmax;
         } else {
             double lo = 0.0, hi = rmax;
             for (int it = 0; it < fr.bisect_iters; it++) {
                 const double mid = 0.5 * (lo + hi);
-                if (wclear(m, s0 - mid * n0, s1 - mid * n1, s2 - mid * n2, fr.onemk * mid, front, &err)) lo = mid;
+                if (wclear(m, s0 - mid * n0, s1 - mid * n1, s2 - mid * n2, fr.onemk * mid, front, cand, &err)) lo = mid;
                 else hi = mid;
             }
             r = lo;
@@ -191,9 +210,10 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
 __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_int(DevMesh m, const double *pos, const double *nrm, int R,
                                                                 int stride, Frame fr, RowBall *ball, Ctrl *ctrl) {
     __shared__ int fronts[kTanWarps][32];
+    __shared__ int cands[kTanWarps][kCandMax + 1];
     const int v = (blockIdx.x * kTanWarps + (threadIdx.x >> 5)) * stride;
     if (v >= R) return;
-    tangent_int_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5]);
+    tangent_int_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5], cands[threadIdx.x >> 5]);
 }
 
 // largest empty radius over rows 0, stride, 2 stride, ..., lowest row on ties
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_ext_frame(DevMesh m, const do
 // r/(|c~|^2 - r^2); the accepted ball is replaced by the image of the primal
 // empty ball B(C, dist(C))
 __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double nt[3], double r, const double o[3],
-                            double onemk, int *front, int *err) {
+                            double onemk, int *front, int *cand, int *err) {
     const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
     const double cc = ct0 * ct0 + ct1 * ct1 + ct2 * ct2;
     const double den = cc - r * r;
@@ -324,12 +344,12 @@ __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double n
     const double inv = 1.0 / den;
     const double C0 = ct0 * inv, C1 = ct1 * inv, C2 = ct2 * inv;
     const double Rp = r * inv;
-    return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], onemk * Rp, front, err);
+    return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], onemk * Rp, front, cand, err);
 }
 
 // exterior tangent ball of row v, by one warp
 __device__ void tangent_ext_row(const DevMesh &m, const double *pos, const double *nrm, int v, const Frame &fr,
-                                RowBall *ball, Ctrl *ctrl, int *front) {
+                                RowBall *ball, Ctrl *ctrl, int *front, int *cand) {
     int err = 0;
     const double o[3] = {ctrl->origin[0], ctrl->origin[1], ctrl->origin[2]};
     const double rmax = ctrl->rmax_ext;
@@ -349,13 +369,13 @@ __device__ void tangent_ext_row(const DevMesh &m, const double *pos, const doubl
     b.kfac = 1.0 / (r2s * sqrt(r2s));
     if (nz) {
         double r;
-        if (inv_ball_ok(m, st, nt, rmax, o, fr.onemk, front, &err)) {
+        if (inv_ball_ok(m, st, nt, rmax, o, fr.onemk, front, cand, &err)) {
             r = rmax;
         } else {
             double lo = 0.0, hi = rmax;
             for (int it = 0; it < fr.bisect_iters; it++) {
                 const double mid = 0.5 * (lo + hi);
-                if (inv_ball_ok(m, st, nt, mid, o, fr.onemk, front, &err)) lo = mid;
+                if (inv_ball_ok(m, st, nt, mid, o, fr.onemk, front, cand, &err)) lo = mid;
                 else hi = mid;
             }
             r = lo;
@@ -392,9 +412,10 @@ __device__ void tangent_ext_row(const DevMesh &m, const double *pos, const doubl
 __global__ void __launch_bounds__(32 * kTanWarps) k_tangent_ext(DevMesh m, const double *pos, const double *nrm, int R,
                                                                 Frame fr, RowBall *ball, Ctrl *ctrl) {
     __shared__ int fronts[kTanWarps][32];
+    __shared__ int cands[kTanWarps][kCandMax + 1];
     const int v = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
     if (v >= R) return;
-    tangent_ext_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5]);
+    tangent_ext_row(m, pos, nrm, v, fr, ball, ctrl, fronts[threadIdx.x >> 5], cands[threadIdx.x >> 5]);
 }
 
 // ---------------------------------------------------------------- walks
@@ -966,12 +987,13 @@ __global__ void k_b_order(const MeshJob *jobs, const int *row0, int n, const uns
 // exterior meshes with an automatic inversion centre; one warp per row
 __global__ void __launch_bounds__(32 * kTanWarps) k_b_tangent_int(const MeshJob *jobs, const int *unit0, int n) {
     __shared__ int fronts[kTanWarps][32];
+    __shared__ int cands[kTanWarps][kCandMax + 1];
     const int u = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
     if (u >= unit0[n]) return;
     const int j = find_job(unit0, n, u);
     const MeshJob &J = jobs[j];
     const int v = (u - unit0[j]) * (J.ext ? J.ostride : 1);
-    tangent_int_row(J.m, J.pos, J.nrm, v, J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5]);
+    tangent_int_row(J.m, J.pos, J.nrm, v, J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5], cands[threadIdx.x >> 5]);
 }
 // exterior meshes: inversion centre and inverted frame, one block each
 __global__ void __launch_bounds__(kFrameThreads) k_b_frame(const MeshJob *jobs) {
@@ -993,11 +1015,13 @@ __global__ void __launch_bounds__(kFrameThreads) k_b_frame(const MeshJob *jobs) 
 __global__ void __launch_bounds__(32 * kTanWarps) k_b_tangent_ext(const MeshJob *jobs, const int *unit0, int n,
                                                                   const int *ext_ids) {
     __shared__ int fronts[kTanWarps][32];
+    __shared__ int cands[kTanWarps][kCandMax + 1];
     const int u = blockIdx.x * kTanWarps + (threadIdx.x >> 5);
     if (u >= unit0[n]) return;
     const int e = find_job(unit0, n, u);
     const MeshJob &J = jobs[ext_ids[e]];
-    tangent_ext_row(J.m, J.pos, J.nrm, u - unit0[e], J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5]);
+    tangent_ext_row(J.m, J.pos, J.nrm, u - unit0[e], J.fr, J.ball, J.ctrl, fronts[threadIdx.x >> 5],
+                    cands[threadIdx.x >> 5]);
 }
 __global__ void k_b_colfactor(const MeshJob *jobs, const int *row0, int n) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;

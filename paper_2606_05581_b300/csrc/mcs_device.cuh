@@ -616,7 +616,8 @@ __device__ void closest_g4(const DevMesh &m, T px, T py, T pz, int guess, Hit<T>
 // Every lane must call it with the same point; `front` is 32 ints of shared
 // memory owned by the warp.
 // --------------------------------------------------------------------------
-constexpr int kFull = 0, kBelow = 1;
+constexpr int kFull = 0, kBelow = 1, kCollect = 2;
+constexpr int kCandMax = 64;  // kCollect: band triangles kept per warp
 constexpr int kNone = 0x7FFFFFFF;
 
 template <typename T>
@@ -626,13 +627,18 @@ __device__ __forceinline__ T warp_min(T v) {
     return v;
 }
 
+//   kCollect: true if some triangle has sqrt(d^2) < lo (early exit); else
+//           the slots of the triangles with lo <= sqrt(d^2) < thr are stored
+//           in cand (shared, kCandMax entries; *ncand counts them, possibly
+//           beyond kCandMax, and must be zero on entry)
 template <typename T, int MODE>
-__device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &out, int *front, int *err) {
+__device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &out, int *front, int *err,
+                           T lo = (T)0, int *cand = nullptr, int *ncand = nullptr) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const T tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
     T bound2;  // prune a box when its squared distance exceeds this
-    if (MODE == kBelow || thr > (T)0) {
+    if (MODE != kFull || thr > (T)0) {
         // kFull with thr > 0: only triangles nearer than thr are searched
         // (out.slot < 0 when there is none)
         const T r = thr + tau;
@@ -649,6 +655,14 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
         const T d2 = Slot<T>::test(m, s, px, py, pz, b, id);
         if (MODE == kBelow) {
             if (rsq<T>(d2) < thr) hit = true;
+        } else if (MODE == kCollect) {
+            const T d = rsq<T>(d2);
+            if (d < lo) {
+                hit = true;
+            } else if (d < thr) {
+                const int k = atomicAdd(ncand, 1);
+                if (k < kCandMax) cand[k] = s;
+            }
         } else if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
             best.d2 = d2; best.id = id; best.slot = s; best.b0 = b[0]; best.b1 = b[1]; best.b2 = b[2];
         }
@@ -705,7 +719,7 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
     int guard = 0;
     while (true) {
         refresh();
-        if (MODE == kBelow && __any_sync(FULL, hit)) { hit = true; break; }
+        if (MODE != kFull && __any_sync(FULL, hit)) { hit = true; break; }
         const bool active = node != kNone;
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
@@ -739,7 +753,7 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
             }
         }
     }
-    if (MODE == kBelow) return hit;
+    if (MODE != kFull) return __any_sync(FULL, hit);
     // ---- lexicographic warp argmin of (d^2, id)
     T bd = best.d2;
     int bi = best.id, bl = lane;
