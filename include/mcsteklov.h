@@ -337,7 +337,8 @@ mcs_status mcs_estimate_dtn_noalloc(mcs_mesh m, const mcs_rows *rows, const mcs_
  * CholeskyQR2 orthonormalisation (shifted CholeskyQR first on the start block), Rayleigh-Ritz with a
  * parallel Jacobi on the block, Ritz values as FP64 Rayleigh quotients. */
 typedef struct {
-    int degree;             /* Chebyshev filter degree per iteration (24)        */
+    int degree;             /* Chebyshev filter degree per iteration (48; <= 256); halved
+                               (down to 8) after two iterations that add no converged pair */
     int max_iters;          /* outer iterations (60)                             */
     double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-5) */
 } mcs_eig_params;

@@ -68,3 +68,28 @@ def test_steklov_on_gpu_estimate_end_to_end():
     # the constant mode: zero up to the solver's accuracy (~1e-6 of the spectral upper bound)
     assert abs(ev[0]) < 1e-5 * st["upper_bound"]
     assert ev[1:4].max() < ev[4:9].min()
+
+
+def test_two_spheres_tend_to_the_single_sphere_limit(oracle):
+    """Exterior of two spheres (R = 0.5, icosphere s3) with killing walks: as the
+    separation grows, the spectrum tends to two copies of the single-sphere
+    exterior spectrum, lambda_l(theta0) + 1/R with multiplicity 2(2l+1) (the
+    cap-corrected jump form plus the killing term; (l+1)/R as theta0 -> 0).
+    The limit is approached up to the lumping/faceting bias of the s3 mesh."""
+    R = 0.5
+    lam = oracle.sphere_eigs_cap(2, 2.5, R) + 1.0 / R
+    limit = np.sort(np.concatenate([np.repeat(lam[l], 2 * (2 * l + 1)) for l in range(3)]))[:16]
+    errs = {}
+    for D in (1.5, 20.0):
+        m = meshgen.two_spheres(3, R, D)
+        mesh = mcs.Mesh(m.V, m.F)
+        rows = mcs.vertex_rows(mesh)
+        res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=2048, prec=32, domain=1,
+                                                              killing_walks=64 * 2048, seed=4))
+        L = res["Lambda"]
+        assert torch.equal(L, L.T)
+        ev, _, st = mcs.steklov_modes(L, rows["area"], 16, vectors=False)
+        assert st["status"] == 0
+        errs[D] = np.abs(ev.cpu().numpy() - limit) / limit
+    assert errs[20.0].max() < 0.08, errs[20.0]
+    assert errs[20.0].mean() < errs[1.5].mean()
