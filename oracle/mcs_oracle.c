@@ -553,10 +553,17 @@ static void tangent_interior(const orc_ctx *cx, const double s[3], const double 
 
 /* Exterior: rows are mapped to s~ = kappa(s - o); the inverted normal is the
  * Householder reflection of n about s^ with its sign flipped, -H n
- * (App. B.3, Eq. jacobian-times-normal).  An inverted ball B(c~, r) not
- * containing 0 is the image of the primal ball with centre c~/(|c~|^2-r^2)
- * and radius r/(|c~|^2-r^2), which one primal query tests.  The accepted
- * ball is replaced by the image of the primal empty ball B(C, dist(C)). */
+ * (App. B.3, Eq. jacobian-times-normal).  The tangent ball lives in the
+ * inverted domain (Sec. 4.3: the inverted jump kernel is an interior one and
+ * takes the interior tangent-ball decomposition), so the slack is relative to
+ * its inverted radius r, as for interior rows: the ball B(c~, (1-kappa) r),
+ * c~ = s~ - r n~, must be empty.  An inverted ball B(c~, r') not containing 0
+ * is the image of the primal ball with centre c~/(|c~|^2-r'^2) and radius
+ * r'/(|c~|^2-r'^2), which one primal query tests.  (A slack taken on the
+ * primal radius instead grows without bound as the inverted ball nears 0 and
+ * lets the ball swallow other components.)  The accepted ball is replaced by
+ * the image of the primal empty ball B(C, dist(C)) at the same primal centre,
+ * which contains B(c~, (1-kappa) r). */
 static int inv_ball_ok(const orc_ctx *cx, const double st[3], const double nt[3], double r,
                        double C[3], double *Rp)
 {
@@ -564,14 +571,15 @@ static int inv_ball_ok(const orc_ctx *cx, const double st[3], const double nt[3]
     double ct[3];
     for (int i = 0; i < 3; i++) ct[i] = st[i] - r * nt[i];
     double cc = ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2];
-    double den = cc - r * r;
+    double rk = (1.0 - pb->kappa) * r;
+    double den = cc - rk * rk;
     /* the ball must stay clear of the inversion centre, and by a margin that
      * keeps its primal image ball (centre ~ 1/den) within FP64 resolution */
     if (!(den > 1e-6 * cc)) return 0;
     double inv = 1.0 / den, q[3];
     for (int i = 0; i < 3; i++) { C[i] = ct[i] * inv; q[i] = C[i] + pb->origin[i]; }
-    *Rp = r * inv;
-    return dist64(cx, q) >= (1.0 - pb->kappa) * (*Rp);
+    *Rp = rk * inv;
+    return dist64(cx, q) >= *Rp;
 }
 
 static void tangent_exterior(const orc_ctx *cx, const double s[3], const double n[3],
@@ -606,7 +614,8 @@ static void tangent_exterior(const orc_ctx *cx, const double s[3], const double 
     double ct[3];
     for (int i = 0; i < 3; i++) ct[i] = st[i] - r * nt[i];
     double cc = ct[0] * ct[0] + ct[1] * ct[1] + ct[2] * ct[2];
-    double den = cc - r * r;
+    double rk = (1.0 - pb->kappa) * r;
+    double den = cc - rk * rk;
     if (!(den > 1e-6 * cc)) return;
     double invd = 1.0 / den, q[3];
     for (int i = 0; i < 3; i++) { C[i] = ct[i] * invd; q[i] = C[i] + pb->origin[i]; }

@@ -329,22 +329,28 @@ __global__ void __launch_bounds__(kFrameThreads) k_ext_frame(DevMesh m, const do
     ext_frame_block(m, V, nv, ctrl, auto_ball);
 }
 
-// exterior tangent ball: the inverted ball B(c~, r) (not containing 0) is the
-// image of the primal ball with centre c~/(|c~|^2 - r^2) and radius
-// r/(|c~|^2 - r^2); the accepted ball is replaced by the image of the primal
-// empty ball B(C, dist(C))
+// exterior tangent ball: an inverted ball B(c~, r') (not containing 0) is the
+// image of the primal ball with centre c~/(|c~|^2 - r'^2) and radius
+// r'/(|c~|^2 - r'^2); the accepted ball is replaced by the image of the primal
+// empty ball B(C, dist(C)) at the same primal centre, which contains
+// B(c~, (1 - kappa) r) and so passes within kappa r of s~
 __device__ bool inv_ball_ok(const DevMesh &m, const double st[3], const double nt[3], double r, const double o[3],
                             double onemk, int *front, int *cand, int *err) {
     const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
     const double cc = ct0 * ct0 + ct1 * ct1 + ct2 * ct2;
-    const double den = cc - r * r;
+    // the slack is taken on the inverted radius, where the ball lives: the
+    // shrunk ball B(c~, (1 - kappa) r) must be empty.  (On the primal image
+    // radius, which grows without bound as the ball nears 0, it would let the
+    // ball swallow other components.)
+    const double rk = onemk * r;
+    const double den = cc - rk * rk;
     // clear of the inversion centre by a margin that keeps the primal image
     // ball (centre ~ 1/den) within FP64 resolution
     if (!(den > 1e-6 * cc)) return false;
     const double inv = 1.0 / den;
     const double C0 = ct0 * inv, C1 = ct1 * inv, C2 = ct2 * inv;
-    const double Rp = r * inv;
-    return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], onemk * Rp, front, cand, err);
+    const double Rp = rk * inv;
+    return wclear(m, C0 + o[0], C1 + o[1], C2 + o[2], Rp, front, cand, err);
 }
 
 // exterior tangent ball of row v, by one warp
@@ -384,7 +390,8 @@ __device__ void tangent_ext_row(const DevMesh &m, const double *pos, const doubl
         if (r > 0.0) {
             const double ct0 = st[0] - r * nt[0], ct1 = st[1] - r * nt[1], ct2 = st[2] - r * nt[2];
             const double cc = ct0 * ct0 + ct1 * ct1 + ct2 * ct2;
-            const double den = cc - r * r;
+            const double rk = fr.onemk * r;
+            const double den = cc - rk * rk;
             if (den > 1e-6 * cc) {
                 const double invd = 1.0 / den;
                 const double C0 = ct0 * invd, C1 = ct1 * invd, C2 = ct2 * invd;

@@ -70,26 +70,45 @@ def test_steklov_on_gpu_estimate_end_to_end():
     assert ev[1:4].max() < ev[4:9].min()
 
 
-def test_two_spheres_tend_to_the_single_sphere_limit(oracle):
-    """Exterior of two spheres (R = 0.5, icosphere s3) with killing walks: as the
-    separation grows, the spectrum tends to two copies of the single-sphere
-    exterior spectrum, lambda_l(theta0) + 1/R with multiplicity 2(2l+1) (the
-    cap-corrected jump form plus the killing term; (l+1)/R as theta0 -> 0).
-    The limit is approached up to the lumping/faceting bias of the s3 mesh."""
-    R = 0.5
-    lam = oracle.sphere_eigs_cap(2, 2.5, R) + 1.0 / R
-    limit = np.sort(np.concatenate([np.repeat(lam[l], 2 * (2 * l + 1)) for l in range(3)]))[:16]
-    errs = {}
-    for D in (1.5, 20.0):
-        m = meshgen.two_spheres(3, R, D)
-        mesh = mcs.Mesh(m.V, m.F)
-        rows = mcs.vertex_rows(mesh)
-        res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=2048, prec=32, domain=1,
-                                                              killing_walks=64 * 2048, seed=4))
-        L = res["Lambda"]
-        assert torch.equal(L, L.T)
-        ev, _, st = mcs.steklov_modes(L, rows["area"], 16, vectors=False)
-        assert st["status"] == 0
-        errs[D] = np.abs(ev.cpu().numpy() - limit) / limit
-    assert errs[20.0].max() < 0.08, errs[20.0]
-    assert errs[20.0].mean() < errs[1.5].mean()
+def test_two_sphere_exterior_capacitance_and_symmetry(two_sphere_capacitance):
+    """Exterior of two spheres (R = 0.5, icosphere s3, centres 1.5 apart) with
+    killing walks, on the GPU at full rate:
+    - the killing mass is 4 pi C (C: the pair's capacitance by the method of
+      images), split evenly between the spheres;
+    - the unsymmetrised jump mass from one sphere to the other equals that
+      back (J(s, t) = J(t, s)), although only one sphere holds the inversion
+      centre;
+    - the lowest eigenvalue lies below the constant's Rayleigh quotient
+      4 pi C / |boundary| and above zero, and Lambda is symmetric."""
+    R, D = 0.5, 1.5
+    m = meshgen.two_spheres(3, R, D)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    W, N = 2048, 1 << 20
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=W, prec=32, domain=1,
+                                                          killing_walks=N, seed=4))
+    st = res["stats"]
+    assert res["status"] == 0 and st["discarded_rows"] == 0
+    o = np.asarray(st["origin"])
+    pos = rows["pos"].cpu().numpy()
+    area = rows["area"].cpu().numpy()
+    cf = np.linalg.norm(pos - o, axis=1)
+    a = (pos - 0.5 * (pos.max(0) + pos.min(0))) @ (o - 0.5 * (pos.max(0) + pos.min(0))) > 0
+    assert a.sum() == m.nv // 2
+    k = 4 * np.pi * cf * res["H0"].cpu().numpy() / N
+    C = two_sphere_capacitance(R, D)
+    assert abs(k.sum() / (4 * np.pi * C) - 1) < 0.01, k.sum() / (4 * np.pi * C)
+    assert abs(k[a].sum() / k.sum() - 0.5) < 0.01
+    H = mcs.dense_hist(res, m.nv).cpu().numpy().astype(np.float64)
+    Wm = res["omega"].cpu().numpy()[:, None] * H / W * cf[None, :]
+    ab, ba = Wm[np.ix_(a, ~a)].sum(), Wm[np.ix_(~a, a)].sum()
+    assert 0.8 < ab / ba < 1.25, (ab, ba)
+    L = res["Lambda"]
+    assert torch.equal(L, L.T)
+    ev, _, sst = mcs.steklov_modes(L, rows["area"], 16, vectors=False)
+    assert sst["status"] == 0
+    ev = ev.cpu().numpy()
+    rq = k.sum() / area.sum()
+    # the solver resolves eigenvalues to ~1e-6 of the spectral upper bound
+    assert 0 < ev[0] <= rq + 1e-5 * sst["upper_bound"], (ev[0], rq)
+    assert ev[0] > 0.9 * rq

@@ -460,3 +460,69 @@ def test_interior_walks_in_the_unbounded_component_are_retired(oracle, prec):
         assert (lost.sum() > 0) == inside_out
         kept = ~est["discarded"].astype(bool)
         assert np.array_equal(est["H"].sum(1)[kept] + lost[kept], np.full(kept.sum(), W))
+
+
+def test_exterior_start_balls_touch_their_rows(oracle):
+    """The tangent-ball decomposition (Sec. 4.2, applied in the inverted domain
+    by Sec. 4.3) needs a ball tangent to the inverted surface at s~.  With the
+    slack kappa the accepted start ball B(c~, rho~) is empty, has rho~ >=
+    (1 - kappa) r and passes within kappa r of s~ (r: the bisected inverted
+    radius).  Two spheres, one holding the inversion centre: the rows of the
+    near sphere that face the other one are where a slack on the primal
+    image radius let the ball reach across the gap."""
+    kappa = 0.05
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    o = np.zeros(3)
+    est = oracle.estimate(m.V, m.F, rows, 2, 1e-3, exterior=True, origin=o, seed=1,
+                          params=dict(kappa=kappa))
+    assert est["discarded"].sum() == 0
+    sp = rows["pos"] - o
+    st = sp / np.einsum("ij,ij->i", sp, sp)[:, None]
+    r, rho = est["r_t"], est["rho"]
+    gap = np.linalg.norm(st - est["center"], axis=1) - rho
+    assert np.all(r > 0)
+    assert np.all(gap >= -1e-9 * r)
+    assert np.all(gap <= kappa * r * (1 + 1e-9))
+    assert np.all(rho >= (1 - kappa) * r * (1 - 1e-9))
+
+
+def test_exterior_jump_mass_between_components_is_symmetric(oracle):
+    """J(s, t) = J(t, s) (Eq. exterior-jump-kernel-final), so the jump mass from
+    sphere A to sphere B equals that from B to A.  Two spheres (R = 0.5,
+    centres 1.5 apart), inversion centre at A's centre; the 2.5 degree cap
+    reaches neither sphere from the other at this gap, so both sums estimate
+    the same integral.  A vertex-row bias of order 20% remains at s2; the
+    tolerance allows it and the noise of ~200 cross hits."""
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    o = np.zeros(3)
+    W = 256
+    est = oracle.estimate(m.V, m.F, rows, W, 1e-3, exterior=True, origin=o, seed=1)
+    a = rows["pos"][:, 0] < 0.75
+    Wm = (oracle.row_weights(est, rows)[:, None] * est["H"] / W
+          * oracle.column_factor(rows, True, o)[None, :])
+    ab, ba = Wm[np.ix_(a, ~a)].sum(), Wm[np.ix_(~a, a)].sum()
+    assert est["H"][np.ix_(a, ~a)].sum() > 100
+    assert 2 / 3 < ab / ba < 1.5, (ab, ba)
+
+
+def test_exterior_killing_mass_of_two_spheres_is_their_capacitance(oracle, two_sphere_capacitance):
+    """The killing measure is the normal derivative of the escape probability
+    (Eq. killing-measure-normal-derivative), so its total is the flux of the
+    equilibrium potential: 4 pi C, with C the capacitance of the surface
+    (4 pi R for one sphere).  Two spheres of radius 0.5, centres 1.5 apart,
+    inversion centre at one of them: C by the method of images; by symmetry
+    each sphere carries half of it, although only one holds the centre
+    (Eq. killing-measure-poisson-kernel)."""
+    m = meshgen.two_spheres(2, 0.5, 1.5)
+    rows = oracle.vertex_rows(m.V, m.F)
+    o = np.zeros(3)
+    N = 20000
+    est = oracle.estimate(m.V, m.F, rows, 2, 1e-3, exterior=True, origin=o, seed=1, killing_walks=N)
+    assert est["kill_stats"][1] == 0 and est["kill_stats"][2] == 0
+    k = 4 * math.pi * oracle.column_factor(rows, True, o) * est["H0"] / N
+    ref = 4 * math.pi * two_sphere_capacitance(0.5, 1.5)
+    assert abs(k.sum() / ref - 1) < 0.03, k.sum() / ref
+    a = rows["pos"][:, 0] < 0.75
+    assert abs(k[a].sum() / k.sum() - 0.5) < 0.03
