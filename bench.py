@@ -139,6 +139,41 @@ def _peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
+WALK_SOURCES = ("paper_2606_05581_b300/csrc/estimate.cu", "paper_2606_05581_b300/csrc/mcs_device.cuh",
+                "paper_2606_05581_b300/csrc/mcs_internal.h", "paper_2606_05581_b300/build.py")
+
+
+def walk_source_digest() -> str:
+    """sha256 over the files that make the walk kernel (sources and build flags)."""
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for f in WALK_SOURCES:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _recorded_traffic(workload, walks, prec):
+    """DRAM bytes per walk-kernel launch from an ncu capture summarised under
+    profiles/ (a 'traffic_record:' line), or None when there is none for this
+    workload, walk count and precision, or the kernel's sources have changed
+    since the capture."""
+    import glob
+    root = os.path.dirname(os.path.abspath(__file__))
+    digest = walk_source_digest()
+    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                if not line.startswith("traffic_record:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:])
+                if (kv.get("workload") == workload and int(kv.get("walks_per_row", -1)) == walks
+                        and int(kv.get("prec", -1)) == prec and kv.get("source_sha256") == digest):
+                    return float(kv["dram_bytes_per_launch"]), os.path.basename(path)
+    return None
+
+
 def _alu_roofline(cst, walk_ms, kernel):
     """FP32 ALU roofline of the walk kernel: algorithmic operations (node
     visits and triangle tests of the same walks, counted in a separate
@@ -152,6 +187,16 @@ def _alu_roofline(cst, walk_ms, kernel):
             "traffic": None, "kernel": kernel, "ops_per_node": OPS_PER_NODE, "ops_per_tri": OPS_PER_TRI,
             "nodes_per_query": cst["nodes_visited"] / q, "tris_per_query": cst["tris_tested"] / q,
             "peak_note": "148 SMs x 128 FP32 lanes x max SM clock (derived)"}
+
+
+def _with_traffic(roof, workload, walks, prec):
+    rec = _recorded_traffic(workload, walks, prec)
+    if rec is not None:
+        roof["traffic"] = rec[0]
+        roof["traffic_source"] = f"profiles/{rec[1]} (ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch)"
+    else:
+        roof["traffic_source"] = "null: no ncu capture of this kernel build at this workload"
+    return roof
 
 
 def run_ours(args, rank, world):
@@ -284,7 +329,8 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "gpu_launches_note": "library kernels counted by the library (mcs_launch_count); CUB sort kernels excluded",
-        "roofline": _alu_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})"),
+        "roofline": _with_traffic(_alu_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})"),
+                                  args.workload, W, args.prec),
         "clocks": clocks,
     }
     if not args.no_cpu:
