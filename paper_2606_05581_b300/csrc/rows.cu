@@ -10,7 +10,9 @@
 //   normals    unit face normal of the sampled face, oriented outward by the
 //              generalized winding number of the other faces (App. A item 1):
 //              keep n when GWN(x - delta n) > GWN(x + delta n),
-//              delta = sqrt(area)/4; winding numbers in FP32, brute force.
+//              delta = sqrt(area)/4; FP32 solid angles, summed over the BVH
+//              with certified far-field bounds, brute force where the bound
+//              does not decide.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -352,70 +354,307 @@ __global__ void k_gwn_points(const double *pos, const double *nrm, const double 
     }
 }
 
-constexpr int kGwnChunks = 16;
-// partial[c][j] = sum over faces of chunk c (except the excluded one) of the
-// signed solid angle (Van Oosterom & Strackee 1983) seen from query j
-__global__ void __launch_bounds__(256) k_gwn(const double *V, const int32_t *F, int nf, const float4 *q, int nq,
-                                             float *partial) {
-    __shared__ float tri[256][9];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int chunk = (nf + kGwnChunks - 1) / kGwnChunks;
-    const int f0 = blockIdx.y * chunk, f1 = min(nf, f0 + chunk);
-    float4 p = j < nq ? q[j] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    const int excl = __float_as_int(p.w);
-    float acc = 0.f;
-    for (int t0 = f0; t0 < f1; t0 += 256) {
-        const int f = t0 + threadIdx.x;
-        if (f < f1) {
-            for (int k = 0; k < 3; k++) {
-                const double *v = V + 3 * F[3 * f + k];
-                tri[threadIdx.x][3 * k] = (float)v[0];
-                tri[threadIdx.x][3 * k + 1] = (float)v[1];
-                tri[threadIdx.x][3 * k + 2] = (float)v[2];
-            }
-        }
-        __syncthreads();
-        const int cnt = min(256, f1 - t0);
-        for (int t = 0; t < cnt; t++) {
-            if (t0 + t == excl) continue;
-            const float ax = tri[t][0] - p.x, ay = tri[t][1] - p.y, az = tri[t][2] - p.z;
-            const float bx = tri[t][3] - p.x, by = tri[t][4] - p.y, bz = tri[t][5] - p.z;
-            const float cx = tri[t][6] - p.x, cy = tri[t][7] - p.y, cz = tri[t][8] - p.z;
-            const float la = sqrtf(ax * ax + ay * ay + az * az), lb = sqrtf(bx * bx + by * by + bz * bz),
-                        lc = sqrtf(cx * cx + cy * cy + cz * cz);
-            const float det = ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx);
-            const float den = la * lb * lc + (ax * bx + ay * by + az * bz) * lc + (bx * cx + by * cy + bz * cz) * la +
-                              (cx * ax + cy * ay + cz * az) * lb;
-            acc += 2.f * atan2f(det, den);
-        }
-        __syncthreads();
-    }
-    if (j < nq) partial[(size_t)blockIdx.y * nq + j] = acc;
+// ---------------------------------------------------------------------------
+// Certified hierarchical winding-number orientation.  The decision needs the
+// sign of D = sum over the other faces f of Omega_f(x - delta n) -
+// Omega_f(x + delta n) (= 4 pi times the GWN gap).  Far BVH nodes enter by
+// their dipole term: a node's faces have vector area N = sum (b-a)x(c-a)/2,
+// total area A, centre C (area-weighted centroid, clamped into the node's
+// box) and radius r (farthest box corner from C); with G(v) = v / |v|^3,
+//   Omega_node(p) = N . G(C - p) + R(p),
+// and since G = -grad(1/|v|) has third-order derivative tensor norm 6/|v|^4,
+// the remainder of the difference between the two query points (2 delta
+// apart, both at least d from the box) obeys
+//   |R(p-) - R(p+)| <= 2 delta * A * r * 6 / d^4.
+// A node is taken by its dipole term when r <= theta d; nearer nodes are
+// opened and their faces summed exactly (the brute-force formula).  E adds
+// the remainder bounds and a bound on the float rounding of every term; a
+// row is decided when |D| > E, since then D has the sign of the exact sum.
+// Rows within the bound (and rows whose frontier overflowed) are summed by
+// brute force.
+// ---------------------------------------------------------------------------
+struct __align__(16) GwnAgg {
+    float4 na;  // N.x N.y N.z A
+    float4 cr;  // C.x C.y C.z r
+};
+constexpr float kGwnTheta = 0.1f;
+constexpr int kGwnWarps = 4;
+constexpr int kGwnStack = 2048;  // frontier entries per warp (shared memory; ~32 x tree depth)
+constexpr float kGwnUlp = 5.9604645e-08f;  // 2^-24
+
+__device__ __forceinline__ void tri_moments(const Tri32 &t, float N[3], float &A, float S[3]) {
+    N[0] = 0.5f * (t.ab.y * t.ac.z - t.ab.z * t.ac.y);
+    N[1] = 0.5f * (t.ab.z * t.ac.x - t.ab.x * t.ac.z);
+    N[2] = 0.5f * (t.ab.x * t.ac.y - t.ab.y * t.ac.x);
+    A = sqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    S[0] = A * (t.a.x + (t.ab.x + t.ac.x) * (1.0f / 3.0f));
+    S[1] = A * (t.a.y + (t.ab.y + t.ac.y) * (1.0f / 3.0f));
+    S[2] = A * (t.a.z + (t.ab.z + t.ac.z) * (1.0f / 3.0f));
 }
 
-__global__ void k_orient(const float *partial, int ns, double *nrm, float *gap) {
+// node aggregates bottom-up: threads start at the nodes with two leaf
+// children; the last internal child to finish continues to the parent
+__global__ void k_gwn_agg(DevMesh m, const int *child, const int *parent, int *arrive, GwnAgg *agg, int *err) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
-    const int nq = 2 * ns;
+    const int ni = m.nf - 1;
+    if (i >= ni || child[2 * i] >= 0 || child[2 * i + 1] >= 0) return;
+    int p = i;
+    for (int level = 0;; level++) {
+        if (level > 70) { atomicOr(err, kErrTree); return; }
+        float N[3] = {0.f, 0.f, 0.f}, S[3] = {0.f, 0.f, 0.f}, A = 0.f;
+        for (int side = 0; side < 2; side++) {
+            const int c = child[2 * p + side];
+            float n3[3], s3[3], a;
+            if (c < 0) {
+                tri_moments(m.t32[~c], n3, a, s3);
+            } else {
+                const float4 na = __ldcg(&agg[c].na), cr = __ldcg(&agg[c].cr);
+                n3[0] = na.x; n3[1] = na.y; n3[2] = na.z; a = na.w;
+                s3[0] = a * cr.x; s3[1] = a * cr.y; s3[2] = a * cr.z;
+            }
+            for (int k = 0; k < 3; k++) { N[k] += n3[k]; S[k] += s3[k]; }
+            A += a;
+        }
+        const Node nd = m.nodes[p];
+        const float lo[3] = {fminf(nd.a.x, nd.b.z), fminf(nd.a.y, nd.b.w), fminf(nd.a.z, nd.c.x)};
+        const float hi[3] = {fmaxf(nd.a.w, nd.c.y), fmaxf(nd.b.x, nd.c.z), fmaxf(nd.b.y, nd.c.w)};
+        float C[3], r2 = 0.f;
+        for (int k = 0; k < 3; k++) {
+            C[k] = A > 0.f ? S[k] / A : 0.5f * (lo[k] + hi[k]);
+            C[k] = fminf(fmaxf(C[k], lo[k]), hi[k]);
+            const float e = fmaxf(C[k] - lo[k], hi[k] - C[k]);
+            r2 += e * e;
+        }
+        GwnAgg g;
+        g.na = make_float4(N[0], N[1], N[2], A);
+        g.cr = make_float4(C[0], C[1], C[2], sqrtf(r2) * (1.0f + 1e-6f));
+        __stcg(&agg[p].na, g.na);
+        __stcg(&agg[p].cr, g.cr);
+        __threadfence();
+        if (p == 0) return;
+        const int q = parent[p];
+        if (q < 0 || q >= ni) { atomicOr(err, kErrTree); return; }
+        const int need = (child[2 * q] >= 0) + (child[2 * q + 1] >= 0);
+        if (need == 2 && atomicAdd(&arrive[q], 1) == 0) return;
+        __threadfence();
+        p = q;
+    }
+}
+
+// solid angle of triangle (a, a + ab, a + ac) seen from p (Van Oosterom &
+// Strackee), and a bound on its float rounding
+__device__ __forceinline__ float tri_omega(const Tri32 &t, float px, float py, float pz, float &err) {
+    const float ax = t.a.x - px, ay = t.a.y - py, az = t.a.z - pz;
+    const float bx = ax + t.ab.x, by = ay + t.ab.y, bz = az + t.ab.z;
+    const float cx = ax + t.ac.x, cy = ay + t.ac.y, cz = az + t.ac.z;
+    const float la = sqrtf(ax * ax + ay * ay + az * az), lb = sqrtf(bx * bx + by * by + bz * bz),
+                lc = sqrtf(cx * cx + cy * cy + cz * cz);
+    const float det = ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx);
+    const float den = la * lb * lc + (ax * bx + ay * by + az * bz) * lc + (bx * cx + by * cy + bz * cz) * la +
+                      (cx * ax + cy * ay + cz * az) * lb;
+    // det and den carry at most ~16 roundings of size ulp * la lb lc; the
+    // angle moves by that over |(det, den)|, atan2f adds a few ulp of pi
+    const float mag = sqrtf(det * det + den * den);
+    const float l3 = la * lb * lc;
+    err = (mag > 1024.f * kGwnUlp * l3) ? (128.f * kGwnUlp) * l3 / mag + 16.f * kGwnUlp : 8.0f;
+    return 2.f * atan2f(det, den);
+}
+
+__global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const GwnAgg *agg, const float4 *q, int n,
+                                                            float *Dout, float *Eout, int *ovf) {
+    __shared__ int stk[kGwnWarps][kGwnStack];
+    __shared__ int top[kGwnWarps];
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = blockIdx.x * kGwnWarps + w;
+    if (row >= n) return;  // warp-uniform
+    const float4 qm = q[2 * row], qp = q[2 * row + 1];
+    const int excl = __float_as_int(qm.w);
+    const float xm = 0.5f * (qm.x + qp.x), ym = 0.5f * (qm.y + qp.y), zm = 0.5f * (qm.z + qp.z);
+    const float sx = qp.x - qm.x, sy = qp.y - qm.y, sz = qp.z - qm.z;
+    // half the segment, rounded up; every point of the segment lies within it of (xm, ym, zm)
+    const float hd = 0.5f * sqrtf(sx * sx + sy * sy + sz * sz) * (1.0f + 1e-5f) + 1e-30f;
+    double D = 0.0;  // FP64 running sum: its rounding stays far below E
+    float E = 0.f;
+    bool over = false;
+    if (lane == 0) { stk[w][0] = 0; top[w] = 1; }
+    __syncwarp();
+    for (int guard = 0;; guard++) {
+        const int t = top[w];
+        if (t == 0) break;
+        if (guard > 4 * m.nf + 64) { over = true; break; }
+        const int take = min(32, t);
+        const int node = lane < take ? stk[w][t - 1 - lane] : -1;
+        __syncwarp();
+        int push[2] = {-1, -1};
+        if (node >= 0) {
+            const Node nd = m.nodes[node];
+            const float bx[2][6] = {{nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y},
+                                    {nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w}};
+            const int ch[2] = {nd.d.x, nd.d.y};
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int c = ch[side];
+                if (c < 0) {
+                    const Tri32 tr = m.t32[~c];
+                    if (__float_as_int(tr.a.w) == excl) continue;
+                    float e1, e2;
+                    const float o1 = tri_omega(tr, qm.x, qm.y, qm.z, e1);
+                    const float o2 = tri_omega(tr, qp.x, qp.y, qp.z, e2);
+                    D += (double)(o1 - o2);
+                    E += e1 + e2 + 2.f * kGwnUlp * (fabsf(o1) + fabsf(o2));
+                    continue;
+                }
+                const float dx = fmaxf(fmaxf(bx[side][0] - xm, 0.f), xm - bx[side][3]);
+                const float dy = fmaxf(fmaxf(bx[side][1] - ym, 0.f), ym - bx[side][4]);
+                const float dz = fmaxf(fmaxf(bx[side][2] - zm, 0.f), zm - bx[side][5]);
+                const float d = sqrtf(dx * dx + dy * dy + dz * dz) * (1.0f - 1e-5f) - hd;
+                const float4 na = agg[c].na, cr = agg[c].cr;
+                if (d > 0.f && cr.w <= kGwnTheta * d) {
+                    const float v1x = cr.x - qm.x, v1y = cr.y - qm.y, v1z = cr.z - qm.z;
+                    const float v2x = cr.x - qp.x, v2y = cr.y - qp.y, v2z = cr.z - qp.z;
+                    const float i1 = rsqrtf(v1x * v1x + v1y * v1y + v1z * v1z);
+                    const float i2 = rsqrtf(v2x * v2x + v2y * v2y + v2z * v2z);
+                    const float g1 = i1 * i1 * i1, g2 = i2 * i2 * i2;
+                    D += (double)(na.x * (v1x * g1 - v2x * g2) + na.y * (v1y * g1 - v2y * g2) +
+                                  na.z * (v1z * g1 - v2z * g2));
+                    const float d2 = d * d;
+                    const float nn = sqrtf(na.x * na.x + na.y * na.y + na.z * na.z);
+                    E += 12.f * hd * na.w * cr.w / (d2 * d2) * (1.0f + 1e-4f) +
+                         64.f * kGwnUlp * nn * (i1 * i1 + i2 * i2);
+                } else {
+                    push[side] = c;
+                }
+            }
+        }
+        const int k = (push[0] >= 0) + (push[1] >= 0);
+        int incl = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int base = t - take;
+        if (base + total > kGwnStack) { over = true; break; }
+        int at = base + incl - k;
+        if (push[0] >= 0) stk[w][at++] = push[0];
+        if (push[1] >= 0) stk[w][at++] = push[1];
+        __syncwarp();
+        if (lane == 0) top[w] = base + total;
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        D += __shfl_xor_sync(FULL, D, o);
+        E += __shfl_xor_sync(FULL, E, o);
+    }
+    if (lane == 0) {
+        // D rounded to float once; E (a sum of positive terms) rounded up generously
+        Dout[row] = (float)D;
+        Eout[row] = E * (1.0f + 1e-3f) + 2.f * kGwnUlp * (float)fabs(D);
+        ovf[row] = over ? 1 : 0;
+    }
+}
+
+// decided rows take the sign of D; the rest go to the brute-force list
+__global__ void k_gwn_decide(int n, int force_all, const float *D, const float *E, const int *ovf, double *nrm,
+                             float *gap, int *fb_list, int *fb_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!force_all && !ovf[i] && fabsf(D[i]) > E[i]) {
+        if (gap) gap[i] = D[i] * 0.07957747154594767f;
+        if (D[i] < 0.f)
+            for (int k = 0; k < 3; k++) nrm[3 * i + k] = -nrm[3 * i + k];
+        return;
+    }
+    fb_list[atomicAdd(fb_count, 1)] = i;
+}
+
+// brute-force sums of the listed rows; the face range is split into as many
+// chunks as fill the grid (at least 16), from the device-side row count
+__device__ __forceinline__ int fb_chunks(int cnt, int nf, int grid) {
+    const int qg = (2 * cnt + 255) / 256;
+    int ch = max(16, (grid + qg - 1) / qg);
+    return max(1, min(ch, (nf + 255) / 256));
+}
+__global__ void __launch_bounds__(256) k_gwn_fb(const double *V, const int32_t *F, int nf, const float4 *q,
+                                                const int *fb_list, const int *fb_count, float *partial) {
+    __shared__ float tri[256][9];
+    const int cnt = *fb_count;
+    if (cnt == 0) return;
+    const int nq = 2 * cnt, qg = (nq + 255) / 256;
+    const int chunks = fb_chunks(cnt, nf, gridDim.x);
+    const int csize = (nf + chunks - 1) / chunks;
+    for (int u = blockIdx.x; u < qg * chunks; u += gridDim.x) {
+        const int g = u % qg, c = u / qg;
+        const int j = g * 256 + threadIdx.x;
+        const float4 p = j < nq ? q[2 * fb_list[j >> 1] + (j & 1)] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        const int excl = __float_as_int(p.w);
+        const int f0 = min(nf, c * csize), f1 = min(nf, f0 + csize);
+        float acc = 0.f;
+        for (int t0 = f0; t0 < f1; t0 += 256) {
+            const int f = t0 + threadIdx.x;
+            if (f < f1) {
+                for (int k = 0; k < 3; k++) {
+                    const double *v = V + 3 * F[3 * f + k];
+                    tri[threadIdx.x][3 * k] = (float)v[0];
+                    tri[threadIdx.x][3 * k + 1] = (float)v[1];
+                    tri[threadIdx.x][3 * k + 2] = (float)v[2];
+                }
+            }
+            __syncthreads();
+            const int nt = min(256, f1 - t0);
+            for (int t = 0; t < nt; t++) {
+                if (t0 + t == excl) continue;
+                const float ax = tri[t][0] - p.x, ay = tri[t][1] - p.y, az = tri[t][2] - p.z;
+                const float bx = tri[t][3] - p.x, by = tri[t][4] - p.y, bz = tri[t][5] - p.z;
+                const float cx = tri[t][6] - p.x, cy = tri[t][7] - p.y, cz = tri[t][8] - p.z;
+                const float la = sqrtf(ax * ax + ay * ay + az * az), lb = sqrtf(bx * bx + by * by + bz * bz),
+                            lc = sqrtf(cx * cx + cy * cy + cz * cz);
+                const float det = ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx);
+                const float den = la * lb * lc + (ax * bx + ay * by + az * bz) * lc +
+                                  (bx * cx + by * cy + bz * cz) * la + (cx * ax + cy * ay + cz * az) * lb;
+                acc += 2.f * atan2f(det, den);
+            }
+            __syncthreads();
+        }
+        if (j < nq) partial[(size_t)c * nq + j] = acc;
+    }
+}
+__global__ void k_orient_fb(const float *partial, int nf, int grid, const int *fb_list, const int *fb_count,
+                            double *nrm, float *gap) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cnt = *fb_count;
+    if (k >= cnt) return;
+    const int nq = 2 * cnt, chunks = fb_chunks(cnt, nf, grid);
     float gi = 0.f, go = 0.f;
-    for (int c = 0; c < kGwnChunks; c++) {
-        gi += partial[(size_t)c * nq + 2 * i];
-        go += partial[(size_t)c * nq + 2 * i + 1];
+    for (int c = 0; c < chunks; c++) {
+        gi += partial[(size_t)c * nq + 2 * k];
+        go += partial[(size_t)c * nq + 2 * k + 1];
     }
     const float inv4pi = 0.07957747154594767f;
     gi *= inv4pi;
     go *= inv4pi;
+    const int i = fb_list[k];
     if (gap) gap[i] = gi - go;
     if (!(gi > go))
-        for (int k = 0; k < 3; k++) nrm[3 * i + k] = -nrm[3 * i + k];
+        for (int d = 0; d < 3; d++) nrm[3 * i + d] = -nrm[3 * i + d];
 }
 
 struct Layout {
     size_t cen, cen_s, cenf, face, farea, mind, owner, cand_v, cand_i, bar, err, keys, vals, skeys, svals, start, q, partial, sort,
-        total;
+        agg, arrive, gD, gE, govf, fb_list, fb_count, total;
     size_t sort_bytes;
 };
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+// brute-force blocks for the undecided rows, and the partial sums they need:
+// at most max(16 chunks x 2 ns queries, 256 x (grid + grid/16 + 2)) floats
+static int gwn_fb_grid() { return num_sms() * 8; }
+static size_t gwn_partial_floats(int ns) {
+    const size_t g = (size_t)gwn_fb_grid();
+    return std::max((size_t)32 * ns, 256 * (g + g / 16 + 2));
+}
 static Layout layout(int nf, int ns, int nblocks) {
     Layout L;
     size_t o = 0;
@@ -437,7 +676,14 @@ static Layout layout(int nf, int ns, int nblocks) {
     L.svals = take(sizeof(int32_t) * nf);
     L.start = take(sizeof(int32_t) * (ns + 1));
     L.q = take(sizeof(float4) * 2 * ns);
-    L.partial = take(sizeof(float) * kGwnChunks * 2 * ns);
+    L.partial = take(sizeof(float) * gwn_partial_floats(ns));
+    L.agg = take(sizeof(GwnAgg) * (size_t)std::max(1, nf - 1));
+    L.arrive = take(sizeof(int) * (size_t)std::max(1, nf - 1));
+    L.gD = take(sizeof(float) * ns);
+    L.gE = take(sizeof(float) * ns);
+    L.govf = take(sizeof(int) * ns);
+    L.fb_list = take(sizeof(int) * ns);
+    L.fb_count = take(sizeof(int));
     size_t sb = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, sb, (int32_t *)nullptr, (int32_t *)nullptr, (int32_t *)nullptr,
                                     (int32_t *)nullptr, nf, 0, 32);
@@ -512,14 +758,34 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
     k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, it.sel, svals, start, n, it.pos, it.nrm,
                                                     it.area);
     if (orient) {
+        // orient 1: hierarchical sums, brute force for the rows within their
+        // bound; orient 2: brute force for every row
         float4 *q = (float4 *)(w + L.q);
         float *partial = (float *)(w + L.partial);
+        float *gD = (float *)(w + L.gD), *gE = (float *)(w + L.gE);
+        int *govf = (int *)(w + L.govf), *fb_list = (int *)(w + L.fb_list), *fb_count = (int *)(w + L.fb_count);
+        const bool tree = orient == 1 && nf >= 2;
         note_launch();
         k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, farea, it.sel, n, q);
+        if (tree) {
+            GwnAgg *agg = (GwnAgg *)(w + L.agg);
+            int *arrive = (int *)(w + L.arrive);
+            MCS_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
+            note_launch();
+            k_gwn_agg<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(m->dev(), m->child, m->parent, arrive, agg,
+                                                            (int *)(w + L.err));
+            note_launch();
+            k_gwn_tree<<<(n + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(m->dev(), agg, q, n, gD, gE, govf);
+        }
+        MCS_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(int), st));
         note_launch();
-        k_gwn<<<dim3((2 * n + 255) / 256, kGwnChunks), 256, 0, st>>>(m->V, m->F, nf, q, 2 * n, partial);
+        k_gwn_decide<<<(n + tb - 1) / tb, tb, 0, st>>>(n, tree ? 0 : 1, gD, gE, govf, it.nrm, it.orient_gap, fb_list,
+                                                        fb_count);
+        const int grid = gwn_fb_grid();
         note_launch();
-        k_orient<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, n, it.nrm, it.orient_gap);
+        k_gwn_fb<<<grid, 256, 0, st>>>(m->V, m->F, nf, q, fb_list, fb_count, partial);
+        note_launch();
+        k_orient_fb<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, nf, grid, fb_list, fb_count, it.nrm, it.orient_gap);
     }
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
@@ -577,7 +843,8 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
     MCS_CUDA(cudaMemcpyAsync(&herr, w + L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaStreamSynchronize(st));
     if (herr) {
-        set_error("mcs_sample_rows: a grid barrier wait timed out");
+        set_error((herr & kErrBarrier) ? "mcs_sample_rows: a grid barrier wait timed out"
+                                       : "mcs_sample_rows: the BVH aggregate pass exceeded its depth bound");
         return MCS_ERR_DEVICE;
     }
     return MCS_OK;

@@ -201,6 +201,54 @@ def test_sample_rows_match_oracle(oracle):
     assert flipped.mean() < 0.01
 
 
+def test_hierarchical_orientation_equals_brute_force(oracle):
+    """Sample-row orientation by the BVH sums with certified far-field bounds
+    (orient 1) against brute force on every row (orient 2) and the oracle's
+    FP64 winding numbers: the same sampling, the same normal wherever the gap
+    is not a near tie, gaps within the far-field tolerance."""
+    m = meshgen.wild_union(10, 40000, seed=17)
+    mesh = mcs.Mesh(m.V, m.F)
+    h = mcs.sample_rows(mesh, 1500, orient=1)
+    b = mcs.sample_rows(mesh, 1500, orient=2)
+    for k in ("sel", "tri2bin", "area", "pos"):
+        assert torch.equal(h[k], b[k]), k
+    gh, gb = h["gap"].cpu().numpy().astype(np.float64), b["gap"].cpu().numpy().astype(np.float64)
+    hn, bn = h["nrm"].cpu().numpy(), b["nrm"].cpu().numpy()
+    same = np.all(hn == bn, axis=1)
+    assert np.all(same | np.all(hn == -bn, axis=1))
+    assert np.all(same | (np.abs(gb) < 1e-4)), np.abs(gb[~same]).max()
+    assert np.abs(gh - gb).max() < 0.02, np.abs(gh - gb).max()
+    # against the FP64 oracle on a sample of rows
+    o = oracle.fps_rows(m.V, m.F, 1500, orient=False)
+    assert np.array_equal(o["sel"], h["sel"].cpu().numpy())
+    for i in range(0, 1500, 97):
+        f = o["sel"][i]
+        a_, b_, c_ = m.V[m.F[f]]
+        delta = 0.25 * np.sqrt(0.5 * np.linalg.norm(np.cross(b_ - a_, c_ - a_)))
+        nrm = o["nrm"][i]
+        gi = oracle.gwn(m.V, m.F, o["pos"][i] - delta * nrm, skip=f)
+        go = oracle.gwn(m.V, m.F, o["pos"][i] + delta * nrm, skip=f)
+        g = gi - go
+        # both gaps refer to the unoriented face normal; the GPU keeps it when its gap is positive
+        kept = np.all(hn[i] == nrm)
+        if abs(g) > 1e-3:
+            assert (g > 0) == kept, (i, g)
+        assert abs(gh[i] - g) < 0.02, (i, gh[i], g)
+
+
+def test_brute_force_orientation_of_a_few_rows():
+    """A handful of rows: the brute-force pass splits the faces into many
+    chunks to fill the grid, with the same normals as the hierarchical pass."""
+    m = meshgen.wild_union(6, 20000, seed=5)
+    mesh = mcs.Mesh(m.V, m.F)
+    h = mcs.sample_rows(mesh, 5, orient=1)
+    b = mcs.sample_rows(mesh, 5, orient=2)
+    gb = b["gap"].cpu().numpy()
+    for i in range(5):
+        if abs(gb[i]) > 1e-4:
+            assert torch.equal(h["nrm"][i], b["nrm"][i]), i
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_sample_rows_estimate_bit_exact(oracle, prec):
     """The estimate on GPU sample rows equals the oracle's on the same rows."""
