@@ -193,7 +193,10 @@ mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, v
  * orient_gap n (optional: GWN(x - delta n) - GWN(x + delta n), within the
  * row's bound for rows decided by the hierarchical sum).  The
  * sampling runs in single precision on the float-rounded centroids (ties ->
- * lowest face id); meshes above 2^18 faces use a cooperative launch.
+ * lowest face id); meshes up to 2^18 faces use one block, larger ones a
+ * thread-block cluster (16 CTAs where the device allows, else 8) that
+ * exchanges candidates through distributed shared memory, and meshes beyond
+ * the cluster's shared memory (~16M faces) a cooperative grid.
  * Synchronises `stream`. */
 size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n);
 mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,

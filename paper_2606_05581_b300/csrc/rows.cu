@@ -2,9 +2,12 @@
 // basis: points sampled on the surface; farthest-point sampling stands in for
 // the paper's blue-noise sampling):
 //   FPS        greedy farthest-point sampling over face centroids from face 0,
-//              FP64, one cooperative persistent kernel with a bounded grid
-//              barrier per selection; each face keeps its nearest sample
-//              (first selected on ties) -> tri2bin;
+//              FP32 on the float-rounded centroids: one block (small meshes),
+//              one thread-block cluster with a hardware barrier and a
+//              distributed-shared-memory exchange per selection (large
+//              meshes), or a cooperative grid with a bounded grid barrier
+//              (beyond the cluster's shared memory); each face keeps its
+//              nearest sample (first selected on ties) -> tri2bin;
 //   areas      each sample's quadrature area = area of the faces it owns,
 //              summed in ascending face order (stable sort + segments);
 //   normals    unit face normal of the sampled face, oriented outward by the
@@ -13,6 +16,7 @@
 //              delta = sqrt(area)/4; FP32 solid angles, summed over the BVH
 //              with certified far-field bounds, brute force where the bound
 //              does not decide.
+#include <cooperative_groups.h>
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -224,6 +228,175 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
         cur = idx;
     }
+}
+
+// The same greedy sampling by ONE thread-block cluster of kFpsThreads-thread
+// CTAs.  CTA k owns a contiguous range of BVH slots, split into sub-ranges of
+// kFpsSub slots whose centroid boxes and largest distances (candidates) live
+// in its shared memory; after each new sample q a sub-range is rescanned only
+// when q can be nearer than its largest distance (the culling test of k_fps,
+// at a finer grain).  The CTAs' candidates are exchanged through distributed
+// shared memory, one hardware cluster barrier per selection (double-buffered,
+// so a CTA never overwrites a candidate another CTA may still be reading).
+constexpr int kFpsSub = 256;
+constexpr int kFpsClusterMaxSub = 4096;  // sub-ranges per CTA (3 x 16 B each, dynamic shared memory)
+
+// warp-wide argmax of (v, lowest i on ties) carrying the winner's centroid
+__device__ __forceinline__ void warp_argmax_xyz(float &v, int &i, float &x, float &y, float &z) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i, o);
+        const float ox = __shfl_xor_sync(0xFFFFFFFFu, x, o), oy = __shfl_xor_sync(0xFFFFFFFFu, y, o),
+                    oz = __shfl_xor_sync(0xFFFFFFFFu, z, o);
+        if (fps_better(ov, oi, v, i)) { v = ov; i = oi; x = ox; y = oy; z = oz; }
+    }
+}
+
+__global__ void __launch_bounds__(kFpsThreads) k_fps_cluster(FpsArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    constexpr int NW = kFpsThreads / 32;
+    constexpr int PER_LANE = kFpsSub / 32;
+    // per sub-range: lo4 = (box lo, candidate value), hi4 = (box hi, candidate
+    // face bits), cc4 = (candidate centroid, -)
+    extern __shared__ float4 sub[];
+    __shared__ float4 wc[NW];  // warp candidates: centroid, value
+    __shared__ int wi[NW];
+    __shared__ float4 cta_c[2];  // this CTA's candidate (double-buffered), read by the others
+    __shared__ int cta_i[2];
+    const unsigned rank = cl.block_rank(), ncta = cl.num_blocks();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per = (a.nf + (int)ncta - 1) / (int)ncta;
+    const int s0 = min(a.nf, (int)rank * per), s1 = min(a.nf, s0 + per);
+    const int nsub = (s1 - s0 + kFpsSub - 1) / kFpsSub;
+    float4 *lo4 = sub, *hi4 = sub + nsub, *cc4 = sub + 2 * nsub;
+    // warp w owns sub-ranges w, w + NW, w + 2 NW, ...: neighbouring sub-ranges
+    // (the ones a new sample tends to reach together) go to different warps
+    const int nown = w < nsub ? (nsub - w + NW - 1) / NW : 0;
+    for (int l = 0; l < nown; l++) {
+        const int j = w + NW * l;
+        const int b0 = s0 + j * kFpsSub, b1 = min(s1, b0 + kFpsSub);
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int s = b0 + lane; s < b1; s += 32)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
+                hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+            }
+        if (lane == 0) {
+            lo4[j] = make_float4(lo[0], lo[1], lo[2], INFINITY);
+            hi4[j] = make_float4(hi[0], hi[1], hi[2], __int_as_float(0x7FFFFFFF));
+            cc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncwarp();
+    if (rank == 0 && threadIdx.x == 0) a.sel[0] = 0;
+    float qx = a.cen[0], qy = a.cen[1], qz = a.cen[2];
+    for (int i = 0; i < a.ns; i++) {
+        float bv = -1.0f, bx = 0.f, by = 0.f, bz = 0.f;
+        int bi = 0x7FFFFFFF;
+        for (int r0 = 0; r0 < nown; r0 += 32) {
+            const int j = w + NW * (r0 + lane);
+            bool need = false;
+            if (r0 + lane < nown) {
+                const float4 l = lo4[j], h = hi4[j];
+                const float e0 = fmaxf(fmaxf(l.x - qx, 0.0f), qx - h.x);
+                const float e1 = fmaxf(fmaxf(l.y - qy, 0.0f), qy - h.y);
+                const float e2 = fmaxf(fmaxf(l.z - qz, 0.0f), qz - h.z);
+                need = !((e0 * e0 + e1 * e1 + e2 * e2) * (1.0f - 1e-5f) > l.w);
+            }
+            unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int jb = w + NW * (r0 + b);
+                const int b0 = s0 + jb * kFpsSub, b1 = min(s1, b0 + kFpsSub);
+                float v = -1.0f, vx = 0.f, vy = 0.f, vz = 0.f;
+                int vi = 0x7FFFFFFF;
+                // all of the lane's slots at once: their loads are independent
+                float cx[PER_LANE], cy[PER_LANE], cz[PER_LANE], md[PER_LANE];
+                int fc[PER_LANE];
+#pragma unroll
+                for (int k = 0; k < PER_LANE; k++) {
+                    const int s = b0 + lane + 32 * k;
+                    if (s < b1) {
+                        cx[k] = a.cen_s[3 * s];
+                        cy[k] = a.cen_s[3 * s + 1];
+                        cz[k] = a.cen_s[3 * s + 2];
+                        md[k] = a.mind[s];
+                        fc[k] = a.face[s];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PER_LANE; k++) {
+                    const int s = b0 + lane + 32 * k;
+                    if (s < b1) {
+                        const float d0 = cx[k] - qx, d1 = cy[k] - qy, d2 = cz[k] - qz;
+                        const float d = d0 * d0 + d1 * d1 + d2 * d2;
+                        if (d < md[k]) {
+                            md[k] = d;
+                            a.mind[s] = d;
+                            a.owner[s] = i;
+                        }
+                        if (fps_better(md[k], fc[k], v, vi)) { v = md[k]; vi = fc[k]; vx = cx[k]; vy = cy[k]; vz = cz[k]; }
+                    }
+                }
+                warp_argmax_xyz(v, vi, vx, vy, vz);
+                if (lane == b) {
+                    lo4[jb].w = v;
+                    hi4[jb].w = __int_as_float(vi);
+                    cc4[jb] = make_float4(vx, vy, vz, 0.f);
+                }
+            }
+            __syncwarp();
+            if (r0 + lane < nown) {
+                const float v = lo4[j].w;
+                const int vi = __float_as_int(hi4[j].w);
+                if (fps_better(v, vi, bv, bi)) {
+                    const float4 c = cc4[j];
+                    bv = v; bi = vi; bx = c.x; by = c.y; bz = c.z;
+                }
+            }
+        }
+        warp_argmax_xyz(bv, bi, bx, by, bz);
+        if (i + 1 == a.ns) break;
+        const int par = i & 1;
+        if (lane == 0) {
+            wc[w] = make_float4(bx, by, bz, bv);
+            wi[w] = bi;
+        }
+        __syncthreads();
+        if (w == 0) {
+            const float4 c = wc[lane];
+            float v = c.w, x = c.x, y = c.y, z = c.z;
+            int idx = wi[lane];
+            warp_argmax_xyz(v, idx, x, y, z);
+            if (lane == 0) {
+                cta_c[par] = make_float4(x, y, z, v);
+                cta_i[par] = idx;
+            }
+        }
+        cl.sync();
+        // every warp folds the CTAs' candidates (any order gives the same winner)
+        float v = -1.0f, x = 0.f, y = 0.f, z = 0.f;
+        int idx = 0x7FFFFFFF;
+        if (lane < (int)ncta) {
+            const float4 c = *cl.map_shared_rank(&cta_c[par], lane);
+            v = c.w; x = c.x; y = c.y; z = c.z;
+            idx = *cl.map_shared_rank(&cta_i[par], lane);
+        }
+        warp_argmax_xyz(v, idx, x, y, z);
+        if (rank == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
+        qx = x; qy = y; qz = z;
+    }
+    // no CTA leaves while another may still read its shared memory
+    cl.sync();
 }
 
 // The same greedy sampling by ONE block of kFpsThreads threads (no grid
@@ -700,6 +873,63 @@ static int fps_blocks(int nf) {
     return std::max(1, std::min(num_sms(), want));
 }
 
+// cluster FPS: the largest cluster size (16 if the device allows it, else 8)
+// that can be resident with this much dynamic shared memory; 0 if neither
+static int fps_cluster_size(int nf, size_t *smem_out) {
+    for (int cs : {16, 8}) {
+        const int per = (nf + cs - 1) / cs;
+        const int nsub = (per + kFpsSub - 1) / kFpsSub;
+        if (nsub > kFpsClusterMaxSub) continue;
+        const size_t smem = sizeof(float4) * 3 * (size_t)nsub;
+        if (cs > 8 && cudaFuncSetAttribute(k_fps_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                          cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (cudaFuncSetAttribute(k_fps_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kFpsThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = cs;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (void *)k_fps_cluster, &cfg) == cudaSuccess && nc >= 1) {
+            *smem_out = smem;
+            return cs;
+        }
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+static mcs_status launch_fps_cluster(const FpsArgs &a, int cs, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(kFpsThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = cs;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    note_launch();
+    MCS_CUDA(cudaLaunchKernelEx(&cfg, k_fps_cluster, a));
+    return MCS_OK;
+}
+
 static mcs_status sample_check(const mcs_sample_item &it, const char *fn) {
     const std::string f(fn);
     MCS_ARG(it.mesh != nullptr, f + ": mesh is NULL");
@@ -826,9 +1056,13 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
     char *w = (char *)workspace;
     FpsArgs a;
     if ((s = sample_prepare(it, w, L, nb, st, &a)) != MCS_OK) return s;
+    size_t csmem = 0;
+    const int cs = m->nf > kFpsSmallFaces ? fps_cluster_size(m->nf, &csmem) : 0;
     if (m->nf <= kFpsSmallFaces) {
         note_launch();
         k_fps_block<<<1, kFpsThreads, 0, st>>>(a);
+    } else if (cs > 0) {
+        if ((s = launch_fps_cluster(a, cs, csmem, st)) != MCS_OK) return s;
     } else {
         int coop = 0, dev = 0;
         MCS_CUDA(cudaGetDevice(&dev));

@@ -236,6 +236,22 @@ def test_hierarchical_orientation_equals_brute_force(oracle):
         assert abs(gh[i] - g) < 0.02, (i, gh[i], g)
 
 
+def test_sample_rows_large_mesh_match_oracle(oracle):
+    """Above 2^18 faces the farthest-point sampling runs on a thread-block
+    cluster (sub-range culling, candidates exchanged through distributed
+    shared memory): selections, owners, areas and positions bit for bit."""
+    m = meshgen.wild_union(24, 320000, seed=23)
+    assert m.nf > 1 << 18
+    mesh = mcs.Mesh(m.V, m.F)
+    g = mcs.sample_rows(mesh, 1200, orient=0)
+    o = oracle.fps_rows(m.V, m.F, 1200, orient=False)
+    assert np.array_equal(g["sel"].cpu().numpy(), o["sel"])
+    assert np.array_equal(g["tri2bin"].cpu().numpy(), o["tri2bin"])
+    assert np.array_equal(g["area"].cpu().numpy(), o["area"])
+    assert np.array_equal(g["pos"].cpu().numpy(), o["pos"])
+    assert np.array_equal(g["nrm"].cpu().numpy(), o["nrm"])
+
+
 def test_brute_force_orientation_of_a_few_rows():
     """A handful of rows: the brute-force pass splits the faces into many
     chunks to fill the grid, with the same normals as the hierarchical pass."""
