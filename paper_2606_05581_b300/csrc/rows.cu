@@ -238,19 +238,20 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(FpsArgs a) {
 // at a finer grain).  The CTAs' candidates are exchanged through distributed
 // shared memory, one hardware cluster barrier per selection (double-buffered,
 // so a CTA never overwrites a candidate another CTA may still be reading).
-constexpr int kFpsSub = 256;
+constexpr int kFpsSub = 128;
 constexpr int kFpsClusterMaxSub = 4096;  // sub-ranges per CTA (3 x 16 B each, dynamic shared memory)
 
-// warp-wide argmax of (v, lowest i on ties) carrying the winner's centroid
+// warp-wide argmax of (v, lowest i on ties); the winner's centroid is then
+// taken from the lowest lane that holds the winning pair
 __device__ __forceinline__ void warp_argmax_xyz(float &v, int &i, float &x, float &y, float &z) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        const int oi = __shfl_xor_sync(0xFFFFFFFFu, i, o);
-        const float ox = __shfl_xor_sync(0xFFFFFFFFu, x, o), oy = __shfl_xor_sync(0xFFFFFFFFu, y, o),
-                    oz = __shfl_xor_sync(0xFFFFFFFFu, z, o);
-        if (fps_better(ov, oi, v, i)) { v = ov; i = oi; x = ox; y = oy; z = oz; }
-    }
+    const float v0 = v;
+    const int i0 = i;
+    warp_argmax(v, i);
+    const unsigned hold = __ballot_sync(0xFFFFFFFFu, v0 == v && i0 == i);
+    const int src = hold ? __ffs(hold) - 1 : 0;
+    x = __shfl_sync(0xFFFFFFFFu, x, src);
+    y = __shfl_sync(0xFFFFFFFFu, y, src);
+    z = __shfl_sync(0xFFFFFFFFu, z, src);
 }
 
 __global__ void __launch_bounds__(kFpsThreads) k_fps_cluster(FpsArgs a) {
