@@ -199,6 +199,47 @@ def _with_traffic(roof, workload, walks, prec):
     return roof
 
 
+def _downstream(mcs, out, dev, reps=5):
+    """Untimed by the headline: Steklov heat of a 16-channel field and heat
+    kernel signatures at 16 log-spaced times from the step's eigenpairs, each
+    timed with CUDA events (mean of `reps` after one warm-up).  Algorithmic
+    bytes: psi read (n k 8) plus the outputs written (heat: psi twice, u0 in)."""
+    import torch
+    _, rows, _, ev = out
+    evals, X = ev[0], ev[1]
+    n, k = int(X.shape[0]), int(X.shape[1])
+    times = torch.logspace(-3, 1, 16, dtype=torch.float64, device=dev)
+    c = 16
+    u0 = torch.randn(n, c, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    ws = mcs.Workspace()
+
+    def clock(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    heat_ms = clock(lambda: mcs.steklov_heat(evals, X, rows["area"], u0, times, workspace=ws))
+    hks_ms = clock(lambda: mcs.hks(evals, X, times))
+    nt = int(times.numel())
+    heat_bytes = 2 * n * k * 8 + n * c * 8 + nt * n * c * 8
+    hks_bytes = n * k * 8 + nt * n * 8
+    peak = _peaks().get("hbm_gbs")
+    gbs = lambda b, ms: b / (ms / 1e3) / 1e9
+    # FP64 multiply-adds: projection n k c, synthesis nt n k c; HKS nt n k
+    heat_tflops = 2.0 * (n * k * c + nt * n * k * c) / (heat_ms / 1e3) / 1e12
+    hks_tflops = 2.0 * nt * n * k / (hks_ms / 1e3) / 1e12
+    return {"n": n, "k": k, "channels": c, "times": nt, "heat_ms": heat_ms, "hks_ms": hks_ms,
+            "heat_gbs": gbs(heat_bytes, heat_ms), "hks_gbs": gbs(hks_bytes, hks_ms), "hbm_peak_gbs": peak,
+            "heat_fp64_tflops": heat_tflops, "hks_fp64_tflops": hks_tflops, "fp64_nominal_tflops": 1.25,
+            "note": "psi (n x k FP64) fits in L2 at this size, so the passes are bound by FP64 arithmetic "
+                    "(B300's nominal FP64 rate) rather than HBM"}
+
+
 def run_ours(args, rank, world):
     """One mesh per step: the default two-sphere exterior workload or wild_2m."""
     import torch
@@ -310,6 +351,7 @@ def run_ours(args, rank, world):
     walk_ms = float(np.mean([s["phase_ms"][1] for s in stats]))
     phase = np.mean([s["phase_ms"] for s in stats], axis=0).tolist()
     walks = n_rows * W + kill
+    downstream = _downstream(mcs, step(V_d, F_d, keep=True), dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -332,6 +374,7 @@ def run_ours(args, rank, world):
         "roofline": _with_traffic(_alu_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})"),
                                   args.workload, W, args.prec),
         "clocks": clocks,
+        "downstream": downstream,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, samples=1)[0]

@@ -369,6 +369,27 @@ size_t mcs_steklov_workspace_size(int n, int k);
 mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, int k, double *evals, double *evecs,
                              void *workspace, size_t workspace_bytes, const mcs_eig_params *params,
                              mcs_eig_stats *stats, void *stream);
+/* Steklov heat (Sec. 5, Eq. steklovHeat, solved in the eigenbasis by Eq.
+ * spectralSteklovHeat): for each time t and each channel column of u0,
+ *   u_t = sum_j exp(-lambda_j t) a_j psi_j,  a_j = psi_j^T M u_0,
+ * with the interior or exterior eigenpairs of mcs_steklov_modes.
+ * evals: device k FP64; evecs: device n x k FP64 row-major, M-orthonormal;
+ * mass: device n; u0: device n x c row-major (c channels); times: device nt;
+ * out: device nt x n x c row-major.  1 <= k <= 128.  workspace: device,
+ * 256-byte aligned, >= mcs_steklov_heat_workspace_size(n, k, c).  FP64, sums
+ * in a fixed order (bitwise reproducible).  Asynchronous on `stream`. */
+size_t mcs_steklov_heat_workspace_size(int n, int k, int c);
+mcs_status mcs_steklov_heat(const double *evals, const double *evecs, const double *mass, int n, int k,
+                            const double *u0, int c, const double *times, int nt, double *out, void *workspace,
+                            size_t workspace_bytes, void *stream);
+/* Heat kernel signature of the Steklov eigenpairs (Sun et al. 2009; the
+ * basis-invariant comparison of spectra in Sec. 5, Fig. hks_comparison):
+ *   out[t][x] = sum_j exp(-lambda_j t) psi_j(x)^2.
+ * evals: device k; evecs: device n x k row-major; times: device nt; out:
+ * device nt x n.  1 <= k <= 128.  FP64, fixed summation order.  Needs no
+ * workspace.  Asynchronous on `stream`. */
+mcs_status mcs_hks(const double *evals, const double *evecs, int n, int k, const double *times, int nt, double *out,
+                   void *stream);
 /* Test hook: Zt = (A X)^T through the same tensor-core product, for a
  * symmetric A (device n x n FP64) and Xt (device m x n FP64, m a multiple
  * of 16 in [16, 160]); Zt device m x n FP64. */

@@ -347,6 +347,29 @@ def steklov(L: np.ndarray, mass: np.ndarray, k: int):
     return w[:k], (X[:, :k] * s[:, None])
 
 
+def steklov_heat(evals, evecs, mass, u0, times) -> np.ndarray:
+    """Steklov heat (Sec. 5, Eq. spectralSteklovHeat): for each t,
+    u_t = sum_j exp(-lambda_j t) a_j psi_j with a_j = <u0, psi_j>_M.
+    u0: n or n x c; returns nt x n (x c)."""
+    evals = np.asarray(evals, np.float64)
+    psi = np.asarray(evecs, np.float64)
+    u = np.asarray(u0, np.float64)
+    a = psi.T @ (np.asarray(mass, np.float64).reshape(-1, *([1] * (u.ndim - 1))) * u)
+    out = []
+    for t in np.asarray(times, np.float64).reshape(-1):
+        decay = np.exp(-evals * t)
+        out.append(psi @ (decay.reshape(-1, *([1] * (u.ndim - 1))) * a))
+    return np.stack(out)
+
+
+def hks(evals, evecs, times) -> np.ndarray:
+    """Heat kernel signature (Sun et al. 2009, the comparison of Fig.
+    hks_comparison): HKS(x, t) = sum_j exp(-lambda_j t) psi_j(x)^2; nt x n."""
+    evals = np.asarray(evals, np.float64)
+    sq = np.asarray(evecs, np.float64) ** 2
+    return np.stack([sq @ np.exp(-evals * t) for t in np.asarray(times, np.float64).reshape(-1)])
+
+
 # ---------------------------------------------------------------------------
 # closed forms (pins)
 # ---------------------------------------------------------------------------

@@ -134,6 +134,10 @@ def lib():
         L.mcs_steklov_workspace_size.restype = C.c_size_t
         L.mcs_steklov_modes.argtypes = [vp, vp, i32, i32, vp, vp, vp, C.c_size_t, C.POINTER(EigParams),
                                         C.POINTER(EigStats), vp]
+        L.mcs_steklov_heat_workspace_size.argtypes = [i32, i32, i32]
+        L.mcs_steklov_heat_workspace_size.restype = C.c_size_t
+        L.mcs_steklov_heat.argtypes = [vp, vp, vp, i32, i32, vp, i32, vp, i32, vp, vp, C.c_size_t, vp]
+        L.mcs_hks.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
         L.mcs_tc_symm_product_workspace_size.argtypes = [i32, i32]
         L.mcs_tc_symm_product_workspace_size.restype = C.c_size_t
         L.mcs_tc_symm_product.argtypes = [vp, vp, i32, i32, vp, vp, C.c_size_t, vp]
@@ -509,6 +513,40 @@ def steklov_modes(Lambda: torch.Tensor, mass: torch.Tensor, k: int, params: EigP
     stats = {f: getattr(st, f) for f, _ in EigStats._fields_}
     stats["status"] = status
     return ev, X, stats
+
+
+def steklov_heat(evals: torch.Tensor, evecs: torch.Tensor, mass: torch.Tensor, u0: torch.Tensor,
+                 times, workspace: "Workspace | None" = None) -> torch.Tensor:
+    """Steklov heat u_t = sum_j exp(-lambda_j t) <u0, psi_j>_M psi_j for each time
+    (u0: n or n x c); returns nt x n (x c) FP64 on the device."""
+    dev = evecs.device
+    ev = evals.to(device=dev, dtype=torch.float64).contiguous()
+    X = evecs.to(torch.float64).contiguous()
+    n, k = int(X.shape[0]), int(X.shape[1])
+    M = mass.to(device=dev, dtype=torch.float64).contiguous()
+    vec = u0.dim() == 1
+    U = u0.to(device=dev, dtype=torch.float64).reshape(n, -1).contiguous()
+    c = int(U.shape[1])
+    T = torch.as_tensor(times, dtype=torch.float64).reshape(-1).to(dev).contiguous()
+    nt = int(T.shape[0])
+    out = torch.empty((nt, n, c), dtype=torch.float64, device=dev)
+    nb = int(lib().mcs_steklov_heat_workspace_size(n, k, c))
+    ws = (workspace or Workspace()).get(nb)
+    _check(lib().mcs_steklov_heat(_ptr(ev), _ptr(X), _ptr(M), n, k, _ptr(U), c, _ptr(T), nt, _ptr(out),
+                                  C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return out[:, :, 0] if vec else out
+
+
+def hks(evals: torch.Tensor, evecs: torch.Tensor, times) -> torch.Tensor:
+    """Heat kernel signature sum_j exp(-lambda_j t) psi_j(x)^2; returns nt x n FP64 on the device."""
+    dev = evecs.device
+    ev = evals.to(device=dev, dtype=torch.float64).contiguous()
+    X = evecs.to(torch.float64).contiguous()
+    n, k = int(X.shape[0]), int(X.shape[1])
+    T = torch.as_tensor(times, dtype=torch.float64).reshape(-1).to(dev).contiguous()
+    out = torch.empty((int(T.shape[0]), n), dtype=torch.float64, device=dev)
+    _check(lib().mcs_hks(_ptr(ev), _ptr(X), n, k, _ptr(T), int(T.shape[0]), _ptr(out), _stream()))
+    return out
 
 
 def tc_symm_product(A: torch.Tensor, Xt: torch.Tensor) -> torch.Tensor:

@@ -112,3 +112,53 @@ def test_two_sphere_exterior_capacitance_and_symmetry(two_sphere_capacitance):
     # the solver resolves eigenvalues to ~1e-6 of the spectral upper bound
     assert 0 < ev[0] <= rq + 1e-5 * sst["upper_bound"], (ev[0], rq)
     assert ev[0] > 0.9 * rq
+
+
+@pytest.mark.parametrize("domain,k,c,nt", [(0, 64, 1, 5), (0, 100, 37, 20), (1, 48, 16, 17)])
+def test_steklov_heat_and_hks_match_oracle(oracle, domain, k, c, nt):
+    """Steklov heat (Eq. spectralSteklovHeat) and heat kernel signatures from
+    GPU eigenpairs, against the oracle's plain sums on the same pairs: FP64 in
+    another summation order.  Sizes cross the kernels' row, channel, time and
+    eigenvector tiles with ragged ends."""
+    m = meshgen.icosphere(3) if domain == 0 else meshgen.two_spheres(2, 0.5, 1.5)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32, domain=domain,
+                                                          killing_walks=4096 if domain else 0))
+    ev, X, st = mcs.steklov_modes(res["Lambda"], rows["area"], k)
+    assert st["status"] == 0
+    n = m.nv
+    g = torch.Generator().manual_seed(k + c)
+    u0 = torch.randn(n, c, generator=g, dtype=torch.float64).cuda()
+    times = np.geomspace(1e-3, 5.0, nt)
+    u = mcs.steklov_heat(ev, X, rows["area"], u0, times).cpu().numpy()
+    h = mcs.hks(ev, X, times).cpu().numpy()
+    evh, Xh, mh = ev.cpu().numpy(), X.cpu().numpy(), rows["area"].cpu().numpy()
+    ur = oracle.steklov_heat(evh, Xh, mh, u0.cpu().numpy(), times)
+    hr = oracle.hks(evh, Xh, times)
+    assert u.shape == ur.shape and h.shape == hr.shape
+    assert np.abs(u - ur).max() <= 1e-12 * np.abs(ur).max()
+    assert np.abs(h - hr).max() <= 1e-12 * np.abs(hr).max()
+    # fixed summation order: a second call is bitwise identical
+    assert torch.equal(mcs.steklov_heat(ev, X, rows["area"], u0, times), torch.from_numpy(u).cuda())
+
+
+def test_interior_steklov_heat_conserves_total_heat():
+    """The interior spectrum's first mode is the constant (lambda ~ 0): total
+    heat sum_x m_x u_t(x) of a unit impulse stays m_x0, up to the computed
+    lambda_0 (zero to the solver's accuracy, ~1e-5 of the spectral bound) and
+    the constant mode's own accuracy."""
+    m = meshgen.icosphere(3)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32))
+    ev, X, st = mcs.steklov_modes(res["Lambda"], rows["area"], 16)
+    u0 = torch.zeros(m.nv, dtype=torch.float64, device="cuda")
+    u0[11] = 1.0
+    times = np.array([0.01, 0.5, 5.0])
+    u = mcs.steklov_heat(ev, X, rows["area"], u0, times)
+    tot = (u * rows["area"][None, :]).sum(1).cpu().numpy()
+    m0 = float(rows["area"][11])
+    lam0 = abs(float(ev[0]))
+    assert lam0 < 1e-5 * st["upper_bound"]
+    assert np.all(np.abs(tot - m0) <= m0 * (lam0 * times + 1e-3)), (tot, m0, lam0)

@@ -526,3 +526,60 @@ def test_exterior_killing_mass_of_two_spheres_is_their_capacitance(oracle, two_s
     assert abs(k.sum() / ref - 1) < 0.03, k.sum() / ref
     a = rows["pos"][:, 0] < 0.75
     assert abs(k[a].sum() / k.sum() - 0.5) < 0.03
+
+
+def _dtn_like(n, seed):
+    """A symmetric Lambda with zero row sums and non-negative off-diagonal
+    weights (the assembled form), positive lumped masses."""
+    rng = np.random.default_rng(seed)
+    W = rng.random((n, n)) * (rng.random((n, n)) < 0.3)
+    W = 0.5 * (W + W.T)
+    np.fill_diagonal(W, 0.0)
+    L = np.diag(W.sum(1)) - W
+    mass = 0.5 + rng.random(n)
+    return L, mass
+
+
+def test_steklov_heat_equals_the_matrix_exponential(oracle):
+    """Eq. steklovHeat, du/dt = -Lambda u in the M inner product: with the
+    full generalized eigenbasis the spectral sum of Eq. spectralSteklovHeat
+    equals expm(-t M^-1 Lambda) u0 (scipy's Pade exponential)."""
+    from scipy.linalg import eigh, expm
+    n = 40
+    L, mass = _dtn_like(n, 3)
+    ev, psi = eigh(L, np.diag(mass))
+    u0 = np.random.default_rng(4).standard_normal((n, 3))
+    times = [0.0, 0.05, 0.7, 3.0]
+    got = oracle.steklov_heat(ev, psi, mass, u0, times)
+    for i, t in enumerate(times):
+        ref = expm(-t * (L / mass[:, None])) @ u0
+        assert np.abs(got[i] - ref).max() < 1e-10 * max(1.0, np.abs(ref).max()), t
+
+
+def test_steklov_heat_conserves_total_heat_with_the_constant_mode(oracle):
+    """Interior Lambda annihilates constants, so the constant is the lambda = 0
+    mode; every other mode is M-orthogonal to it, so sum_x m_x u_t(x) stays
+    sum_x m_x u0(x) for any truncation that keeps the constant mode."""
+    from scipy.linalg import eigh
+    n = 50
+    L, mass = _dtn_like(n, 5)
+    ev, psi = eigh(L, np.diag(mass))
+    u0 = np.zeros(n)
+    u0[7] = 1.0  # a unit impulse at one node
+    for k in (1, 5, 20):
+        u = oracle.steklov_heat(ev[:k], psi[:, :k], mass, u0, [0.1, 1.0, 10.0])
+        assert np.allclose(u @ mass, mass[7], rtol=1e-12, atol=0), k
+
+
+def test_hks_diagonal_and_trace(oracle):
+    """With the complete M-orthonormal basis, sum_j psi_j(x)^2 = 1/m_x (the
+    diagonal of M^-1), so HKS(x, 0) = 1/m_x; and sum_x m_x HKS(x, t) is the heat
+    trace sum_j exp(-lambda_j t)."""
+    from scipy.linalg import eigh
+    n = 30
+    L, mass = _dtn_like(n, 6)
+    ev, psi = eigh(L, np.diag(mass))
+    h = oracle.hks(ev, psi, [0.0, 0.3, 2.0])
+    assert np.allclose(h[0], 1.0 / mass, rtol=1e-10)
+    for i, t in enumerate([0.0, 0.3, 2.0]):
+        assert np.isclose(h[i] @ mass, np.exp(-ev * t).sum(), rtol=1e-10)
