@@ -240,6 +240,36 @@ def _downstream(mcs, out, dev, reps=5):
                     "(B300's nominal FP64 rate) rather than HBM"}
 
 
+def _galerkin(mcs, V, F, params, ws, kill, k):
+    """Untimed by the headline: the Galerkin estimator on the same walks
+    (exit barycentrics recorded), K = k + 32 cotangent-Laplacian modes as the
+    basis; each phase timed with CUDA events after one warm-up."""
+    import torch
+    mesh = mcs.Mesh(V, F)
+    vrows = mcs.vertex_rows(mesh)
+    res = mcs.estimate_dtn(mesh, vrows, params, assemble=False, record_exits=True, record_bary=True, workspace=ws)
+    K = k + 32
+    gws = mcs.Workspace()
+
+    def clock(fn, reps=3):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            r = fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps, r
+
+    basis_ms, (_, Phi, est) = clock(lambda: mcs.steklov_modes(mcs.cotan_laplacian(mesh), vrows["area"], K), 1)
+    gal_ms, S = clock(lambda: mcs.galerkin_dtn(mesh, vrows, res, Phi, exterior=True, killing_walks=kill, workspace=gws))
+    modes_ms, (ev, _, _) = clock(lambda: mcs.galerkin_modes(S, k))
+    walks = int(res["exit_tri"].numel())
+    return {"K": K, "basis_ms": basis_ms, "galerkin_dtn_ms": gal_ms, "modes_ms": modes_ms,
+            "walks": walks, "walks_per_s": walks / (gal_ms / 1e3), "basis_status": est["status"],
+            "evals_head": [round(float(x), 4) for x in ev[:8].cpu()]}
+
+
 def run_ours(args, rank, world):
     """One mesh per step: the default two-sphere exterior workload or wild_2m."""
     import torch
@@ -352,6 +382,8 @@ def run_ours(args, rank, world):
     phase = np.mean([s["phase_ms"] for s in stats], axis=0).tolist()
     walks = n_rows * W + kill
     downstream = _downstream(mcs, step(V_d, F_d, keep=True), dev)
+    if not wild:
+        downstream["galerkin"] = _galerkin(mcs, V_d, F_d, params, ws, kill, args.k)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

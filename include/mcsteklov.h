@@ -121,6 +121,9 @@ typedef struct {
     int32_t *H0;            /* n_rows, or NULL                                  */
     int32_t *exit_tri;      /* optional debug: n_rows * W exit triangle per walk (-1 discarded) */
     float *Lambda32;        /* optional: n_rows * n_rows FP32 copy of Lambda (needs Lambda) */
+    double *exit_bary;      /* optional: n_rows * W * 3 barycentrics of each walk's exit point
+                               on its exit triangle (F order of the vertices; 0 for a discarded
+                               row or a walk without a hit); the input of the Galerkin estimator */
 } mcs_outputs;
 
 typedef struct {
@@ -369,6 +372,48 @@ size_t mcs_steklov_workspace_size(int n, int k);
 mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, int k, double *evals, double *evecs,
                              void *workspace, size_t workspace_bytes, const mcs_eig_params *params,
                              mcs_eig_stats *stats, void *stream);
+/* Galerkin estimator (Sec. 4.4, mesh-based Galerkin basis; boxed
+ * estimators Eq. main-estimator and Eq. main-exterior-estimator with
+ * d(s,t) = b(s) - b(t), b evaluated by barycentric interpolation).
+ *
+ * mcs_cotan_laplacian: the dense cotangent Laplacian of the mesh, L[a][b] =
+ * -(cot alpha + cot beta)/2 over the faces sharing edge (a, b), L[a][a] = -sum
+ * of the row; device nv x nv FP64 row-major (overwritten).  Its smallest
+ * generalized eigenpairs with the lumped vertex areas (mcs_steklov_modes with
+ * mass = the vertex-row areas) are the paper's default basis Phi.
+ *
+ * mcs_galerkin_dtn: S = Phi^T Lambda_bary Phi (device K x K FP64), where
+ * Lambda_bary = sum over recorded walks of w (e_s - beta_t)(e_s - beta_t)^T:
+ * e_s the row point's nodal coefficients (vertex rows: its vertex; sample
+ * rows: row_face[v]'s vertices, 1/3 each), beta_t the exit barycentrics on the
+ * exit triangle, w = omega_v / (2 W) (the boxed estimators' factor 1/2)
+ * times |t - o| at the hit point t for an
+ * exterior estimate (o = origin, host 3 doubles).  Inputs from an estimate
+ * with exit_tri and exit_bary recorded (mcs_outputs): omega n_rows, exit_tri
+ * and exit_bary n_rows x W (x 3).  Killing walks (exterior, H0 with
+ * killing_walks > 0, optional) enter lumped at their bin: 4 pi |p - o| H0 /
+ * N0.  Phi: device nv x K FP64 row-major, M-orthonormal; K a multiple of 16
+ * in [16, 160]; nv >= 16.  Lambda_bary: optional device nv x nv output, else
+ * held in the workspace (own_lambda = 1 in the size query).  Lambda_bary is
+ * assembled with FP64 atomics (reproducible to rounding); Lambda_bary Phi
+ * runs on the tensor cores (split tf32, FP32-level accuracy).  Synchronises
+ * `stream`.
+ *
+ * mcs_galerkin_modes: eigenpairs of the symmetric K x K matrix S (with Phi
+ * M-orthonormal, the Galerkin Steklov problem S c = lambda c), cyclic Jacobi
+ * in FP64: evals device K (ascending), coeffs device K x K (eigenvectors in
+ * columns), psi optional device n x k = Phi coeffs[:, :k] (the Steklov modes
+ * on the vertices).  2 <= K <= 160.  Asynchronous on `stream`. */
+mcs_status mcs_cotan_laplacian(mcs_mesh m, double *L, void *stream);
+size_t mcs_galerkin_workspace_size(mcs_mesh m, int K, int own_lambda);
+mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row_face, const double *omega,
+                            const int32_t *exit_tri, const double *exit_bary, int walks_per_row, int exterior,
+                            const double *origin, const int32_t *H0, long long killing_walks, const double *Phi,
+                            int K, double *S, double *Lambda_bary, void *workspace, size_t workspace_bytes,
+                            void *stream);
+mcs_status mcs_galerkin_modes(const double *S, int K, int k, const double *Phi, int n, double *evals, double *coeffs,
+                              double *psi, void *stream);
+
 /* Steklov heat (Sec. 5, Eq. steklovHeat, solved in the eigenbasis by Eq.
  * spectralSteklovHeat): for each time t and each channel column of u0,
  *   u_t = sum_j exp(-lambda_j t) a_j psi_j,  a_j = psi_j^T M u_0,

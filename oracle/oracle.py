@@ -347,6 +347,81 @@ def steklov(L: np.ndarray, mass: np.ndarray, k: int):
     return w[:k], (X[:, :k] * s[:, None])
 
 
+def cotan_laplacian(V, F) -> np.ndarray:
+    """Dense cotangent Laplacian: for each face and each edge (p, q) with
+    opposite corner c, w = cot(angle at c) / 2 is subtracted from L[p, q] and
+    L[q, p] and added to L[p, p] and L[q, q] (degenerate faces skipped)."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    n = V.shape[0]
+    L = np.zeros((n, n))
+    for f in F:
+        for i in range(3):
+            p, q, c = int(f[i]), int(f[(i + 1) % 3]), int(f[(i + 2) % 3])
+            u, w = V[p] - V[c], V[q] - V[c]
+            cr = np.linalg.norm(np.cross(u, w))
+            if not cr > 0:
+                continue
+            wgt = 0.5 * float(u @ w) / cr
+            L[p, q] -= wgt
+            L[q, p] -= wgt
+            L[p, p] += wgt
+            L[q, q] += wgt
+    return L
+
+
+def galerkin_lambda(V, F, est: dict, rows, exterior: bool = False, origin=None, row_face=None,
+                    killing: bool = False) -> np.ndarray:
+    """Hat-basis Galerkin stiffness of the boxed estimators with barycentric
+    basis evaluation (Sec. 4.4): sum over walks of w (e_s - beta_t)(e_s - beta_t)^T,
+    w = omega_v / (2 W) (the boxed estimators' factor 1/2; times |t - o| at the
+    exit point t for exterior walks);
+    e_s: the row's vertex, or 1/3 on each vertex of row_face[v] for sample
+    rows.  Killing walks (exterior, optional) lumped at their bin:
+    4 pi |p - o| H0 / N0 at the bin vertex (sample rows: 1/9 on each pair of
+    the row face's vertices, p the face centroid)."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    nv = V.shape[0]
+    W = est["walks"]
+    omega = row_weights(est, rows)
+    o = np.zeros(3) if origin is None else np.asarray(origin, np.float64)
+    L = np.zeros((nv, nv))
+    for li, v in enumerate(np.asarray(est["row_list"])):
+        tri = est["exit_tri"][li]
+        ok = tri >= 0
+        if not ok.any() or omega[li] == 0:
+            continue
+        tv = F[tri[ok]]                      # walks x 3 exit vertices
+        beta = est["exit_bary"][li][ok]      # walks x 3
+        w = np.full(tv.shape[0], 0.5 * omega[li] / W)
+        if exterior:
+            t = np.einsum("wi,wik->wk", beta, V[tv])
+            w = w * np.linalg.norm(t - o, axis=1)
+        if row_face is None:
+            sidx, sval = np.array([v]), np.array([1.0])
+        else:
+            sidx, sval = np.asarray(F[row_face[v]]), np.full(3, 1.0 / 3.0)
+        idx = np.concatenate([np.broadcast_to(sidx, (tv.shape[0], sidx.size)), tv], axis=1)
+        val = np.concatenate([np.broadcast_to(sval, (tv.shape[0], sval.size)), -beta], axis=1)
+        for a in range(idx.shape[1]):
+            for b in range(idx.shape[1]):
+                np.add.at(L, (idx[:, a], idx[:, b]), w * val[:, a] * val[:, b])
+    if exterior and killing and est["killing_walks"] > 0:
+        N0 = est["killing_walks"]
+        for u in np.flatnonzero(est["H0"]):
+            if row_face is None:
+                L[u, u] += 4 * math.pi * np.linalg.norm(V[u] - o) * est["H0"][u] / N0
+            else:
+                fv = F[row_face[u]]
+                c = V[fv].mean(0)
+                x = 4 * math.pi * np.linalg.norm(c - o) * est["H0"][u] / N0 / 9.0
+                for a in fv:
+                    for b in fv:
+                        L[a, b] += x
+    return L
+
+
 def steklov_heat(evals, evecs, mass, u0, times) -> np.ndarray:
     """Steklov heat (Sec. 5, Eq. spectralSteklovHeat): for each t,
     u_t = sum_j exp(-lambda_j t) a_j psi_j with a_j = <u0, psi_j>_M.

@@ -45,7 +45,7 @@ class Rows(C.Structure):
 class Outputs(C.Structure):
     _fields_ = [("hist_bin", C.c_void_p), ("hist_cnt", C.c_void_p), ("hist_nnz", C.c_void_p),
                 ("Lambda", C.c_void_p), ("omega", C.c_void_p), ("H0", C.c_void_p), ("exit_tri", C.c_void_p),
-                ("Lambda32", C.c_void_p)]
+                ("Lambda32", C.c_void_p), ("exit_bary", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -134,6 +134,12 @@ def lib():
         L.mcs_steklov_workspace_size.restype = C.c_size_t
         L.mcs_steklov_modes.argtypes = [vp, vp, i32, i32, vp, vp, vp, C.c_size_t, C.POINTER(EigParams),
                                         C.POINTER(EigStats), vp]
+        L.mcs_cotan_laplacian.argtypes = [vp, vp, vp]
+        L.mcs_galerkin_workspace_size.argtypes = [vp, i32, i32]
+        L.mcs_galerkin_workspace_size.restype = C.c_size_t
+        L.mcs_galerkin_dtn.argtypes = [vp, C.POINTER(Rows), vp, vp, vp, vp, i32, i32, C.POINTER(C.c_double), vp, i64,
+                                       vp, i32, vp, vp, vp, C.c_size_t, vp]
+        L.mcs_galerkin_modes.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp]
         L.mcs_steklov_heat_workspace_size.argtypes = [i32, i32, i32]
         L.mcs_steklov_heat_workspace_size.restype = C.c_size_t
         L.mcs_steklov_heat.argtypes = [vp, vp, vp, i32, i32, vp, i32, vp, i32, vp, vp, C.c_size_t, vp]
@@ -295,10 +301,11 @@ def _aligned_ptr(buf: torch.Tensor) -> int:
     return (p + 255) & ~255
 
 
-_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri", "Lambda32")
+_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri", "Lambda32", "exit_bary")
 
 
-def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32_copy: bool = False) -> dict:
+def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32_copy: bool = False,
+                   record_bary: bool = False) -> dict:
     cap = min(W, R)
     return dict(hist_bin=torch.empty(R * cap, dtype=torch.int32, device=dev),
                 hist_cnt=torch.empty(R * cap, dtype=torch.int32, device=dev),
@@ -307,7 +314,8 @@ def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32
                 H0=torch.empty(R, dtype=torch.int32, device=dev),
                 Lambda=torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None,
                 exit_tri=torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None,
-                Lambda32=torch.empty((R, R), dtype=torch.float32, device=dev) if (assemble and fp32_copy) else None)
+                Lambda32=torch.empty((R, R), dtype=torch.float32, device=dev) if (assemble and fp32_copy) else None,
+                exit_bary=torch.empty((R, W, 3), dtype=torch.float64, device=dev) if record_bary else None)
 
 
 def _rows_struct(rows: dict) -> Rows:
@@ -326,13 +334,14 @@ def _stats_dict(st: Stats) -> dict:
 
 def estimate_dtn(mesh: Mesh, rows: dict, params: Params, assemble: bool = True, want_stats: bool = True,
                  record_exits: bool = False, workspace: Workspace | None = None, outputs: dict | None = None,
-                 fp32_copy: bool = False):
-    """Run the DtN estimator; returns a dict of device tensors (+ stats)."""
+                 fp32_copy: bool = False, record_bary: bool = False):
+    """Run the DtN estimator; returns a dict of device tensors (+ stats).
+    record_exits / record_bary: also each walk's exit triangle / exit barycentrics."""
     pos = rows["pos"]
     R = int(pos.shape[0])
     W = int(params.walks_per_row)
     cap = min(W, R)
-    o = outputs or _alloc_outputs(R, W, pos.device, assemble, record_exits, fp32_copy)
+    o = outputs or _alloc_outputs(R, W, pos.device, assemble, record_exits, fp32_copy, record_bary)
     rs = _rows_struct(rows)
     out = _outputs_struct(o)
     nbytes = workspace_size(mesh, R, W, params.killing_walks)
@@ -513,6 +522,55 @@ def steklov_modes(Lambda: torch.Tensor, mass: torch.Tensor, k: int, params: EigP
     stats = {f: getattr(st, f) for f, _ in EigStats._fields_}
     stats["status"] = status
     return ev, X, stats
+
+
+def cotan_laplacian(mesh: Mesh) -> torch.Tensor:
+    """Dense cotangent Laplacian of the mesh (nv x nv FP64, device)."""
+    L = torch.empty((mesh.nv, mesh.nv), dtype=torch.float64, device="cuda")
+    _check(lib().mcs_cotan_laplacian(mesh.handle, _ptr(L), _stream()))
+    return L
+
+
+def galerkin_dtn(mesh: Mesh, rows: dict, res: dict, Phi: torch.Tensor, exterior: bool = False,
+                 killing_walks: int = 0, want_lambda: bool = False, workspace: "Workspace | None" = None):
+    """Galerkin estimate S = Phi^T Lambda_bary Phi (K x K) from an estimate
+    recorded with record_exits and record_bary; rows as given to that
+    estimate (sample rows: their "sel" faces are the row points' faces).
+    Returns S, or (S, Lambda_bary) with want_lambda."""
+    P = Phi.to(torch.float64).contiguous()
+    K = int(P.shape[1])
+    S = torch.empty((K, K), dtype=torch.float64, device=P.device)
+    Lb = torch.empty((mesh.nv, mesh.nv), dtype=torch.float64, device=P.device) if want_lambda else None
+    rs = _rows_struct(rows)
+    sel = rows.get("sel") if rows.get("tri2bin") is not None else None
+    origin = (C.c_double * 3)(*res["stats"]["origin"])
+    nb = int(lib().mcs_galerkin_workspace_size(mesh.handle, K, 0 if want_lambda else 1))
+    if nb == 0:
+        raise MCSError("galerkin_dtn: K must be a multiple of 16 in [16, 160]")
+    ws = (workspace or Workspace()).get(nb)
+    H0 = res.get("H0") if (exterior and killing_walks > 0) else None
+    _check(lib().mcs_galerkin_dtn(mesh.handle, C.byref(rs), _ptr(sel), _ptr(res["omega"]), _ptr(res["exit_tri"]),
+                                  _ptr(res["exit_bary"]), int(res["walks"]), int(exterior), origin, _ptr(H0),
+                                  int(killing_walks), _ptr(P), K, _ptr(S), _ptr(Lb), C.c_void_p(_aligned_ptr(ws)), nb,
+                                  _stream()))
+    return (S, Lb) if want_lambda else S
+
+
+def galerkin_modes(S: torch.Tensor, k: int, Phi: "torch.Tensor | None" = None):
+    """Eigenpairs of the K x K Galerkin matrix: (evals K ascending, coeffs K x K,
+    psi = Phi coeffs[:, :k] or None)."""
+    S = S.to(torch.float64).contiguous()
+    K = int(S.shape[0])
+    ev = torch.empty(K, dtype=torch.float64, device=S.device)
+    Cm = torch.empty((K, K), dtype=torch.float64, device=S.device)
+    psi = None
+    n = 0
+    if Phi is not None:
+        Phi = Phi.to(torch.float64).contiguous()
+        n = int(Phi.shape[0])
+        psi = torch.empty((n, k), dtype=torch.float64, device=S.device)
+    _check(lib().mcs_galerkin_modes(_ptr(S), K, k, _ptr(Phi), n, _ptr(ev), _ptr(Cm), _ptr(psi), _stream()))
+    return ev, Cm, psi
 
 
 def steklov_heat(evals: torch.Tensor, evecs: torch.Tensor, mass: torch.Tensor, u0: torch.Tensor,

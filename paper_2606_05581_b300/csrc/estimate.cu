@@ -436,6 +436,7 @@ struct WalkJob {
     const int32_t *tri2bin;
     int32_t *exits;        // R x W, by sorted row position
     int32_t *exit_tri;     // optional, R x W by canonical row
+    double *exit_bary;     // optional, R x W x 3 by canonical row: barycentrics of the exit point
     int32_t *H0;           // killing histogram
     Ctrl *ctrl;            // the mesh's control block (origin, Kelvin frame)
     unsigned long long n_rows_walks;  // R * W
@@ -565,7 +566,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         s.k++;
     };
 
-    auto finish = [&](const WalkJob &J, int bin, int f, bool capped, bool lost) {
+    auto finish = [&](const WalkJob &J, int bin, int f, bool capped, bool lost, double b0 = 0.0, double b1 = 0.0,
+                      double b2 = 0.0) {
         active = false;
         if (!writer) return;
         if (s.kill) n_kcapped += capped; else n_capped += capped;
@@ -577,6 +579,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
             const int rp = (int)(s.li / (unsigned long long)J.W) * J.row_stride, j = (int)(s.li % (unsigned long long)J.W);
             J.exits[(size_t)rp * J.W + j] = bin;
             if (J.exit_tri) J.exit_tri[(size_t)s.v * J.W + j] = f;
+            if (J.exit_bary) {
+                double *eb = J.exit_bary + ((size_t)s.v * J.W + j) * 3;
+                eb[0] = b0; eb[1] = b1; eb[2] = b2;
+            }
         }
     };
 
@@ -627,6 +633,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                         if (!b.valid) {
                             J.exits[(size_t)rp * J.W + j] = -1;
                             if (J.exit_tri) J.exit_tri[(size_t)v * J.W + j] = -1;
+                            if (J.exit_bary) {
+                                double *eb = J.exit_bary + ((size_t)v * J.W + j) * 3;
+                                eb[0] = eb[1] = eb[2] = 0.0;
+                            }
                         } else {
                             s.g = (unsigned long long)v * (unsigned long long)J.W + (unsigned long long)j;
                             const unsigned long long gp = s.g - (unsigned long long)(j & 1);
@@ -688,13 +698,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         if (!ext) {
             if (d < epsT || s.k == a.max_steps) {
                 if (sizeof(T) == 8) {
-                    finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false);
+                    finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false,
+                           (double)h.b0, (double)h.b1, (double)h.b2);
                     continue;
                 }
                 double b[3];
                 const double d64 = sqrt(recheck64(J.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
                 if (d64 < a.eps || s.k == a.max_steps) {
-                    finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false);
+                    finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false, b[0], b[1], b[2]);
                     continue;
                 }
             }
@@ -713,7 +724,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         const T rho = ri > r0 ? ri : r0;
         if (rho < epsT || s.k == a.max_steps) {
             if (sizeof(T) == 8) {
-                finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false);
+                finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false,
+                       (double)h.b0, (double)h.b1, (double)h.b2);
                 continue;
             }
             const double o64[3] = {J.ctrl->origin[0], J.ctrl->origin[1], J.ctrl->origin[2]};
@@ -728,7 +740,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
             const double r0d = r0max64 - sqrt(r2d);
             const double rhod = rid > r0d ? rid : r0d;
             if (rhod < a.eps || s.k == a.max_steps) {
-                finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false);
+                finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false, b[0], b[1], b[2]);
                 continue;
             }
         }
@@ -1272,6 +1284,7 @@ static WalkJob make_job(const Plan &pl, unsigned long long n_row_walks, unsigned
     J.tri2bin = pl.rows.tri2bin;
     J.exits = pl.exits();
     J.exit_tri = pl.out.exit_tri;
+    J.exit_bary = pl.out.exit_bary;
     J.H0 = pl.H0();
     J.ctrl = pl.ctrl;
     J.n_rows_walks = n_row_walks;

@@ -583,3 +583,85 @@ def test_hks_diagonal_and_trace(oracle):
     assert np.allclose(h[0], 1.0 / mass, rtol=1e-10)
     for i, t in enumerate([0.0, 0.3, 2.0]):
         assert np.isclose(h[i] @ mass, np.exp(-ev * t).sum(), rtol=1e-10)
+
+
+def test_cotan_laplacian_properties(oracle):
+    """The cotangent Laplacian is symmetric with zero row sums; it is exact on
+    linear functions at interior vertices of a planar mesh (linear
+    precision); on the unit icosphere its smallest generalized eigenvalues
+    with lumped vertex areas approach l(l+1) = 0, 2 (x3), 6 (x5)."""
+    from scipy.linalg import eigh
+    # planar: a jittered 9 x 9 grid of the unit square, two triangles per cell
+    rng = np.random.default_rng(2)
+    g = 9
+    xs, ys = np.meshgrid(np.linspace(0, 1, g), np.linspace(0, 1, g), indexing="ij")
+    P = np.stack([xs.ravel(), ys.ravel(), np.zeros(g * g)], 1)
+    inner = (xs.ravel() > 0) & (xs.ravel() < 1) & (ys.ravel() > 0) & (ys.ravel() < 1)
+    P[inner, :2] += 0.02 * rng.standard_normal((inner.sum(), 2))
+    idx = np.arange(g * g).reshape(g, g)
+    F = []
+    for i in range(g - 1):
+        for j in range(g - 1):
+            a, b, c, d = idx[i, j], idx[i + 1, j], idx[i + 1, j + 1], idx[i, j + 1]
+            F += [[a, b, c], [a, c, d]]
+    L = oracle.cotan_laplacian(P, np.array(F))
+    assert np.allclose(L, L.T, atol=1e-14) and np.allclose(L.sum(1), 0, atol=1e-12)
+    for f in (P[:, 0], P[:, 1], 2 * P[:, 0] - 3 * P[:, 1] + 0.5):
+        assert np.abs((L @ f)[inner]).max() < 1e-12
+    m = meshgen.icosphere(3)
+    rows = oracle.vertex_rows(m.V, m.F)
+    mu = eigh(oracle.cotan_laplacian(m.V, m.F), np.diag(rows["area"]), eigvals_only=True)[:9]
+    ref = np.array([0, 2, 2, 2, 6, 6, 6, 6, 6.0])
+    assert abs(mu[0]) < 1e-10 and np.abs(mu[1:] - ref[1:]).max() < 0.03 * 6
+
+
+def test_galerkin_quadratic_form_of_linear_functions(oracle):
+    """Barycentric interpolation reproduces linear functions exactly, so for a
+    linear f the hat-basis Galerkin form f^T Lambda_bary f equals the jump
+    form sum_walks w (f(s) - f(t))^2 summed over the exit points t in space
+    (Sec. 4.4 with the boxed estimators), for vertex and sample rows, interior
+    and exterior; on the unit sphere it approaches the cap-corrected l = 1
+    value (Funk-Hecke) for f = z.  With one-hot barycentrics at the bin
+    vertex the Galerkin matrix is exactly the nodal Lambda (symmetrised
+    histogram assembly)."""
+    R = 1.0
+    m = meshgen.icosphere(2, R)
+    lam = oracle.sphere_eigs_cap(1, 2.5, R)
+    for kind in ("vertex", "sample"):
+        rows = oracle.vertex_rows(m.V, m.F) if kind == "vertex" else oracle.fps_rows(m.V, m.F, m.nf, orient=False)
+        rf = None if kind == "vertex" else rows["sel"]
+        for ext in (False, True):
+            o = np.zeros(3)
+            est = oracle.estimate(m.V, m.F, rows, 64, 1e-3, exterior=ext, origin=o, seed=2, record_exits=True)
+            L = oracle.galerkin_lambda(m.V, m.F, est, rows, exterior=ext, origin=o, row_face=rf)
+            W = est["walks"]
+            omega = oracle.row_weights(est, rows)
+            P = oracle.exit_points(m.V, m.F, est["exit_tri"], est["exit_bary"])
+            ok = est["exit_tri"] >= 0
+            for f3 in (np.array([0, 0, 1.0]), np.array([0.3, -1.0, 0.2])):
+                f = m.V @ f3
+                fs = rows["pos"] @ f3
+                ft = P @ f3
+                w = np.where(ok, 0.5 * omega[:, None] / W, 0.0)
+                if ext:
+                    w = w * np.linalg.norm(P - o, axis=-1)
+                E = float(np.sum(w * (fs[:, None] - ft) ** 2))
+                assert abs(f @ L @ f - E) <= 1e-10 * E, (kind, ext)
+            if kind == "vertex":
+                est1 = dict(est)
+                eb = np.zeros_like(est["exit_bary"])
+                tri = np.maximum(est["exit_tri"], 0)
+                vb = m.F[tri]                                   # R x W x 3
+                # the bin is the vertex with the largest barycentric (ties -> lower vertex id)
+                best = est["exit_bary"].max(-1, keepdims=True)
+                cand = np.where(est["exit_bary"] == best, vb, np.iinfo(np.int32).max)
+                binv = cand.min(-1)
+                eb[vb == binv[..., None]] = 1.0
+                est1["exit_bary"] = eb
+                L1 = oracle.galerkin_lambda(m.V, m.F, est1, rows, exterior=ext, origin=o)
+                Ln = oracle.assemble(est, rows, exterior=ext, origin=o)
+                assert np.abs(L1 - Ln).max() <= 1e-12 * np.abs(Ln).max(), (kind, ext)
+            if not ext and kind == "sample":
+                f = m.V[:, 2]
+                Mf = np.sum(rows["area"] * rows["pos"][:, 2] ** 2)
+                assert abs((f @ L @ f) / Mf - lam[1]) < 0.12 * lam[1]
