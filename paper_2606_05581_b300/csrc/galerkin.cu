@@ -158,10 +158,12 @@ __global__ void k_project_S(const double *Zt, const double *Phi, int n, int K, d
 }
 
 // cyclic Jacobi on a K x K symmetric matrix in FP64, one block: A (rows
-// padded to K + 1) in shared memory, the rotations accumulated in C (K x K
-// row-major, global).  Eigenvalues ascending into ev (K), eigenvectors in the
+// padded to K + 1) in shared memory, the rotations accumulated transposed in
+// C (Qt[p][row], so a rotation of columns p, q touches contiguous rows of
+// Qt), transposed back at the end.  Eigenvalues ascending into ev (K), eigenvectors in the
 // columns of C in the same order.  Stops when the off-diagonal mass is below
-// 1e-28 of the total or after max_sweeps.
+// 1e-24 of the total (off-diagonal norm 1e-12 relative: eigenvalue errors of
+// order its square over the gaps) or after max_sweeps.
 constexpr int kJacThreads = 256;
 __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K, int max_sweeps, double *ev,
                                                           double *C) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
         const int r = e / K, c = e % K;
         A[r * ld + c] = 0.5 * (S[(size_t)r * K + c] + S[(size_t)c * K + r]);
-        Q[(size_t)r * K + c] = r == c ? 1.0 : 0.0;
+        Q[(size_t)c * K + r] = r == c ? 1.0 : 0.0;
     }
     __syncthreads();
     const int half = Ke / 2;
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
         if (threadIdx.x == 0) {
             double so = 0.0, st = 0.0;
             for (int w = 0; w < kJacThreads / 32; w++) { so += red_o[w]; st += red_t[w]; }
-            stop = !(so > 1e-28 * st);
+            stop = !(so > 1e-24 * st);
         }
         __syncthreads();
         if (stop) break;
@@ -234,9 +236,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
                 const double ap = A[row * ld + p], aq = A[row * ld + q];
                 A[row * ld + p] = c * ap - s * aq;
                 A[row * ld + q] = s * ap + c * aq;
-                const double qp = Q[(size_t)row * K + p], qv = Q[(size_t)row * K + q];
-                Q[(size_t)row * K + p] = c * qp - s * qv;
-                Q[(size_t)row * K + q] = s * qp + c * qv;
+                const double qp = Q[(size_t)p * K + row], qv = Q[(size_t)q * K + row];
+                Q[(size_t)p * K + row] = c * qp - s * qv;
+                Q[(size_t)q * K + row] = s * qp + c * qv;
             }
             __syncthreads();
             // rows p, q of A
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
     for (int i = threadIdx.x; i < K; i += blockDim.x) ev[i] = dg[order[i]];
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
         const int r = e / K, c = e % K;
-        C[(size_t)r * K + c] = A[(size_t)r * K + order[c]];
+        C[(size_t)r * K + c] = A[(size_t)order[c] * K + r];  // A holds Qt here
     }
 }
 
