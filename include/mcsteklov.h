@@ -186,12 +186,14 @@ mcs_status mcs_vertex_rows(mcs_mesh m, double *pos, double *nrm, double *area, v
  * the total area of the faces it owns; its normal is the unit normal of the
  * sampled face, oriented (orient != 0) by the generalized winding number of
  * the other faces at x -/+ delta n, delta = sqrt(face area)/4 (App. A item 1):
- * the normal is kept when GWN(x - delta n) > GWN(x + delta n).  orient 1
+ * the normal is kept when GWN(x - delta n) > GWN(x + delta n).  orient 3
  * sums the solid angles over the BVH, far nodes by their dipole term with a
  * certified bound on the remainder and on the float rounding; a row whose
  * gap does not exceed its bound is summed by brute force, so the decision is
  * the sign of the exact sum over the float-rounded triangles either way.
- * orient 2 sums every row by brute force (FP32).
+ * orient 2 sums every row by brute force (FP32).  orient 1 takes orient 3
+ * when faces x rows >= 2^28 and orient 2 below (where the extra launches of
+ * the hierarchical pass cost more than the brute-force sums).
  * Device outputs: sel n, pos n x 3, nrm n x 3, area n, tri2bin nf,
  * orient_gap n (optional: GWN(x - delta n) - GWN(x + delta n), within the
  * row's bound for rows decided by the hierarchical sum).  The

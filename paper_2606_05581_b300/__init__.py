@@ -226,8 +226,9 @@ def vertex_rows(mesh: Mesh):
 
 def sample_rows(mesh: Mesh, n: int, orient: "bool | int" = True, workspace: "Workspace | None" = None):
     """Farthest-point sample rows with Voronoi areas and oriented face normals
-    (orient: 0 none, 1 / True hierarchical winding numbers with brute force
-    where the certified bound does not decide, 2 brute force for every row)."""
+    (orient: 0 none; 3 hierarchical winding numbers with brute force where the
+    certified bound does not decide; 2 brute force for every row; 1 / True
+    the first for faces x rows >= 2^28, else the second)."""
     dev = torch.device("cuda")
     sel = torch.empty(n, dtype=torch.int32, device=dev)
     pos = torch.empty((n, 3), dtype=torch.float64, device=dev)

@@ -552,6 +552,7 @@ struct __align__(16) GwnAgg {
     float4 cr;  // C.x C.y C.z r
 };
 constexpr float kGwnTheta = 0.1f;
+constexpr double kGwnTreeMin = 268435456.0;  // 2^28 face-row pairs (~2 ms of brute force)
 constexpr int kGwnWarps = 4;
 constexpr int kGwnStack = 2048;  // frontier entries per warp (shared memory; ~32 x tree depth)
 constexpr float kGwnUlp = 5.9604645e-08f;  // 2^-24
@@ -989,13 +990,15 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
     k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, it.sel, svals, start, n, it.pos, it.nrm,
                                                     it.area);
     if (orient) {
-        // orient 1: hierarchical sums, brute force for the rows within their
-        // bound; orient 2: brute force for every row
+        // orient 3: hierarchical sums, brute force for the rows within their
+        // bound; orient 2: brute force for every row; orient 1: the first
+        // when faces x rows reach kGwnTreeMin, else the second (small meshes
+        // pay more for the extra launches than for the brute-force sums)
         float4 *q = (float4 *)(w + L.q);
         float *partial = (float *)(w + L.partial);
         float *gD = (float *)(w + L.gD), *gE = (float *)(w + L.gE);
         int *govf = (int *)(w + L.govf), *fb_list = (int *)(w + L.fb_list), *fb_count = (int *)(w + L.fb_count);
-        const bool tree = orient == 1 && nf >= 2;
+        const bool tree = nf >= 2 && (orient == 3 || (orient == 1 && (double)nf * n >= kGwnTreeMin));
         note_launch();
         k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, farea, it.sel, n, q);
         if (tree) {

@@ -203,12 +203,12 @@ def test_sample_rows_match_oracle(oracle):
 
 def test_hierarchical_orientation_equals_brute_force(oracle):
     """Sample-row orientation by the BVH sums with certified far-field bounds
-    (orient 1) against brute force on every row (orient 2) and the oracle's
+    (orient 3) against brute force on every row (orient 2) and the oracle's
     FP64 winding numbers: the same sampling, the same normal wherever the gap
     is not a near tie, gaps within the far-field tolerance."""
     m = meshgen.wild_union(10, 40000, seed=17)
     mesh = mcs.Mesh(m.V, m.F)
-    h = mcs.sample_rows(mesh, 1500, orient=1)
+    h = mcs.sample_rows(mesh, 1500, orient=3)
     b = mcs.sample_rows(mesh, 1500, orient=2)
     for k in ("sel", "tri2bin", "area", "pos"):
         assert torch.equal(h[k], b[k]), k
@@ -257,7 +257,7 @@ def test_brute_force_orientation_of_a_few_rows():
     chunks to fill the grid, with the same normals as the hierarchical pass."""
     m = meshgen.wild_union(6, 20000, seed=5)
     mesh = mcs.Mesh(m.V, m.F)
-    h = mcs.sample_rows(mesh, 5, orient=1)
+    h = mcs.sample_rows(mesh, 5, orient=3)
     b = mcs.sample_rows(mesh, 5, orient=2)
     gb = b["gap"].cpu().numpy()
     for i in range(5):
