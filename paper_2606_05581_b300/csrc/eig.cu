@@ -942,10 +942,12 @@ size_t mcs_tc_symm_product_workspace_size(int n, int m) {
 
 void mcs_default_eig_params(mcs_eig_params *p) {
     if (!p) return;
-    // degree 48: fewer FP64 orthogonalisations and Rayleigh-Ritz steps per
-    // converged block than 24 (measured, two-sphere exterior n = 5124, k = 64:
-    // degree 24 44 ms, 48 34 ms, 64 31 ms; 10,000-row union: 120, 78, 71 ms),
-    // while 64 stalled on a sphere's interior spectrum (n = 642, k = 64)
+    // degree 48 (measured, k = 64: two-sphere exterior n = 5124: degree 48
+    // 34.5 ms, 64 57.7 ms, 80 48.7 ms; 10,000-row union: 92.2, 90.5, 104 ms;
+    // icosphere s3 interior n = 642: 13.9, 25.1, 31.5 ms): higher degrees
+    // spread the wanted components over more magnitudes than the FP32-accurate
+    // products keep, stall, and pay for the halving; 24 needs more FP64
+    // orthogonalisations and Rayleigh-Ritz steps per converged block
     p->degree = 48;
     p->max_iters = 60;
     p->tol = 1e-5;
