@@ -51,7 +51,7 @@ OPS_PER_NODE = 36
 OPS_PER_TRI = 90
 
 
-WORKLOADS = ("two_spheres_s4_exterior", "wild_2m", "batch", "precision")
+WORKLOADS = ("two_spheres_s4_exterior", "wild_2m", "batch", "precision", "variance")
 
 
 def workload_config(args):
@@ -268,6 +268,54 @@ def _galerkin(mcs, V, F, params, ws, kill, k):
     return {"K": K, "basis_ms": basis_ms, "galerkin_dtn_ms": gal_ms, "modes_ms": modes_ms,
             "walks": walks, "walks_per_s": walks / (gal_ms / 1e3), "basis_status": est["status"],
             "evals_head": [round(float(x), 4) for x in ev[:8].cpu()]}
+
+
+def run_variance(args, rank, world):
+    """Variance study (Sec. 5, Fig. variance_comparison): the quadratic form of
+    f = z on the unit icosphere s3 (1280 face sample rows) by the importance-
+    sampled tangent ball (the estimator), the uniformly sampled tangent ball
+    (weighted walks) and the naive finite-difference estimator (Alg. 1,
+    h = 0.02), each over 8 x --seeds seeds at several walk counts; all on the GPU
+    (walks, exit barycentrics, Galerkin assembly).  value = the naive
+    estimator's variance over the importance sampler's at the largest N."""
+    import torch
+    import meshgen
+    import paper_2606_05581_b300 as mcs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    m = meshgen.icosphere(3)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.sample_rows(mesh, m.nf, orient=False)
+    f = torch.from_numpy(np.ascontiguousarray(m.V[:, 2])).cuda()
+    Phi = torch.zeros((m.nv, 16), dtype=torch.float64, device=dev)
+    Phi[:, 0] = f
+    Ws, seeds = (8, 32, 128), range(8 * args.seeds)
+    names = {0: "importance_ball", 1: "uniform_ball", 2: "naive_fd"}
+    table = {}
+    t0 = time.time()
+    for mode in (0, 1, 2):
+        for W in Ws:
+            vals = []
+            for sd in seeds:
+                p = mcs.default_params(walks_per_row=W, prec=32, seed=sd, eps=1e-4 if mode == 2 else 1e-3)
+                p.start_mode = mode
+                if mode == 2:
+                    p.inset = 0.02
+                res = mcs.estimate_dtn(mesh, rows, p, assemble=False, record_exits=True, record_bary=True)
+                _, Lb = mcs.galerkin_dtn(mesh, rows, res, Phi, want_lambda=True, start_mode=mode)
+                vals.append(float(f @ Lb @ f))
+            table.setdefault(names[mode], []).append(
+                {"walks_per_row": W, "samples": m.nf * W, "mean": float(np.mean(vals)),
+                 "variance": float(np.var(vals, ddof=1)), "variance_x_N": float(np.var(vals, ddof=1)) * m.nf * W})
+    wall = time.time() - t0
+    ratio = table["naive_fd"][-1]["variance"] / table["importance_ball"][-1]["variance"]
+    return {"metric": "variance ratio naive / importance-sampled tangent ball, quadratic form of z on the unit sphere",
+            "value": ratio, "unit": "x", "n_gpus": 1, "steps": len(Ws) * len(seeds) * 3, "warmup": 0,
+            "ms_per_step": wall * 1e3 / (len(Ws) * len(seeds) * 3), "higher_is_better": True, "scaling": "none",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "variance", "mesh": "unit icosphere s3", "rows": "1280 face sample rows",
+                       "seeds": len(seeds), "inset_h": 0.02, "exact_l1_form": 4 * math.pi / 3},
+            "table": table}
 
 
 def run_ours(args, rank, world):
@@ -760,7 +808,8 @@ def main():
     ap.add_argument("--workload", default="two_spheres_s4_exterior", choices=WORKLOADS)
     ap.add_argument("--walks", type=int, default=0, help="walks per row (0: the workload's)")
     ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
-    ap.add_argument("--seeds", type=int, default=4, help="precision workload: seeds per configuration")
+    ap.add_argument("--seeds", type=int, default=4,
+                    help="precision workload: seeds per configuration (variance workload: 8x as many)")
     ap.add_argument("--ref-walks", type=int, default=65536, help="precision workload: reference walks per row")
     ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
     ap.add_argument("--k", type=int, default=64)
@@ -781,6 +830,8 @@ def main():
         line = run_batch(args, rank, world)
     elif args.workload == "precision":
         line = run_precision(args, rank, world) if rank == 0 else None
+    elif args.workload == "variance":
+        line = run_variance(args, rank, world) if rank == 0 else None
     else:
         line = run_ours(args, rank, world)
     if line is not None:

@@ -91,6 +91,15 @@ typedef struct {
                                mcs_mesh_build_wide).  Same results either way. */
     int lanes_per_query;    /* with bvh_layout 4: 4 = a group of four lanes runs each walk,
                                lane r testing child r of each node; 0/1 = one lane per walk */
+    int start_mode;         /* start points of the walks (interior estimates without the
+                               nodal Lambda; for the variance comparison of Sec. 5):
+                               0 = importance-sampled tangent ball (the estimator),
+                               1 = cos(theta) uniform on the tangent ball outside the cap,
+                               each walk weighted by q = |dB outside the cap| J^B / M
+                               (outputs walk_w), 2 = the naive estimator (Alg. 1): one
+                               uniform walk-on-spheres step from s - inset n, no cap,
+                               row weight A_v / inset */
+    double inset;           /* start_mode 2: the inset distance h (> 0)             */
 } mcs_params;
 
 /* Rows of the estimate.  Vertex rows: n_rows = nv, tri2bin = NULL, a walk's
@@ -124,6 +133,8 @@ typedef struct {
     double *exit_bary;      /* optional: n_rows * W * 3 barycentrics of each walk's exit point
                                on its exit triangle (F order of the vertices; 0 for a discarded
                                row or a walk without a hit); the input of the Galerkin estimator */
+    double *walk_w;         /* optional: n_rows * W per-walk weights q (start_mode 1; 1 otherwise,
+                               0 for a discarded row) */
 } mcs_outputs;
 
 typedef struct {
@@ -394,7 +405,11 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
  * with exit_tri and exit_bary recorded (mcs_outputs): omega n_rows, exit_tri
  * and exit_bary n_rows x W (x 3).  Killing walks (exterior, H0 with
  * killing_walks > 0, optional) enter lumped at their bin: 4 pi |p - o| H0 /
- * N0.  Phi: device nv x K FP64 row-major, M-orthonormal; K a multiple of 16
+ * N0.  walk_w (optional, n_rows x W): per-walk weights multiplying w
+ * (start_mode 1).  form 0: the jump form above; form 1 (interior; start_mode
+ * 2): the naive estimator's (Alg. 1) symmetrised
+ * w [e_s (e_s - beta_t)^T + (e_s - beta_t) e_s^T] / 2 with w = omega_v / W.
+ * Phi: device nv x K FP64 row-major, M-orthonormal; K a multiple of 16
  * in [16, 160]; nv >= 16.  Lambda_bary: optional device nv x nv output, else
  * held in the workspace (own_lambda = 1 in the size query).  Lambda_bary is
  * assembled with FP64 atomics (reproducible to rounding); Lambda_bary Phi
@@ -409,7 +424,8 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
 mcs_status mcs_cotan_laplacian(mcs_mesh m, double *L, void *stream);
 size_t mcs_galerkin_workspace_size(mcs_mesh m, int K, int own_lambda);
 mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row_face, const double *omega,
-                            const int32_t *exit_tri, const double *exit_bary, int walks_per_row, int exterior,
+                            const int32_t *exit_tri, const double *exit_bary, const double *walk_w, int form,
+                            int walks_per_row, int exterior,
                             const double *origin, const int32_t *H0, long long killing_walks, const double *Phi,
                             int K, double *S, double *Lambda_bary, void *workspace, size_t workspace_bytes,
                             void *stream);

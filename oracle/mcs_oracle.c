@@ -113,6 +113,11 @@ typedef struct {
     int prec;                /* 64 or 32 */
     int n_threads;
     long long killing_walks; /* exterior only; 0 = no killing walks           */
+    int start_mode;          /* 0 importance-sampled ball (the estimator), 1  */
+                             /* uniform on the ball outside the cap, weighted */
+                             /* by q = A J^B / M; 2 naive inset (Alg. 1): one */
+                             /* uniform WoS step from s - inset n, no cap     */
+    double inset;            /* start_mode 2: inset distance h                */
 } orc_problem;
 
 typedef struct {
@@ -130,6 +135,8 @@ typedef struct {
     int64_t *kill_stats; /* [steps, capped, lost]                             */
     int32_t *exit_tri;   /* optional n_list x W: exit triangle                */
     double  *exit_bary;  /* optional n_list x W x 3: exit barycentrics        */
+    double  *walk_w;     /* optional n_list x W: the walk's weight q (1 in    */
+                         /* modes 0 and 2)                                    */
 } orc_result;
 
 /* ------------------------------------------------------------------------- */
@@ -311,17 +318,32 @@ static void basis32(const float n[3], float e1[3], float e2[3])
  * dA = 4 rho^2 w dw dphi, so w has density ~ 1/w^2 on [w0, 1] and
  * 1/w = 1/w0 - u (1/w0 - 1).  The azimuth is uniform; the odd walk takes
  * phi + pi (antithetic pair, Sec. 5), which keeps |p - z|. */
+/* Start points (Sec. 4.2).  mode 0: w = sin(theta/2) with pdf ~ 1/w^2 on
+ * [w0, 1] (J^B importance sampling outside the cap theta < theta0); mode 1:
+ * cos(theta) uniform on [-1, cos(theta0)] with the weight
+ * q = |dB outside the cap| J^B(p, z) / M = (1 - w0^2) / (2 w^3 (1/w0 - 1));
+ * mode 2: cos(theta) uniform on [-1, 1] (one WoS step, no cap), q = 1. */
 static void start64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t gp, int odd,
-                    const double c[3], double rho, const double n[3], double z[3])
+                    const double c[3], double rho, const double n[3], double z[3], int mode, double *q)
 {
     uint32_t key[2] = {k0, k1}, x[4];
     uint32_t ctr[4] = {(uint32_t)gp, (uint32_t)(gp >> 32), 0u, TAG_RADIAL};
     orc_philox(ctr, key, x);
     double u = uni64(x[0], x[1]);
     double iw0 = cx->iw0;
-    double iw = iw0 - u * (iw0 - 1.0);
-    double w = 1.0 / iw;
-    double cth = 1.0 - 2.0 * (w * w);
+    double w, cth;
+    *q = 1.0;
+    if (mode == 0) {
+        double iw = iw0 - u * (iw0 - 1.0);
+        w = 1.0 / iw;
+        cth = 1.0 - 2.0 * (w * w);
+    } else {
+        double w0 = 1.0 / iw0;
+        double c0 = mode == 1 ? 1.0 - 2.0 * (w0 * w0) : 1.0;
+        cth = c0 - u * (c0 + 1.0);
+        w = sqrt((1.0 - cth) * 0.5);
+        if (mode == 1) *q = (1.0 - w0 * w0) / (2.0 * (w * w * w) * (iw0 - 1.0));
+    }
     double sth = (2.0 * w) * sqrt(1.0 - w * w);
     double cph = 1.0, sph = 0.0;
     for (uint32_t t = 0; t < MAX_REJECT; t++) {
@@ -339,16 +361,29 @@ static void start64(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t gp, in
         z[i] = c[i] + rho * (cth * n[i] + sth * (cph * e1[i] + sph * e2[i]));
 }
 static void start32(const orc_ctx *cx, uint32_t k0, uint32_t k1, uint64_t gp, int odd,
-                    const float c[3], float rho, const float n[3], float z[3])
+                    const float c[3], float rho, const float n[3], float z[3], int mode, double *q)
 {
     uint32_t key[2] = {k0, k1}, x[4];
     uint32_t ctr[4] = {(uint32_t)gp, (uint32_t)(gp >> 32), 0u, TAG_RADIAL};
     orc_philox(ctr, key, x);
     float u = uni32(x[0]);
     float iw0 = (float)cx->iw0;
-    float iw = iw0 - u * (iw0 - 1.0f);
-    float w = 1.0f / iw;
-    float cth = 1.0f - 2.0f * (w * w);
+    float w, cth;
+    *q = 1.0;
+    if (mode == 0) {
+        float iw = iw0 - u * (iw0 - 1.0f);
+        w = 1.0f / iw;
+        cth = 1.0f - 2.0f * (w * w);
+    } else {
+        float w0 = 1.0f / iw0;
+        float c0 = mode == 1 ? 1.0f - 2.0f * (w0 * w0) : 1.0f;
+        cth = c0 - u * (c0 + 1.0f);
+        w = sqrtf((1.0f - cth) * 0.5f);
+        if (mode == 1) {
+            double wd = (double)w, w0d = 1.0 / cx->iw0;
+            *q = (1.0 - w0d * w0d) / (2.0 * (wd * wd * wd) * (cx->iw0 - 1.0));
+        }
+    }
     float sth = (2.0f * w) * sqrtf(1.0f - w * w);
     float cph = 1.0f, sph = 0.0f;
     for (uint32_t t = 0; t < MAX_REJECT; t++) {
@@ -745,6 +780,11 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
             if (pb->exterior) {
                 double st[3];
                 tangent_exterior(&cx, s, n, &r, c, &rho, st, nb, &s3);
+            } else if (pb->start_mode == 2) {
+                /* naive estimator (Alg. 1): the walk starts at the inset point */
+                for (int i = 0; i < 3; i++) c[i] = s[i] - pb->inset * n[i];
+                r = pb->inset;
+                rho = dist64(&cx, c);
             } else {
                 tangent_interior(&cx, s, n, &r, c, &rho);
             }
@@ -768,7 +808,7 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
         }
         /* importance-sampled jump mass over theta > theta0:
          * int J^B(p,z) dz = (1/w0 - 1) / (2 rho) */
-        res->Mjump[li] = (iw0 - 1.0) / (2.0 * rho);
+        res->Mjump[li] = pb->start_mode == 2 ? 1.0 / pb->inset : (iw0 - 1.0) / (2.0 * rho);
         const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
         const float nf3[3] = {(float)nb[0], (float)nb[1], (float)nb[2]};
         const float rf = (float)rho;
@@ -777,14 +817,15 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
             uint64_t gp = g - (uint64_t)(j & 1);
             int capped = 0, lost = 0, bin;
             orc_exit ex = {-1, {0, 0, 0}};
+            double q = 1.0;
             if (pb->prec == 32) {
                 float z[3];
-                start32(&cx, k0, k1, gp, j & 1, cf, rf, nf3, z);
+                start32(&cx, k0, k1, gp, j & 1, cf, rf, nf3, z, pb->start_mode, &q);
                 bin = pb->exterior ? walk_ext32(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex)
                                    : walk_int32(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex);
             } else {
                 double z[3];
-                start64(&cx, k0, k1, gp, j & 1, c, rho, nb, z);
+                start64(&cx, k0, k1, gp, j & 1, c, rho, nb, z, pb->start_mode, &q);
                 bin = pb->exterior ? walk_ext64(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex)
                                    : walk_int64(&cx, k0, k1, g, z, &res->steps[li], &capped, &lost, &ex);
             }
@@ -798,6 +839,7 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
                 res->exit_bary[3 * e + 1] = ex.b[1];
                 res->exit_bary[3 * e + 2] = ex.b[2];
             }
+            if (res->walk_w) res->walk_w[(size_t)li * pb->walks + j] = q;
         }
     }
     /* killing walks from the inverted origin (Eq. killing-measure-poisson-kernel) */
@@ -959,10 +1001,12 @@ void orc_start_points(uint64_t seed, double cap_deg, const double c[3], double r
             if (prec == 32) {
                 float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
                 float nf3[3] = {(float)n[0], (float)n[1], (float)n[2]}, zf[3];
-                start32(&cx, (uint32_t)seed, (uint32_t)(seed >> 32), 2 * q, odd, cf, (float)rho, nf3, zf);
+                double qw;
+                start32(&cx, (uint32_t)seed, (uint32_t)(seed >> 32), 2 * q, odd, cf, (float)rho, nf3, zf, 0, &qw);
                 z[0] = zf[0]; z[1] = zf[1]; z[2] = zf[2];
             } else {
-                start64(&cx, (uint32_t)seed, (uint32_t)(seed >> 32), 2 * q, odd, c, rho, n, z);
+                double qw;
+                start64(&cx, (uint32_t)seed, (uint32_t)(seed >> 32), 2 * q, odd, c, rho, n, z, 0, &qw);
             }
         }
     }

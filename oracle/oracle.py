@@ -56,13 +56,13 @@ class _Problem(C.Structure):
                 ("origin", C.c_double * 3), ("seed", C.c_uint64), ("cap_deg", C.c_double),
                 ("bisect_iters", C.c_int), ("kappa", C.c_double), ("max_steps", C.c_int),
                 ("rho_min_factor", C.c_double), ("prec", C.c_int), ("n_threads", C.c_int),
-                ("killing_walks", C.c_longlong)]
+                ("killing_walks", C.c_longlong), ("start_mode", C.c_int), ("inset", C.c_double)]
 
 
 class _Result(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("H", "Mjump", "kfac", "discarded", "r_t", "rho", "center",
                                           "steps", "capped", "lost", "H0", "kill_stats", "exit_tri",
-                                          "exit_bary")]
+                                          "exit_bary", "walk_w")]
 
 
 def lib():
@@ -214,6 +214,8 @@ def _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, row_list, n_t
     pb.prec = prec
     pb.n_threads = n_threads
     pb.killing_walks = killing_walks
+    pb.start_mode = int(prm.get("start_mode", 0))
+    pb.inset = float(prm.get("inset", 0.0))
     return pb, keep
 
 
@@ -266,9 +268,11 @@ def estimate(V, F, rows, walks: int, eps: float, exterior: bool = False, origin=
     if record_exits:
         out["exit_tri"] = np.zeros((nl, walks), np.int32)
         out["exit_bary"] = np.zeros((nl, walks, 3))
+        out["walk_w"] = np.zeros((nl, walks))
     res = _Result()
     if record_exits:
         res.exit_tri, res.exit_bary = _p(out["exit_tri"]), _p(out["exit_bary"])
+        res.walk_w = _p(out["walk_w"])
     for name, key in (("H", "H"), ("Mjump", "M"), ("kfac", "kfac"), ("discarded", "discarded"),
                       ("r_t", "r_t"), ("rho", "rho"), ("center", "center"), ("steps", "steps"),
                       ("capped", "capped"), ("lost", "lost"), ("H0", "H0"), ("kill_stats", "kill_stats")):
@@ -371,13 +375,16 @@ def cotan_laplacian(V, F) -> np.ndarray:
 
 
 def galerkin_lambda(V, F, est: dict, rows, exterior: bool = False, origin=None, row_face=None,
-                    killing: bool = False) -> np.ndarray:
+                    killing: bool = False, walk_w=None, form: str = "jump") -> np.ndarray:
     """Hat-basis Galerkin stiffness of the boxed estimators with barycentric
     basis evaluation (Sec. 4.4): sum over walks of w (e_s - beta_t)(e_s - beta_t)^T,
     w = omega_v / (2 W) (the boxed estimators' factor 1/2; times |t - o| at the
     exit point t for exterior walks);
     e_s: the row's vertex, or 1/3 on each vertex of row_face[v] for sample
-    rows.  Killing walks (exterior, optional) lumped at their bin:
+    rows.  walk_w (R x W, optional) multiplies each walk's weight (start
+    mode 1).  form "naive" (Alg. 1, start mode 2): the sum of
+    w e_s (e_s - beta_t)^T, symmetrised, with w = omega_v / W.  Killing walks
+    (exterior, optional) lumped at their bin:
     4 pi |p - o| H0 / N0 at the bin vertex (sample rows: 1/9 on each pair of
     the row face's vertices, p the face centroid)."""
     V = np.asarray(V, np.float64)
@@ -394,7 +401,9 @@ def galerkin_lambda(V, F, est: dict, rows, exterior: bool = False, origin=None, 
             continue
         tv = F[tri[ok]]                      # walks x 3 exit vertices
         beta = est["exit_bary"][li][ok]      # walks x 3
-        w = np.full(tv.shape[0], 0.5 * omega[li] / W)
+        w = np.full(tv.shape[0], (0.5 if form == "jump" else 1.0) * omega[li] / W)
+        if walk_w is not None:
+            w = w * np.asarray(walk_w)[li][ok]
         if exterior:
             t = np.einsum("wi,wik->wk", beta, V[tv])
             w = w * np.linalg.norm(t - o, axis=1)
@@ -404,9 +413,15 @@ def galerkin_lambda(V, F, est: dict, rows, exterior: bool = False, origin=None, 
             sidx, sval = np.asarray(F[row_face[v]]), np.full(3, 1.0 / 3.0)
         idx = np.concatenate([np.broadcast_to(sidx, (tv.shape[0], sidx.size)), tv], axis=1)
         val = np.concatenate([np.broadcast_to(sval, (tv.shape[0], sval.size)), -beta], axis=1)
+        # row-point part of each entry (the e_s factor of the naive form)
+        sv = np.concatenate([np.broadcast_to(sval, (tv.shape[0], sval.size)), np.zeros_like(beta)], axis=1)
         for a in range(idx.shape[1]):
             for b in range(idx.shape[1]):
-                np.add.at(L, (idx[:, a], idx[:, b]), w * val[:, a] * val[:, b])
+                if form == "jump":
+                    x = val[:, a] * val[:, b]
+                else:
+                    x = 0.5 * (sv[:, a] * val[:, b] + val[:, a] * sv[:, b])
+                np.add.at(L, (idx[:, a], idx[:, b]), w * x)
     if exterior and killing and est["killing_walks"] > 0:
         N0 = est["killing_walks"]
         for u in np.flatnonzero(est["H0"]):

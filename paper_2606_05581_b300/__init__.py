@@ -34,7 +34,8 @@ class Params(C.Structure):
                 ("origin_auto", C.c_int), ("origin", C.c_double * 3), ("killing_walks", C.c_longlong),
                 ("seed", C.c_uint64), ("walks_per_row", C.c_int), ("blocks_per_sm", C.c_int),
                 ("threads_per_block", C.c_int), ("timing", C.c_int), ("count_work", C.c_int),
-                ("queue_order", C.c_int), ("bvh_layout", C.c_int), ("lanes_per_query", C.c_int)]
+                ("queue_order", C.c_int), ("bvh_layout", C.c_int), ("lanes_per_query", C.c_int),
+                ("start_mode", C.c_int), ("inset", C.c_double)]
 
 
 class Rows(C.Structure):
@@ -45,7 +46,7 @@ class Rows(C.Structure):
 class Outputs(C.Structure):
     _fields_ = [("hist_bin", C.c_void_p), ("hist_cnt", C.c_void_p), ("hist_nnz", C.c_void_p),
                 ("Lambda", C.c_void_p), ("omega", C.c_void_p), ("H0", C.c_void_p), ("exit_tri", C.c_void_p),
-                ("Lambda32", C.c_void_p), ("exit_bary", C.c_void_p)]
+                ("Lambda32", C.c_void_p), ("exit_bary", C.c_void_p), ("walk_w", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -137,8 +138,8 @@ def lib():
         L.mcs_cotan_laplacian.argtypes = [vp, vp, vp]
         L.mcs_galerkin_workspace_size.argtypes = [vp, i32, i32]
         L.mcs_galerkin_workspace_size.restype = C.c_size_t
-        L.mcs_galerkin_dtn.argtypes = [vp, C.POINTER(Rows), vp, vp, vp, vp, i32, i32, C.POINTER(C.c_double), vp, i64,
-                                       vp, i32, vp, vp, vp, C.c_size_t, vp]
+        L.mcs_galerkin_dtn.argtypes = [vp, C.POINTER(Rows), vp, vp, vp, vp, vp, i32, i32, i32, C.POINTER(C.c_double),
+                                       vp, i64, vp, i32, vp, vp, vp, C.c_size_t, vp]
         L.mcs_galerkin_modes.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp, vp]
         L.mcs_steklov_heat_workspace_size.argtypes = [i32, i32, i32]
         L.mcs_steklov_heat_workspace_size.restype = C.c_size_t
@@ -302,7 +303,8 @@ def _aligned_ptr(buf: torch.Tensor) -> int:
     return (p + 255) & ~255
 
 
-_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri", "Lambda32", "exit_bary")
+_OUT_KEYS = ("hist_bin", "hist_cnt", "hist_nnz", "Lambda", "omega", "H0", "exit_tri", "Lambda32", "exit_bary",
+             "walk_w")
 
 
 def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32_copy: bool = False,
@@ -316,7 +318,8 @@ def _alloc_outputs(R: int, W: int, dev, assemble: bool, record_exits: bool, fp32
                 Lambda=torch.empty((R, R), dtype=torch.float64, device=dev) if assemble else None,
                 exit_tri=torch.empty((R, W), dtype=torch.int32, device=dev) if record_exits else None,
                 Lambda32=torch.empty((R, R), dtype=torch.float32, device=dev) if (assemble and fp32_copy) else None,
-                exit_bary=torch.empty((R, W, 3), dtype=torch.float64, device=dev) if record_bary else None)
+                exit_bary=torch.empty((R, W, 3), dtype=torch.float64, device=dev) if record_bary else None,
+                walk_w=torch.empty((R, W), dtype=torch.float64, device=dev) if record_bary else None)
 
 
 def _rows_struct(rows: dict) -> Rows:
@@ -533,11 +536,13 @@ def cotan_laplacian(mesh: Mesh) -> torch.Tensor:
 
 
 def galerkin_dtn(mesh: Mesh, rows: dict, res: dict, Phi: torch.Tensor, exterior: bool = False,
-                 killing_walks: int = 0, want_lambda: bool = False, workspace: "Workspace | None" = None):
+                 killing_walks: int = 0, want_lambda: bool = False, workspace: "Workspace | None" = None,
+                 start_mode: int = 0):
     """Galerkin estimate S = Phi^T Lambda_bary Phi (K x K) from an estimate
     recorded with record_exits and record_bary; rows as given to that
     estimate (sample rows: their "sel" faces are the row points' faces).
-    Returns S, or (S, Lambda_bary) with want_lambda."""
+    start_mode: that of the estimate (1: per-walk weights; 2: the naive
+    form).  Returns S, or (S, Lambda_bary) with want_lambda."""
     P = Phi.to(torch.float64).contiguous()
     K = int(P.shape[1])
     S = torch.empty((K, K), dtype=torch.float64, device=P.device)
@@ -550,8 +555,11 @@ def galerkin_dtn(mesh: Mesh, rows: dict, res: dict, Phi: torch.Tensor, exterior:
         raise MCSError("galerkin_dtn: K must be a multiple of 16 in [16, 160]")
     ws = (workspace or Workspace()).get(nb)
     H0 = res.get("H0") if (exterior and killing_walks > 0) else None
+    ww = res.get("walk_w") if start_mode == 1 else None
+    form = 1 if start_mode == 2 else 0
     _check(lib().mcs_galerkin_dtn(mesh.handle, C.byref(rs), _ptr(sel), _ptr(res["omega"]), _ptr(res["exit_tri"]),
-                                  _ptr(res["exit_bary"]), int(res["walks"]), int(exterior), origin, _ptr(H0),
+                                  _ptr(res["exit_bary"]), _ptr(ww), form, int(res["walks"]), int(exterior), origin,
+                                  _ptr(H0),
                                   int(killing_walks), _ptr(P), K, _ptr(S), _ptr(Lb), C.c_void_p(_aligned_ptr(ws)), nb,
                                   _stream()))
     return (S, Lb) if want_lambda else S

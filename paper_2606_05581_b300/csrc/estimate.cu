@@ -63,6 +63,8 @@ struct Ctrl {
 struct Frame {
     double onemk, iw0, eps, rho_min_factor, rmax;
     int bisect_iters;
+    int start_mode;  // 2: naive rows (the walk starts at s - inset n)
+    double inset;
 };
 
 __device__ __forceinline__ double dist64(const DevMesh &m, double x, double y, double z, int *err) {
@@ -179,7 +181,13 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
     b.c[0] = b.c[1] = b.c[2] = 0.0;
     b.n[0] = n0; b.n[1] = n1; b.n[2] = n2;
     b.rho = 0.0; b.r = 0.0; b.kfac = 1.0;
-    if (nz) {
+    if (nz && fr.start_mode == 2) {
+        // naive estimator (Alg. 1): the ball of the first walk-on-spheres step
+        // from the inset point
+        b.c[0] = s0 - fr.inset * n0; b.c[1] = s1 - fr.inset * n1; b.c[2] = s2 - fr.inset * n2;
+        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err);
+        b.r = fr.inset;
+    } else if (nz) {
         const double rmax = fr.rmax;
         double r;
         if (wclear(m, s0 - rmax * n0, s1 - rmax * n1, s2 - rmax * n2, fr.onemk * rmax, front, cand, &err)) {
@@ -198,7 +206,7 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
         b.r = r;
     }
     b.valid = nz && (b.rho >= fr.rho_min_factor * fr.eps);
-    b.M = b.valid ? (fr.iw0 - 1.0) / (2.0 * b.rho) : 0.0;
+    b.M = b.valid ? (fr.start_mode == 2 ? 1.0 / fr.inset : (fr.iw0 - 1.0) / (2.0 * b.rho)) : 0.0;
     b.pad = 0;
     if ((threadIdx.x & 31) == 0) {
         ball[v] = b;
@@ -437,6 +445,8 @@ struct WalkJob {
     int32_t *exits;        // R x W, by sorted row position
     int32_t *exit_tri;     // optional, R x W by canonical row
     double *exit_bary;     // optional, R x W x 3 by canonical row: barycentrics of the exit point
+    double *walk_w;        // optional, R x W by canonical row: the walk's weight q
+    int start_mode;        // 0 importance-sampled ball, 1 uniform ball (weighted), 2 naive inset
     int32_t *H0;           // killing histogram
     Ctrl *ctrl;            // the mesh's control block (origin, Kelvin frame)
     unsigned long long n_rows_walks;  // R * W
@@ -637,12 +647,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                                 double *eb = J.exit_bary + ((size_t)v * J.W + j) * 3;
                                 eb[0] = eb[1] = eb[2] = 0.0;
                             }
+                            if (J.walk_w) J.walk_w[(size_t)v * J.W + j] = 0.0;
                         } else {
                             s.g = (unsigned long long)v * (unsigned long long)J.W + (unsigned long long)j;
                             const unsigned long long gp = s.g - (unsigned long long)(j & 1);
+                            double q = 1.0;
                             s.x = start_point<T>(J.k0, s.k1, gp, j & 1, (T)a.iw0,
                                                  V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]}, (T)b.rho,
-                                                 V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]});
+                                                 V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]}, J.start_mode, a.iw0,
+                                                 &q);
+                            if (J.walk_w && writer) J.walk_w[(size_t)v * J.W + j] = q;
                             active = true;
                         }
                     }
@@ -1174,6 +1188,16 @@ static mcs_status check_common(const mcs_params *p, const std::string &f) {
     MCS_ARG(p->bvh_layout == 0 || p->bvh_layout == 2 || p->bvh_layout == 4, f + ": bvh_layout must be 0, 2 or 4");
     MCS_ARG(p->lanes_per_query == 0 || p->lanes_per_query == 1 || (p->lanes_per_query == 4 && p->bvh_layout == 4),
             f + ": lanes_per_query must be 0, 1, or 4 (with bvh_layout 4)");
+    MCS_ARG(p->start_mode >= 0 && p->start_mode <= 2, f + ": start_mode must be 0, 1 or 2");
+    MCS_ARG(p->start_mode != 2 || (p->inset > 0.0 && std::isfinite(p->inset)), f + ": start_mode 2 needs inset > 0");
+    return MCS_OK;
+}
+
+// start modes 1 and 2 serve the Galerkin assembly of interior estimates: the
+// nodal Lambda takes neither per-walk weights nor the naive form
+static mcs_status check_start_mode(const mcs_params *p, int domain, const mcs_outputs *out, const std::string &f) {
+    MCS_ARG(p->start_mode == 0 || (domain == MCS_INTERIOR && out->Lambda == nullptr),
+            f + ": start_mode 1 and 2 are for interior estimates without Lambda (use the Galerkin assembly)");
     return MCS_OK;
 }
 
@@ -1213,6 +1237,8 @@ static Plan make_plan(mcs_mesh m, const mcs_rows &rows, const mcs_outputs &out, 
     pl.fr.rho_min_factor = p->rho_min_factor;
     pl.fr.rmax = m->rmax;
     pl.fr.bisect_iters = p->bisect_iters;
+    pl.fr.start_mode = p->start_mode;
+    pl.fr.inset = p->start_mode == 2 ? p->inset : 0.0;
     return pl;
 }
 
@@ -1285,6 +1311,8 @@ static WalkJob make_job(const Plan &pl, unsigned long long n_row_walks, unsigned
     J.exits = pl.exits();
     J.exit_tri = pl.out.exit_tri;
     J.exit_bary = pl.out.exit_bary;
+    J.walk_w = pl.out.walk_w;
+    J.start_mode = pl.fr.start_mode;
     J.H0 = pl.H0();
     J.ctrl = pl.ctrl;
     J.n_rows_walks = n_row_walks;
@@ -1537,6 +1565,8 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
     for (int i = 0; i < n; i++) {
         s = check_mesh_rows(items[i].mesh, &items[i].rows, &items[i].out, items[i].domain, p->walks_per_row,
                             f + " item " + std::to_string(i));
+        if (s != MCS_OK) return s;
+        s = check_start_mode(p, items[i].domain, &items[i].out, f + " item " + std::to_string(i));
         if (s != MCS_OK) return s;
         MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(items[i].mesh),
                 f + " item " + std::to_string(i) + ": bvh_layout 4 needs mcs_mesh_build_wide first");
@@ -1846,6 +1876,8 @@ void mcs_default_params(mcs_params *p) {
     p->queue_order = 0;
     p->bvh_layout = 0;
     p->lanes_per_query = 0;
+    p->start_mode = 0;
+    p->inset = 0.0;
 }
 
 size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, long long killing_walks) {
@@ -1861,6 +1893,7 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     mcs_status s = check_common(p, f);
     if (s != MCS_OK) return s;
     if ((s = check_mesh_rows(m, rows, out, p->domain, p->walks_per_row, f)) != MCS_OK) return s;
+    if ((s = check_start_mode(p, p->domain, out, f)) != MCS_OK) return s;
     MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(m), f + ": bvh_layout 4 needs mcs_mesh_build_wide first");
     const Layout L = layout(rows->n_rows, p->walks_per_row, true);
     MCS_ARG(workspace != nullptr && workspace_bytes >= L.total, f + ": workspace too small");

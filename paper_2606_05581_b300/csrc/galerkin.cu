@@ -65,18 +65,22 @@ __global__ void k_cotan(const double *V, const int32_t *F, const int32_t *inc_f,
     row[a] += diag;
 }
 
-// Lambda_bary += w (e_s - beta_t)(e_s - beta_t)^T for every recorded walk.
-// Row point basis: vertex rows e_v; sample rows the centroid of their face
-// (1/3 on each of its vertices).
+// Lambda_bary += w (e_s - beta_t)(e_s - beta_t)^T for every recorded walk
+// (form 0), or the naive estimator's (Alg. 1) symmetrised
+// w [e_s (e_s - beta_t)^T + (e_s - beta_t) e_s^T] / 2 with w = omega_v / W
+// (form 1).  walk_w (optional) multiplies each walk's weight.  Row point
+// basis: vertex rows e_v; sample rows the centroid of their face (1/3 on each
+// of its vertices).
 __global__ void k_assemble(const double *V, const int32_t *F, int nv, int n_rows, int W, const int32_t *row_face,
-                           const double *omega, const int32_t *exit_tri, const double *exit_bary, int exterior,
-                           double o0, double o1, double o2, double *L) {
+                           const double *omega, const int32_t *exit_tri, const double *exit_bary,
+                           const double *walk_w, int form, int exterior, double o0, double o1, double o2, double *L) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)n_rows * W) return;
     const int v = (int)(e / W);
     const int t = exit_tri[e];
     if (t < 0) return;
-    double w = 0.5 * omega[v] / (double)W;
+    double w = (form == 0 ? 0.5 : 1.0) * omega[v] / (double)W;
+    if (walk_w) w *= walk_w[e];
     if (!(w != 0.0)) return;
     const double *bt = exit_bary + 3 * e;
     const int tv[3] = {F[3 * t], F[3 * t + 1], F[3 * t + 2]};
@@ -89,18 +93,18 @@ __global__ void k_assemble(const double *V, const int32_t *F, int nv, int n_rows
     }
     // sparse d: up to 3 row-point entries and 3 exit entries
     int idx[6];
-    double val[6];
+    double val[6], sv[6];  // d's entries and its row-point part e_s
     int nz = 0;
     if (row_face) {
         const int f = row_face[v];
-        for (int i = 0; i < 3; i++) { idx[nz] = F[3 * f + i]; val[nz] = 1.0 / 3.0; nz++; }
+        for (int i = 0; i < 3; i++) { idx[nz] = F[3 * f + i]; val[nz] = sv[nz] = 1.0 / 3.0; nz++; }
     } else {
-        idx[nz] = v; val[nz] = 1.0; nz++;
+        idx[nz] = v; val[nz] = sv[nz] = 1.0; nz++;
     }
-    for (int i = 0; i < 3; i++) { idx[nz] = tv[i]; val[nz] = -bt[i]; nz++; }
+    for (int i = 0; i < 3; i++) { idx[nz] = tv[i]; val[nz] = -bt[i]; sv[nz] = 0.0; nz++; }
     for (int i = 0; i < nz; i++)
         for (int j = 0; j < nz; j++) {
-            const double x = w * val[i] * val[j];
+            const double x = form == 0 ? w * val[i] * val[j] : w * (0.5 * (sv[i] * val[j] + val[i] * sv[j]));
             if (x != 0.0) atomicAdd(&L[(size_t)idx[i] * nv + idx[j]], x);
         }
 }
@@ -329,7 +333,8 @@ size_t mcs_galerkin_workspace_size(mcs_mesh m, int K, int own_lambda) {
 }
 
 mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row_face, const double *omega,
-                            const int32_t *exit_tri, const double *exit_bary, int walks_per_row, int exterior,
+                            const int32_t *exit_tri, const double *exit_bary, const double *walk_w, int form,
+                            int walks_per_row, int exterior,
                             const double *origin, const int32_t *H0, long long killing_walks, const double *Phi,
                             int K, double *S, double *Lambda_bary, void *workspace, size_t workspace_bytes,
                             void *stream) {
@@ -338,6 +343,7 @@ mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row
     MCS_ARG(walks_per_row >= 1 && rows->n_rows >= 1, "mcs_galerkin_dtn: need walks_per_row, n_rows >= 1");
     MCS_ARG(row_face || rows->n_rows == m->nv, "mcs_galerkin_dtn: vertex rows need n_rows == nv (else pass row_face)");
     MCS_ARG(!exterior || origin, "mcs_galerkin_dtn: exterior needs the inversion centre");
+    MCS_ARG(form == 0 || (form == 1 && !exterior), "mcs_galerkin_dtn: form 0 (jump), or 1 (naive, interior)");
     MCS_ARG(m->nv >= 16, "mcs_galerkin_dtn: need nv >= 16");
     const Layout l = layout(m->nv, K, Lambda_bary == nullptr);
     MCS_ARG(workspace && workspace_bytes >= l.total, "mcs_galerkin_dtn: workspace too small");
@@ -351,7 +357,8 @@ mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row
     const size_t nw = (size_t)R * walks_per_row;
     note_launch();
     k_assemble<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(m->V, m->F, nv, R, walks_per_row, row_face, omega,
-                                                               exit_tri, exit_bary, exterior, o0, o1, o2, L);
+                                                               exit_tri, exit_bary, walk_w, form, exterior, o0, o1,
+                                                               o2, L);
     if (exterior && H0 && killing_walks > 0) {
         note_launch();
         k_killing<<<(R + 255) / 256, 256, 0, st>>>(m->V, m->F, nv, R, row_face, H0, (double)killing_walks, o0, o1,

@@ -104,12 +104,29 @@ __device__ __forceinline__ void onb(V3<T> n, V3<T> &e1, V3<T> &e2) {
 // kernel outside the cap), azimuth uniform, odd partner at phi + pi.
 template <typename T>
 __device__ __forceinline__ V3<T> start_point(uint32_t k0, uint32_t k1, unsigned long long gp, int odd, T iw0,
-                                             V3<T> c, T rho, V3<T> n) {
+                                             V3<T> c, T rho, V3<T> n, int mode = 0, double iw0d = 0.0,
+                                             double *q = nullptr) {
     const uint4 xr = philox(make_uint4((uint32_t)gp, (uint32_t)(gp >> 32), 0u, kTagRadial), k0, k1);
     const T u = Uni<T>::one(xr);
-    const T iw = iw0 - u * (iw0 - (T)1);
-    const T w = (T)1 / iw;
-    const T cth = (T)1 - (T)2 * (w * w);
+    T w, cth;
+    if (mode == 0) {
+        // w = sin(theta/2) with pdf ~ 1/w^2 on [w0, 1]: J^B importance sampling
+        const T iw = iw0 - u * (iw0 - (T)1);
+        w = (T)1 / iw;
+        cth = (T)1 - (T)2 * (w * w);
+        if (q) *q = 1.0;
+    } else {
+        // cos(theta) uniform on [-1, cos(theta0)] (mode 1) or [-1, 1] (mode 2);
+        // mode 1 walks carry q = |dB outside the cap| J^B(p, z) / M
+        const T w0 = (T)1 / iw0;
+        const T c0 = mode == 1 ? (T)1 - (T)2 * (w0 * w0) : (T)1;
+        cth = c0 - u * (c0 + (T)1);
+        w = rsq<T>(((T)1 - cth) * (T)0.5);
+        if (q) {
+            const double wd = (double)w, w0d = 1.0 / iw0d;
+            *q = mode == 1 ? (1.0 - w0d * w0d) / (2.0 * (wd * wd * wd) * (iw0d - 1.0)) : 1.0;
+        }
+    }
     const T sth = ((T)2 * w) * rsq<T>((T)1 - w * w);
     T cph = (T)1, sph = (T)0;
     for (uint32_t t = 0; t < (uint32_t)kMaxReject; t++) {

@@ -134,3 +134,101 @@ def test_galerkin_sphere_spectrum():
     assert abs(ev[0]) < 1e-5 * abs(ev).max()
     assert ev[1:4].max() < ev[4:9].min()
     assert np.abs(ev[1:4] - 0.978).max() < 0.06
+
+
+def _mode_params(mode, W, prec, seed, inset=0.02):
+    p = mcs.default_params(walks_per_row=W, prec=prec, seed=seed, eps=1e-4 if mode == 2 else 1e-3)
+    p.start_mode = mode
+    if mode == 2:
+        p.inset = inset
+    return p
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_start_modes_bit_exact_and_assembled(oracle, mode, prec):
+    """Uniform-ball (weighted) and naive (Alg. 1, inset h) start modes: exit
+    triangles, barycentrics and per-walk weights bit-exact with the oracle;
+    row weights A_v M_v (naive: A_v / h); the weighted jump form (mode 1) and
+    the naive form (mode 2) assembled as the oracle does."""
+    m = meshgen.icosphere(2)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.sample_rows(mesh, m.nf, orient=False)
+    rows_np = dict(pos=rows["pos"].cpu().numpy(), nrm=rows["nrm"].cpu().numpy(), area=rows["area"].cpu().numpy(),
+                   tri2bin=rows["tri2bin"].cpu().numpy(), sel=rows["sel"].cpu().numpy())
+    W = 32
+    p = _mode_params(mode, W, prec, 9)
+    res = mcs.estimate_dtn(mesh, rows, p, assemble=False, record_exits=True, record_bary=True)
+    prm = dict(start_mode=mode, inset=0.02) if mode == 2 else dict(start_mode=mode)
+    est = oracle.estimate(m.V, m.F, rows_np, W, p.eps, seed=9, prec=prec, record_exits=True, params=prm)
+    tri = res["exit_tri"].cpu().numpy()
+    assert np.array_equal(tri, est["exit_tri"])
+    ok = tri >= 0
+    assert np.array_equal(res["exit_bary"].cpu().numpy()[ok], est["exit_bary"][ok])
+    assert np.array_equal(res["walk_w"].cpu().numpy()[ok], est["walk_w"][ok])
+    assert np.allclose(res["omega"].cpu().numpy(), oracle.row_weights(est, rows_np), rtol=1e-14)
+    Phi = torch.eye(m.nv, dtype=torch.float64, device="cuda")[:, :32].contiguous()
+    _, Lb = mcs.galerkin_dtn(mesh, rows, res, Phi, want_lambda=True, start_mode=mode)
+    Lref = oracle.galerkin_lambda(m.V, m.F, est, rows_np, row_face=rows_np["sel"],
+                                  walk_w=est["walk_w"] if mode == 1 else None, form="naive" if mode == 2 else "jump")
+    assert np.abs(Lb.cpu().numpy() - Lref).max() <= 1e-12 * np.abs(Lref).max()
+
+
+def test_start_modes_are_rejected_where_they_do_not_apply():
+    m = meshgen.icosphere(2)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.vertex_rows(mesh)
+    with pytest.raises(mcs.MCSError):  # the nodal Lambda ignores weights and form
+        mcs.estimate_dtn(mesh, rows, _mode_params(1, 8, 32, 0), assemble=True)
+    p = _mode_params(2, 8, 32, 0)
+    p.inset = 0.0
+    with pytest.raises(mcs.MCSError):
+        mcs.estimate_dtn(mesh, rows, p, assemble=False)
+    p = _mode_params(1, 8, 32, 0)
+    p.domain = 1
+    with pytest.raises(mcs.MCSError):
+        mcs.estimate_dtn(mesh, rows, p, assemble=False)
+
+
+def _variance_table(mesh, m, rows, Ws, seeds):
+    """Quadratic form of f = z on the unit sphere for the three estimators:
+    mean and variance over seeds at each walk count."""
+    f = torch.from_numpy(np.ascontiguousarray(m.V[:, 2])).cuda()
+    Phi = torch.zeros((m.nv, 16), dtype=torch.float64, device="cuda")
+    Phi[:, 0] = f
+    out = {}
+    for mode in (0, 1, 2):
+        for W in Ws:
+            vals = []
+            for sd in seeds:
+                res = mcs.estimate_dtn(mesh, rows, _mode_params(mode, W, 32, sd), assemble=False, record_exits=True,
+                                       record_bary=True)
+                _, Lb = mcs.galerkin_dtn(mesh, rows, res, Phi, want_lambda=True, start_mode=mode)
+                vals.append(float(f @ Lb @ f))
+            out[(mode, W)] = (float(np.mean(vals)), float(np.var(vals, ddof=1)))
+    return out
+
+
+def test_variance_study_converges_at_one_over_n():
+    """Sec. 5 (Fig. variance_comparison): the tangent-ball estimators
+    (importance-sampled and uniformly sampled ball) and the naive
+    finite-difference estimator (Alg. 1, h = 0.02) converge at O(1/N), and the
+    two ball samplers estimate the same cap-excluded form.  Their variances
+    are compared, over more seeds, by bench.py --workload variance."""
+    m = meshgen.icosphere(3)
+    mesh = mcs.Mesh(m.V, m.F)
+    rows = mcs.sample_rows(mesh, m.nf, orient=False)
+    n = 24
+    t = _variance_table(mesh, m, rows, (8, 64), range(n))
+    for mode in (0, 2):
+        # O(1/N) gives 8; two 24-sample variances put the ratio in ~[3.4, 18]
+        # (F(23, 23), 95%), far from O(1) (1) and O(1/N^2) (64)
+        r = t[(mode, 8)][1] / t[(mode, 64)][1]
+        assert 2.5 < r < 25.0, (mode, r)
+    # the uniform sampler's weights are heavy-tailed (up to ~1/(2 w0^2)), so its
+    # sample variances scatter far more than the F bounds above; it must still
+    # fall with N
+    assert t[(1, 8)][1] > 1.5 * t[(1, 64)][1], t
+    m0, v0 = t[(0, 64)]
+    m1, v1 = t[(1, 64)]
+    assert abs(m0 - m1) < 5 * np.sqrt((v0 + v1) / n), (m0, m1)

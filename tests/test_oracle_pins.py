@@ -665,3 +665,47 @@ def test_galerkin_quadratic_form_of_linear_functions(oracle):
                 f = m.V[:, 2]
                 Mf = np.sum(rows["area"] * rows["pos"][:, 2] ** 2)
                 assert abs((f @ L @ f) / Mf - lam[1]) < 0.12 * lam[1]
+
+
+def test_uniform_ball_weights_have_mean_one(oracle):
+    """Start mode 1 samples cos(theta) uniformly outside the cap and weights
+    each walk by q = |dB outside the cap| J^B(p, z) / M, whose mean is exactly
+    1 (so the weighted estimator has the importance sampler's expectation);
+    Var(q) = (1 - w0^2)(w0^-4 - 1) / (8 (1/w0 - 1)^2) - 1 sets the tolerance."""
+    m = meshgen.icosphere(3)
+    rows = oracle.fps_rows(m.V, m.F, m.nf, orient=False)
+    est = oracle.estimate(m.V, m.F, rows, 64, 1e-3, seed=4, record_exits=True, params=dict(start_mode=1))
+    q = est["walk_w"][est["exit_tri"] >= 0]
+    w0 = math.sin(math.radians(2.5) / 2)
+    var = (1 - w0 ** 2) * (w0 ** -4 - 1) / (8 * (1 / w0 - 1) ** 2) - 1
+    assert abs(q.mean() - 1) < 5 * math.sqrt(var / q.size), (q.mean(), q.size)
+    assert q.min() > 0 and q.max() <= (1 - w0 ** 2) / (2 * w0 ** 3 * (1 / w0 - 1)) * (1 + 1e-9)
+    est0 = oracle.estimate(m.V, m.F, rows, 8, 1e-3, seed=4, record_exits=True)
+    assert np.all(est0["walk_w"] == 1.0)
+
+
+def test_naive_estimator_is_unbiased_for_linear_functions(oracle):
+    """Alg. 1 on the hat basis: a linear f is its own harmonic extension, so
+    E f(t) = f(s - h n_s) exactly and the naive form's expectation is
+    sum_s A_s f(s) (f(s) - f(s - h n_s)) / h, computed here directly (equal
+    to int f df/dn up to the quadrature).  The estimate agrees within its
+    Monte Carlo error."""
+    m = meshgen.icosphere(3)
+    rows = oracle.fps_rows(m.V, m.F, m.nf, orient=False)
+    h = 0.02
+    W = 64
+    est = oracle.estimate(m.V, m.F, rows, W, 1e-4, seed=6, record_exits=True,
+                          params=dict(start_mode=2, inset=h))
+    assert est["discarded"].sum() == 0
+    assert np.allclose(est["M"], 1.0 / h)
+    L = oracle.galerkin_lambda(m.V, m.F, est, rows, row_face=rows["sel"], form="naive")
+    P = oracle.exit_points(m.V, m.F, est["exit_tri"], est["exit_bary"])
+    for f3 in (np.array([0, 0, 1.0]), np.array([0.4, 0.5, -0.2])):
+        f = m.V @ f3
+        fs = rows["pos"] @ f3
+        ref = float(np.sum(rows["area"] * fs * (fs - (rows["pos"] - h * rows["nrm"]) @ f3) / h))
+        got = float(f @ L @ f)
+        # per-walk terms A_s f(s) (f(s) - f(t)) / (W h); their spread sets the error
+        terms = rows["area"][:, None] * fs[:, None] * (fs[:, None] - P @ f3) / (W * h)
+        se = math.sqrt(terms.shape[0] * W * terms.var())
+        assert abs(got - ref) < 5 * se + 1e-3 * abs(ref), (got, ref, se)
