@@ -523,7 +523,8 @@ template <typename T> struct WalkState {
     uint32_t k1;            // Philox key word (killing walks use their own)
 };
 
-// MODE: 0 interior jobs only, 1 exterior jobs only, 2 both (the job decides).
+// MODE: 0 interior jobs only, 1 exterior jobs only, 2 both (the job decides), 3
+// one interior job with a start mode of the variance study (mcs_params.start_mode).
 // WIDE: closest-point queries on the 4-wide BVH, else on the binary one
 // (identical results; the node layout is an autotuner knob).
 // FP32 walks are capped at 48 registers for 10 resident blocks per SM: the
@@ -651,12 +652,20 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                         } else {
                             s.g = (unsigned long long)v * (unsigned long long)J.W + (unsigned long long)j;
                             const unsigned long long gp = s.g - (unsigned long long)(j & 1);
-                            double q = 1.0;
-                            s.x = start_point<T>(J.k0, s.k1, gp, j & 1, (T)a.iw0,
-                                                 V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]}, (T)b.rho,
-                                                 V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]}, J.start_mode, a.iw0,
-                                                 &q);
-                            if (J.walk_w && writer) J.walk_w[(size_t)v * J.W + j] = q;
+                            if constexpr (MODE == 3) {
+                                // interior walks with the variance study's start modes
+                                double q = 1.0;
+                                s.x = start_point<T>(J.k0, s.k1, gp, j & 1, (T)a.iw0,
+                                                     V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]}, (T)b.rho,
+                                                     V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]}, J.start_mode, a.iw0,
+                                                     &q);
+                                if (J.walk_w && writer) J.walk_w[(size_t)v * J.W + j] = q;
+                            } else {
+                                s.x = start_point<T>(J.k0, s.k1, gp, j & 1, (T)a.iw0,
+                                                     V3<T>{(T)b.c[0], (T)b.c[1], (T)b.c[2]}, (T)b.rho,
+                                                     V3<T>{(T)b.n[0], (T)b.n[1], (T)b.n[2]});
+                                if (J.walk_w && writer) J.walk_w[(size_t)v * J.W + j] = 1.0;
+                            }
                             active = true;
                         }
                     }
@@ -1356,7 +1365,9 @@ static mcs_status store_jobs(const std::vector<WalkJob> &jobs, WalkJob *d_jobs, 
 typedef void (*WalkKernel)(MultiArgs);
 
 template <typename T, bool COUNT, int TRAV> static WalkKernel walk_kernel_mode(int mode, bool multi) {
-    if (!multi) return mode == 0 ? k_walks<T, 0, COUNT, false, TRAV> : k_walks<T, 1, COUNT, false, TRAV>;
+    if (!multi)
+        return mode == 0 ? k_walks<T, 0, COUNT, false, TRAV>
+                         : (mode == 3 ? k_walks<T, 3, COUNT, false, TRAV> : k_walks<T, 1, COUNT, false, TRAV>);
     return mode == 0 ? k_walks<T, 0, COUNT, true, TRAV>
                      : (mode == 1 ? k_walks<T, 1, COUNT, true, TRAV> : k_walks<T, 2, COUNT, true, TRAV>);
 }
@@ -1566,8 +1577,7 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
         s = check_mesh_rows(items[i].mesh, &items[i].rows, &items[i].out, items[i].domain, p->walks_per_row,
                             f + " item " + std::to_string(i));
         if (s != MCS_OK) return s;
-        s = check_start_mode(p, items[i].domain, &items[i].out, f + " item " + std::to_string(i));
-        if (s != MCS_OK) return s;
+        MCS_ARG(p->start_mode == 0, f + ": start_mode 1 and 2 are for single estimates (mcs_estimate_dtn)");
         MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(items[i].mesh),
                 f + " item " + std::to_string(i) + ": bvh_layout 4 needs mcs_mesh_build_wide first");
     }
@@ -1912,7 +1922,7 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     if ((s = enqueue_setup(pl, p->queue_order, st)) != MCS_OK) { release(); return s; }
     const WalkJob job = make_job(pl, pl.walks(), (unsigned long long)pl.killing);
     int tpb = 0, bps = 0;
-    const int mode = pl.ext ? 1 : 0;
+    const int mode = pl.ext ? 1 : (p->start_mode != 0 ? 3 : 0);
     if ((s = walk_residency(p, mode, false, &tpb, &bps)) != MCS_OK) { release(); return s; }
     if ((s = prepare_histogram(hist_smem(rows->n_rows))) != MCS_OK) { release(); return s; }
     mark(1);
