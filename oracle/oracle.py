@@ -461,6 +461,202 @@ def hks(evals, evecs, times) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# point-based Galerkin basis (Sec. 4.4 "Point-based Galerkin basis"; appendix
+# "Point-based k-NN Interpolator")
+# ---------------------------------------------------------------------------
+
+def knn(P, Q, k: int, exclude=None, chunk: int = 2048):
+    """The k nearest points of P (n x 3) to each query of Q (nq x 3), brute
+    force: squared distance ((dx*dx + dy*dy) + dz*dz) in FP64 with d = q - p,
+    ascending, equal distances by the smaller point index.  exclude[q]
+    (optional) removes that point from query q's candidates.  Returns
+    (idx nq x k, d2 nq x k)."""
+    P = np.asarray(P, np.float64)
+    Q = np.asarray(Q, np.float64)
+    n, nq = P.shape[0], Q.shape[0]
+    idx = np.empty((nq, k), np.int64)
+    d2 = np.empty((nq, k))
+    ar = np.arange(n)
+    for a in range(0, nq, chunk):
+        q = Q[a:a + chunk]
+        dx = q[:, None, 0] - P[None, :, 0]
+        dy = q[:, None, 1] - P[None, :, 1]
+        dz = q[:, None, 2] - P[None, :, 2]
+        s = (dx * dx + dy * dy) + dz * dz
+        if exclude is not None:
+            s[np.arange(q.shape[0]), np.asarray(exclude)[a:a + chunk]] = np.inf
+        order = np.lexsort((np.broadcast_to(ar, s.shape), s), axis=-1)[:, :k]
+        idx[a:a + chunk] = order
+        d2[a:a + chunk] = np.take_along_axis(s, order, axis=-1)
+    return idx, d2
+
+
+def knn_bilateral(P, NP, Q, NQ, k: int = 8, sigma: float = 0.025, tau_n: float = 0.8):
+    """k-NN interpolation weights (appendix, point-based interpolator): over
+    the k nearest points x_i of the query q, w~_i = exp(-|q - x_i|^2 / (2 sigma^2))
+    * exp(-(1 - <n_q, n_i>) / tau_n), normalised to sum 1.  Returns
+    (idx nq x k, w nq x k)."""
+    idx, d2 = knn(P, Q, k)
+    NP = np.asarray(NP, np.float64)
+    NQ = np.asarray(NQ, np.float64)
+    nb = NP[idx]                                          # nq x k x 3
+    dot = (NQ[:, None, 0] * nb[..., 0] + NQ[:, None, 1] * nb[..., 1]) + NQ[:, None, 2] * nb[..., 2]
+    wt = np.exp(-d2 / (2.0 * sigma * sigma)) * np.exp(-(1.0 - dot) / tau_n)
+    return idx, wt / wt.sum(axis=1, keepdims=True)
+
+
+def tangent_frame(n):
+    """An orthonormal tangent pair of the unit normal n: e1 = n x a / |n x a|
+    with a the coordinate axis of n's smallest |component| (the first on
+    ties), e2 = n x e1."""
+    n = np.asarray(n, np.float64)
+    ax = int(np.argmin(np.abs(n)))
+    a = np.zeros(3)
+    a[ax] = 1.0
+    e1 = np.cross(n, a)
+    e1 = e1 / math.sqrt(e1 @ e1)
+    return e1, np.cross(n, e1)
+
+
+def local_voronoi(u):
+    """Voronoi cell of the origin among the planar points u (k x 2): the box
+    |x|, |y| <= 2 max|u_j| clipped by each bisector half-plane
+    x . u_j <= |u_j|^2 / 2 in turn (Sutherland-Hodgman).  Returns
+    (length of the cell edge on each bisector (k), cell area, closed: no box
+    edge left).  Points at the origin have no bisector (length 0)."""
+    u = np.asarray(u, np.float64)
+    R = 2.0 * max(float(np.sqrt((u * u).sum(1)).max()), 0.0) if len(u) else 0.0
+    poly = [(-R, -R, -1), (R, -R, -1), (R, R, -1), (-R, R, -1)]   # vertex, tag of the edge leaving it
+    for j, (a, b) in enumerate(u):
+        c = 0.5 * (a * a + b * b)
+        if c == 0.0 or not poly:
+            continue
+        out = []
+        m = len(poly)
+        for i in range(m):
+            px, py, tag = poly[i]
+            qx, qy, _ = poly[(i + 1) % m]
+            fp = px * a + py * b - c
+            fq = qx * a + qy * b - c
+            if fp <= 0.0:
+                out.append((px, py, tag))
+                if fq > 0.0:
+                    s = fp / (fp - fq)
+                    out.append((px + s * (qx - px), py + s * (qy - py), j))
+            elif fq <= 0.0:
+                s = fp / (fp - fq)
+                out.append((px + s * (qx - px), py + s * (qy - py), tag))
+        poly = out
+    lens = np.zeros(len(u))
+    area = 0.0
+    closed = True
+    m = len(poly)
+    for i in range(m):
+        px, py, tag = poly[i]
+        qx, qy, _ = poly[(i + 1) % m]
+        area += px * qy - qx * py
+        if tag >= 0:
+            lens[tag] += math.hypot(qx - px, qy - py)
+        else:
+            closed = False
+    return lens, 0.5 * area, closed
+
+
+def point_laplacian(P, NP, k_nbr: int = 16):
+    """Point-cloud Laplacian (Sec. 4.4, point-based basis): each point's k_nbr
+    nearest other points are projected onto its tangent plane; the Voronoi
+    cell of the point among them gives the dual/primal weight
+    w_ij = |cell edge on the (i, j) bisector| / |u_j| (the cotangent weight
+    of the local Delaunay triangulation) and the cell area.  The dense
+    symmetric Laplacian takes L_ij = -(w_ij + w_ji) / 2 and
+    L_ii = -sum_{j != i} L_ij (ascending j).  Returns (L, cell areas,
+    neighbour indices n x k_nbr, local weights n x k_nbr)."""
+    P = np.asarray(P, np.float64)
+    NP = np.asarray(NP, np.float64)
+    n = P.shape[0]
+    idx, _ = knn(P, P, k_nbr, exclude=np.arange(n))
+    Wl = np.zeros((n, k_nbr))
+    area = np.zeros(n)
+    for i in range(n):
+        e1, e2 = tangent_frame(NP[i])
+        d = P[idx[i]] - P[i]
+        u = np.stack([d @ e1, d @ e2], axis=1)
+        lens, area[i], _ = local_voronoi(u)
+        r = np.sqrt((u * u).sum(1))
+        Wl[i] = np.where(r > 0.0, lens / np.where(r > 0.0, r, 1.0), 0.0)
+    L = np.zeros((n, n))
+    for i in range(n):
+        for s in range(k_nbr):
+            j = idx[i, s]
+            L[i, j] -= 0.5 * Wl[i, s]
+            L[j, i] -= 0.5 * Wl[i, s]
+    np.fill_diagonal(L, 0.0)
+    np.fill_diagonal(L, -L.sum(axis=1))
+    return L, area, idx, Wl
+
+
+def exit_points_ordered(V, F, tri, bary) -> np.ndarray:
+    """Exit positions t = (b0 v0 + b1 v1) + b2 v2 in FP64, the sum in this order."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    T = V[F[np.maximum(tri, 0)]]
+    b = np.asarray(bary, np.float64)
+    return (b[..., 0:1] * T[..., 0, :] + b[..., 1:2] * T[..., 1, :]) + b[..., 2:3] * T[..., 2, :]
+
+
+def face_normals(V, F) -> np.ndarray:
+    """Unit normals (v1 - v0) x (v2 - v0) / |.| of the faces."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    c = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    return c / np.linalg.norm(c, axis=1, keepdims=True)
+
+
+def point_galerkin_lambda(V, F, est: dict, rows, P, NP, exterior: bool = False, origin=None,
+                          killing: bool = False, k: int = 8, sigma: float = 0.025,
+                          tau_n: float = 0.8) -> np.ndarray:
+    """Point-basis Galerkin stiffness (Sec. 4.4 with the boxed estimators): the
+    rows are the points P themselves (walks start at p_r), basis values come
+    from the bilateral k-NN interpolator at both ends (b_s at p_r with normal
+    n_r; b_t at the exit point t with the exit face's normal), and every walk
+    adds w (b_s - b_t)(b_s - b_t)^T with w = omega_r / (2 W) (times |t - o|
+    for exterior walks).  Killing walks (exterior, optional) add
+    4 pi |p_r - o| H0_r / N0 b_s b_s^T at their bin row."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F)
+    P = np.asarray(P, np.float64)
+    NP = np.asarray(NP, np.float64)
+    n = P.shape[0]
+    W = est["walks"]
+    omega = row_weights(est, rows)
+    o = np.zeros(3) if origin is None else np.asarray(origin, np.float64)
+    si, sw = knn_bilateral(P, NP, P, NP, k, sigma, tau_n)
+    fn = face_normals(V, F)
+    L = np.zeros((n, n))
+    for li, r in enumerate(np.asarray(est["row_list"])):
+        tri = est["exit_tri"][li]
+        ok = tri >= 0
+        if not ok.any() or omega[li] == 0:
+            continue
+        t = exit_points_ordered(V, F, tri[ok], est["exit_bary"][li][ok])
+        ti, tw = knn_bilateral(P, NP, t, fn[tri[ok]], k, sigma, tau_n)
+        w = np.full(t.shape[0], 0.5 * omega[li] / W)
+        if exterior:
+            w = w * np.linalg.norm(t - o, axis=1)
+        idx = np.concatenate([np.broadcast_to(si[r], ti.shape), ti], axis=1)
+        val = np.concatenate([np.broadcast_to(sw[r], tw.shape), -tw], axis=1)
+        for a in range(idx.shape[1]):
+            for b in range(idx.shape[1]):
+                np.add.at(L, (idx[:, a], idx[:, b]), w * val[:, a] * val[:, b])
+    if exterior and killing and est["killing_walks"] > 0:
+        N0 = est["killing_walks"]
+        for u in np.flatnonzero(est["H0"]):
+            x = 4 * math.pi * np.linalg.norm(P[u] - o) * est["H0"][u] / N0
+            L[np.ix_(si[u], si[u])] += x * np.outer(sw[u], sw[u])
+    return L
+
+
+# ---------------------------------------------------------------------------
 # closed forms (pins)
 # ---------------------------------------------------------------------------
 

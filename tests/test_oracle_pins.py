@@ -709,3 +709,144 @@ def test_naive_estimator_is_unbiased_for_linear_functions(oracle):
         terms = rows["area"][:, None] * fs[:, None] * (fs[:, None] - P @ f3) / (W * h)
         se = math.sqrt(terms.shape[0] * W * terms.var())
         assert abs(got - ref) < 5 * se + 1e-3 * abs(ref), (got, ref, se)
+
+
+# ---------------------------------------------------------------------------
+# point-based Galerkin basis (Sec. 4.4; appendix "Point-based k-NN Interpolator")
+# ---------------------------------------------------------------------------
+
+def _fibonacci_sphere(n):
+    i = np.arange(n) + 0.5
+    z = 1 - 2 * i / n
+    r = np.sqrt(1 - z * z)
+    ph = i * math.pi * (3 - math.sqrt(5))
+    return np.stack([r * np.cos(ph), r * np.sin(ph), z], 1)
+
+
+def test_knn_matches_kdtree(oracle):
+    """Brute-force k nearest points = scipy's k-d tree (distinct distances),
+    and the self-exclusion drops exactly the query's own point."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(0)
+    P = rng.standard_normal((700, 3))
+    Q = rng.standard_normal((300, 3))
+    idx, d2 = oracle.knn(P, Q, 8)
+    dd, jj = cKDTree(P).query(Q, 8)
+    assert np.array_equal(idx, jj)
+    assert np.abs(np.sqrt(d2) - dd).max() <= 1e-14
+    idx, _ = oracle.knn(P, P, 5, exclude=np.arange(700))
+    _, jj = cKDTree(P).query(P, 6)
+    assert np.array_equal(idx, jj[:, 1:])
+    # equal distances: the smaller index first
+    G = np.array([[1.0, 0, 0], [0, 1.0, 0], [-1.0, 0, 0], [0, -1.0, 0], [3.0, 0, 0]])
+    idx, _ = oracle.knn(G[::-1].copy(), np.zeros((1, 3)), 4)
+    assert list(idx[0]) == [1, 2, 3, 4]
+
+
+def test_bilateral_weights_special_cases(oracle):
+    """The interpolator's weights sum to one; they are uniform when both
+    falloffs are switched off and when the neighbours are equidistant with one
+    normal; a point at distance sigma weighs e^(-1/2) against one at the query,
+    and an opposite normal e^(-2/tau_n) against an aligned one (the scales of
+    the two factors); with a tiny sigma the query's own point takes it all."""
+    rng = np.random.default_rng(1)
+    P = rng.standard_normal((200, 3))
+    NP = rng.standard_normal((200, 3))
+    NP /= np.linalg.norm(NP, axis=1, keepdims=True)
+    Q = rng.standard_normal((50, 3))
+    NQ = NP[:50]
+    idx, w = oracle.knn_bilateral(P, NP, Q, NQ, 8, 0.5, 0.8)
+    assert np.abs(w.sum(1) - 1).max() <= 1e-15 * 8
+    _, w = oracle.knn_bilateral(P, NP, Q, NQ, 8, 1e8, 1e16)
+    assert np.abs(w - 1 / 8).max() <= 1e-12
+    ang = 2 * math.pi * np.arange(6) / 6
+    ring = np.stack([np.cos(ang), np.sin(ang), np.zeros(6)], 1)
+    up = np.tile([0, 0, 1.0], (6, 1))
+    _, w = oracle.knn_bilateral(ring, up, np.zeros((1, 3)), up[:1], 6, 0.3, 0.8)
+    assert np.abs(w - 1 / 6).max() <= 1e-15
+    sig = 0.2
+    two = np.array([[0, 0, 0], [sig, 0, 0]], float)
+    _, w = oracle.knn_bilateral(two, up[:2], np.zeros((1, 3)), up[:1], 2, sig, 0.8)
+    assert abs(w[0, 1] / w[0, 0] - math.exp(-0.5)) <= 1e-15
+    sym = np.array([[1.0, 0, 0], [-1.0, 0, 0]])
+    nrm = np.array([[0, 0, 1.0], [0, 0, -1.0]])
+    _, w = oracle.knn_bilateral(sym, nrm, np.zeros((1, 3)), nrm[:1], 2, 1.0, 0.8)
+    assert abs(w[0, 1] / w[0, 0] - math.exp(-2 / 0.8)) <= 1e-15
+    idx, w = oracle.knn_bilateral(P, NP, P[:20], NP[:20], 8, 1e-3, 0.8)
+    assert np.array_equal(idx[:, 0], np.arange(20)) and np.abs(w[:, 0] - 1).max() <= 1e-15
+
+
+def test_point_laplacian_is_the_planar_voronoi_dual(oracle):
+    """On a jittered planar grid (one normal) every inner point's local cell is
+    its Voronoi cell: the areas and the weights |Voronoi edge| / |x_i - x_j|
+    equal scipy's Voronoi diagram, and L reproduces linear functions."""
+    from scipy.spatial import ConvexHull, Voronoi
+    rng = np.random.default_rng(0)
+    g = 14
+    xy = np.stack(np.meshgrid(np.arange(g), np.arange(g), indexing="ij"), -1).reshape(-1, 2) * 0.1
+    xy = xy + rng.uniform(-0.03, 0.03, xy.shape)
+    P = np.concatenate([xy, np.zeros((len(xy), 1))], 1)
+    L, area, _, _ = oracle.point_laplacian(P, np.tile([0, 0, 1.0], (len(P), 1)), 16)
+    vor = Voronoi(xy)
+    inner = {i for i in range(len(xy)) if 3 <= i // g < g - 3 and 3 <= i % g < g - 3}
+    nchk = 0
+    for i in inner:
+        A = ConvexHull(vor.vertices[vor.regions[vor.point_region[i]]]).volume
+        assert abs(A - area[i]) <= 1e-12 * A
+    for (a, b), rv in zip(vor.ridge_points, vor.ridge_vertices):
+        if a in inner and b in inner and -1 not in rv:
+            ratio = np.linalg.norm(vor.vertices[rv[0]] - vor.vertices[rv[1]]) / np.linalg.norm(xy[a] - xy[b])
+            assert abs(-L[a, b] - ratio) <= 1e-12 * max(ratio, 1.0)
+            nchk += 1
+    assert nchk > 150
+    assert np.array_equal(L, L.T)
+    ii = sorted(inner)
+    for f in (P[:, 0], P[:, 1], 0.3 * P[:, 0] - 2.0 * P[:, 1]):
+        assert np.abs((L @ f)[ii]).max() <= 1e-12 * np.abs(L).max()
+    assert np.abs(L.sum(1)).max() <= 1e-12 * np.abs(L).max()
+
+
+def test_point_laplacian_sphere_spectrum(oracle):
+    """800 Fibonacci points on the unit sphere, normals = positions, mass
+    4 pi / n: the generalised eigenvalues approach l (l + 1) with
+    multiplicities 1, 3, 5, 7 (to 2%: the O(h^2) discretisation error at
+    h^2 ~ 4 pi / n)."""
+    import scipy.linalg as sl
+    n = 800
+    S = _fibonacci_sphere(n)
+    L, area, _, _ = oracle.point_laplacian(S, S, 16)
+    assert abs(area.sum() - 4 * math.pi) < 0.01 * 4 * math.pi
+    ev = sl.eigh(L, np.diag(np.full(n, 4 * math.pi / n)), eigvals_only=True)[:16]
+    assert abs(ev[0]) < 1e-10
+    for lo, hi, l in ((1, 4, 1), (4, 9, 2), (9, 16, 3)):
+        assert np.abs(ev[lo:hi] - l * (l + 1)).max() < 0.02 * l * (l + 1)
+
+
+def test_point_galerkin_lambda_properties(oracle):
+    """Point-basis Galerkin matrix on the unit icosphere (face sample rows as
+    the point set, W = 64): symmetric positive semidefinite, constants in its
+    null space (both interpolators are partitions of unity), and the Rayleigh
+    quotient of z near the cap-corrected l = 1 value (Funk-Hecke); exterior
+    walks (origin at the centre, with killing walks) keep the same
+    structure."""
+    m = meshgen.icosphere(2)
+    rows = oracle.fps_rows(m.V, m.F, m.nf, orient=False)
+    lam = oracle.sphere_eigs_cap(1, 2.5, 1.0)
+    est = oracle.estimate(m.V, m.F, rows, 64, 1e-3, seed=2, record_exits=True)
+    L = oracle.point_galerkin_lambda(m.V, m.F, est, rows, rows["pos"], rows["nrm"], sigma=0.1)
+    sc = np.abs(L).max()
+    assert np.abs(L - L.T).max() <= 1e-14 * sc
+    assert np.abs(L.sum(1)).max() <= 1e-13 * sc
+    assert np.linalg.eigvalsh(L).min() >= -1e-13 * sc
+    z = rows["pos"][:, 2]
+    assert abs((z @ L @ z) / np.sum(rows["area"] * z * z) - lam[1]) < 0.12 * lam[1]
+    est = oracle.estimate(m.V, m.F, rows, 64, 1e-3, exterior=True, origin=np.zeros(3), seed=2, record_exits=True,
+                          killing_walks=4096)
+    Le = oracle.point_galerkin_lambda(m.V, m.F, est, rows, rows["pos"], rows["nrm"], exterior=True,
+                                      origin=np.zeros(3), killing=True, sigma=0.1)
+    assert np.abs(Le - Le.T).max() <= 1e-14 * np.abs(Le).max()
+    assert np.linalg.eigvalsh(Le).min() >= -1e-13 * np.abs(Le).max()
+    # exterior of the unit sphere: the constant is not in the null space (the
+    # killing walks carry it: l = 0 exterior eigenvalue 1)
+    one = np.ones(len(z))
+    assert (one @ Le @ one) / rows["area"].sum() > 0.5
