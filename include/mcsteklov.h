@@ -432,6 +432,68 @@ mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row
 mcs_status mcs_galerkin_modes(const double *S, int K, int k, const double *Phi, int n, double *evals, double *coeffs,
                               double *psi, void *stream);
 
+/* mcs_galerkin_project: S = Phi^T Lambda Phi (device K x K FP64) for any
+ * symmetric device n x n FP64 Lambda (e.g. the point-basis matrix of
+ * mcs_point_galerkin_lambda) and device n x K FP64 Phi; K a multiple of 16 in
+ * [16, 160], n >= 16.  Lambda Phi runs on the tensor cores (split tf32,
+ * FP32-level accuracy).  workspace: device, 256-byte aligned,
+ * >= mcs_galerkin_project_workspace_size(n, K) (0 for invalid sizes).
+ * Synchronises `stream`. */
+size_t mcs_galerkin_project_workspace_size(int n, int K);
+mcs_status mcs_galerkin_project(const double *Lambda, const double *Phi, int n, int K, double *S, void *workspace,
+                                size_t workspace_bytes, void *stream);
+
+/* Point-based Galerkin basis (Sec. 4.4 "Point-based Galerkin basis";
+ * appendix "Point-based k-NN Interpolator").  P: device n_points x 3 FP64
+ * surface points (e.g. farthest-point sample rows), NP: their unit normals
+ * (device n_points x 3).  Each call builds a uniform grid over P in its
+ * workspace (device, 256-byte aligned, >= mcs_points_workspace_size(n_points))
+ * and synchronises `stream` once (to read the grid's size); the rest is
+ * asynchronous on `stream`.  All FP64.
+ *
+ * mcs_point_knn: the k (1..32) nearest points of each query Q (device
+ * n_queries x 3): squared distances ((dx dx + dy dy) + dz dz), d = q - p,
+ * ascending, equal distances by the smaller index (exact and reproducible).
+ * exclude_self = 1 (queries = the points) skips each query's own point.
+ * Outputs (each optional, at least one): idx device n_queries x k int32, d2
+ * device n_queries x k, w device n_queries x k bilateral weights
+ * (needs NP, NQ = the query normals, sigma, tau_n > 0):
+ * w_i proportional to exp(-|q - x_i|^2 / (2 sigma^2)) exp(-(1 - <n_q, n_i>) / tau_n),
+ * normalised to sum 1 (the paper's values: sigma 0.025, tau_n 0.8, k 8).
+ *
+ * mcs_point_laplacian: the point-cloud Laplacian.  Each point's k_nbr
+ * (3..32, < n_points) nearest other points are projected on its tangent plane
+ * (frame e1 = n x a / |n x a|, a the axis of n's smallest |component|,
+ * e2 = n x e1); the Voronoi cell of the point among them (a box of half-size
+ * 2 max |u_j| cut by the bisector half-planes) gives the weight
+ * w_ij = |cell edge on the (i, j) bisector| / |u_j|.  L (device n x n,
+ * overwritten): L_ij = -(w_ij + w_ji) / 2, L_ii = -sum_{j != i} L_ij.
+ * nbr / nbr_w (device n x k_nbr): the neighbours and their local weights;
+ * cell_area (optional, device n): the local cell areas.
+ *
+ * mcs_point_galerkin_lambda: the Galerkin matrix over the points (device
+ * n_points x n_points, overwritten) from an estimate whose rows were the
+ * points themselves (row r starts at P[r]) with exit_tri / exit_bary
+ * recorded: sum over walks of w (b_s - b_t)(b_s - b_t)^T, b_s the
+ * interpolator at P[r] (normal NP[r]), b_t at the exit point (normal of the
+ * exit face), w = omega_r / (2 W), times |t - o| for an exterior estimate
+ * (origin host 3 doubles).  Killing walks (exterior, H0 with killing_walks >
+ * 0, optional) add 4 pi |P[r] - o| H0[r] / N0 b_s b_s^T.  FP64 atomics
+ * (reproducible to rounding).  Its smallest generalised eigenpairs with the
+ * point areas give Phi for mcs_galerkin_project. */
+size_t mcs_points_workspace_size(int n_points);
+mcs_status mcs_point_knn(const double *P, const double *NP, int n_points, const double *Q, const double *NQ,
+                         int n_queries, int k, double sigma, double tau_n, int exclude_self, int32_t *idx, double *w,
+                         double *d2, void *workspace, size_t workspace_bytes, void *stream);
+mcs_status mcs_point_laplacian(const double *P, const double *NP, int n_points, int k_nbr, double *L,
+                               double *cell_area, int32_t *nbr, double *nbr_w, void *workspace,
+                               size_t workspace_bytes, void *stream);
+mcs_status mcs_point_galerkin_lambda(mcs_mesh m, const double *P, const double *NP, int n_points,
+                                     const double *omega, const int32_t *exit_tri, const double *exit_bary,
+                                     int walks_per_row, int exterior, const double *origin, const int32_t *H0,
+                                     long long killing_walks, int k, double sigma, double tau_n, double *Lambda_P,
+                                     void *workspace, size_t workspace_bytes, void *stream);
+
 /* Steklov heat (Sec. 5, Eq. steklovHeat, solved in the eigenbasis by Eq.
  * spectralSteklovHeat): for each time t and each channel column of u0,
  *   u_t = sum_j exp(-lambda_j t) a_j psi_j,  a_j = psi_j^T M u_0,

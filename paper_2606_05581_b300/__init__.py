@@ -145,6 +145,15 @@ def lib():
         L.mcs_steklov_heat_workspace_size.restype = C.c_size_t
         L.mcs_steklov_heat.argtypes = [vp, vp, vp, i32, i32, vp, i32, vp, i32, vp, vp, C.c_size_t, vp]
         L.mcs_hks.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp]
+        L.mcs_galerkin_project_workspace_size.argtypes = [i32, i32]
+        L.mcs_galerkin_project_workspace_size.restype = C.c_size_t
+        L.mcs_galerkin_project.argtypes = [vp, vp, i32, i32, vp, vp, C.c_size_t, vp]
+        L.mcs_points_workspace_size.argtypes = [i32]
+        L.mcs_points_workspace_size.restype = C.c_size_t
+        L.mcs_point_knn.argtypes = [vp, vp, i32, vp, vp, i32, i32, dbl, dbl, i32, vp, vp, vp, vp, C.c_size_t, vp]
+        L.mcs_point_laplacian.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, C.c_size_t, vp]
+        L.mcs_point_galerkin_lambda.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, i32, C.POINTER(C.c_double), vp,
+                                                i64, i32, dbl, dbl, vp, vp, C.c_size_t, vp]
         L.mcs_tc_symm_product_workspace_size.argtypes = [i32, i32]
         L.mcs_tc_symm_product_workspace_size.restype = C.c_size_t
         L.mcs_tc_symm_product.argtypes = [vp, vp, i32, i32, vp, vp, C.c_size_t, vp]
@@ -580,6 +589,97 @@ def galerkin_modes(S: torch.Tensor, k: int, Phi: "torch.Tensor | None" = None):
         psi = torch.empty((n, k), dtype=torch.float64, device=S.device)
     _check(lib().mcs_galerkin_modes(_ptr(S), K, k, _ptr(Phi), n, _ptr(ev), _ptr(Cm), _ptr(psi), _stream()))
     return ev, Cm, psi
+
+
+def galerkin_project(Lam: torch.Tensor, Phi: torch.Tensor, workspace: "Workspace | None" = None) -> torch.Tensor:
+    """S = Phi^T Lam Phi (K x K FP64) for a symmetric n x n Lam (tensor-core product)."""
+    Lam = Lam.to(torch.float64).contiguous()
+    P = Phi.to(torch.float64).contiguous()
+    n, K = int(P.shape[0]), int(P.shape[1])
+    S = torch.empty((K, K), dtype=torch.float64, device=P.device)
+    nb = int(lib().mcs_galerkin_project_workspace_size(n, K))
+    if nb == 0:
+        raise MCSError("galerkin_project: need n >= 16 and K a multiple of 16 in [16, 160]")
+    ws = (workspace or Workspace()).get(nb)
+    _check(lib().mcs_galerkin_project(_ptr(Lam), _ptr(P), n, K, _ptr(S), C.c_void_p(_aligned_ptr(ws)), nb,
+                                      _stream()))
+    return S
+
+
+# point-based Galerkin basis (Sec. 4.4; appendix "Point-based k-NN Interpolator")
+KNN_K, KNN_SIGMA, KNN_TAU = 8, 0.025, 0.8
+
+
+def _points_ws(n: int, workspace):
+    nb = int(lib().mcs_points_workspace_size(n))
+    return nb, (workspace or Workspace()).get(nb)
+
+
+def point_knn(P: torch.Tensor, NP: "torch.Tensor | None", Q: torch.Tensor, NQ: "torch.Tensor | None" = None,
+              k: int = KNN_K, sigma: float = KNN_SIGMA, tau_n: float = KNN_TAU, exclude_self: bool = False,
+              weights: bool = True, workspace: "Workspace | None" = None):
+    """The k nearest points of P to each query of Q (exact FP64 distances, ties
+    by index) and, with weights, the bilateral interpolation weights (needs the
+    point normals NP and query normals NQ).  Returns (idx, w or None, d2)."""
+    P = P.to(torch.float64).contiguous()
+    Q = Q.to(torch.float64).contiguous()
+    n, nq = int(P.shape[0]), int(Q.shape[0])
+    dev = P.device
+    idx = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((nq, k), dtype=torch.float64, device=dev)
+    w = torch.empty((nq, k), dtype=torch.float64, device=dev) if weights else None
+    NPc = NP.to(torch.float64).contiguous() if NP is not None else None
+    NQc = NQ.to(torch.float64).contiguous() if NQ is not None else None
+    nb, ws = _points_ws(n, workspace)
+    _check(lib().mcs_point_knn(_ptr(P), _ptr(NPc), n, _ptr(Q), _ptr(NQc), nq, k, float(sigma), float(tau_n),
+                               int(exclude_self), _ptr(idx), _ptr(w), _ptr(d2), C.c_void_p(_aligned_ptr(ws)), nb,
+                               _stream()))
+    return idx, w, d2
+
+
+def point_laplacian(P: torch.Tensor, NP: torch.Tensor, k_nbr: int = 16, workspace: "Workspace | None" = None):
+    """Point-cloud Laplacian from local tangent-plane Voronoi cells (dense
+    n x n FP64).  Returns (L, cell_area, nbr, nbr_w)."""
+    P = P.to(torch.float64).contiguous()
+    NP = NP.to(torch.float64).contiguous()
+    n = int(P.shape[0])
+    dev = P.device
+    L = torch.empty((n, n), dtype=torch.float64, device=dev)
+    area = torch.empty(n, dtype=torch.float64, device=dev)
+    nbr = torch.empty((n, k_nbr), dtype=torch.int32, device=dev)
+    nbw = torch.empty((n, k_nbr), dtype=torch.float64, device=dev)
+    nb, ws = _points_ws(n, workspace)
+    _check(lib().mcs_point_laplacian(_ptr(P), _ptr(NP), n, k_nbr, _ptr(L), _ptr(area), _ptr(nbr), _ptr(nbw),
+                                     C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return L, area, nbr, nbw
+
+
+def point_basis(rows: dict, K: int, k_nbr: int = 16, workspace: "Workspace | None" = None):
+    """The point-based Galerkin basis: the K lowest generalised eigenvectors of
+    the point-cloud Laplacian with the rows' areas as the mass (M-orthonormal,
+    n x K).  Returns (Phi, evals, eig stats)."""
+    L, _, _, _ = point_laplacian(rows["pos"], rows["nrm"], k_nbr, workspace)
+    ev, Phi, st = steklov_modes(L, rows["area"], K)
+    return Phi, ev, st
+
+
+def point_galerkin_lambda(mesh: Mesh, rows: dict, res: dict, exterior: bool = False, killing_walks: int = 0,
+                          k: int = KNN_K, sigma: float = KNN_SIGMA, tau_n: float = KNN_TAU,
+                          workspace: "Workspace | None" = None) -> torch.Tensor:
+    """Point-basis Galerkin matrix (n_rows x n_rows FP64) of an estimate whose
+    rows are the points (recorded with record_exits and record_bary)."""
+    P = rows["pos"].to(torch.float64).contiguous()
+    NP = rows["nrm"].to(torch.float64).contiguous()
+    n = int(P.shape[0])
+    Lp = torch.empty((n, n), dtype=torch.float64, device=P.device)
+    origin = (C.c_double * 3)(*res["stats"]["origin"])
+    H0 = res.get("H0") if (exterior and killing_walks > 0) else None
+    nb, ws = _points_ws(n, workspace)
+    _check(lib().mcs_point_galerkin_lambda(mesh.handle, _ptr(P), _ptr(NP), n, _ptr(res["omega"]),
+                                           _ptr(res["exit_tri"]), _ptr(res["exit_bary"]), int(res["walks"]),
+                                           int(exterior), origin, _ptr(H0), int(killing_walks), k, float(sigma),
+                                           float(tau_n), _ptr(Lp), C.c_void_p(_aligned_ptr(ws)), nb, _stream()))
+    return Lp
 
 
 def steklov_heat(evals: torch.Tensor, evecs: torch.Tensor, mass: torch.Tensor, u0: torch.Tensor,

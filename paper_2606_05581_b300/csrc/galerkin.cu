@@ -375,6 +375,32 @@ mcs_status mcs_galerkin_dtn(mcs_mesh m, const mcs_rows *rows, const int32_t *row
     return MCS_OK;
 }
 
+size_t mcs_galerkin_project_workspace_size(int n, int K) {
+    if (n < 16 || K < 16 || K > 160 || (K % 16)) return 0;
+    return layout(n, K, false).total;
+}
+
+mcs_status mcs_galerkin_project(const double *Lambda, const double *Phi, int n, int K, double *S, void *workspace,
+                                size_t workspace_bytes, void *stream) {
+    MCS_ARG(Lambda && Phi && S, "mcs_galerkin_project: NULL argument");
+    MCS_ARG(K >= 16 && K <= 160 && K % 16 == 0, "mcs_galerkin_project: K must be a multiple of 16 in [16, 160]");
+    MCS_ARG(n >= 16, "mcs_galerkin_project: need n >= 16");
+    const Layout l = layout(n, K, false);
+    MCS_ARG(workspace && workspace_bytes >= l.total, "mcs_galerkin_project: workspace too small");
+    MCS_ARG(((uintptr_t)workspace & 255) == 0, "mcs_galerkin_project: workspace must be 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    char *w = (char *)workspace;
+    double *Xt = (double *)(w + l.Xt), *Zt = (double *)(w + l.Zt);
+    note_launch();
+    k_transpose<<<(unsigned)(((size_t)n * K + 255) / 256), 256, 0, st>>>(Phi, n, K, Xt);
+    mcs_status s = mcs_tc_symm_product(Lambda, Xt, n, K, Zt, w + l.tc, mcs_tc_symm_product_workspace_size(n, K), stream);
+    if (s != MCS_OK) return s;
+    note_launch();
+    k_project_S<<<dim3(K, K), 256, 0, st>>>(Zt, Phi, n, K, S);
+    MCS_CUDA(cudaGetLastError());
+    return MCS_OK;
+}
+
 mcs_status mcs_galerkin_modes(const double *S, int K, int k, const double *Phi, int n, double *evals, double *coeffs,
                               double *psi, void *stream) {
     MCS_ARG(S && evals, "mcs_galerkin_modes: NULL argument");
