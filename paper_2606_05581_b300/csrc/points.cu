@@ -449,8 +449,8 @@ size_t mcs_points_workspace_size(int n_points) {
 mcs_status mcs_point_knn(const double *P, const double *NP, int n_points, const double *Q, const double *NQ,
                          int n_queries, int k, double sigma, double tau_n, int exclude_self, int32_t *idx, double *w,
                          double *d2, void *workspace, size_t workspace_bytes, void *stream) {
-    MCS_ARG(P && Q && (idx || w || d2), "mcs_point_knn: NULL argument");
     MCS_ARG(n_points >= 1 && n_queries >= 0, "mcs_point_knn: need n_points >= 1");
+    MCS_ARG(P && (n_queries == 0 || (Q && (idx || w || d2))), "mcs_point_knn: NULL argument");
     MCS_ARG(k >= 1 && k <= kMaxK && k <= n_points - (exclude_self ? 1 : 0), "mcs_point_knn: need 1 <= k <= 32 and k <= the candidates");
     MCS_ARG(!exclude_self || n_queries == n_points, "mcs_point_knn: exclude_self needs the points as the queries");
     MCS_ARG(!w || (NP && NQ && sigma > 0.0 && tau_n > 0.0), "mcs_point_knn: weights need both normals and sigma, tau_n > 0");
