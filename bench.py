@@ -247,7 +247,8 @@ def _downstream(mcs, out, dev, reps=5):
 def _galerkin(mcs, V, F, params, ws, kill, k):
     """Untimed by the headline: the Galerkin estimator on the same walks
     (exit barycentrics recorded), K = k + 32 cotangent-Laplacian modes as the
-    basis; each phase timed with CUDA events after one warm-up."""
+    basis, and the point-based basis (Sec. 4.4) on the same walks; each phase
+    timed with CUDA events after one warm-up."""
     import torch
     mesh = mcs.Mesh(V, F)
     vrows = mcs.vertex_rows(mesh)
@@ -269,9 +270,21 @@ def _galerkin(mcs, V, F, params, ws, kill, k):
     gal_ms, S = clock(lambda: mcs.galerkin_dtn(mesh, vrows, res, Phi, exterior=True, killing_walks=kill, workspace=gws))
     modes_ms, (ev, _, _) = clock(lambda: mcs.galerkin_modes(S, k))
     walks = int(res["exit_tri"].numel())
+    # the point-based basis on the same walks: the vertex rows as the points,
+    # sigma = the mean point spacing sqrt(area / n), tau_n and k the paper's
+    sigma = float(torch.sqrt(vrows["area"].sum() / vrows["area"].numel()))
+    pws = mcs.Workspace()
+    pb_ms, (PhiP, _, pst) = clock(lambda: mcs.point_basis(vrows, K, workspace=pws), 1)
+    pl_ms, Lp = clock(lambda: mcs.point_galerkin_lambda(mesh, vrows, res, exterior=True, killing_walks=kill,
+                                                        sigma=sigma, workspace=pws))
+    pp_ms, SP = clock(lambda: mcs.galerkin_project(Lp, PhiP, workspace=gws))
+    pev, _, _ = mcs.galerkin_modes(SP, k)
+    point = {"points": int(vrows["area"].numel()), "sigma": sigma, "tau_n": mcs.KNN_TAU, "knn": mcs.KNN_K,
+             "basis_ms": pb_ms, "lambda_ms": pl_ms, "project_ms": pp_ms, "basis_status": pst["status"],
+             "walks_per_s": walks / (pl_ms / 1e3), "evals_head": [round(float(x), 4) for x in pev[:8].cpu()]}
     return {"K": K, "basis_ms": basis_ms, "galerkin_dtn_ms": gal_ms, "modes_ms": modes_ms,
             "walks": walks, "walks_per_s": walks / (gal_ms / 1e3), "basis_status": est["status"],
-            "evals_head": [round(float(x), 4) for x in ev[:8].cpu()]}
+            "evals_head": [round(float(x), 4) for x in ev[:8].cpu()], "point_basis": point}
 
 
 def run_variance(args, rank, world):
