@@ -309,6 +309,10 @@ __global__ void k_combine(const float *P, int splits, int m, int n, int n_pad, d
     }
 }
 
+// The FP64 products below (Gram, Cholesky, triangular inverse, block times)
+// are bound by B300's FP64 rate, so their multiply-adds are explicit fma()
+// (one instruction, one rounding); the library is otherwise built without
+// contraction.
 // Gp[q][a][b] = sum_{i in chunk q} A[a][i] B[b][i] (FP64): 32 x 32 output
 // tiles per block, the n dimension split into chunks across blockIdx.z
 constexpr int kGramChunks = 16;
@@ -329,7 +333,7 @@ __global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, 
         for (int q = 0; q < 4; q++) {
             const int r = ty + 8 * q;
             double s = 0.0;
-            for (int t = 0; t < 32; t++) s += sa[r][t] * sb[tx][t];
+            for (int t = 0; t < 32; t++) s = fma(sa[r][t], sb[tx][t], s);
             acc[q] += s;
         }
         __syncthreads();
@@ -383,7 +387,7 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
         const int w = m - j - 1;
         for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
             const int a = j + 1 + e / w, b = j + 1 + e % w;
-            if (b >= a) sg[a * m + b] -= sg[j * m + a] * sg[j * m + b];
+            if (b >= a) sg[a * m + b] = fma(-sg[j * m + a], sg[j * m + b], sg[a * m + b]);
         }
         __syncthreads();
     }
@@ -401,7 +405,7 @@ __global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
     for (int i = m - 1; i >= 0; i--) {
         double s = 0.0;
         if (i < c)
-            for (int k = i + 1 + lane; k <= c; k += 32) s += R[i * m + k] * Rinv[k * m + c];
+            for (int k = i + 1 + lane; k <= c; k += 32) s = fma(R[i * m + k], Rinv[k * m + c], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
         if (lane == 0) Rinv[i * m + c] = i > c ? 0.0 : ((i == c ? 1.0 : 0.0) - s) / R[i * m + i];
         __syncwarp();
@@ -431,7 +435,7 @@ __global__ void k_block_times(const double *C, const double *In, int m, int n_pa
     for (int k = 0; k < m; k++) {
         const double x = In[(size_t)k * n_pad + i];
 #pragma unroll
-        for (int jj = 0; jj < kJG; jj++) acc[jj] += sc[k * kJG + jj] * x;
+        for (int jj = 0; jj < kJG; jj++) acc[jj] = fma(sc[k * kJG + jj], x, acc[jj]);
     }
 #pragma unroll
     for (int jj = 0; jj < kJG; jj++)

@@ -168,6 +168,8 @@ __global__ void k_project_S(const double *Zt, const double *Phi, int n, int K, d
 // columns of C in the same order.  Stops when the off-diagonal mass is below
 // 1e-24 of the total (off-diagonal norm 1e-12 relative: eigenvalue errors of
 // order its square over the gaps) or after max_sweeps.
+// (the rotations' multiply-adds are explicit fma(): this kernel is bound by
+// one SM's FP64 rate)
 constexpr int kJacThreads = 256;
 __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K, int max_sweeps, double *ev,
                                                           double *C) {
@@ -238,11 +240,11 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
                 if (p == q) continue;
                 const double c = cs[i], s = sn[i];
                 const double ap = A[row * ld + p], aq = A[row * ld + q];
-                A[row * ld + p] = c * ap - s * aq;
-                A[row * ld + q] = s * ap + c * aq;
+                A[row * ld + p] = fma(c, ap, -s * aq);
+                A[row * ld + q] = fma(s, ap, c * aq);
                 const double qp = Q[(size_t)p * K + row], qv = Q[(size_t)q * K + row];
-                Q[(size_t)p * K + row] = c * qp - s * qv;
-                Q[(size_t)q * K + row] = s * qp + c * qv;
+                Q[(size_t)p * K + row] = fma(c, qp, -s * qv);
+                Q[(size_t)q * K + row] = fma(s, qp, c * qv);
             }
             __syncthreads();
             // rows p, q of A
@@ -252,8 +254,8 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
                 if (p == q) continue;
                 const double c = cs[i], s = sn[i];
                 const double ap = A[p * ld + col], aq = A[q * ld + col];
-                A[p * ld + col] = c * ap - s * aq;
-                A[q * ld + col] = s * ap + c * aq;
+                A[p * ld + col] = fma(c, ap, -s * aq);
+                A[q * ld + col] = fma(s, ap, c * aq);
             }
             __syncthreads();
         }
