@@ -522,25 +522,29 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
                 cs[i] = c; sn[i] = sv;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
-                const int i = e / m, row = e % m;
+            // one warp per pair, lanes over rows (no index division; the
+            // padded rows keep the column accesses on distinct banks)
+            for (int i = warp; i < half; i += nwarps) {
                 const int p = pp[i], q = qq[i];
                 const float c = cs[i], sv = sn[i];
-                const float hp = H[row * ld + p], hq = H[row * ld + q];
-                H[row * ld + p] = c * hp - sv * hq;
-                H[row * ld + q] = sv * hp + c * hq;
-                const float vp = V[row * ld + p], vq = V[row * ld + q];
-                V[row * ld + p] = c * vp - sv * vq;
-                V[row * ld + q] = sv * vp + c * vq;
+                for (int row = lane; row < m; row += 32) {
+                    const float hp = H[row * ld + p], hq = H[row * ld + q];
+                    H[row * ld + p] = c * hp - sv * hq;
+                    H[row * ld + q] = sv * hp + c * hq;
+                    const float vp = V[row * ld + p], vq = V[row * ld + q];
+                    V[row * ld + p] = c * vp - sv * vq;
+                    V[row * ld + q] = sv * vp + c * vq;
+                }
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < half * m; e += blockDim.x) {
-                const int i = e / m, col = e % m;
+            for (int i = warp; i < half; i += nwarps) {
                 const int p = pp[i], q = qq[i];
                 const float c = cs[i], sv = sn[i];
-                const float hp = H[p * ld + col], hq = H[q * ld + col];
-                H[p * ld + col] = c * hp - sv * hq;
-                H[q * ld + col] = sv * hp + c * hq;
+                for (int col = lane; col < m; col += 32) {
+                    const float hp = H[p * ld + col], hq = H[q * ld + col];
+                    H[p * ld + col] = c * hp - sv * hq;
+                    H[q * ld + col] = sv * hp + c * hq;
+                }
             }
             __syncthreads();
         }
@@ -823,7 +827,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
                                     nullptr, nullptr, Z);
         gram(X, Z, 1);
         note_launch();
-        k_jacobi<<<1, 512, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
+        k_jacobi<<<1, 1024, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
         note_launch();
         k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
         note_launch();

@@ -234,28 +234,31 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi64(const double *S, int K
             }
             __syncthreads();
             // columns p, q of A and Q
-            for (int e = threadIdx.x; e < half * K; e += blockDim.x) {
-                const int i = e / K, row = e % K;
+            // one warp per pair, lanes over rows (no index division)
+            for (int i = warp; i < half; i += kJacThreads / 32) {
                 const int p = pp[i], q = qq[i];
                 if (p == q) continue;
                 const double c = cs[i], s = sn[i];
-                const double ap = A[row * ld + p], aq = A[row * ld + q];
-                A[row * ld + p] = fma(c, ap, -s * aq);
-                A[row * ld + q] = fma(s, ap, c * aq);
-                const double qp = Q[(size_t)p * K + row], qv = Q[(size_t)q * K + row];
-                Q[(size_t)p * K + row] = fma(c, qp, -s * qv);
-                Q[(size_t)q * K + row] = fma(s, qp, c * qv);
+                for (int row = lane; row < K; row += 32) {
+                    const double ap = A[row * ld + p], aq = A[row * ld + q];
+                    A[row * ld + p] = fma(c, ap, -s * aq);
+                    A[row * ld + q] = fma(s, ap, c * aq);
+                    const double qp = Q[(size_t)p * K + row], qv = Q[(size_t)q * K + row];
+                    Q[(size_t)p * K + row] = fma(c, qp, -s * qv);
+                    Q[(size_t)q * K + row] = fma(s, qp, c * qv);
+                }
             }
             __syncthreads();
             // rows p, q of A
-            for (int e = threadIdx.x; e < half * K; e += blockDim.x) {
-                const int i = e / K, col = e % K;
+            for (int i = warp; i < half; i += kJacThreads / 32) {
                 const int p = pp[i], q = qq[i];
                 if (p == q) continue;
                 const double c = cs[i], s = sn[i];
-                const double ap = A[p * ld + col], aq = A[q * ld + col];
-                A[p * ld + col] = fma(c, ap, -s * aq);
-                A[q * ld + col] = fma(s, ap, c * aq);
+                for (int col = lane; col < K; col += 32) {
+                    const double ap = A[p * ld + col], aq = A[q * ld + col];
+                    A[p * ld + col] = fma(c, ap, -s * aq);
+                    A[q * ld + col] = fma(s, ap, c * aq);
+                }
             }
             __syncthreads();
         }
