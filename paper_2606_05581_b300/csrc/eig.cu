@@ -382,12 +382,13 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
         }
         d = sqrt(d);
         __syncthreads();
-        for (int c = j + threadIdx.x; c < m; c += blockDim.x) sg[j * m + c] = c == j ? d : sg[j * m + c] / d;
+        const double inv = 1.0 / d;
+        for (int c = j + threadIdx.x; c < m; c += blockDim.x) sg[j * m + c] = c == j ? d : sg[j * m + c] * inv;
         __syncthreads();
-        const int w = m - j - 1;
-        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-            const int a = j + 1 + e / w, b = j + 1 + e % w;
-            if (b >= a) sg[a * m + b] = fma(-sg[j * m + a], sg[j * m + b], sg[a * m + b]);
+        // trailing upper triangle: one warp per row a, lanes over b >= a
+        for (int a = j + 1 + (int)(threadIdx.x >> 5); a < m; a += (int)(blockDim.x >> 5)) {
+            const double ra = sg[j * m + a];
+            for (int b = a + (int)(threadIdx.x & 31); b < m; b += 32) sg[a * m + b] = fma(-ra, sg[j * m + b], sg[a * m + b]);
         }
         __syncthreads();
     }
@@ -397,19 +398,25 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
     }
 }
 
-// Rinv = R^-1 for upper-triangular R: one warp per column c, back
-// substitution with the inner products reduced across the warp
+// Rinv = R^-1 for upper-triangular R (m <= 160): one warp per column c (eight
+// per block of 256 threads), back substitution with the column held in
+// shared memory and the inner products reduced across the warp
 __global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (c >= m) return;
-    for (int i = m - 1; i >= 0; i--) {
+    __shared__ double colv[8][160];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + wl;
+    if (wl >= 8 || c >= m) return;
+    double *x = colv[wl];
+    for (int i = lane; i < m; i += 32) x[i] = 0.0;
+    __syncwarp();
+    for (int i = c; i >= 0; i--) {
         double s = 0.0;
-        if (i < c)
-            for (int k = i + 1 + lane; k <= c; k += 32) s = fma(R[i * m + k], Rinv[k * m + c], s);
+        for (int k = i + 1 + lane; k <= c; k += 32) s = fma(R[i * m + k], x[k], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) Rinv[i * m + c] = i > c ? 0.0 : ((i == c ? 1.0 : 0.0) - s) / R[i * m + i];
+        if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - s) / R[i * m + i];
         __syncwarp();
     }
+    for (int i = lane; i < m; i += 32) Rinv[i * m + c] = x[i];
 }
 __global__ void k_f32_to_f64(const float *a, int n, double *b) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
