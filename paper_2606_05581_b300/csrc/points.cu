@@ -369,15 +369,36 @@ __global__ void k_point_assemble(GridView V, const double *Vm, const int32_t *F,
     bilateral(NP, fn[0], fn[1], fn[2], k, sigma, tau, bd, bi, tw);
     const int32_t *si = sidx + (size_t)r * k;
     const double *sv = sw + (size_t)r * k;
+    // the upper triangle only (k_mirror copies it down): pair (a, b), a < b,
+    // adds w d_a d_b at (min, max) of its two points, twice on the diagonal
+    // when both entries name the same point
     for (int a = 0; a < 2 * k; a++) {
         const int ia = a < k ? si[a] : bi[a - k];
-        const double va = a < k ? sv[a] : -tw[a - k];
-        for (int b = 0; b < 2 * k; b++) {
+        const double wa = w * (a < k ? sv[a] : -tw[a - k]);
+        atomicAdd(&L[(size_t)ia * n + ia], wa * (a < k ? sv[a] : -tw[a - k]));
+        for (int b = a + 1; b < 2 * k; b++) {
             const int ib = b < k ? si[b] : bi[b - k];
-            const double vb = b < k ? sv[b] : -tw[b - k];
-            const double x = w * va * vb;
-            if (x != 0.0) atomicAdd(&L[(size_t)ia * n + ib], x);
+            const double x = wa * (b < k ? sv[b] : -tw[b - k]);
+            if (ia == ib) atomicAdd(&L[(size_t)ia * n + ia], 2.0 * x);
+            else atomicAdd(&L[(size_t)min(ia, ib) * n + max(ia, ib)], x);
         }
+    }
+}
+
+// lower triangle = upper triangle (32 x 32 tiles through shared memory)
+__global__ void k_mirror(int n, double *L) {
+    __shared__ double t[32][33];
+    const int bx = blockIdx.x, by = blockIdx.y;
+    if (bx < by) return;  // tile (by, bx) in the upper part feeds tile (bx, by)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = by * 32 + r, j = bx * 32 + tx;
+        t[r][tx] = (i < n && j < n) ? L[(size_t)i * n + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bx * 32 + r, j = by * 32 + tx;  // lower element (i, j) = upper (j, i)
+        if (i < n && j < n && i > j) L[(size_t)i * n + j] = t[tx][r];
     }
 }
 
@@ -388,10 +409,13 @@ __global__ void k_point_killing(const double *P, int n, const int32_t *H0, doubl
     if (r >= n || H0[r] == 0) return;
     const double d0 = P[3 * r] - o0, d1 = P[3 * r + 1] - o1, d2 = P[3 * r + 2] - o2;
     const double x = 12.566370614359172 * sqrt(d0 * d0 + d1 * d1 + d2 * d2) * H0[r] / n_kill;
-    for (int a = 0; a < k; a++)
-        for (int b = 0; b < k; b++)
-            atomicAdd(&L[(size_t)sidx[(size_t)r * k + a] * n + sidx[(size_t)r * k + b]],
-                      x * sw[(size_t)r * k + a] * sw[(size_t)r * k + b]);
+    const int32_t *si = sidx + (size_t)r * k;
+    const double *sv = sw + (size_t)r * k;
+    for (int a = 0; a < k; a++) {
+        atomicAdd(&L[(size_t)si[a] * n + si[a]], x * sv[a] * sv[a]);
+        for (int b = a + 1; b < k; b++)  // distinct points: one neighbour list
+            atomicAdd(&L[(size_t)min(si[a], si[b]) * n + max(si[a], si[b])], x * sv[a] * sv[b]);
+    }
 }
 
 // build the grid of P in the workspace; returns the view the queries use
@@ -508,6 +532,9 @@ mcs_status mcs_point_galerkin_lambda(mcs_mesh m, const double *P, const double *
         k_point_killing<<<(n_points + 127) / 128, 128, 0, st>>>(P, n_points, H0, (double)killing_walks, o0, o1, o2,
                                                                 k, sidx, sw, Lambda_P);
     }
+    note_launch();
+    const unsigned nt = (unsigned)((n_points + 31) / 32);
+    k_mirror<<<dim3(nt, nt), 256, 0, st>>>(n_points, Lambda_P);
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
 }
