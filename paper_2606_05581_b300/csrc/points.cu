@@ -39,7 +39,7 @@ constexpr int kMaxPoly = 4 + kMaxK;
 
 struct Grid {
     double lo[3];
-    double h;
+    double h, inv_h;
     int g[3];
     int n;
 };
@@ -108,12 +108,13 @@ __global__ void k_grid(const double *P, int n, long long cap, Grid *G) {
         h = hn;
     }
     G->h = h;
+    G->inv_h = 1.0 / h;
     for (int a = 0; a < 3; a++) G->g[a] = (int)(floor(ext[a] / h) + 1.0);
     G->n = n;
 }
 
-__device__ __forceinline__ int cell_coord(double x, double lo, double h, int g) {
-    const double f = floor((x - lo) / h);
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv_h, int g) {
+    const double f = floor((x - lo) * inv_h);
     return f < 0.0 ? 0 : (f > (double)(g - 1) ? g - 1 : (int)f);
 }
 
@@ -121,9 +122,9 @@ __global__ void k_keys(const double *P, int n, const Grid *G, unsigned long long
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Grid g = *G;
-    const int cx = cell_coord(P[3 * i], g.lo[0], g.h, g.g[0]);
-    const int cy = cell_coord(P[3 * i + 1], g.lo[1], g.h, g.g[1]);
-    const int cz = cell_coord(P[3 * i + 2], g.lo[2], g.h, g.g[2]);
+    const int cx = cell_coord(P[3 * i], g.lo[0], g.inv_h, g.g[0]);
+    const int cy = cell_coord(P[3 * i + 1], g.lo[1], g.inv_h, g.g[1]);
+    const int cz = cell_coord(P[3 * i + 2], g.lo[2], g.inv_h, g.g[2]);
     const unsigned long long c = ((unsigned long long)cz * g.g[1] + cy) * g.g[0] + cx;
     keys[i] = (c << 32) | (unsigned)i;
 }
@@ -154,8 +155,8 @@ __device__ __forceinline__ bool before(double a, int ia, double b, int ib) { ret
 // returns how many were found (k unless the set is smaller)
 __device__ int knn_query(const GridView &V, double qx, double qy, double qz, int k, int skip, double *bd, int *bi) {
     const Grid &g = V.g;
-    const int c[3] = {cell_coord(qx, g.lo[0], g.h, g.g[0]), cell_coord(qy, g.lo[1], g.h, g.g[1]),
-                      cell_coord(qz, g.lo[2], g.h, g.g[2])};
+    const int c[3] = {cell_coord(qx, g.lo[0], g.inv_h, g.g[0]), cell_coord(qy, g.lo[1], g.inv_h, g.g[1]),
+                      cell_coord(qz, g.lo[2], g.inv_h, g.g[2])};
     const double q[3] = {qx, qy, qz};
     int cnt = 0;
     const int smax = max(g.g[0], max(g.g[1], g.g[2]));
@@ -207,10 +208,11 @@ __device__ int knn_query(const GridView &V, double qx, double qy, double qz, int
 __device__ void bilateral(const double *NP, double nx, double ny, double nz, int k, double sigma, double tau,
                           const double *bd, const int *bi, double *w) {
     double amin = INFINITY;
+    const double is = 1.0 / (2.0 * sigma * sigma), it = 1.0 / tau;  // reciprocals: FP64 divisions are costly here
     for (int i = 0; i < k; i++) {
         const double *m = NP + 3 * bi[i];
         const double dot = nx * m[0] + ny * m[1] + nz * m[2];
-        w[i] = bd[i] / (2.0 * sigma * sigma) + (1.0 - dot) / tau;
+        w[i] = bd[i] * is + (1.0 - dot) * it;
         amin = fmin(amin, w[i]);
     }
     double sum = 0.0;
@@ -218,7 +220,8 @@ __device__ void bilateral(const double *NP, double nx, double ny, double nz, int
         w[i] = exp(-(w[i] - amin));
         sum += w[i];
     }
-    for (int i = 0; i < k; i++) w[i] /= sum;
+    const double inv = 1.0 / sum;
+    for (int i = 0; i < k; i++) w[i] *= inv;
 }
 
 __global__ void k_knn(GridView V, const double *NP, const double *Q, const double *NQ, int nq, int k, double sigma,
@@ -362,7 +365,8 @@ __global__ void k_point_assemble(GridView V, const double *Vm, const int32_t *F,
                  v2 = Vm[3 * tv[2] + 2] - Vm[3 * tv[0] + 2];
     double fn[3] = {u1 * v2 - u2 * v1, u2 * v0 - u0 * v2, u0 * v1 - u1 * v0};
     const double fl = sqrt(fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
-    for (int a = 0; a < 3; a++) fn[a] = fl > 0.0 ? fn[a] / fl : 0.0;
+    const double ifl = fl > 0.0 ? 1.0 / fl : 0.0;
+    for (int a = 0; a < 3; a++) fn[a] *= ifl;
     double bd[kMaxK], tw[kMaxK];
     int bi[kMaxK];
     knn_query(V, p[0], p[1], p[2], k, -1, bd, bi);
