@@ -149,7 +149,12 @@ struct GridView {
     const double *Ps;
 };
 
-__device__ __forceinline__ bool before(double a, int ia, double b, int ib) { return a < b || (a == b && ia < ib); }
+// (d2, index) order; squared distances are never negative, so their bit
+// patterns order like the values and the comparison stays off the FP64 pipe
+__device__ __forceinline__ bool before(double a, int ia, double b, int ib) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return x < y || (x == y && ia < ib);
+}
 
 // the k nearest points of q (skipping point `skip`), ascending (d2, index);
 // returns how many were found (k unless the set is smaller)
