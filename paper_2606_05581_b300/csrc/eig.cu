@@ -399,10 +399,13 @@ __global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, 
 }
 
 // Rinv = R^-1 for upper-triangular R (m <= 160): one warp per column c (eight
-// per block of 256 threads), back substitution with the column held in
-// shared memory and the inner products reduced across the warp
+// per block of 256 threads), back substitution with R's upper triangle and
+// the columns in shared memory and the inner products reduced across the warp
 __global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
+    extern __shared__ double sr[];  // m x m (upper triangle used)
     __shared__ double colv[8][160];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sr[e] = R[e];
+    __syncthreads();
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * 8 + wl;
     if (wl >= 8 || c >= m) return;
@@ -411,9 +414,9 @@ __global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
     __syncwarp();
     for (int i = c; i >= 0; i--) {
         double s = 0.0;
-        for (int k = i + 1 + lane; k <= c; k += 32) s = fma(R[i * m + k], x[k], s);
+        for (int k = i + 1 + lane; k <= c; k += 32) s = fma(sr[i * m + k], x[k], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - s) / R[i * m + i];
+        if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - s) / sr[i * m + i];
         __syncwarp();
     }
     for (int i = lane; i < m; i += 32) Rinv[i * m + c] = x[i];
@@ -738,6 +741,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
     const size_t smm = (size_t)m * m * sizeof(double);
     MCS_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    MCS_CUDA(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
     const size_t jsm = 2 * (size_t)m * (m + 1) * sizeof(float);
     MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
     cudaStream_t st = c.st;
@@ -775,7 +779,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
             note_launch();
             k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
             note_launch();
-            k_tri_inverse<<<(m + 7) / 8, 256, 0, st>>>(c.w.R, m, c.w.Rinv);
+            k_tri_inverse<<<(m + 7) / 8, 256, smm, st>>>(c.w.R, m, c.w.Rinv);
             note_launch();
             k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T);
             std::swap(X, T);
