@@ -344,9 +344,16 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
  * passes rows, parameters and outputs as for mcs_estimate_dtn.
  *  - Estimates whose scratch (mcs_estimate_workspace_size) exceeds
  *    mcs_estimate_dtn_noalloc_capacity() bytes are rejected with MCS_ERR_ARG.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before capturing a stream.
+ *  - CUDA loads a library's code and device arrays lazily, at first use, and
+ *    loading reserves device memory.  mcs_build_bvh (which allocates the
+ *    mesh anyway) therefore loads this array and every kernel the estimate
+ *    launches on the current device, so that a call on a mesh built earlier
+ *    in the same CUDA context allocates nothing.  Each call looks up the
+ *    array's device address (cudaGetSymbolAddress) with the mesh's device
+ *    current; make the first call before capturing a stream.
+ *  - The walks run in the caller's row order (queue_order bit 0 is set): the
+ *    Z-order schedule would need a library sort.  The results are those of
+ *    mcs_estimate_dtn, which do not depend on the schedule.
  *  - All calls share the one array, which keeps the last call's contents;
  *    every part the estimate reads is rewritten or cleared by the call itself.
  *    Calls that overlap on the GPU (other streams, other threads) race on it:

@@ -47,6 +47,11 @@ int num_sms();
 // kernels of this library enqueued since it was loaded (mcs_launch_count)
 extern std::atomic<unsigned long long> g_launches;
 inline void note_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// load (CUDA loads code lazily) every kernel of a one-mesh estimate
+mcs_status preload_estimate_kernels();
+// load the allocation-free estimate's scratch array and the estimate's
+// kernels on the current device; called by mesh creation, which allocates anyway
+mcs_status noalloc_prepare();
 }  // namespace mcs
 
 #define MCS_CUDA(call)                                                      \

@@ -508,6 +508,10 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     for (void *p : tmp) cudaFree(p);
     tmp.clear();
 #undef MB_CUDA
+    // mesh creation may allocate: load here what the allocation-free
+    // estimate needs, so that it loads (and allocates) nothing itself; a
+    // failure here only surfaces when that entry point is called
+    (void)noalloc_prepare();
     *out = m;
     return MCS_OK;
 }

@@ -8,8 +8,6 @@
 // runs the same estimator with its scratch taken from one fixed array that
 // the library reserves in device memory when it is loaded, so the call itself
 // allocates nothing.
-#include <mutex>
-
 #include "mcs_internal.h"
 
 namespace {
@@ -19,32 +17,29 @@ namespace {
 constexpr size_t kNoAllocBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_ptr[kMaxDevices] = {};
-
-// device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol's name as a device address)
+// device address of the scratch array in the current CUDA context (host
+// code cannot use the symbol's name as a device address).  Looked up on
+// every call, so that a new context (after cudaDeviceReset) never sees a
+// stale address; once the module is loaded the lookup allocates nothing.
 mcs_status scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return mcs::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        mcs::set_error("mcs_estimate_dtn_noalloc: device index out of range");
-        return MCS_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return mcs::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_ptr[dev] = p;
-    }
-    *out = g_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return mcs::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
     return MCS_OK;
 }
 
 }  // namespace
+
+// called by mesh creation (which allocates anyway) on the current device:
+// loading noalloc.cu's module reserves the scratch array, and the estimate's
+// kernels are loaded too, so that the entry point below loads nothing
+mcs_status mcs::noalloc_prepare() {
+    void *p = nullptr;
+    const mcs_status s = scratch_address(&p);
+    if (s != MCS_OK) return s;
+    return mcs::preload_estimate_kernels();
+}
 
 extern "C" {
 
@@ -64,9 +59,13 @@ mcs_status mcs_estimate_dtn_noalloc(mcs_mesh m, const mcs_rows *rows, const mcs_
     void *scratch = nullptr;
     const mcs_status s = scratch_address(&scratch);
     if (s != MCS_OK) return s;
-    // phase timing would create CUDA events; keep this call free of them
+    // phase timing would create CUDA events; keep this call free of them.
+    // The walks run in the caller's row order: the Z-order schedule needs a
+    // library sort whose kernels depend on the size; the results do not
+    // depend on the schedule (counter-based walks, exact argmin)
     mcs_params q = *p;
     q.timing = 0;
+    q.queue_order |= 1;
     return mcs_estimate_dtn(m, rows, &q, out, scratch, kNoAllocBytes, stats, stream);
 }
 

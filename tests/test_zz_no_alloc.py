@@ -33,6 +33,8 @@ def _outputs(R, W):
 
 @pytest.mark.parametrize("exterior", [False, True])
 def test_noalloc_matches_regular_estimate_twice(exterior):
+    """Two calls in a row give the regular estimate's hit counts, Lambda, H0
+    and step count, and neither changes the device's free memory."""
     m = meshgen.two_spheres(2, 0.5, 1.5) if exterior else meshgen.icosphere(3)
     mesh = mcs.Mesh(m.V, m.F)
     rows = mcs.vertex_rows(mesh)
@@ -46,8 +48,12 @@ def test_noalloc_matches_regular_estimate_twice(exterior):
     Lref = ref["Lambda"].cpu().numpy()
     for _ in range(2):  # the fixed scratch keeps the previous call's contents
         o = _outputs(R, W)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = mcs.estimate_dtn_noalloc(mesh, rows, p, o)
         torch.cuda.synchronize()
+        # the call reserved no device memory (its code and scratch were loaded with the mesh)
+        assert torch.cuda.mem_get_info()[0] == free0
         o["cap"] = min(W, R)
         H = mcs.dense_hist(o, R).cpu().numpy()
         assert np.array_equal(H, Href)
