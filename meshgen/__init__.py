@@ -239,15 +239,24 @@ def wild_union(n_prims: int = 300, target_faces: int = 2_000_000, seed: int = 0,
     return Mesh(V, F, f"wild union n_prims={n_prims} seed={seed}")
 
 
+def batch_mesh_params(i: int, seed0: int = 1000, faces_range=(5_000, 200_000), prims_range=(1, 50)):
+    """(faces, primitives, min_faces) of mesh i of a batch: F_i ~
+    log-uniform(faces_range), n_prims ~ U{prims_range}, both from seed seed0 + i."""
+    rng = np.random.default_rng(seed0 + i)
+    nf = int(round(math.exp(rng.uniform(math.log(faces_range[0]), math.log(faces_range[1])))))
+    npr = int(rng.integers(prims_range[0], prims_range[1] + 1))
+    return nf, npr, max(20, min(200, nf // (2 * npr)))
+
+
+def batch_mesh(i: int, seed0: int = 1000, faces_range=(5_000, 200_000), prims_range=(1, 50)) -> Mesh:
+    """Mesh i of a batch: a wild union with the batch's face count and
+    primitive count for i, generated with seed seed0 + i."""
+    nf, npr, min_faces = batch_mesh_params(i, seed0, faces_range, prims_range)
+    return wild_union(npr, nf, seed0 + i, min_faces=min_faces)
+
+
 def batch_meshes(n: int = 512, seed0: int = 1000, faces_range=(5_000, 200_000),
                  prims_range=(1, 50)) -> list:
     """``n`` wild unions; mesh i has F_i ~ log-uniform(faces_range),
     n_prims ~ U{prims_range} and seed seed0 + i."""
-    out = []
-    for i in range(n):
-        rng = np.random.default_rng(seed0 + i)
-        nf = int(round(math.exp(rng.uniform(math.log(faces_range[0]), math.log(faces_range[1])))))
-        npr = int(rng.integers(prims_range[0], prims_range[1] + 1))
-        min_faces = max(20, min(200, nf // (2 * npr)))
-        out.append(wild_union(npr, nf, seed0 + i, min_faces=min_faces))
-    return out
+    return [batch_mesh(i, seed0, faces_range, prims_range) for i in range(n)]

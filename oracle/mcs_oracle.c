@@ -118,6 +118,9 @@ typedef struct {
                              /* by q = A J^B / M; 2 naive inset (Alg. 1): one */
                              /* uniform WoS step from s - inset n, no cap     */
     double inset;            /* start_mode 2: inset distance h                */
+    int walk_limit;          /* > 0: simulate only walks j < walk_limit of    */
+                             /* each listed row (counters still use W); the   */
+                             /* other exit records are -1                     */
 } orc_problem;
 
 typedef struct {
@@ -812,7 +815,10 @@ int orc_estimate(const orc_problem *pb, orc_result *res)
         const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
         const float nf3[3] = {(float)nb[0], (float)nb[1], (float)nb[2]};
         const float rf = (float)rho;
-        for (int j = 0; j < pb->walks; j++) {
+        const int nwalk = pb->walk_limit > 0 && pb->walk_limit < pb->walks ? pb->walk_limit : pb->walks;
+        if (res->exit_tri)
+            for (int j = nwalk; j < pb->walks; j++) res->exit_tri[(size_t)li * pb->walks + j] = -1;
+        for (int j = 0; j < nwalk; j++) {
             uint64_t g = (uint64_t)v * (uint64_t)pb->walks + (uint64_t)j;
             uint64_t gp = g - (uint64_t)(j & 1);
             int capped = 0, lost = 0, bin;
@@ -1094,6 +1100,7 @@ double orc_gwn(const double *V, const int32_t *F, int nf, const double q[3])
  * the inside across the face: keep n when GWN'(x - delta n) > GWN'(x +
  * delta n), delta = sqrt(area_f)/4, flip it otherwise. */
 void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int orient,
+                  const int32_t *orient_list, int n_orient,
                   int32_t *sel, double *pos, double *nrm, double *area, int32_t *tri2bin)
 {
     (void)nv;
@@ -1118,16 +1125,29 @@ void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int
      * centroids (reading R16): the squared distance is ((dx dx + dy dy) + dz dz)
      * in float; a face's owner is the first sample strictly nearest; the next
      * sample is the face with the largest distance, lowest face id on ties */
+    /* the faces are split into contiguous ranges over the threads; each
+     * range's first maximum, then the largest value, lowest face on ties:
+     * the same choice as one ascending scan */
     sel[0] = 0;
     for (int i = 0; i < ns; i++) {
         const float *q = cenf + 3 * sel[i];
         int arg = 0;
         float best = -1.0f;
-        for (int f = 0; f < nf; f++) {
-            float d[3] = {cenf[3 * f] - q[0], cenf[3 * f + 1] - q[1], cenf[3 * f + 2] - q[2]};
-            float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (d2 < mind[f]) { mind[f] = d2; tri2bin[f] = i; }
-            if (mind[f] > best) { best = mind[f]; arg = f; }
+        #pragma omp parallel
+        {
+            int targ = 0;
+            float tbest = -1.0f;
+            #pragma omp for schedule(static)
+            for (int f = 0; f < nf; f++) {
+                float d[3] = {cenf[3 * f] - q[0], cenf[3 * f + 1] - q[1], cenf[3 * f + 2] - q[2]};
+                float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (d2 < mind[f]) { mind[f] = d2; tri2bin[f] = i; }
+                if (mind[f] > tbest) { tbest = mind[f]; targ = f; }
+            }
+            #pragma omp critical
+            {
+                if (tbest > best || (tbest == best && targ < arg)) { best = tbest; arg = targ; }
+            }
         }
         if (i + 1 < ns) sel[i + 1] = arg;
     }
@@ -1145,7 +1165,12 @@ void orc_fps_rows(const double *V, int nv, const int32_t *F, int nf, int ns, int
         double l = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
         double n[3];
         for (int k = 0; k < 3; k++) { n[k] = l > 0.0 ? N[k] / l : 0.0; pos[3 * i + k] = cen[3 * f + k]; }
-        if (orient && l > 0.0) {
+        int want = orient;
+        if (orient && orient_list) {
+            want = 0;
+            for (int k = 0; k < n_orient; k++) want |= orient_list[k] == i;
+        }
+        if (want && l > 0.0) {
             double delta = 0.25 * sqrt(far_[f]);
             double qi[3], qo[3];
             for (int k = 0; k < 3; k++) { qi[k] = cen[3 * f + k] - delta * n[k]; qo[k] = cen[3 * f + k] + delta * n[k]; }

@@ -56,7 +56,8 @@ class _Problem(C.Structure):
                 ("origin", C.c_double * 3), ("seed", C.c_uint64), ("cap_deg", C.c_double),
                 ("bisect_iters", C.c_int), ("kappa", C.c_double), ("max_steps", C.c_int),
                 ("rho_min_factor", C.c_double), ("prec", C.c_int), ("n_threads", C.c_int),
-                ("killing_walks", C.c_longlong), ("start_mode", C.c_int), ("inset", C.c_double)]
+                ("killing_walks", C.c_longlong), ("start_mode", C.c_int), ("inset", C.c_double),
+                ("walk_limit", C.c_int)]
 
 
 class _Result(C.Structure):
@@ -84,7 +85,7 @@ def lib():
         _lib.orc_vertex_rows.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
         _lib.orc_fps_rows.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
-                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.orc_gwn.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         _lib.orc_gwn.restype = C.c_double
         _lib.orc_gwn_skip.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
@@ -163,15 +164,17 @@ def vertex_rows(V, F):
     return dict(pos=pos, nrm=nrm, area=area, tri2bin=None, kind="vertex")
 
 
-def fps_rows(V, F, n: int, orient: bool = True):
-    """Rows = farthest-point samples over face centroids (start at face 0)."""
+def fps_rows(V, F, n: int, orient: bool = True, orient_rows=None):
+    """Rows = farthest-point samples over face centroids (start at face 0).
+    orient_rows: orient only these rows (the others keep the face normal)."""
     V = np.ascontiguousarray(V, np.float64)
     F = np.ascontiguousarray(F, np.int32)
     nf = F.shape[0]
     sel = np.zeros(n, np.int32); pos = np.zeros((n, 3)); nrm = np.zeros((n, 3)); area = np.zeros(n)
     t2b = np.zeros(nf, np.int32)
-    lib().orc_fps_rows(_p(V), V.shape[0], _p(F), nf, n, int(orient), _p(sel), _p(pos), _p(nrm), _p(area),
-                       _p(t2b))
+    ol = None if orient_rows is None else np.ascontiguousarray(orient_rows, np.int32)
+    lib().orc_fps_rows(_p(V), V.shape[0], _p(F), nf, n, int(orient), _p(ol), 0 if ol is None else len(ol),
+                       _p(sel), _p(pos), _p(nrm), _p(area), _p(t2b))
     return dict(pos=pos, nrm=nrm, area=area, tri2bin=t2b, sel=sel, kind="sample")
 
 
@@ -216,6 +219,7 @@ def _problem(V, F, rows, walks, eps, exterior, origin, seed, prec, row_list, n_t
     pb.killing_walks = killing_walks
     pb.start_mode = int(prm.get("start_mode", 0))
     pb.inset = float(prm.get("inset", 0.0))
+    pb.walk_limit = int(prm.get("walk_limit", 0))
     return pb, keep
 
 
