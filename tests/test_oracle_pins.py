@@ -850,3 +850,95 @@ def test_point_galerkin_lambda_properties(oracle):
     # killing walks carry it: l = 0 exterior eigenvalue 1)
     one = np.ones(len(z))
     assert (one @ Le @ one) / rows["area"].sum() > 0.5
+
+
+# --------------------------------------------------------------------------- inversion centre (Sec. 4.3)
+def _gwn_numpy(V, F, q):
+    """Generalized winding number (Jacobson et al. 2013) at q: the signed solid
+    angles of the triangles (van Oosterom and Strackee 1983) over 4 pi."""
+    a, b, c = (V[F[:, k]] - q for k in range(3))
+    la, lb, lc = (np.linalg.norm(x, axis=1) for x in (a, b, c))
+    det = np.einsum("ij,ij->i", a, np.cross(b, c))
+    den = (la * lb * lc + np.einsum("ij,ij->i", a, b) * lc + np.einsum("ij,ij->i", b, c) * la
+           + np.einsum("ij,ij->i", c, a) * lb)
+    return float(np.sum(2.0 * np.arctan2(det, den)) / (4.0 * math.pi))
+
+
+@pytest.mark.parametrize("which", ["two_spheres", "wild"])
+def test_interior_origin_lies_inside_the_shape(oracle, which):
+    """The Kelvin transform needs its centre inside Omega (Sec. 4.3: 0 in Omega by
+    translation).  The chosen centre (reading R14: the centre of the largest interior
+    tangent ball of a strided row subset) has winding number >= 1 (inside at least one
+    component of a union), a positive empty radius, and that radius is its distance to
+    the surface.  On two spheres (vertex rows) it lies inside one of them; on a union
+    of thin and overlapping primitives the rows are farthest-point sample rows, the
+    row kind of the exterior batch meshes (vertex rows, with their relative slack,
+    can reach through a feature thinner than kappa r_max: reading R1)."""
+    if which == "two_spheres":
+        m = meshgen.two_spheres(3, 0.5, 1.5)
+        rows = oracle.vertex_rows(m.V, m.F)
+    else:
+        m = meshgen.wild_union(8, 8000, seed=3, flip_frac=0.0)
+        rows = oracle.fps_rows(m.V, m.F, 1024, orient=True)
+    o = oracle.interior_origin(m.V, m.F, rows)
+    st = oracle.origin_stride(len(rows["pos"]))
+    sub = dict(pos=np.ascontiguousarray(rows["pos"][::st]), nrm=np.ascontiguousarray(rows["nrm"][::st]),
+               tri2bin=rows.get("tri2bin"))
+    _, c, rho = oracle.tangent_balls(m.V, m.F, sub)
+    assert rho.max() > 0
+    d2, _, _ = oracle.closest_points(m.V, m.F, o[None], 64)
+    assert abs(math.sqrt(d2[0]) - rho.max()) <= 1e-12 * rho.max()
+    assert _gwn_numpy(m.V, m.F, o) > 0.99
+    if which == "two_spheres":
+        assert min(np.linalg.norm(o), np.linalg.norm(o - np.array([1.5, 0, 0]))) < 0.5 - rho.max() * 0.5
+
+
+# --------------------------------------------------------------------------- sample rows (reading R16)
+def test_fps_float_selection_equals_fp64_selection_until_a_near_tie(oracle):
+    """Farthest-point sampling in FP64 (numpy, the greedy definition) picks the same
+    faces as the oracle's single-precision sampling up to the first step whose two best
+    FP64 candidates lie within single-precision rounding of each other; on this mesh
+    that step comes late or never."""
+    m = meshgen.wild_union(6, 5000, seed=9)
+    n = 300
+    r = oracle.fps_rows(m.V, m.F, n, orient=False)
+    cen = ((m.V[m.F[:, 0]] + m.V[m.F[:, 1]]) + m.V[m.F[:, 2]]) / 3.0
+    mind = np.full(m.nf, np.inf)
+    sel = [0]
+    agree = n
+    for i in range(n - 1):
+        mind = np.minimum(mind, np.sum((cen - cen[sel[-1]]) ** 2, 1))
+        top2 = np.partition(mind, -2)[-2:]
+        nxt = int(np.argmax(mind))
+        if nxt != r["sel"][i + 1]:
+            # a disagreement is allowed only at a near tie of the FP64 distances
+            assert top2[1] - top2[0] <= 1e-5 * top2[1], (i + 1, top2)
+            agree = i + 1
+            break
+        sel.append(nxt)
+    assert agree >= 100
+
+
+# --------------------------------------------------------------------------- vertex rows under refinement (reading R1)
+def test_vertex_row_rayleigh_quotients_converge_under_refinement(oracle):
+    """Vertex rows of the unit icosphere (the small sphere workload at subdivision 2,
+    then 3 and 4): the Rayleigh quotients f' Lambda f / f' M f of the l = 1 and l = 2
+    harmonics (linear in Lambda, so unbiased in the walk count) approach the
+    cap-corrected closed form lambda_l(theta0).  The excess tracks the jump mass times
+    the depth r - rho of the vertex above its empty ball, which falls like h^2: it must
+    shrink by more than half per subdivision and be below 12% at subdivision 4."""
+    lam = oracle.sphere_eigs_cap(2, 2.5)
+    gaps = []
+    for s in (2, 3, 4):
+        m = meshgen.icosphere(s)
+        rows = oracle.vertex_rows(m.V, m.F)
+        est = oracle.estimate(m.V, m.F, rows, 32, 1e-3, seed=0)
+        L = oracle.assemble(est, rows)
+        P = m.V
+        g = []
+        for l, f in ((1, P[:, 2]), (1, P[:, 0]), (2, P[:, 0] ** 2 - P[:, 1] ** 2), (2, P[:, 0] * P[:, 1])):
+            g.append((f @ L @ f) / (f @ (rows["area"] * f)) / lam[l] - 1.0)
+        gaps.append(float(np.mean(g)))
+    assert gaps[0] > 0 and gaps[1] > 0 and gaps[2] > 0
+    assert gaps[1] < 0.5 * gaps[0] and gaps[2] < 0.5 * gaps[1], gaps
+    assert gaps[2] < 0.12, gaps
