@@ -3,7 +3,7 @@
 One step = the whole hot path on one synthetic workload.  Workloads
 (--workload):
 
-  two_spheres_s4_exterior (default)  two icosphere-s4 spheres (R = 0.5,
+  two_spheres_s4_exterior  two icosphere-s4 spheres (R = 0.5,
       centres 1.5 apart; 5124 vertices, 10240 triangles), exterior estimator
       with killing walks (N0 = 64 W), FP32 walks, W = 1024 per vertex,
       eps = 1e-3, k = 64 Steklov pairs.  Step: BVH build, vertex rows,
@@ -11,11 +11,13 @@ One step = the whole hot path on one synthetic workload.  Workloads
   wild_2m   a ~2.0M-face union of 300 ellipsoids / tori (noise, flipped
       faces, slivers), 10,000 farthest-point sample rows, W = 4096, FP32,
       interior, k = 64.  Same step with sample rows instead of vertex rows.
-  batch     --meshes (512) unions with 5k-200k faces each (mesh i: seed
-      1000 + i, exterior when i is odd), 1024 sample rows x 512 walks each,
-      FP32, autotuned launch; step = one replay of the graph-captured batched
-      estimate (all meshes' setup, ONE persistent walk launch, histograms,
-      assembly).  BVH builds and sample rows are preprocessing, timed apart.
+  batch (default)  --meshes (512) unions with 5k-200k faces each (mesh i:
+      seed 1000 + i, exterior when i is odd), 1024 sample rows x 512 walks
+      each, FP32, killing walks 64 W on exterior meshes, autotuned launch;
+      step = one replay of the graph-captured batched estimate (all meshes'
+      setup, ONE persistent walk launch, histograms, assembly).  BVH builds
+      and sample rows are preprocessing, timed apart; the end-to-end figure
+      includes them with the host copies in and every Lambda out.
   precision FP32 vs FP64 walks on the two-sphere mesh at W = 1024, 4096,
       16384 (4 seeds each), k = 128, against an FP64 W = 65536 reference;
       per-eigenvalue errors, their standard errors and walks/s.
@@ -49,10 +51,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walk steps/s and DtN rows/s at fixed walks/row; FP32-batched vs FP64-plain at equal error"
 UNIT = "walk steps/s"
-# FP32 operations (add, mul, min, max, compare) of one BVH node visit (two
-# child boxes) and one point-triangle test on the interior-region path
-OPS_PER_NODE = 36
-OPS_PER_TRI = 90
 
 
 WORKLOADS = ("two_spheres_s4_exterior", "wild_2m", "batch", "precision", "variance")
@@ -143,64 +141,47 @@ def _peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
-WALK_SOURCES = ("paper_2606_05581_b300/csrc/estimate.cu", "paper_2606_05581_b300/csrc/mcs_device.cuh",
-                "paper_2606_05581_b300/csrc/mcs_internal.h", "paper_2606_05581_b300/build.py")
+# Algorithmic work of one closest-point query (one walk step), per unit of
+# the traversal (the scope table's measurement row): each visited node reads
+# its children's boxes, 32 B each (binary node: 2, four-wide node: 4), and
+# costs ~12 FP32 operations per box; each tested triangle reads 36 B (three
+# FP32 vertices) and costs ~70 operations; the step itself (Philox block,
+# direction, update) ~25 operations.
+BOX_BYTES, TRI_BYTES = 32, 36
+OPS_PER_BOX, OPS_PER_TRI, OPS_PER_STEP = 12, 70, 25
 
 
-def walk_source_digest() -> str:
-    """sha256 over the files that make the walk kernel (sources and build flags)."""
-    import hashlib
-    h = hashlib.sha256()
-    root = os.path.dirname(os.path.abspath(__file__))
-    for f in WALK_SOURCES:
-        with open(os.path.join(root, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
-
-
-def _recorded_traffic(workload, walks, prec):
-    """DRAM bytes per walk-kernel launch from an ncu capture summarised under
-    profiles/ (a 'traffic_record:' line), or None when there is none for this
-    workload, walk count and precision, or the kernel's sources have changed
-    since the capture."""
-    import glob
-    root = os.path.dirname(os.path.abspath(__file__))
-    digest = walk_source_digest()
-    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
-        with open(path) as fh:
-            for line in fh:
-                if not line.startswith("traffic_record:"):
-                    continue
-                kv = dict(t.split("=", 1) for t in line.split()[1:])
-                if (kv.get("workload") == workload and int(kv.get("walks_per_row", -1)) == walks
-                        and int(kv.get("prec", -1)) == prec and kv.get("source_sha256") == digest):
-                    return float(kv["dram_bytes_per_launch"]), os.path.basename(path)
-    return None
-
-
-def _alu_roofline(cst, walk_ms, kernel):
-    """FP32 ALU roofline of the walk kernel: algorithmic operations (node
-    visits and triangle tests of the same walks, counted in a separate
-    untimed run) over the kernel's event-timed duration."""
-    sm_max = _peaks().get("sm_max_mhz", 2032.0)
-    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x clock, T op/s
-    ops = OPS_PER_NODE * cst["nodes_visited"] + OPS_PER_TRI * cst["tris_tested"]
-    achieved = ops / (walk_ms / 1e3) / 1e12
+def _walk_roofline(cst, walk_ms, kernel, peaks, width=2):
+    """Roofline of the walk kernel: queries (walk steps) of the timed launch x
+    the algorithmic bytes and operations per query (node and triangle counts
+    per query from an untimed counting run of the same walks) over the
+    kernel's event-timed duration, against the L2 read bandwidth and the FP32
+    instruction rate measured on this GPU by the library's probes.  The
+    bound reported is the ceiling the kernel is closer to."""
     q = max(1, cst["steps"] + cst["killing_steps"])
-    return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s", "frac": achieved / alu_peak,
-            "traffic": None, "kernel": kernel, "ops_per_node": OPS_PER_NODE, "ops_per_tri": OPS_PER_TRI,
-            "nodes_per_query": cst["nodes_visited"] / q, "tris_per_query": cst["tris_tested"] / q,
-            "peak_note": "148 SMs x 128 FP32 lanes x max SM clock (derived)"}
-
-
-def _with_traffic(roof, workload, walks, prec):
-    rec = _recorded_traffic(workload, walks, prec)
-    if rec is not None:
-        roof["traffic"] = rec[0]
-        roof["traffic_source"] = f"profiles/{rec[1]} (ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch)"
+    npq = cst["nodes_visited"] / q
+    tpq = cst["tris_tested"] / q
+    bytes_q = width * BOX_BYTES * npq + TRI_BYTES * tpq
+    ops_q = width * OPS_PER_BOX * npq + OPS_PER_TRI * tpq + OPS_PER_STEP
+    secs = walk_ms / 1e3
+    gbs = q * bytes_q / secs / 1e9
+    tops = q * ops_q / secs / 1e12
+    l2, alu = peaks["l2_read_gbs"], peaks["fp32_fma_tinst_s"]
+    l2_frac, alu_frac = gbs / l2, tops / alu
+    if l2_frac >= alu_frac:
+        head = {"bound": "l2", "achieved": gbs, "peak": l2, "unit": "GB/s", "frac": l2_frac}
     else:
-        roof["traffic_source"] = "null: no ncu capture of this kernel build at this workload"
-    return roof
+        head = {"bound": "alu", "achieved": tops, "peak": alu, "unit": "Top/s", "frac": alu_frac}
+    return dict(head, traffic=None, kernel=kernel, l2_frac=l2_frac, alu_frac=alu_frac,
+                l2_achieved_gbs=gbs, l2_peak_gbs=l2, alu_achieved_tops=tops, alu_peak_tops=alu,
+                queries=q, kernel_ms=walk_ms, nodes_per_query=npq, tris_per_query=tpq,
+                bytes_per_query=bytes_q, ops_per_query=ops_q, node_width=width,
+                per_unit={"box_bytes": BOX_BYTES, "tri_bytes": TRI_BYTES, "ops_per_box": OPS_PER_BOX,
+                          "ops_per_tri": OPS_PER_TRI, "ops_per_step": OPS_PER_STEP},
+                peak_note="of measured: L2 read bandwidth and FP32 FMA instruction rate from the library's "
+                          "probes on this GPU before the timed region",
+                traffic_note="DRAM bytes of this kernel come from ncu captures summarised with the profiles; "
+                             "not measured in this run")
 
 
 def _downstream(mcs, out, dev, reps=5):
@@ -392,6 +373,7 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         step(V_d, F_d)
     torch.cuda.synchronize()
+    peaks = mcs.probe_peaks()  # the roofline's ceilings, measured before the timed region
 
     pinned = {}  # the host buffer Lambda is read into: allocated once, outside the timed region
     side = torch.cuda.Stream(device=dev)  # Lambda's device-to-host copy overlaps the eigensolve
@@ -483,8 +465,9 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "gpu_launches_note": "library kernels counted by the library (mcs_launch_count); CUB sort kernels excluded",
-        "roofline": _with_traffic(_alu_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})"),
-                                  args.workload, W, args.prec),
+        "roofline": _walk_roofline(cst, walk_ms, f"k_walks (FP{args.prec}, {'interior' if wild else 'exterior'})",
+                                   peaks, 4 if args.bvh_layout == 4 else 2),
+        "peaks_measured": peaks,
         "clocks": clocks,
         "downstream": downstream,
     }
@@ -521,6 +504,11 @@ def _batch_setup(args, dev, rank):
 
 
 def run_batch(args, rank, world):
+    """The 512-mesh batch: every step is one replay of the graph-captured
+    batched estimate (all meshes' setup and tangent balls, ONE persistent walk
+    launch over all meshes, histograms and assembly).  The graph records CUDA
+    events around its phases at every replay, so the walk kernel's time is
+    measured inside the timed steps."""
     import torch
     import paper_2606_05581_b300 as mcs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -532,6 +520,8 @@ def run_batch(args, rank, world):
     t0 = time.time()
     tuned, trials = b.autotune(sample_fraction=1.0 / 64)
     tune_s = time.time() - t0
+    tuned.timing = 1  # phase events inside the captured graph
+    b.params = tuned
     t0 = time.time()
     nodes = b.capture()
     capture_s = time.time() - t0
@@ -540,12 +530,13 @@ def run_batch(args, rank, world):
     for _ in range(args.warmup):
         b.launch()
     torch.cuda.synchronize()
+    peaks = mcs.probe_peaks()  # the roofline's ceilings, measured before the timed region
     barrier(world)
     clk = ClockSampler(dev.index) if rank == 0 else None
     if clk:
         clk.start()
     l0 = mcs.launch_count()
-    times = []
+    times, phases = [], []
     for _ in range(args.steps):
         flush.fill_(1)
         s0 = torch.cuda.Event(enable_timing=True)
@@ -555,6 +546,7 @@ def run_batch(args, rank, world):
         s1.record(stream)
         s1.synchronize()
         times.append(s0.elapsed_time(s1))
+        phases.append(b.graph_stats()[1]["phase_ms"])  # this replay's phases (read after its end)
     launches = mcs.launch_count() - l0
     barrier(world)
     clocks = clk.stop() if clk else None
@@ -567,13 +559,15 @@ def run_batch(args, rank, world):
     e2e = _batch_e2e(args, hosts, tuned, stream)
     if rank != 0:
         return None
-    # the walk kernel alone, event-timed, for the roofline (plain enqueue with phase timing)
-    tp = mcs.default_params(**{f: getattr(tuned, f) for f, _ in mcs.Params._fields_
+    phase = np.mean(np.array(phases), axis=0).tolist()
+    # node and triangle counts of the same walks (counter-based: identical walks), untimed
+    cp = mcs.default_params(**{f: getattr(tuned, f) for f, _ in mcs.Params._fields_
                                if f not in ("origin", "domain", "seed", "origin_auto")})
-    tp.timing = 1
-    _, tst, _ = b.run(tp)
-    tp.count_work = 1
-    _, cst, _ = b.run(tp)
+    cp.timing = 0
+    cp.count_work = 1
+    _, cst, _ = b.run(cp)
+    assert cst["steps"] + cst["killing_steps"] == steps
+    width = 4 if tuned.bvh_layout == 4 else 2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -582,19 +576,24 @@ def run_batch(args, rank, world):
                        total_faces=int(sum(h.nf for h in hosts))),
         "rows_per_s": n_rows * world / (ms_max / 1e3),
         "walks_per_s": walks * world / (ms_max / 1e3),
+        "closest_point_queries_per_s": value,
         "walk_steps_per_step": steps, "capped_walks_per_step": tot["capped"] + tot["killing_capped"],
+        "lost_walks_per_step": tot["lost"],
         "discarded_rows": tot["discarded_rows"], "status": status,
         "phase_ms": {"mesh_generation_host": t_gen * 1e3, "bvh_builds_and_sample_rows": prep_ms,
-                     "setup_and_tangent_balls": tst["phase_ms"][0], "walks": tst["phase_ms"][1],
-                     "histogram_and_assembly": tst["phase_ms"][2]},
+                     "setup_and_tangent_balls": phase[0], "walks": phase[1], "histogram_and_assembly": phase[2]},
         "autotune": {"seconds": tune_s, "chosen": {"threads_per_block": tuned.threads_per_block,
                                                    "blocks_per_sm": tuned.blocks_per_sm,
-                                                   "queue_order": tuned.queue_order}, "trials": trials},
+                                                   "queue_order": tuned.queue_order,
+                                                   "bvh_layout": tuned.bvh_layout,
+                                                   "lanes_per_query": tuned.lanes_per_query}, "trials": trials},
         "graph": {"nodes": nodes, "capture_and_instantiate_s": capture_s},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "gpu_launches_note": "library kernels per graph replay x steps (mcs_launch_count); CUB kernels excluded",
-        "roofline": _alu_roofline(cst, tst["phase_ms"][1], f"k_walks (FP{args.prec}, mixed batch)"),
+        "roofline": _walk_roofline(cst, phase[1], f"k_walks (FP{args.prec}, mixed batch, one launch)", peaks,
+                                   width),
+        "peaks_measured": peaks,
         "clocks": clocks,
     }
     if not args.no_cpu:
@@ -755,25 +754,32 @@ def cpu_baseline(args, samples=1, hosts=None):
     out = []
     if args.workload == "batch":
         import meshgen
-        hosts = hosts or meshgen.batch_meshes(4, 1000)
+        hosts = hosts or [meshgen.batch_mesh(0), meshgen.batch_mesh(1)]
         W = args.walks or 512
+        nr, nw = max(2, nthr), W // 2
+        rows_of = []
+        for i in range(2):  # mesh 0 (interior) and mesh 1 (exterior): the oracle's own rows and origin
+            h = hosts[i]
+            rows = O.fps_rows(h.V, h.F, 1024, orient=True)
+            rows_of.append((rows, O.interior_origin(h.V, h.F, rows) if i % 2 else None))
         for s in range(samples):
             steps = 0
             dt = 0.0
-            for i in range(2):  # mesh 0 (interior) and mesh 1 (exterior)
+            for i in range(2):
                 h = hosts[i]
-                rows = O.fps_rows(h.V, h.F, 1024, orient=True)
-                rl = np.sort(rng.choice(1024, max(2, nthr // 2), replace=False)).astype(np.int32)
-                origin = O.interior_origin(h.V, h.F, rows) if i % 2 else None
+                rows, origin = rows_of[i]
+                rl = np.sort(rng.choice(1024, nr, replace=False)).astype(np.int32)
                 t0 = time.time()
-                est = O.estimate(h.V, h.F, rows, W // 8, 1e-3, exterior=bool(i % 2), origin=origin, seed=i,
-                                 prec=args.prec, row_list=rl)
+                est = O.estimate(h.V, h.F, rows, W, 1e-3, exterior=bool(i % 2), origin=origin, seed=i,
+                                 prec=args.prec, row_list=rl, params=dict(walk_limit=nw))
                 dt += time.time() - t0
                 steps += int(est["steps"].sum())
             out.append({"value": steps / dt, "unit": UNIT, "cores": nthr, "kind": "oracle",
                         "sample": f"meshes 0 (interior, {hosts[0].nf} faces) and 1 (exterior, {hosts[1].nf} "
-                                  f"faces): {max(2, nthr // 2)} sample rows x {W // 8} walks each "
-                                  f"(fp{args.prec}); {steps} walk steps in {dt:.1f} s"})
+                                  f"faces) of the batch: {nr} random sample rows x the first {nw} of their {W} "
+                                  f"walks each (fp{args.prec}, brute-force closest point); {steps} walk steps in "
+                                  f"{dt:.1f} s; walk steps/s is per-step work, so it carries over to the whole "
+                                  f"batch unchanged"})
         return out
     m = make_mesh(args)
     if args.workload == "wild_2m":
@@ -839,7 +845,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="two_spheres_s4_exterior", choices=WORKLOADS)
+    ap.add_argument("--workload", default="batch", choices=WORKLOADS)
     ap.add_argument("--walks", type=int, default=0, help="walks per row (0: the workload's)")
     ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
     ap.add_argument("--seeds", type=int, default=4,

@@ -303,8 +303,11 @@ mcs_status mcs_estimate_batched(const mcs_batch_item *items, int n, const mcs_pa
  * device pointers of the items, outputs and workspace given here: they must
  * stay valid, and the inputs may change in place between launches (not the
  * sizes).  mcs_graph_stats synchronises `stream` and reads the counters of
- * the last finished launch.  A graph may not be launched concurrently with
- * itself or with another call that uses the same workspace. */
+ * the last finished launch.  With p->timing set, the graph records CUDA
+ * events around its phases at every replay, and mcs_graph_stats also returns
+ * the last replay's phase times (phase_ms: setup, walks, histogram and
+ * assembly).  A graph may not be launched concurrently with itself or with
+ * another call that uses the same workspace. */
 typedef struct mcs_graph_s *mcs_graph;
 mcs_status mcs_graph_create(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
                             size_t workspace_bytes, mcs_graph *out);
@@ -533,6 +536,25 @@ mcs_status mcs_tc_symm_product(const double *A, const double *Xt, int n, int m, 
  * i = start .. start+n-1, key (k0, k1); device output n x 4. */
 mcs_status mcs_philox_words(uint64_t start, uint64_t n, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                             uint32_t *out, void *stream);
+
+/* Measurement probes (the paper has no counterpart): the hardware ceilings
+ * the walk kernel's roofline is stated against, measured on the running GPU.
+ * The caller times each call with CUDA events on `stream`.
+ *  - mcs_probe_l2_read: every SM streams `reps` passes over the device
+ *    buffer buf (bytes, a multiple of 16, 16-byte aligned) with loads that
+ *    bypass L1 (ld.global.cg); a buffer below the L2 size measures L2 read
+ *    bandwidth (bytes * reps / time).  sink: device 8 bytes (written only
+ *    to keep the loads).
+ *  - mcs_probe_fma32 / mcs_probe_fma64: 148-SM-filling grid, every thread
+ *    runs 8 independent fused multiply-add chains of `iters` steps; the
+ *    instruction rate is threads * 8 * iters / time (2 FLOP each).
+ *    mcs_probe_threads() is the thread count of that grid.  out: device
+ *    4 bytes (FP32) / 8 bytes (FP64), written only to keep the chains.
+ * Invalid sizes give MCS_ERR_ARG; asynchronous on `stream`. */
+mcs_status mcs_probe_l2_read(const void *buf, size_t bytes, int reps, unsigned long long *sink, void *stream);
+mcs_status mcs_probe_fma32(int iters, float *out, void *stream);
+mcs_status mcs_probe_fma64(int iters, double *out, void *stream);
+long long mcs_probe_threads(void);
 
 #ifdef __cplusplus
 }

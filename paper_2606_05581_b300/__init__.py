@@ -109,6 +109,10 @@ def lib():
         L.mcs_estimate_dtn.argtypes = [vp, C.POINTER(Rows), C.POINTER(Params), C.POINTER(Outputs), vp, C.c_size_t,
                                        C.POINTER(Stats), vp]
         L.mcs_philox_words.argtypes = [u64, u64, u32, u32, u32, u32, vp, vp]
+        L.mcs_probe_l2_read.argtypes = [vp, C.c_size_t, i32, vp, vp]
+        L.mcs_probe_fma32.argtypes = [i32, vp, vp]
+        L.mcs_probe_fma64.argtypes = [i32, vp, vp]
+        L.mcs_probe_threads.restype = i64
         L.mcs_sample_rows_workspace_size.argtypes = [vp, i32]
         L.mcs_sample_rows_workspace_size.restype = C.c_size_t
         L.mcs_sample_rows.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
@@ -289,6 +293,46 @@ def philox_words(start: int, n: int, c2: int, c3: int, key: int) -> torch.Tensor
     out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
     _check(lib().mcs_philox_words(start, n, c2, c3, key & 0xFFFFFFFF, key >> 32, _ptr(out), _stream()))
     return out
+
+
+def probe_peaks(l2_sizes_mib=(8, 16, 32, 64, 96), pass_bytes: int = 8 << 30) -> dict:
+    """Ceilings of the running GPU for the walk kernel's roofline, each the
+    best of 3 event-timed calls of the library's probes: L2 read bandwidth
+    (GB/s; L1-bypassing loads over device buffers below the L2 size, the best
+    size taken) and FP32 / FP64 fused multiply-add instruction rates (T
+    instructions/s)."""
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def best(fn, k=3):
+        fn()
+        out = []
+        for _ in range(k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b) / 1e3)
+        return min(out)
+
+    l2 = {}
+    for mib in l2_sizes_mib:
+        buf = torch.ones(mib << 20, dtype=torch.uint8, device=dev)
+        reps = max(1, pass_bytes // buf.numel())
+        t = best(lambda: _check(lib().mcs_probe_l2_read(_ptr(buf), buf.numel(), reps, _ptr(sink), _stream())))
+        l2[mib] = buf.numel() * reps / t / 1e9
+        del buf
+    th = int(lib().mcs_probe_threads())
+    o32 = torch.zeros(1, dtype=torch.float32, device=dev)
+    o64 = torch.zeros(1, dtype=torch.float64, device=dev)
+    i32, i64 = 16384, 256
+    t32 = best(lambda: _check(lib().mcs_probe_fma32(i32, _ptr(o32), _stream())))
+    t64 = best(lambda: _check(lib().mcs_probe_fma64(i64, _ptr(o64), _stream())))
+    return {"l2_read_gbs": max(l2.values()), "l2_read_gbs_by_mib": l2,
+            "fp32_fma_tinst_s": th * 8 * i32 / t32 / 1e12, "fp64_fma_tinst_s": th * 8 * i64 / t64 / 1e12,
+            "probe_threads": th}
 
 
 def workspace_size(mesh: Mesh, n_rows: int, walks: int, killing_walks: int = 0) -> int:

@@ -597,6 +597,103 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         }
     };
 
+    // the query point of the walk's next step (exterior: the primal image of
+    // x~); false when the walk ended, or stepped, without a query
+    auto query_point = [&](const WalkJob &J, bool ext, T &qx, T &qy, T &qz) -> bool {
+        qx = s.x.x; qy = s.x.y; qz = s.x.z;
+        if (!ext) {
+            // farther from the box centre than the box diagonal: the walk is in
+            // the unbounded component and is retired without a hit
+            const T e0 = s.x.x - pick<T>(J.box_c[0], J.box_cf[0]), e1 = s.x.y - pick<T>(J.box_c[1], J.box_cf[1]),
+                    e2 = s.x.z - pick<T>(J.box_c[2], J.box_cf[2]);
+            if (e0 * e0 + e1 * e1 + e2 * e2 > pick<T>(J.esc_int2, J.esc_int2f)) {
+                finish(J, -1, -1, false, true);
+                return false;
+            }
+        } else {
+            const Ctrl &C = *J.ctrl;
+            const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
+            if (r2 > pick<T>(C.esc2, C.esc2_f)) { finish(J, -1, -1, false, true); return false; }  // escaped
+            if (r2 == (T)0) {
+                // the empty ball around the inverted origin; no query
+                if (s.k == a.max_steps) { finish(J, -1, -1, true, true); return false; }
+                advance(pick<T>(C.rho0max, C.rho0max_f), J);
+                return false;
+            }
+            const T inv = (T)1 / r2;
+            qx = s.x.x * inv + pick<T>(C.origin[0], C.origin_f[0]);
+            qy = s.x.y * inv + pick<T>(C.origin[1], C.origin_f[1]);
+            qz = s.x.z * inv + pick<T>(C.origin[2], C.origin_f[2]);
+        }
+        return true;
+    };
+
+    // after the closest-point query h: the walk exits in the epsilon-shell (or at
+    // the step cap), or steps
+    auto decide = [&](const WalkJob &J, bool ext, const Hit<T> &h) {
+        if (writer) {
+            if (s.kill) n_ksteps++; else n_steps++;
+        }
+        if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
+            err |= kErrNoHit;
+            if (writer) record_nohit(J.ctrl, ext ? 2 : 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
+            finish(J, -1, -1, true, true);
+            return;
+        }
+        const T d = rsq<T>(h.d2);
+        if (!ext) {
+            if (d < epsT || s.k == a.max_steps) {
+                if (sizeof(T) == 8) {
+                    finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false,
+                           (double)h.b0, (double)h.b1, (double)h.b2);
+                    return;
+                }
+                double b[3];
+                const double d64 = sqrt(recheck64(J.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
+                if (d64 < a.eps || s.k == a.max_steps) {
+                    finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false, b[0], b[1], b[2]);
+                    return;
+                }
+            }
+            s.prev = h.slot;
+            advance(d, J);
+            return;
+        }
+        // exterior: the step radius in inverted coordinates (reading R7)
+        const double r0max64 = J.ctrl->rho0max;
+        const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
+        const T inv = (T)1 / r2;
+        const T xp0 = s.x.x * inv, xp1 = s.x.y * inv, xp2 = s.x.z * inv;
+        const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
+        const T ri = d / (nx * (nx + d));
+        const T r0 = pick<T>(r0max64, J.ctrl->rho0max_f) - rsq<T>(r2);
+        const T rho = ri > r0 ? ri : r0;
+        if (rho < epsT || s.k == a.max_steps) {
+            if (sizeof(T) == 8) {
+                finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false,
+                       (double)h.b0, (double)h.b1, (double)h.b2);
+                return;
+            }
+            const double o64[3] = {J.ctrl->origin[0], J.ctrl->origin[1], J.ctrl->origin[2]};
+            const double xd0 = (double)s.x.x, xd1 = (double)s.x.y, xd2 = (double)s.x.z;
+            const double r2d = xd0 * xd0 + xd1 * xd1 + xd2 * xd2;
+            const double invd = 1.0 / r2d;
+            const double xpd0 = xd0 * invd, xpd1 = xd1 * invd, xpd2 = xd2 * invd;
+            double b[3];
+            const double dd = sqrt(recheck64(J.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
+            const double nxd = sqrt(xpd0 * xpd0 + xpd1 * xpd1 + xpd2 * xpd2);
+            const double rid = dd / (nxd * (nxd + dd));
+            const double r0d = r0max64 - sqrt(r2d);
+            const double rhod = rid > r0d ? rid : r0d;
+            if (rhod < a.eps || s.k == a.max_steps) {
+                finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false, b[0], b[1], b[2]);
+                return;
+            }
+        }
+        s.prev = h.slot;
+        advance(rho, J);
+    };
+
     while (true) {
         const bool need = !active && more;
         // groups: one queue entry per group, taken by its lane 0
@@ -674,101 +771,17 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         }
         if (!__any_sync(FULL, active || more)) break;
         if (!active) continue;
-
         // ---- one walk-on-spheres step: the query point (exterior: the primal
         // image of x~), the closest-point query, the decision
         const WalkJob &J = job_of<MULTI>(a, s.job);
         const bool ext = MODE == 1 || (MODE == 2 && J.ext);
-        T qx = s.x.x, qy = s.x.y, qz = s.x.z;
-        if (!ext) {
-            // farther from the box centre than the box diagonal: the walk is in
-            // the unbounded component and is retired without a hit
-            const T e0 = s.x.x - pick<T>(J.box_c[0], J.box_cf[0]), e1 = s.x.y - pick<T>(J.box_c[1], J.box_cf[1]),
-                    e2 = s.x.z - pick<T>(J.box_c[2], J.box_cf[2]);
-            if (e0 * e0 + e1 * e1 + e2 * e2 > pick<T>(J.esc_int2, J.esc_int2f)) {
-                finish(J, -1, -1, false, true);
-                continue;
-            }
-        } else {
-            const Ctrl &C = *J.ctrl;
-            const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
-            if (r2 > pick<T>(C.esc2, C.esc2_f)) { finish(J, -1, -1, false, true); continue; }  // escaped
-            if (r2 == (T)0) {
-                // the empty ball around the inverted origin; no query
-                if (s.k == a.max_steps) { finish(J, -1, -1, true, true); continue; }
-                advance(pick<T>(C.rho0max, C.rho0max_f), J);
-                continue;
-            }
-            const T inv = (T)1 / r2;
-            qx = s.x.x * inv + pick<T>(C.origin[0], C.origin_f[0]);
-            qy = s.x.y * inv + pick<T>(C.origin[1], C.origin_f[1]);
-            qz = s.x.z * inv + pick<T>(C.origin[2], C.origin_f[2]);
-        }
+        T qx, qy, qz;
+        if (!query_point(J, ext, qx, qy, qz)) continue;
         Hit<T> h;
-        if (TRAV == 2) closest_g4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work, gmask, gr);
-        else if (TRAV == 1) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
+        if constexpr (TRAV == 2) closest_g4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work, gmask, gr);
+        else if constexpr (TRAV == 1) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
         else closest<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
-        if (writer) {
-            if (s.kill) n_ksteps++; else n_steps++;
-        }
-        if (h.slot < 0 || h.id < 0 || h.id >= J.m.nf) {
-            err |= kErrNoHit;
-            if (writer) record_nohit(J.ctrl, ext ? 2 : 1, s.kill, s.g, s.k, (double)s.x.x, (double)s.x.y, (double)s.x.z);
-            finish(J, -1, -1, true, true);
-            continue;
-        }
-        const T d = rsq<T>(h.d2);
-        if (!ext) {
-            if (d < epsT || s.k == a.max_steps) {
-                if (sizeof(T) == 8) {
-                    finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(d < epsT), false,
-                           (double)h.b0, (double)h.b1, (double)h.b2);
-                    continue;
-                }
-                double b[3];
-                const double d64 = sqrt(recheck64(J.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
-                if (d64 < a.eps || s.k == a.max_steps) {
-                    finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(d64 < a.eps), false, b[0], b[1], b[2]);
-                    continue;
-                }
-            }
-            s.prev = h.slot;
-            advance(d, J);
-            continue;
-        }
-        // exterior: the step radius in inverted coordinates (reading R7)
-        const double r0max64 = J.ctrl->rho0max;
-        const T r2 = s.x.x * s.x.x + s.x.y * s.x.y + s.x.z * s.x.z;
-        const T inv = (T)1 / r2;
-        const T xp0 = s.x.x * inv, xp1 = s.x.y * inv, xp2 = s.x.z * inv;
-        const T nx = rsq<T>(xp0 * xp0 + xp1 * xp1 + xp2 * xp2);
-        const T ri = d / (nx * (nx + d));
-        const T r0 = pick<T>(r0max64, J.ctrl->rho0max_f) - rsq<T>(r2);
-        const T rho = ri > r0 ? ri : r0;
-        if (rho < epsT || s.k == a.max_steps) {
-            if (sizeof(T) == 8) {
-                finish(J, exit_bin(J, h.id, (double)h.b0, (double)h.b1, (double)h.b2), h.id, !(rho < epsT), false,
-                       (double)h.b0, (double)h.b1, (double)h.b2);
-                continue;
-            }
-            const double o64[3] = {J.ctrl->origin[0], J.ctrl->origin[1], J.ctrl->origin[2]};
-            const double xd0 = (double)s.x.x, xd1 = (double)s.x.y, xd2 = (double)s.x.z;
-            const double r2d = xd0 * xd0 + xd1 * xd1 + xd2 * xd2;
-            const double invd = 1.0 / r2d;
-            const double xpd0 = xd0 * invd, xpd1 = xd1 * invd, xpd2 = xd2 * invd;
-            double b[3];
-            const double dd = sqrt(recheck64(J.m, h.slot, xpd0 + o64[0], xpd1 + o64[1], xpd2 + o64[2], b));
-            const double nxd = sqrt(xpd0 * xpd0 + xpd1 * xpd1 + xpd2 * xpd2);
-            const double rid = dd / (nxd * (nxd + dd));
-            const double r0d = r0max64 - sqrt(r2d);
-            const double rhod = rid > r0d ? rid : r0d;
-            if (rhod < a.eps || s.k == a.max_steps) {
-                finish(J, exit_bin(J, h.id, b[0], b[1], b[2]), h.id, !(rhod < a.eps), false, b[0], b[1], b[2]);
-                continue;
-            }
-        }
-        s.prev = h.slot;
-        advance(rho, J);
+        decide(J, ext, h);
     }
     if constexpr (MULTI) {
         flush();
@@ -1799,24 +1812,30 @@ static std::vector<int> job_order(const Batch &b) {
 }
 
 // everything a batched estimate launches, in stream order; `ev` (optional,
-// 4 events) marks setup | walks | histogram + assembly
-static mcs_status enqueue_batch(const Batch &b, cudaStream_t st, cudaEvent_t *ev) {
+// 4 events) marks setup | walks | histogram + assembly; `external`: the
+// events are recorded by the graph being captured, at each replay
+static mcs_status enqueue_batch(const Batch &b, cudaStream_t st, cudaEvent_t *ev, bool external = false) {
     mcs_status s;
-    if (ev) cudaEventRecord(ev[0], st);
+    auto mark = [&](int i) {
+        if (!ev) return;
+        if (external) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+        else cudaEventRecord(ev[i], st);
+    };
+    mark(0);
     if ((s = enqueue_batch_setup(b, b.p.queue_order, st)) != MCS_OK) return s;
     std::vector<WalkJob> jobs;
     for (int i : job_order(b)) jobs.push_back(make_job(b.plans[i], b.plans[i].walks(), (unsigned long long)b.plans[i].killing));
     if (b.n > 1 && (s = store_jobs(jobs, b.jobs, b.offs, st)) != MCS_OK) return s;
     int tpb = 0, bps = 0;
     if ((s = walk_residency(&b.p, b.mode, b.n > 1, &tpb, &bps)) != MCS_OK) return s;
-    if (ev) cudaEventRecord(ev[1], st);
+    mark(1);
     // one mesh: the one-job kernel, counters straight into the mesh's block
     if ((s = launch_walks(b.jobs, b.offs, b.n, b.n > 1 ? nullptr : &jobs[0], b.n > 1 ? b.launch_ctrl() : b.plans[0].ctrl,
                           &b.p, b.mode, tpb, bps, st)) != MCS_OK)
         return s;
-    if (ev) cudaEventRecord(ev[2], st);
+    mark(2);
     if ((s = enqueue_batch_finish(b, st)) != MCS_OK) return s;
-    if (ev) cudaEventRecord(ev[3], st);
+    mark(3);
     return MCS_OK;
 }
 
@@ -1882,6 +1901,13 @@ struct mcs_graph_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches = 0;  // library kernels per replay
+    // params.timing: phase events recorded by every replay (setup | walks | finish)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+    ~mcs_graph_s() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 using namespace mcs;
@@ -2007,6 +2033,12 @@ mcs_status mcs_graph_create(const mcs_batch_item *items, int n, const mcs_params
     int tpb = 0, bps = 0;
     if (s == MCS_OK) s = walk_residency(p, g->b.mode, n > 1, &tpb, &bps);  // occupancy queried before capture
     if (s != MCS_OK) { delete g; return s; }
+    g->timed = p->timing != 0;
+    if (g->timed)
+        for (auto &ev : g->ev) {
+            const cudaError_t ee = cudaEventCreate(&ev);
+            if (ee != cudaSuccess) { delete g; return cuda_fail(ee, "mcs_graph_create: cudaEventCreate"); }
+        }
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "mcs_graph_create: cudaStreamCreateWithFlags"); }
@@ -2017,7 +2049,7 @@ mcs_status mcs_graph_create(const mcs_batch_item *items, int n, const mcs_params
         return cuda_fail(e, "mcs_graph_create: cudaStreamBeginCapture");
     }
     const unsigned long long before = g_launches.load();
-    s = enqueue_batch(g->b, cs, nullptr);
+    s = enqueue_batch(g->b, cs, g->timed ? g->ev : nullptr, true);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);
     // captured kernels run at each replay, not here
@@ -2049,7 +2081,12 @@ mcs_status mcs_graph_launch(mcs_graph g, void *stream) {
 
 mcs_status mcs_graph_stats(mcs_graph g, mcs_stats *total, mcs_stats *per_item, void *stream) {
     MCS_ARG(g != nullptr, "mcs_graph_stats: NULL graph");
-    return batch_stats(g->b, total, per_item, as_stream(stream), "mcs_graph_stats");
+    const mcs_status s = batch_stats(g->b, total, per_item, as_stream(stream), "mcs_graph_stats");
+    if (total && g->timed)  // the last replay's phases (batch_stats synchronised the stream)
+        for (int i = 0; i < 3; i++)
+            if (cudaEventElapsedTime(&total->phase_ms[i], g->ev[i], g->ev[i + 1]) != cudaSuccess)
+                total->phase_ms[i] = 0.f;
+    return s;
 }
 
 size_t mcs_graph_nodes(mcs_graph g) {
