@@ -327,3 +327,4 @@ def test_group_traversal_bit_exact(oracle, prec):
     assert np.array_equal(res["exit_tri"].cpu().numpy(), est["exit_tri"])
     assert np.array_equal(res["H0"].cpu().numpy(), est["H0"])
     assert st["steps"] == est["steps"].sum()
+
