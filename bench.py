@@ -407,7 +407,9 @@ def run_ours(args, rank, world):
                 d2h = L_h.numel() * 8 + lam_h.numel() * 8
                 st = dict(res["stats"])
             else:
+                torch.cuda.nvtx.range_push("timed_step")
                 st, _ = step(V_d, F_d)
+                torch.cuda.nvtx.range_pop()
             s1.record(stream)
             s1.synchronize()
             times.append(s0.elapsed_time(s1))
@@ -541,9 +543,11 @@ def run_batch(args, rank, world):
         flush.fill_(1)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")
         s0.record(stream)
         b.launch()
         s1.record(stream)
+        torch.cuda.nvtx.range_pop()
         s1.synchronize()
         times.append(s0.elapsed_time(s1))
         phases.append(b.graph_stats()[1]["phase_ms"])  # this replay's phases (read after its end)

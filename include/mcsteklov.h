@@ -318,18 +318,20 @@ void mcs_graph_destroy(mcs_graph g);
 
 /* Autotuner of the walk launch.  Runs the batch's row setup, then times the
  * walk kernel on a sample (every s-th row of every mesh's row schedule,
- * s = floor(1 / sample_fraction), no killing walks) for the two BVH node layouts (when
- * p->bvh_layout is 0), candidate block sizes (64, 128 threads), resident
- * blocks per SM (the three largest residencies the kernel allows) and queue
- * orders (row order, mesh order), by coordinate search in that order; the
- * best two-run minimum wins.  tuned (host) = p with bvh_layout, lanes_per_query,
+ * s = floor(1 / sample_fraction), no killing walks) for the queue orders (row
+ * order, mesh order), the BVH node layouts (when p->bvh_layout is 0),
+ * candidate block sizes (64, 128 threads) and resident blocks per SM (the
+ * three largest residencies the kernel allows), by coordinate search in that
+ * order; each trial takes the best of three runs, and a candidate replaces
+ * the incumbent only when it is more than 2% faster (smaller differences are
+ * the sample's run-to-run noise).  tuned (host) = p with bvh_layout, lanes_per_query,
  * threads_per_block, blocks_per_sm and queue_order set.  trials (host, optional) receives up to
  * max_trials entries, n_trials their count.  Synchronises `stream`.  The
  * workspace and outputs are those of the batch; their contents are left
  * undefined (the estimate rewrites them). */
 typedef struct {
     int threads_per_block, blocks_per_sm, queue_order, bvh_layout, lanes_per_query;
-    float ms;               /* walk-kernel time of the sample (best of 2)       */
+    float ms;               /* walk-kernel time of the sample (best of 3)       */
 } mcs_tune_trial;
 mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_params *p, void *workspace,
                               size_t workspace_bytes, double sample_fraction, mcs_params *tuned,

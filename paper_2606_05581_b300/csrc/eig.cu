@@ -714,6 +714,7 @@ size_t mcs_steklov_workspace_size(int n, int k) {
 mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, int k, double *evals, double *evecs,
                              void *workspace, size_t workspace_bytes, const mcs_eig_params *ep, mcs_eig_stats *stats,
                              void *stream_) {
+    NvtxRange nvtx_range("mcs_steklov_modes");
     MCS_ARG(Lambda && mass && evals, "mcs_steklov_modes: NULL Lambda, mass or evals");
     MCS_ARG(n >= 16 && k >= 1 && k <= 128 && k < n / 2, "mcs_steklov_modes: need n >= 16 and 1 <= k <= min(128, n/2 - 1)");
     mcs_eig_params prm;

@@ -6,6 +6,8 @@
 #include <atomic>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mcsteklov.h"
 #include "mcs_device.cuh"
 
@@ -47,6 +49,14 @@ int num_sms();
 // kernels of this library enqueued since it was loaded (mcs_launch_count)
 extern std::atomic<unsigned long long> g_launches;
 inline void note_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// an NVTX range over a scope (entry points and their phases: profilers
+// attribute the kernels launched inside it; no cost without a tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 // load (CUDA loads code lazily) every kernel of a one-mesh estimate
 mcs_status preload_estimate_kernels();
 // load the allocation-free estimate's scratch array and the estimate's

@@ -365,6 +365,7 @@ int mcs_mesh_nv(mcs_mesh m) { return m ? m->nv : 0; }
 int mcs_mesh_nf(mcs_mesh m) { return m ? m->nf : 0; }
 
 mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream_, mcs_mesh *out) {
+    NvtxRange nvtx_range("mcs_build_bvh");
     MCS_ARG(out != nullptr, "mcs_build_bvh: out is NULL");
     *out = nullptr;
     MCS_ARG(V != nullptr && F != nullptr, "mcs_build_bvh: V or F is NULL");

@@ -1041,6 +1041,7 @@ size_t mcs_sample_rows_workspace_size(mcs_mesh m, int n) {
 mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *pos, double *nrm, double *area,
                            int32_t *tri2bin, float *orient_gap, void *workspace, size_t workspace_bytes,
                            void *stream_) {
+    NvtxRange nvtx_range("mcs_sample_rows");
     mcs_sample_item it;
     it.mesh = m;
     it.n = n;
@@ -1100,6 +1101,7 @@ size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int 
 
 mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int orient, void *workspace,
                                    size_t workspace_bytes, void *stream_) {
+    NvtxRange nvtx_range("mcs_sample_rows_batched");
     MCS_ARG(items != nullptr && count > 0, "mcs_sample_rows_batched: no items");
     for (int i = 0; i < count; i++) {
         const mcs_status s = sample_check(items[i], "mcs_sample_rows_batched");
