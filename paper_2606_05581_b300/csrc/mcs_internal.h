@@ -14,7 +14,9 @@
 struct mcs_mesh_s {
     int device = 0;
     int nv = 0, nf = 0;
-    // device memory owned by the mesh
+    // device memory owned by the mesh: one block (`block`) holding the arrays
+    // below, except the 4-wide copy (`nodes4`, its own allocation)
+    void *block = nullptr;
     double *V = nullptr;           // nv x 3
     int32_t *F = nullptr;          // nf x 3
     mcs::Node *nodes = nullptr;    // nf - 1

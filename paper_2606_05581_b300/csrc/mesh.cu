@@ -347,9 +347,8 @@ static bool is_device_ptr(const void *p) {
 
 static void mesh_free(mcs_mesh_s *m) {
     if (!m) return;
-    cudaFree(m->V); cudaFree(m->F); cudaFree(m->nodes); cudaFree(m->nodes4); cudaFree(m->t32); cudaFree(m->t64);
-    cudaFree(m->child); cudaFree(m->parent); cudaFree(m->nodebox);
-    cudaFree(m->inc_f); cudaFree(m->vstart); cudaFree(m->err);
+    cudaFree(m->block);  // every array of the mesh but the 4-wide copy
+    cudaFree(m->nodes4);
     delete m;
 }
 
@@ -377,9 +376,11 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     m->nv = nv;
     m->nf = nf;
     cudaGetDevice(&m->device);
-    std::vector<void *> tmp;
+    // two device allocations: the mesh's arrays (one block it owns) and the
+    // build's temporaries (one block, freed before returning); parts 256-byte aligned
+    void *tbuf = nullptr;
     auto fail = [&](mcs_status s) {
-        for (void *p : tmp) cudaFree(p);
+        cudaFree(tbuf);
         mesh_free(m);
         return s;
     };
@@ -388,24 +389,69 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         cudaError_t e_ = (call);                                 \
         if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call)); \
     } while (0)
-    auto talloc = [&](size_t bytes) -> void * {
-        void *p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-        tmp.push_back(p);
-        return p;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t ni = nf > 1 ? (size_t)(nf - 1) : 0;
+    const size_t msz[11] = {sizeof(double) * 3 * nv, sizeof(int32_t) * 3 * nf, sizeof(int),
+                            sizeof(Tri32) * nf,      sizeof(Tri64) * nf,       sizeof(Node) * ni,
+                            sizeof(int) * 2 * ni,    sizeof(int) * ni,         sizeof(float) * 12 * ni,
+                            sizeof(int32_t) * 3 * nf, sizeof(int32_t) * (nv + 1)};
+    size_t mtot = 0;
+    for (size_t x : msz) mtot += al(x);
+    MB_CUDA(cudaMalloc(&m->block, mtot));
+    char *mp = (char *)m->block;
+    auto mtake = [&](size_t bytes) -> void * {
+        if (!bytes) return nullptr;
+        void *r = mp;
+        mp += al(bytes);
+        return r;
     };
-    MB_CUDA(cudaMalloc(&m->V, sizeof(double) * 3 * nv));
-    MB_CUDA(cudaMalloc(&m->F, sizeof(int32_t) * 3 * nf));
-    MB_CUDA(cudaMalloc(&m->err, sizeof(int)));
+    m->V = (double *)mtake(msz[0]);
+    m->F = (int32_t *)mtake(msz[1]);
+    m->err = (int *)mtake(msz[2]);
+    m->t32 = (Tri32 *)mtake(msz[3]);
+    m->t64 = (Tri64 *)mtake(msz[4]);
+    m->nodes = (Node *)mtake(msz[5]);
+    m->child = (int *)mtake(msz[6]);
+    m->parent = (int *)mtake(msz[7]);
+    m->nodebox = (float *)mtake(msz[8]);
+    m->inc_f = (int32_t *)mtake(msz[9]);
+    m->vstart = (int32_t *)mtake(msz[10]);
+
+    size_t sort_bytes = 0, sort_bytes2 = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
+                                   nf, 0, 62, st);
+    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes2, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
+                                   3 * nf, 0, 64, st);
+    const int nbp = 256;
+    const size_t tsz[11] = {sizeof(int) * 2,  sizeof(double) * 6 * nbp, sizeof(double) * 6,
+                            sizeof(unsigned long long) * nf, sizeof(unsigned long long) * nf,
+                            sizeof(unsigned long long) * 3 * nf, sizeof(unsigned long long) * 3 * nf,
+                            std::max(sort_bytes, sort_bytes2), sizeof(float) * 6 * nf, sizeof(int) * nf,
+                            sizeof(int) * ni};
+    size_t ttot = 0;
+    for (size_t x : tsz) ttot += al(x);
+    MB_CUDA(cudaMalloc(&tbuf, ttot));
+    char *tp = (char *)tbuf;
+    auto ttake = [&](size_t bytes) -> void * {
+        void *r = tp;
+        tp += al(bytes);
+        return r;
+    };
+    int *d_bad = (int *)ttake(tsz[0]);
+    double *d_part = (double *)ttake(tsz[1]);
+    double *d_box = (double *)ttake(tsz[2]);
+    unsigned long long *keys = (unsigned long long *)ttake(tsz[3]);
+    unsigned long long *keys_s = (unsigned long long *)ttake(tsz[4]);
+    unsigned long long *pairs = (unsigned long long *)ttake(tsz[5]);
+    unsigned long long *pairs_s = (unsigned long long *)ttake(tsz[6]);
+    void *d_sort = ttake(tsz[7]);
+    float *slotbox = (float *)ttake(tsz[8]);
+    int *par_l = (int *)ttake(tsz[9]);
+    int *arrive = (int *)ttake(tsz[10]);
+
     MB_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), st));
     MB_CUDA(cudaMemcpyAsync(m->V, V, sizeof(double) * 3 * nv, vdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     MB_CUDA(cudaMemcpyAsync(m->F, F, sizeof(int32_t) * 3 * nf, fdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-
-    int *d_bad = (int *)talloc(sizeof(int) * 2);
-    const int nbp = 256;
-    double *d_part = (double *)talloc(sizeof(double) * 6 * nbp);
-    double *d_box = (double *)talloc(sizeof(double) * 6);
-    if (!d_bad || !d_part || !d_box) return fail(MCS_ERR_OOM);
     MB_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int) * 2, st));
     note_launch();
     k_validate<<<num_sms() * 4, 256, 0, st>>>(m->V, nv, m->F, nf, d_bad);
@@ -441,57 +487,27 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         fr.lo[k] = box[k];
         fr.inv[k] = 1.0 / (box[3 + k] - box[k]);
     }
-    unsigned long long *keys = (unsigned long long *)talloc(sizeof(unsigned long long) * nf);
-    unsigned long long *keys_s = (unsigned long long *)talloc(sizeof(unsigned long long) * nf);
-    if (!keys || !keys_s) return fail(MCS_ERR_OOM);
     const int tb = 256;
     note_launch();
     k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, fr, keys);
-    size_t sort_bytes = 0, sort_bytes2 = 0;
-    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes, keys, keys_s, nf, 0, 62, st);
-    unsigned long long *pairs = nullptr, *pairs_s = nullptr;
-    pairs = (unsigned long long *)talloc(sizeof(unsigned long long) * 3 * nf);
-    pairs_s = (unsigned long long *)talloc(sizeof(unsigned long long) * 3 * nf);
-    if (!pairs || !pairs_s) return fail(MCS_ERR_OOM);
-    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st);
-    void *d_sort = talloc(std::max(sort_bytes, sort_bytes2));
-    if (!d_sort) return fail(MCS_ERR_OOM);
     MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes, keys, keys_s, nf, 0, 62, st));
-
-    MB_CUDA(cudaMalloc(&m->t32, sizeof(Tri32) * nf));
-    MB_CUDA(cudaMalloc(&m->t64, sizeof(Tri64) * nf));
-    float *slotbox = (float *)talloc(sizeof(float) * 6 * nf);
-    if (!slotbox) return fail(MCS_ERR_OOM);
     note_launch();
     k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, m->t32, m->t64, slotbox);
     if (nf > 1) {
-        int *child = (int *)talloc(sizeof(int) * 2 * (nf - 1));
-        int *par_i = (int *)talloc(sizeof(int) * (nf - 1));
-        int *par_l = (int *)talloc(sizeof(int) * nf);
-        float *nodebox = (float *)talloc(sizeof(float) * 12 * (nf - 1));
-        int *arrive = (int *)talloc(sizeof(int) * (nf - 1));
-        if (!child || !par_i || !par_l || !nodebox || !arrive) return fail(MCS_ERR_OOM);
+        // links, parents and child boxes go straight into the mesh (kept for
+        // an on-demand 4-wide copy, mcs_mesh_build_wide)
         MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
-        MB_CUDA(cudaMemsetAsync(par_i, 0xFF, sizeof(int) * (nf - 1), st));
+        MB_CUDA(cudaMemsetAsync(m->parent, 0xFF, sizeof(int) * (nf - 1), st));
         MB_CUDA(cudaMemsetAsync(par_l, 0xFF, sizeof(int) * nf, st));
         note_launch();
-        k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, child, par_i, par_l);
+        k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, m->child, m->parent, par_l);
         note_launch();
-        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, child, par_i, par_l, slotbox, nodebox, arrive, d_bad + 1);
-        MB_CUDA(cudaMalloc(&m->nodes, sizeof(Node) * (nf - 1)));
+        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->parent, par_l, slotbox, m->nodebox, arrive,
+                                                     d_bad + 1);
         note_launch();
-        k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, child, nodebox, m->nodes);
-        // kept for an on-demand 4-wide copy (mcs_mesh_build_wide)
-        MB_CUDA(cudaMalloc(&m->child, sizeof(int) * 2 * (nf - 1)));
-        MB_CUDA(cudaMalloc(&m->parent, sizeof(int) * (nf - 1)));
-        MB_CUDA(cudaMalloc(&m->nodebox, sizeof(float) * 12 * (nf - 1)));
-        MB_CUDA(cudaMemcpyAsync(m->child, child, sizeof(int) * 2 * (nf - 1), cudaMemcpyDeviceToDevice, st));
-        MB_CUDA(cudaMemcpyAsync(m->parent, par_i, sizeof(int) * (nf - 1), cudaMemcpyDeviceToDevice, st));
-        MB_CUDA(cudaMemcpyAsync(m->nodebox, nodebox, sizeof(float) * 12 * (nf - 1), cudaMemcpyDeviceToDevice, st));
+        k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->nodebox, m->nodes);
     }
     // vertex -> incident faces, ascending
-    MB_CUDA(cudaMalloc(&m->inc_f, sizeof(int32_t) * 3 * nf));
-    MB_CUDA(cudaMalloc(&m->vstart, sizeof(int32_t) * (nv + 1)));
     note_launch();
     k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
     MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
@@ -506,8 +522,8 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
         set_error("mcs_build_bvh: internal error, malformed hierarchy");
         return fail(MCS_ERR_DEVICE);
     }
-    for (void *p : tmp) cudaFree(p);
-    tmp.clear();
+    cudaFree(tbuf);
+    tbuf = nullptr;
 #undef MB_CUDA
     // mesh creation may allocate: load here what the allocation-free
     // estimate needs, so that it loads (and allocates) nothing itself; a
