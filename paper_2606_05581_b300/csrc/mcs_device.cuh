@@ -189,15 +189,9 @@ __device__ __noinline__ T tri_degenerate(T ap0, T ap1, T ap2, T ab0, T ab1, T ab
     return best;
 }
 
+// the Voronoi-region tests of a triangle with a nonzero normal (ap = p - a)
 template <typename T>
-__device__ __forceinline__ T tri_closest(T p0, T p1, T p2, T a0, T a1, T a2, T ab0, T ab1, T ab2, T ac0, T ac1, T ac2,
-                                         T *bary) {
-    const T ap0 = p0 - a0, ap1 = p1 - a1, ap2 = p2 - a2;
-    const T n0 = ab1 * ac2 - ab2 * ac1;
-    const T n1 = ab2 * ac0 - ab0 * ac2;
-    const T n2 = ab0 * ac1 - ab1 * ac0;
-    if (n0 == (T)0 && n1 == (T)0 && n2 == (T)0)
-        return tri_degenerate<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
+__device__ __forceinline__ T tri_regions(T ap0, T ap1, T ap2, T ab0, T ab1, T ab2, T ac0, T ac1, T ac2, T *bary) {
     const T d1 = ab0 * ap0 + ab1 * ap1 + ab2 * ap2;
     const T d2 = ac0 * ap0 + ac1 * ap1 + ac2 * ap2;
     if (d1 <= (T)0 && d2 <= (T)0) {
@@ -257,6 +251,25 @@ __device__ __forceinline__ T tri_closest(T p0, T p1, T p2, T a0, T a1, T a2, T a
     return tri_degenerate<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
 }
 
+// a zero normal (n = ab x ac, every component exactly 0 in T) marks a
+// degenerate triangle, whose closest point is on its nearest edge
+template <typename T>
+__device__ __forceinline__ bool tri_zero_normal(T ab0, T ab1, T ab2, T ac0, T ac1, T ac2) {
+    const T n0 = ab1 * ac2 - ab2 * ac1;
+    const T n1 = ab2 * ac0 - ab0 * ac2;
+    const T n2 = ab0 * ac1 - ab1 * ac0;
+    return n0 == (T)0 && n1 == (T)0 && n2 == (T)0;
+}
+
+template <typename T>
+__device__ __forceinline__ T tri_closest(T p0, T p1, T p2, T a0, T a1, T a2, T ab0, T ab1, T ab2, T ac0, T ac1, T ac2,
+                                         T *bary) {
+    const T ap0 = p0 - a0, ap1 = p1 - a1, ap2 = p2 - a2;
+    if (tri_zero_normal<T>(ab0, ab1, ab2, ac0, ac1, ac2))
+        return tri_degenerate<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
+    return tri_regions<T>(ap0, ap1, ap2, ab0, ab1, ab2, ac0, ac1, ac2, bary);
+}
+
 // --------------------------------------------------------------------------
 // mesh on the device
 // --------------------------------------------------------------------------
@@ -278,7 +291,8 @@ struct __align__(128) Node4 {
     int4 child;
     int4 pad;
 };
-// triangle slot in BVH order, FP32: (a, id) (ab, -) (ac, -)
+// triangle slot in BVH order, FP32: (a, id) (ab, zero-normal flag) (ac, -);
+// the flag (an int in ab.w) is tri_zero_normal of the float ab, ac
 struct __align__(16) Tri32 {
     float4 a;
     float4 ab;
@@ -313,7 +327,11 @@ template <> struct Slot<float> {
     __device__ static float test(const DevMesh &m, int s, float px, float py, float pz, float *b, int &id) {
         const Tri32 t = m.t32[s];
         id = __float_as_int(t.a.w);
-        return tri_closest<float>(px, py, pz, t.a.x, t.a.y, t.a.z, t.ab.x, t.ab.y, t.ab.z, t.ac.x, t.ac.y, t.ac.z, b);
+        // tri_closest with the normal test taken from the slot's flag
+        const float ap0 = px - t.a.x, ap1 = py - t.a.y, ap2 = pz - t.a.z;
+        if (__float_as_int(t.ab.w) != 0)
+            return tri_degenerate<float>(ap0, ap1, ap2, t.ab.x, t.ab.y, t.ab.z, t.ac.x, t.ac.y, t.ac.z, b);
+        return tri_regions<float>(ap0, ap1, ap2, t.ab.x, t.ab.y, t.ab.z, t.ac.x, t.ac.y, t.ac.z, b);
     }
 };
 template <> struct Slot<double> {

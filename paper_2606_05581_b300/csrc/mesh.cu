@@ -127,7 +127,8 @@ __global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const uns
     t.id = f;
     t.pad = 0;
     u.a = make_float4(fa[0], fa[1], fa[2], __int_as_float(f));
-    u.ab = make_float4(fab[0], fab[1], fab[2], 0.f);
+    u.ab = make_float4(fab[0], fab[1], fab[2],
+                       __int_as_float(tri_zero_normal<float>(fab[0], fab[1], fab[2], fac[0], fac[1], fac[2]) ? 1 : 0));
     u.ac = make_float4(fac[0], fac[1], fac[2], 0.f);
     t64[s] = t;
     t32[s] = u;
