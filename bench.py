@@ -572,6 +572,7 @@ def run_batch(args, rank, world):
     _, cst, _ = b.run(cp)
     assert cst["steps"] + cst["killing_steps"] == steps
     width = 4 if tuned.bvh_layout == 4 else 2
+    precision = _fp32_batched_vs_fp64_plain(mcs, items[:16], W, tuned)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -598,11 +599,56 @@ def run_batch(args, rank, world):
         "roofline": _walk_roofline(cst, phase[1], f"k_walks (FP{args.prec}, mixed batch, one launch)", peaks,
                                    width),
         "peaks_measured": peaks,
+        "fp32_batched_vs_fp64_plain": precision,
         "clocks": clocks,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, samples=1, hosts=hosts)[0]
     return line
+
+
+def _fp32_batched_vs_fp64_plain(mcs, items, W, tuned):
+    """The metric's comparison on the batch's first meshes, untimed by the
+    headline: FP32 walks of all of them in one batched launch (the tuned
+    shape) against FP64 walks estimated one mesh at a time (the plain path),
+    each timed with CUDA events around the whole estimate.  Both precisions
+    draw the same Philox counters, so at equal walks per row they reach the
+    same error (the precision workload's table; the statistical GPU tests):
+    the walk-step rates compare them at equal error.  Lambda's largest
+    relative difference between the two shows how close they are."""
+    import torch
+    dev_events = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    p32 = mcs.default_params(**{f: getattr(tuned, f) for f, _ in mcs.Params._fields_
+                                if f not in ("origin", "domain", "seed", "origin_auto", "timing", "count_work")})
+    b = mcs.Batch(items, p32, assemble=True)
+    b.run()
+    a, e = dev_events()
+    a.record()
+    _, t32, _ = b.run()
+    e.record()
+    e.synchronize()
+    ms32 = a.elapsed_time(e)
+    steps32 = t32["steps"] + t32["killing_steps"]
+    ms64, steps64, rel = 0.0, 0, 0.0
+    ws = mcs.Workspace()
+    for i, it in enumerate(items):
+        p64 = mcs.default_params(walks_per_row=W, prec=64, killing_walks=64 * W, domain=it["domain"],
+                                 seed=it["seed"])
+        a, e = dev_events()
+        a.record()
+        r = mcs.estimate_dtn(it["mesh"], it["rows"], p64, workspace=ws)
+        e.record()
+        e.synchronize()
+        ms64 += a.elapsed_time(e)
+        steps64 += r["stats"]["steps"] + r["stats"]["killing_steps"]
+        L32, L64 = b.outputs[i]["Lambda"], r["Lambda"]
+        rel = max(rel, float((L32 - L64).abs().max() / L64.abs().max()))
+    return {"meshes": len(items), "fp32_batched_steps_per_s": steps32 / (ms32 / 1e3),
+            "fp64_plain_steps_per_s": steps64 / (ms64 / 1e3),
+            "ratio": (steps32 / (ms32 / 1e3)) / (steps64 / (ms64 / 1e3)),
+            "walk_steps": {"fp32": steps32, "fp64": steps64}, "lambda_max_rel_diff": rel,
+            "note": "same meshes, rows, seeds and walks per row; the two precisions share their Philox counters, "
+                    "so equal walks per row is equal error"}
 
 
 def _batch_e2e(args, hosts, params, stream):
