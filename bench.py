@@ -614,8 +614,9 @@ def _fp32_batched_vs_fp64_plain(mcs, items, W, tuned):
     each timed with CUDA events around the whole estimate.  Both precisions
     draw the same Philox counters, so at equal walks per row they reach the
     same error (the precision workload's table; the statistical GPU tests):
-    the walk-step rates compare them at equal error.  Lambda's largest
-    relative difference between the two shows how close they are."""
+    the walk-step rates compare them at equal error.  Lambda's relative
+    difference (Frobenius norm) and the share of equal hit-count entries
+    show how close the two estimates are."""
     import torch
     dev_events = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     p32 = mcs.default_params(**{f: getattr(tuned, f) for f, _ in mcs.Params._fields_
@@ -629,7 +630,9 @@ def _fp32_batched_vs_fp64_plain(mcs, items, W, tuned):
     e.synchronize()
     ms32 = a.elapsed_time(e)
     steps32 = t32["steps"] + t32["killing_steps"]
-    ms64, steps64, rel = 0.0, 0, 0.0
+    ms64, steps64 = 0.0, 0
+    num = den = 0.0
+    same = total = 0
     ws = mcs.Workspace()
     for i, it in enumerate(items):
         p64 = mcs.default_params(walks_per_row=W, prec=64, killing_walks=64 * W, domain=it["domain"],
@@ -642,11 +645,17 @@ def _fp32_batched_vs_fp64_plain(mcs, items, W, tuned):
         ms64 += a.elapsed_time(e)
         steps64 += r["stats"]["steps"] + r["stats"]["killing_steps"]
         L32, L64 = b.outputs[i]["Lambda"], r["Lambda"]
-        rel = max(rel, float((L32 - L64).abs().max() / L64.abs().max()))
+        num += float(((L32 - L64) ** 2).sum())
+        den += float((L64 ** 2).sum())
+        R = int(it["rows"]["pos"].shape[0])
+        H32, H64 = mcs.dense_hist(b.result(i), R), mcs.dense_hist(r, R)
+        same += int((H32 == H64).sum())
+        total += H32.numel()
     return {"meshes": len(items), "fp32_batched_steps_per_s": steps32 / (ms32 / 1e3),
             "fp64_plain_steps_per_s": steps64 / (ms64 / 1e3),
             "ratio": (steps32 / (ms32 / 1e3)) / (steps64 / (ms64 / 1e3)),
-            "walk_steps": {"fp32": steps32, "fp64": steps64}, "lambda_max_rel_diff": rel,
+            "walk_steps": {"fp32": steps32, "fp64": steps64},
+            "lambda_rel_diff_frobenius": (num / den) ** 0.5, "hit_count_entries_equal": same / total,
             "note": "same meshes, rows, seeds and walks per row; the two precisions share their Philox counters, "
                     "so equal walks per row is equal error"}
 

@@ -466,9 +466,157 @@ __device__ void fps_one_block(const FpsArgs &a) {
         cur = idx;
     }
 }
-__global__ void __launch_bounds__(kFpsThreads) k_fps_block(FpsArgs a) { fps_one_block(a); }
+// The same greedy sampling by ONE block with k_fps_cluster's sub-range
+// culling: the mesh's slots split into sub-ranges of kFpsSub whose centroid
+// boxes and largest distances live in this block's shared memory (`sub`,
+// 3 x 16 B per sub-range), warp w owning sub-ranges w, w + NW, ...; after each
+// new sample only the sub-ranges it can reach are rescanned, and the warps'
+// candidates are folded through double-buffered shared memory.  The choice is
+// that of fps_one_block (largest distance, lowest face on ties); the finer
+// culling rescans a few sub-ranges per selection instead of whole warp ranges.
+__device__ void fps_subrange_block(const FpsArgs &a, float4 *sub) {
+    constexpr int NW = kFpsThreads / 32;
+    constexpr int PER_LANE = kFpsSub / 32;
+    static_assert(NW == 32, "one warp candidate per lane in the fold");
+    __shared__ float4 wc[2][NW];
+    __shared__ int wi[2][NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int s1 = a.nf;
+    const int nsub = (a.nf + kFpsSub - 1) / kFpsSub;
+    float4 *lo4 = sub, *hi4 = sub + nsub, *cc4 = sub + 2 * nsub;
+    const int nown = w < nsub ? (nsub - w + NW - 1) / NW : 0;
+    for (int l = 0; l < nown; l++) {
+        const int j = w + NW * l;
+        const int b0 = j * kFpsSub, b1 = min(s1, b0 + kFpsSub);
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int s = b0 + lane; s < b1; s += 32)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fminf(lo[k], a.cen_s[3 * s + k]);
+                hi[k] = fmaxf(hi[k], a.cen_s[3 * s + k]);
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], o));
+            }
+        if (lane == 0) {
+            lo4[j] = make_float4(lo[0], lo[1], lo[2], INFINITY);
+            hi4[j] = make_float4(hi[0], hi[1], hi[2], __int_as_float(0x7FFFFFFF));
+            cc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) a.sel[0] = 0;
+    float qx = a.cen[0], qy = a.cen[1], qz = a.cen[2];
+    for (int i = 0; i < a.ns; i++) {
+        float bv = -1.0f, bx = 0.f, by = 0.f, bz = 0.f;
+        int bi = 0x7FFFFFFF;
+        for (int r0 = 0; r0 < nown; r0 += 32) {
+            const int j = w + NW * (r0 + lane);
+            bool need = false;
+            if (r0 + lane < nown) {
+                const float4 l = lo4[j], h = hi4[j];
+                const float e0 = fmaxf(fmaxf(l.x - qx, 0.0f), qx - h.x);
+                const float e1 = fmaxf(fmaxf(l.y - qy, 0.0f), qy - h.y);
+                const float e2 = fmaxf(fmaxf(l.z - qz, 0.0f), qz - h.z);
+                need = !((e0 * e0 + e1 * e1 + e2 * e2) * (1.0f - 1e-5f) > l.w);
+            }
+            unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int jb = w + NW * (r0 + b);
+                const int b0 = jb * kFpsSub, b1 = min(s1, b0 + kFpsSub);
+                float v = -1.0f, vx = 0.f, vy = 0.f, vz = 0.f;
+                int vi = 0x7FFFFFFF;
+                float cx[PER_LANE], cy[PER_LANE], cz[PER_LANE], md[PER_LANE];
+                int fc[PER_LANE];
+#pragma unroll
+                for (int k = 0; k < PER_LANE; k++) {
+                    const int s = b0 + lane + 32 * k;
+                    if (s < b1) {
+                        cx[k] = a.cen_s[3 * s];
+                        cy[k] = a.cen_s[3 * s + 1];
+                        cz[k] = a.cen_s[3 * s + 2];
+                        md[k] = a.mind[s];
+                        fc[k] = a.face[s];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PER_LANE; k++) {
+                    const int s = b0 + lane + 32 * k;
+                    if (s < b1) {
+                        const float d0 = cx[k] - qx, d1 = cy[k] - qy, d2 = cz[k] - qz;
+                        const float d = d0 * d0 + d1 * d1 + d2 * d2;
+                        if (d < md[k]) {
+                            md[k] = d;
+                            a.mind[s] = d;
+                            a.owner[s] = i;
+                        }
+                        if (fps_better(md[k], fc[k], v, vi)) { v = md[k]; vi = fc[k]; vx = cx[k]; vy = cy[k]; vz = cz[k]; }
+                    }
+                }
+                warp_argmax_xyz(v, vi, vx, vy, vz);
+                if (lane == b) {
+                    lo4[jb].w = v;
+                    hi4[jb].w = __int_as_float(vi);
+                    cc4[jb] = make_float4(vx, vy, vz, 0.f);
+                }
+            }
+            __syncwarp();
+            if (r0 + lane < nown) {
+                const float v = lo4[j].w;
+                const int vi = __float_as_int(hi4[j].w);
+                if (fps_better(v, vi, bv, bi)) {
+                    const float4 c = cc4[j];
+                    bv = v; bi = vi; bx = c.x; by = c.y; bz = c.z;
+                }
+            }
+        }
+        warp_argmax_xyz(bv, bi, bx, by, bz);
+        if (i + 1 == a.ns) break;
+        // the block's winner: every warp folds the warps' candidates; the two
+        // buffers alternate, so a warp writing the next candidates never
+        // overwrites ones another warp may still be reading
+        const int par = i & 1;
+        if (lane == 0) {
+            wc[par][w] = make_float4(bx, by, bz, bv);
+            wi[par][w] = bi;
+        }
+        __syncthreads();
+        const float4 c = wc[par][lane];
+        float v = c.w, x = c.x, y = c.y, z = c.z;
+        int idx = wi[par][lane];
+        warp_argmax_xyz(v, idx, x, y, z);
+        if (threadIdx.x == 0) a.sel[i + 1] = idx;
+        qx = x; qy = y; qz = z;
+    }
+}
+
+// bytes of dynamic shared memory fps_subrange_block needs for nf faces
+static size_t fps_sub_smem(int nf) { return sizeof(float4) * 3 * (size_t)((nf + kFpsSub - 1) / kFpsSub); }
+
+__global__ void __launch_bounds__(kFpsThreads) k_fps_block(FpsArgs a) {
+    extern __shared__ float4 fps_sub[];
+    fps_subrange_block(a, fps_sub);
+}
 // many meshes at once: block b samples mesh b
-__global__ void __launch_bounds__(kFpsThreads) k_fps_blocks(const FpsArgs *table) { fps_one_block(table[blockIdx.x]); }
+__global__ void __launch_bounds__(kFpsThreads) k_fps_blocks(const FpsArgs *table) {
+    extern __shared__ float4 fps_sub[];
+    fps_subrange_block(table[blockIdx.x], fps_sub);
+}
+// the same for batches holding a mesh whose sub-ranges exceed shared memory
+__global__ void __launch_bounds__(kFpsThreads) k_fps_blocks_coarse(const FpsArgs *table) {
+    fps_one_block(table[blockIdx.x]);
+}
+// shared memory fps_subrange_block may take (sub-range boxes of up to ~570k faces)
+constexpr size_t kFpsSubSmemMax = 212 * 1024;
+
+static mcs_status fps_block_attr(const void *k, size_t smem) {
+    MCS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return MCS_OK;
+}
 constexpr int kFpsChunk = 100;
 struct FpsChunk {
     FpsArgs a[kFpsChunk];
@@ -1064,8 +1212,10 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
     size_t csmem = 0;
     const int cs = m->nf > kFpsSmallFaces ? fps_cluster_size(m->nf, &csmem) : 0;
     if (m->nf <= kFpsSmallFaces) {
+        const size_t smem = fps_sub_smem(m->nf);
+        if ((s = fps_block_attr((const void *)k_fps_block, smem)) != MCS_OK) return s;
         note_launch();
-        k_fps_block<<<1, kFpsThreads, 0, st>>>(a);
+        k_fps_block<<<1, kFpsThreads, smem, st>>>(a);
     } else if (cs > 0) {
         if ((s = launch_fps_cluster(a, cs, csmem, st)) != MCS_OK) return s;
     } else {
@@ -1133,8 +1283,15 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
         note_launch();
         k_store_fps<<<1, 128, 0, st>>>(c, table);
     }
+    size_t smem = 0;
+    for (int i = 0; i < count; i++) smem = std::max(smem, fps_sub_smem(items[i].mesh->nf));
     note_launch();
-    k_fps_blocks<<<count, kFpsThreads, 0, st>>>(table);
+    if (smem <= kFpsSubSmemMax) {
+        if ((s = fps_block_attr((const void *)k_fps_blocks, smem)) != MCS_OK) return s;
+        k_fps_blocks<<<count, kFpsThreads, smem, st>>>(table);
+    } else {
+        k_fps_blocks_coarse<<<count, kFpsThreads, 0, st>>>(table);
+    }
     for (int i = 0; i < count; i++)
         if ((s = sample_finish(items[i], orient, w + base[i], lay[i], st)) != MCS_OK) return s;
     MCS_CUDA(cudaStreamSynchronize(st));
