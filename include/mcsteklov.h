@@ -255,8 +255,10 @@ size_t mcs_estimate_workspace_size(mcs_mesh m, int n_rows, int walks_per_row, lo
  *                  pairs, Philox-4x32-10 counters (seed, row*W + walk, step);
  *                  WoS with BVH closest-point queries to the eps-shell;
  *                  exterior walks in the Kelvin-inverted domain;
- *   histogram   -- exit bins per row, warp-aggregated shared-memory counts,
- *                  padded CSR;
+ *   histogram   -- exit bins per row, warp-aggregated shared-memory counts
+ *                  (up to 51200 rows), or the row's exits radix-sorted in
+ *                  the block and run-length counted (more rows; then
+ *                  walks_per_row <= 8192), into the padded CSR;
  *   assembly    -- W_vu = omega_v cf_u H_vu / W, Lambda = diag(Wsym 1) - Wsym
  *                  with Wsym = (W + W^T)/2 (+ diag of the killing measure).
  * workspace: device, >= mcs_estimate_workspace_size bytes, 256-byte aligned.

@@ -915,6 +915,85 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(const int32_t *exits
                   hist, scan_tmp);
 }
 
+// Rows beyond the shared-memory histogram (R ints per block): the row's W exit
+// bins are radix-sorted within the block (keys bin + 1; bin -1, no exit, is 0;
+// padding 2^end_bit - 1 > R), then every run of equal valid keys is one
+// (bin, count) pair.  A run's first item writes its bin and index into the
+// row's own CSR slots, its last item (after a barrier) turns the index into the
+// count: no array of R or W entries in shared memory.  Bins ascend and the
+// counts, omega and Lambda entries are those of row_histogram.
+constexpr int kHistDenseMaxRows = 51200;
+template <int ITEMS>
+__global__ void __launch_bounds__(kHistThreads) k_histogram_sorted(const int32_t *exits, const int32_t *order,
+                                                                  const RowBall *ball, const double *area,
+                                                                  const double *cf, int R, int W, int cap,
+                                                                  int32_t *hbin, int32_t *hcnt, int32_t *hnnz,
+                                                                  double *Lambda, double *omega_out, Ctrl *ctrl,
+                                                                  int end_bit) {
+    typedef cub::BlockRadixSort<unsigned, kHistThreads, ITEMS> Sort;
+    __shared__ union {
+        typename Sort::TempStorage sort;
+        typename HistScan::TempStorage scan;
+    } tmp;
+    __shared__ unsigned first_s[kHistThreads], last_s[kHistThreads];
+    const int t = threadIdx.x, rp = blockIdx.x;
+    const int v = order[rp];
+    const RowBall &b = ball[v];
+    const double omega = b.valid ? area[v] * b.M * b.kfac : 0.0;
+    if (t == 0 && omega_out) omega_out[v] = omega;
+    if (!b.valid) {
+        if (t == 0) { hnnz[v] = 0; atomicAdd(&ctrl->discarded, 1); }
+        return;
+    }
+    const int32_t *ex = exits + (size_t)rp * W;
+    const unsigned pad = (1u << end_bit) - 1u;
+    unsigned key[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        const int j = k * kHistThreads + t;  // any arrangement: the sort orders them
+        key[k] = j < W ? (unsigned)(ex[j] + 1) : pad;
+    }
+    Sort(tmp.sort).Sort(key, 0, end_bit);  // blocked: thread t holds sorted items t * ITEMS + k
+    first_s[t] = key[0];
+    last_s[t] = key[ITEMS - 1];
+    __syncthreads();
+    const unsigned prev = t > 0 ? last_s[t - 1] : 0u, next = t + 1 < kHistThreads ? first_s[t + 1] : 0u;
+    unsigned st = 0, en = 0;  // run starts / ends among this thread's items (bit k)
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        const bool valid = key[k] >= 1u && key[k] <= (unsigned)R;
+        const unsigned p = k > 0 ? key[k - 1] : prev, n = k + 1 < ITEMS ? key[k + 1] : next;
+        if (valid && key[k] != p) st |= 1u << k;
+        if (valid && key[k] != n) en |= 1u << k;
+    }
+    int sbase, total, ebase;
+    HistScan(tmp.scan).ExclusiveSum(__popc(st), sbase, total);
+    __syncthreads();
+    HistScan(tmp.scan).ExclusiveSum(__popc(en), ebase);
+    int32_t *ob = hbin + (size_t)v * cap, *oc = hcnt + (size_t)v * cap;
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++)
+        if (st >> k & 1u) {
+            ob[sbase] = (int32_t)key[k] - 1;
+            oc[sbase] = t * ITEMS + k;
+            sbase++;
+        }
+    __syncthreads();
+    double *Lrow = Lambda ? Lambda + (size_t)v * R : nullptr;
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++)
+        if (en >> k & 1u) {
+            const int h = t * ITEMS + k - oc[ebase] + 1;
+            oc[ebase] = h;
+            const int u = (int)key[k] - 1;
+            if (Lrow) Lrow[u] = ((omega * (double)h) / (double)W) * (cf ? cf[u] : 1.0);
+            ebase++;
+        }
+    if (t == 0) hnnz[v] = total;
+}
+// exits per row the sorted histogram takes (kHistThreads x 32 items)
+constexpr int kHistSortMaxW = kHistThreads * 32;
+
 // Lambda <- -(D + D^T)/2 off the diagonal, by 32 x 32 tile pairs (I <= J);
 // one block of 32 x 8 threads per pair
 __device__ void symmetrize_tiles(double *L, int R, int I, int J, double (*A)[33], double (*B)[33]) {
@@ -1224,7 +1303,7 @@ static mcs_status check_start_mode(const mcs_params *p, int domain, const mcs_ou
 }
 
 static mcs_status check_mesh_rows(mcs_mesh m, const mcs_rows *rows, const mcs_outputs *out, int domain, int W,
-                                  const std::string &f) {
+                                  const std::string &f, bool batched = false) {
     MCS_ARG(m != nullptr, f + ": NULL mesh");
     const int R = rows->n_rows;
     MCS_ARG(R > 0, f + ": n_rows must be positive");
@@ -1233,7 +1312,11 @@ static mcs_status check_mesh_rows(mcs_mesh m, const mcs_rows *rows, const mcs_ou
     MCS_ARG((long long)R * W < (1LL << 40), f + ": too many walks");
     MCS_ARG(domain == MCS_INTERIOR || domain == MCS_EXTERIOR, f + ": bad domain");
     MCS_ARG(out->hist_bin && out->hist_cnt && out->hist_nnz, f + ": NULL histogram outputs");
-    MCS_ARG((size_t)R * sizeof(int) <= 200 * 1024, f + ": more than 51200 rows per estimate");
+    if (batched)
+        MCS_ARG(R <= kHistDenseMaxRows, f + ": more than 51200 rows in a batch item");
+    else
+        MCS_ARG(R <= kHistDenseMaxRows || W <= kHistSortMaxW,
+                f + ": more than 51200 rows need walks_per_row <= 8192");
     return MCS_OK;
 }
 
@@ -1484,9 +1567,19 @@ static mcs_status enqueue_hist(const Plan &pl, cudaStream_t st) {
         k_fill_zero<<<num_sms() * 8, 256, 0, st>>>(pl.out.Lambda, (size_t)R * R);
     }
     note_launch();
-    k_histogram<<<R, kHistThreads, sizeof(int) * (size_t)R, st>>>(
-        pl.exits(), pl.order(), pl.ball(), pl.rows.area, pl.cf(), R, W, std::min(W, R), pl.out.hist_bin,
-        pl.out.hist_cnt, pl.out.hist_nnz, pl.out.Lambda, pl.out.omega, pl.ctrl);
+    if (R <= kHistDenseMaxRows) {
+        k_histogram<<<R, kHistThreads, sizeof(int) * (size_t)R, st>>>(
+            pl.exits(), pl.order(), pl.ball(), pl.rows.area, pl.cf(), R, W, std::min(W, R), pl.out.hist_bin,
+            pl.out.hist_cnt, pl.out.hist_nnz, pl.out.Lambda, pl.out.omega, pl.ctrl);
+    } else {
+        // keys bin + 1 in [0, R] and the padding 2^end_bit - 1 > R
+        const int end_bit = 32 - __builtin_clz((unsigned)R + 1u);
+        auto *k = W <= kHistThreads * 4 ? k_histogram_sorted<4>
+                                        : (W <= kHistThreads * 16 ? k_histogram_sorted<16> : k_histogram_sorted<32>);
+        k<<<R, kHistThreads, 0, st>>>(pl.exits(), pl.order(), pl.ball(), pl.rows.area, pl.cf(), R, W, std::min(W, R),
+                                      pl.out.hist_bin, pl.out.hist_cnt, pl.out.hist_nnz, pl.out.Lambda, pl.out.omega,
+                                      pl.ctrl, end_bit);
+    }
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
 }
@@ -1612,7 +1705,7 @@ static mcs_status make_batch(const mcs_batch_item *items, int n, const mcs_param
     if (s != MCS_OK) return s;
     for (int i = 0; i < n; i++) {
         s = check_mesh_rows(items[i].mesh, &items[i].rows, &items[i].out, items[i].domain, p->walks_per_row,
-                            f + " item " + std::to_string(i));
+                            f + " item " + std::to_string(i), true);
         if (s != MCS_OK) return s;
         MCS_ARG(p->start_mode == 0, f + ": start_mode 1 and 2 are for single estimates (mcs_estimate_dtn)");
         MCS_ARG(!use_wide(p) || mcs_mesh_has_wide(items[i].mesh),
@@ -1978,7 +2071,10 @@ mcs_status mcs_estimate_dtn(mcs_mesh m, const mcs_rows *rows, const mcs_params *
     int tpb = 0, bps = 0;
     const int mode = pl.ext ? 1 : (p->start_mode != 0 ? 3 : 0);
     if ((s = walk_residency(p, mode, false, &tpb, &bps)) != MCS_OK) { release(); return s; }
-    if ((s = prepare_histogram(hist_smem(rows->n_rows))) != MCS_OK) { release(); return s; }
+    if (rows->n_rows <= kHistDenseMaxRows && (s = prepare_histogram(hist_smem(rows->n_rows))) != MCS_OK) {
+        release();
+        return s;
+    }
     mark(1);
     {
         NvtxRange phase("walks");

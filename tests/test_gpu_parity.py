@@ -328,3 +328,66 @@ def test_group_traversal_bit_exact(oracle, prec):
     assert np.array_equal(res["H0"].cpu().numpy(), est["H0"])
     assert st["steps"] == est["steps"].sum()
 
+
+
+def _csr_row(res, v):
+    cap = res["cap"]
+    n = int(res["hist_nnz"][v])
+    return (res["hist_bin"][v * cap: v * cap + n].cpu().numpy(), res["hist_cnt"][v * cap: v * cap + n].cpu().numpy())
+
+
+def test_more_rows_than_the_shared_histogram_holds(oracle):
+    """60,000 sample rows (beyond the 51,200 of the shared-memory histogram):
+    each row's exits are sorted within its block and run-length counted.  The
+    rows equal the oracle's own sampling, sampled rows' (bin, count) pairs
+    equal the oracle's histograms, and every row's counts sum to W less its
+    walks retired without a hit."""
+    m = meshgen.wild_union(10, 70000, seed=31)
+    R, W = 60000, 64
+    assert m.nf > R
+    mesh = mcs.Mesh(m.V, m.F)
+    g = mcs.sample_rows(mesh, R, orient=True)
+    rl = np.array([0, 1, 12345, 51199, 51200, 51201, 59998, 59999], np.int32)
+    o = oracle.fps_rows(m.V, m.F, R, orient=True, orient_rows=rl)
+    assert np.array_equal(g["sel"].cpu().numpy(), o["sel"])
+    assert np.array_equal(g["tri2bin"].cpu().numpy(), o["tri2bin"])
+    assert np.array_equal(g["pos"].cpu().numpy(), o["pos"])
+    rows = {k: g[k] for k in ("pos", "nrm", "area", "tri2bin")}
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=W, seed=4), assemble=False)
+    torch.cuda.synchronize()
+    nnz = res["hist_nnz"].cpu().numpy()
+    cnt = res["hist_cnt"].view(R, res["cap"]).cpu().numpy()
+    bins = res["hist_bin"].view(R, res["cap"]).cpu().numpy()
+    sums = np.array([cnt[v, :nnz[v]].sum() for v in range(R)])
+    disc = res["omega"].cpu().numpy() == 0.0
+    # walks retired without a hit (reading R18, stats.lost) leave their row short
+    assert np.all(sums[~disc] <= W) and np.all(nnz[disc] == 0)
+    assert int((W - sums[~disc]).sum()) == res["stats"]["lost"]
+    assert all(np.all(np.diff(bins[v, :nnz[v]]) > 0) for v in range(0, R, 97))  # ascending, distinct
+    same = np.all(g["nrm"].cpu().numpy()[rl] == o["nrm"][rl], axis=1)
+    rl = rl[same]
+    rows_np = dict(pos=o["pos"], nrm=o["nrm"], area=o["area"], tri2bin=o["tri2bin"])
+    est = oracle.estimate(m.V, m.F, rows_np, W, 1e-3, seed=4, prec=32, row_list=rl)
+    for li, v in enumerate(rl):
+        b, c = _csr_row(res, int(v))
+        ob = np.flatnonzero(est["H"][li])
+        assert np.array_equal(b, ob) and np.array_equal(c, est["H"][li][ob]), int(v)
+
+
+def test_lambda_beyond_the_shared_histogram():
+    """Lambda assembled from the sorted histograms at 52,000 rows (a 21.6 GB
+    matrix): symmetric and with zero row sums on sampled rows, as everywhere."""
+    m = meshgen.wild_union(8, 60000, seed=37)
+    R, W = 52000, 32
+    mesh = mcs.Mesh(m.V, m.F)
+    g = mcs.sample_rows(mesh, R, orient=True)
+    rows = {k: g[k] for k in ("pos", "nrm", "area", "tri2bin")}
+    res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=W, seed=5))
+    torch.cuda.synchronize()
+    L = res["Lambda"]
+    scale = float(L.diagonal().abs().max())
+    for v in (0, 7, 25000, 51199, 51200, 51999):
+        assert torch.equal(L[v], L[:, v])
+        assert abs(float(L[v].sum())) <= 1e-12 * scale * 50
+    del L, res
+    torch.cuda.empty_cache()
