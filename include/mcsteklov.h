@@ -373,19 +373,28 @@ mcs_status mcs_estimate_dtn_noalloc(mcs_mesh m, const mcs_rows *rows, const mcs_
  * lambda M psi with M = diag(mass); smallest k pairs, Sec. 4.4 / Sec. 5).
  * Chebyshev-filtered subspace iteration on a block of m = k + 32 vectors
  * (rounded up to 16, at most 160): filter products A*Y on the tensor cores
- * (tcgen05 kind::tf32, operands split into tf32 high/low parts), FP64
- * CholeskyQR2 orthonormalisation (shifted CholeskyQR first on the start block), Rayleigh-Ritz with a
+ * (tcgen05 kind::tf32, operands split into tf32 high/low parts), or, for a
+ * sparse A (histogram rows of a large surface reach few bins), on A in CSR
+ * with FP32 values, one fused SIMT kernel per filter term; FP64
+ * CholeskyQR2 orthonormalisation (a shifted CholeskyQR first on the start block, and after a filter
+ * whose block has lost numerical rank), Rayleigh-Ritz with a
  * parallel Jacobi on the block, Ritz values as FP64 Rayleigh quotients. */
 typedef struct {
     int degree;             /* Chebyshev filter degree per iteration (48; <= 256); halved
                                (down to 8) after two iterations that add no converged pair */
     int max_iters;          /* outer iterations (60)                             */
     double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-5) */
+    int product;            /* operator of the filter products: 0 chooses (the sparse one when
+                               at most one entry of A in 32 is nonzero), 1 dense tf32-split
+                               tensor-core product, 2 sparse (CSR, FP32 values and sums) */
 } mcs_eig_params;
 typedef struct {
-    int iterations, converged, block, tc_products;
+    int iterations, converged, block, tc_products;  /* tc_products: filter and Rayleigh-Ritz
+                                                       products of either kind */
     double upper_bound, max_residual;
     int device_error;
+    int product;            /* the operator used: 1 dense, 2 sparse                          */
+    long long nnz;          /* nonzeros of A (entries that round to a nonzero float)         */
 } mcs_eig_stats;
 void mcs_default_eig_params(mcs_eig_params *p);
 size_t mcs_steklov_workspace_size(int n, int k);

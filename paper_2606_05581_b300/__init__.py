@@ -73,12 +73,13 @@ class TuneTrial(C.Structure):
 
 
 class EigParams(C.Structure):
-    _fields_ = [("degree", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double)]
+    _fields_ = [("degree", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double), ("product", C.c_int)]
 
 
 class EigStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("block", C.c_int), ("tc_products", C.c_int),
-                ("upper_bound", C.c_double), ("max_residual", C.c_double), ("device_error", C.c_int)]
+                ("upper_bound", C.c_double), ("max_residual", C.c_double), ("device_error", C.c_int),
+                ("product", C.c_int), ("nnz", C.c_longlong)]
 
 
 _lib = None

@@ -9,7 +9,10 @@
 //              FP32-level accuracy), fed by TMA into 128B-swizzled shared
 //              memory, accumulated in TMEM, split over K and combined by a
 //              deterministic FP32 kernel that also applies the recurrence;
-//   orthonorm  shifted CholeskyQR followed by CholeskyQR2, all in FP64;
+//   orthonorm  CholeskyQR2 in FP64, preceded on the start block by a shifted
+//              CholeskyQR (CholeskyQR3); after a filter the first pass turns
+//              into the shifted one when it meets a pivot that is not
+//              clearly positive, and a third pass follows;
 //   Rayleigh-Ritz  H = X^T A X (FP64 Gram of the tensor-core product), its
 //              eigenvectors by a parallel cyclic Jacobi in FP32 on one SM, the
 //              rotated block re-orthonormalised in FP64 at the next step;
@@ -213,19 +216,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---------------------------------------------------------------- SIMT kernels
+// sinv = M^-1/2 (FP64, once per solve: B300's FP64 divide and square root
+// are too slow to repeat per matrix entry)
+__global__ void k_inv_sqrt(const double *mass, int n, double *sinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sinv[i] = 1.0 / sqrt(mass[i]);
+}
+
 // A = M^-1/2 Lambda M^-1/2 as tf32 high/low parts (zero padded), and the
 // absolute row sums of A (Gershgorin bound of its spectrum)
-__global__ void k_prep_A(const double *L, const double *mass, int n, int n_pad, float *Ahi, float *Alo,
+__global__ void k_prep_A(const double *L, const double *sinv, int n, int n_pad, float *Ahi, float *Alo,
                          double *rowabs) {
     const int i = blockIdx.x;
     __shared__ double red[256];
     double acc = 0.0;
-    const double si = i < n ? 1.0 / sqrt(mass[i]) : 0.0;
+    const double si = i < n ? sinv[i] : 0.0;
     for (int j = threadIdx.x; j < n_pad; j += blockDim.x) {
         float h = 0.f, l = 0.f;
         if (i < n && j < n) {
-            const double sj = 1.0 / sqrt(mass[j]);
-            const double v = L[(size_t)i * n + j] * (si * sj);
+            const double v = L[(size_t)i * n + j] * (si * sinv[j]);
             acc += fabs(v);
             const float f = (float)v;
             h = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
@@ -240,7 +249,7 @@ __global__ void k_prep_A(const double *L, const double *mass, int n, int n_pad, 
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && i < n) rowabs[i] = red[0];
+    if (threadIdx.x == 0 && i < n && rowabs) rowabs[i] = red[0];
 }
 
 __global__ void k_max_reduce(const double *x, int n, double *out) {
@@ -314,10 +323,14 @@ __global__ void k_combine(const float *P, int splits, int m, int n, int n_pad, d
 // (one instruction, one rounding); the library is otherwise built without
 // contraction.
 // Gp[q][a][b] = sum_{i in chunk q} A[a][i] B[b][i] (FP64): 32 x 32 output
-// tiles per block, the n dimension split into chunks across blockIdx.z
+// tiles per block, the n dimension split into chunks across blockIdx.z.  For
+// B = A (upper != 0) only the tiles on and above the diagonal are formed: an
+// entry and its mirror are the same products in the same order, so the lower
+// tiles would repeat the upper ones bit for bit.
 constexpr int kGramChunks = 16;
-__global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, double *Gp) {
+__global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, double *Gp, int upper) {
     __shared__ double sa[32][33], sb[32][33];
+    if (upper && blockIdx.y > blockIdx.x) return;
     const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
     const int chunk = (n_pad + kGramChunks - 1) / kGramChunks;
     const int i0 = blockIdx.z * chunk, i1 = min(n_pad, i0 + chunk);
@@ -343,10 +356,18 @@ __global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, 
         if (a0 + r < m && b0 + tx < m) Gp[((size_t)blockIdx.z * m + a0 + r) * m + b0 + tx] = acc[q];
     }
 }
-__global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym) {
+__global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym, int upper) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m * m) return;
     double s = 0.0;
+    if (upper) {
+        // (a, b) from the tile on or above the diagonal; exactly symmetric
+        const int a = e / m, b = e % m;
+        const int src = (a >> 5) <= (b >> 5) ? e : b * m + a;
+        for (int q = 0; q < kGramChunks; q++) s += Gp[(size_t)q * m * m + src];
+        G[e] = s;
+        return;
+    }
     for (int q = 0; q < kGramChunks; q++) s += Gp[(size_t)q * m * m + e];
     if (sym) {
         const int a = e / m, b = e % m;
@@ -357,79 +378,129 @@ __global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym) {
     G[e] = s;
 }
 
-// upper Cholesky factor of G + shift I (FP64, one block, right-looking: after
-// row j of R is formed the trailing block is updated by all threads)
-__global__ void k_cholesky(const double *G, int m, double shift_rel, double *R, int *err) {
-    extern __shared__ double sg[];
+// R^-1 for the upper Cholesky factor R of G (+ shift I, shift = shift_rel *
+// trace G), FP64, one block of 1024 threads, S = m x (m + 1) in shared memory.
+// B300's FP64 pipe is narrow, so every FP64 warp instruction here does useful
+// work on its lanes (no reductions) and the FP64 divides and square roots are
+// done once per pivot.
+//  1. right-looking elimination on the upper triangle without square roots:
+//     S[a][b] -= S[j][a] S[j][b] / S[j][j] for j < a <= b, one barrier per
+//     step; the lane that updates the next pivot also forms its reciprocal;
+//  2. R[j][c] = S[j][c] / sqrt(S[j][j]); R's diagonal is 1 / rs;
+//  3. Z = R^-1, right-looking from the bottom row: once row k of Z is final,
+//     every row r < k takes acc[r][c] += R[r][k] Z[k][c] (c >= k, Z[k][k] =
+//     rs[k]), and row k - 1, whose sum is then complete, becomes
+//     Z[k-1][c] = -rs[k-1] acc[k-1][c]; Z's strict upper part lives transposed
+//     in S's strict lower triangle.
+// mode 0: no shift; 1: shift; 2: no shift first, and on a pivot <= 1e-15 *
+// trace a restart with the shift, reported in *shifted.  A pivot that is
+// still not positive sets kErrChol and is replaced by 1e-300.
+__global__ void __launch_bounds__(1024) k_chol_inv(const double *G, int m, double shift_rel, int mode, double *Rinv,
+                                                   int *shifted, int *err) {
+    extern __shared__ double S[];  // m x (m + 1)
+    __shared__ double rpiv[160], rs[160];
     __shared__ double tr;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sg[e] = G[e];
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    __shared__ int bad;
+    const int ld = m + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (warp == 0) {
         double t = 0.0;
-        for (int j = threadIdx.x; j < m; j += 32) t += sg[j * m + j];
+        for (int j = lane; j < m; j += 32) t += G[j * m + j];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-        if (threadIdx.x == 0) tr = t;
+        if (lane == 0) tr = t;
+    }
+    int used_shift = 0;
+    for (int attempt = mode == 1 ? 1 : 0; attempt < 2; attempt++) {
+        used_shift = attempt;
+        __syncthreads();
+        const double shift = attempt ? shift_rel * tr : 0.0;
+        const double floor_piv = mode == 2 && attempt == 0 ? 1e-15 * tr : 0.0;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int r = e / m, c = e % m;
+            S[r * ld + c] = G[e] + (r == c ? shift : 0.0);
+        }
+        if (threadIdx.x == 0) bad = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double d = S[0];
+            if (!(d > floor_piv)) {
+                if (floor_piv > 0.0) bad = 1;
+                else atomicOr(err, kErrChol);
+                d = S[0] = 1e-300;
+            }
+            rpiv[0] = 1.0 / d;
+        }
+        __syncthreads();
+        for (int j = 0; j < m - 1; j++) {
+            const double inv = rpiv[j];
+            for (int a = j + 1 + warp; a < m; a += nw) {
+                const double ra = S[j * ld + a] * inv;
+                for (int b = a + lane; b < m; b += 32) S[a * ld + b] = fma(-ra, S[j * ld + b], S[a * ld + b]);
+                if (a == j + 1 && lane == 0) {
+                    double d = S[a * ld + a];
+                    if (!(d > floor_piv)) {
+                        if (floor_piv > 0.0) bad = 1;
+                        else atomicOr(err, kErrChol);
+                        d = S[a * ld + a] = 1e-300;
+                    }
+                    rpiv[a] = 1.0 / d;
+                }
+            }
+            __syncthreads();
+        }
+        if (!bad) break;  // uniform: read after the last barrier
+    }
+    if (threadIdx.x == 0 && shifted) *shifted = used_shift;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) rs[j] = 1.0 / sqrt(S[j * ld + j]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        if (c > r) S[r * ld + c] *= rs[r];
+        else if (c < r) S[r * ld + c] = 0.0;
     }
     __syncthreads();
-    const double shift = shift_rel * tr;
-    for (int e = threadIdx.x; e < m; e += blockDim.x) sg[e * m + e] += shift;
-    __syncthreads();
-    for (int j = 0; j < m; j++) {
-        double d = sg[j * m + j];
-        if (!(d > 0.0)) {
-            if (threadIdx.x == 0) atomicOr(err, kErrChol);
-            d = 1e-300;
-        }
-        d = sqrt(d);
-        __syncthreads();
-        const double inv = 1.0 / d;
-        for (int c = j + threadIdx.x; c < m; c += blockDim.x) sg[j * m + c] = c == j ? d : sg[j * m + c] * inv;
-        __syncthreads();
-        // trailing upper triangle: one warp per row a, lanes over b >= a
-        for (int a = j + 1 + (int)(threadIdx.x >> 5); a < m; a += (int)(blockDim.x >> 5)) {
-            const double ra = sg[j * m + a];
-            for (int b = a + (int)(threadIdx.x & 31); b < m; b += 32) sg[a * m + b] = fma(-ra, sg[j * m + b], sg[a * m + b]);
+    for (int k = m - 1; k >= 1; k--) {
+        const double zk = rs[k];
+        if (m - k >= 32) {
+            // warp per row r < k, lanes over columns c >= k
+            for (int r = warp; r < k; r += nw) {
+                const double rk = S[r * ld + k];
+                for (int c = k + lane; c < m; c += 32) {
+                    double v = fma(rk, c == k ? zk : S[c * ld + k], S[c * ld + r]);
+                    if (r == k - 1) v *= -rs[r];
+                    S[c * ld + r] = v;
+                }
+            }
+        } else {
+            // warp per column c >= k, lanes over rows r < k
+            for (int c = k + warp; c < m; c += nw) {
+                const double z = c == k ? zk : S[c * ld + k];
+                for (int r = lane; r < k; r += 32) {
+                    double v = fma(S[r * ld + k], z, S[c * ld + r]);
+                    if (r == k - 1) v *= -rs[r];
+                    S[c * ld + r] = v;
+                }
+            }
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e / m, c = e % m;
-        R[e] = c >= r ? sg[e] : 0.0;
+        Rinv[e] = c > r ? S[c * ld + r] : c == r ? rs[r] : 0.0;
     }
 }
 
-// Rinv = R^-1 for upper-triangular R (m <= 160): one warp per column c (eight
-// per block of 256 threads), back substitution with R's upper triangle and
-// the columns in shared memory and the inner products reduced across the warp
-__global__ void k_tri_inverse(const double *R, int m, double *Rinv) {
-    extern __shared__ double sr[];  // m x m (upper triangle used)
-    __shared__ double colv[8][160];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sr[e] = R[e];
-    __syncthreads();
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 8 + wl;
-    if (wl >= 8 || c >= m) return;
-    double *x = colv[wl];
-    for (int i = lane; i < m; i += 32) x[i] = 0.0;
-    __syncwarp();
-    for (int i = c; i >= 0; i--) {
-        double s = 0.0;
-        for (int k = i + 1 + lane; k <= c; k += 32) s = fma(sr[i * m + k], x[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - s) / sr[i * m + i];
-        __syncwarp();
-    }
-    for (int i = lane; i < m; i += 32) Rinv[i * m + c] = x[i];
-}
 __global__ void k_f32_to_f64(const float *a, int n, double *b) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) b[e] = (double)a[e];
 }
 
 // Out[j][i] = sum_k C[k][j] In[k][i] (FP64): X <- X C for a block stored by
-// rows of X^T; eight output rows j per block, C's slice in shared memory
+// rows of X^T; eight output rows j per block, C's slice in shared memory.
+// For an upper-triangular C (tri != 0) the sum stops at the block's last j:
+// the skipped terms are exact zeros.
 constexpr int kJG = 8;
-__global__ void k_block_times(const double *C, const double *In, int m, int n_pad, double *Out) {
+__global__ void k_block_times(const double *C, const double *In, int m, int n_pad, double *Out, int tri) {
     extern __shared__ double sc[];  // m x kJG
     const int j0 = blockIdx.y * kJG;
     for (int e = threadIdx.x; e < m * kJG; e += blockDim.x) {
@@ -442,7 +513,8 @@ __global__ void k_block_times(const double *C, const double *In, int m, int n_pa
     double acc[kJG];
 #pragma unroll
     for (int jj = 0; jj < kJG; jj++) acc[jj] = 0.0;
-    for (int k = 0; k < m; k++) {
+    const int kend = tri ? min(m, j0 + kJG) : m;
+    for (int k = 0; k < kend; k++) {
         const double x = In[(size_t)k * n_pad + i];
 #pragma unroll
         for (int jj = 0; jj < kJG; jj++) acc[jj] = fma(sc[k * kJG + jj], x, acc[jj]);
@@ -532,28 +604,43 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
                 cs[i] = c; sn[i] = sv;
             }
             __syncthreads();
-            // one warp per pair, lanes over rows (no index division; the
-            // padded rows keep the column accesses on distinct banks)
+            // H <- J^T H J by 2 x 2 blocks: block (a, b) holds rows {p_a, q_a}
+            // and columns {p_b, q_b}; the column rotation of pair b, then the
+            // row rotation of pair a (the order of a column pass followed by
+            // a row pass), written to (a, b) and mirrored to (b, a).  One warp
+            // per pair a, lanes over b >= a; V <- V J one warp per pair, lanes
+            // over rows.  Blocks are disjoint, so one barrier ends the round.
+            for (int a = warp; a < half; a += nwarps) {
+                const int pa = pp[a], qa = qq[a];
+                const float ca = cs[a], sa = sn[a];
+                for (int b = a + lane; b < half; b += 32) {
+                    const int pb = pp[b], qb = qq[b];
+                    const float cb = cs[b], sb = sn[b];
+                    const float b00 = H[pa * ld + pb], b01 = H[pa * ld + qb];
+                    const float b10 = H[qa * ld + pb], b11 = H[qa * ld + qb];
+                    const float c00 = cb * b00 - sb * b01, c01 = sb * b00 + cb * b01;
+                    const float c10 = cb * b10 - sb * b11, c11 = sb * b10 + cb * b11;
+                    const float d00 = ca * c00 - sa * c10, d10 = sa * c00 + ca * c10;
+                    const float d01 = ca * c01 - sa * c11, d11 = sa * c01 + ca * c11;
+                    H[pa * ld + pb] = d00;
+                    H[pa * ld + qb] = d01;
+                    H[qa * ld + pb] = d10;
+                    H[qa * ld + qb] = d11;
+                    if (b != a) {
+                        H[pb * ld + pa] = d00;
+                        H[qb * ld + pa] = d01;
+                        H[pb * ld + qa] = d10;
+                        H[qb * ld + qa] = d11;
+                    }
+                }
+            }
             for (int i = warp; i < half; i += nwarps) {
                 const int p = pp[i], q = qq[i];
                 const float c = cs[i], sv = sn[i];
                 for (int row = lane; row < m; row += 32) {
-                    const float hp = H[row * ld + p], hq = H[row * ld + q];
-                    H[row * ld + p] = c * hp - sv * hq;
-                    H[row * ld + q] = sv * hp + c * hq;
                     const float vp = V[row * ld + p], vq = V[row * ld + q];
                     V[row * ld + p] = c * vp - sv * vq;
                     V[row * ld + q] = sv * vp + c * vq;
-                }
-            }
-            __syncthreads();
-            for (int i = warp; i < half; i += nwarps) {
-                const int p = pp[i], q = qq[i];
-                const float c = cs[i], sv = sn[i];
-                for (int col = lane; col < m; col += 32) {
-                    const float hp = H[p * ld + col], hq = H[q * ld + col];
-                    H[p * ld + col] = c * hp - sv * hq;
-                    H[q * ld + col] = sv * hp + c * hq;
                 }
             }
             __syncthreads();
@@ -568,6 +655,178 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
         }
         evals[rank] = d;
         for (int r = 0; r < m; r++) Q[r * m + rank] = V[r * ld + j];
+    }
+}
+
+// ---------------------------------------------------------------- sparse product
+// A Lambda estimated from walk histograms is mostly zeros when its rows are
+// sample points of a large surface (each row only reaches the bins its walks
+// exit in).  Then A = M^-1/2 Lambda M^-1/2 is kept in CSR (FP32 values, the
+// same rounding of each entry as the dense path's before its tf32 split,
+// columns ascending) and each filter term is one fused SIMT kernel reading
+// the block vectors by rows (V[i][j], n_pad x m FP32).
+
+// pass 1: nonzeros of row i of A (entries that round to a nonzero float) and
+// its absolute row sum (Gershgorin bound); one block per row
+__global__ void k_row_stats(const double *L, const double *sinv, int n, long long *cnt, double *rowabs) {
+    const int i = blockIdx.x;
+    __shared__ double red[256];
+    __shared__ int redc[256];
+    const double si = sinv[i];
+    double acc = 0.0;
+    int c = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = L[(size_t)i * n + j] * (si * sinv[j]);
+        acc += fabs(v);
+        c += (float)v != 0.f;
+    }
+    red[threadIdx.x] = acc;
+    redc[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[threadIdx.x] += red[threadIdx.x + s];
+            redc[threadIdx.x] += redc[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rowabs[i] = red[0];
+        cnt[i + 1] = redc[0];
+    }
+}
+
+// in-place inclusive scan of rp[1..n] (rp[0] = 0): one block of 1024 threads,
+// each owning a contiguous chunk
+__global__ void k_row_scan(long long *rp, int n) {
+    __shared__ long long part[1024];
+    const int t = threadIdx.x, chunk = (n + 1023) / 1024;
+    const int a = 1 + t * chunk, b = min(n + 1, a + chunk);
+    long long s = 0;
+    for (int i = a; i < b; i++) s += rp[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const long long v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = t > 0 ? part[t - 1] : 0;
+    for (int i = a; i < b; i++) {
+        run += rp[i];
+        rp[i] = run;
+    }
+    if (t == 0) rp[0] = 0;
+}
+
+// pass 2: row i's nonzeros in ascending column order; one block per row, the
+// columns in chunks of 256 compacted by warp ballots
+__global__ void k_csr_fill(const double *L, const double *sinv, int n, const long long *rp, float *vals, int *cols) {
+    const int i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int wcount[8];
+    const double si = sinv[i];
+    long long base = rp[i];
+    for (int j0 = 0; j0 < n; j0 += 256) {
+        const int j = j0 + threadIdx.x;
+        float f = 0.f;
+        if (j < n) f = (float)(L[(size_t)i * n + j] * (si * sinv[j]));
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f != 0.f);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < 8; w++) {
+            off += w < warp ? wcount[w] : 0;
+            tot += wcount[w];
+        }
+        if (f != 0.f) {
+            const long long e = base + off + __popc(bal & ((1u << lane) - 1u));
+            vals[e] = f;
+            cols[e] = j;
+        }
+        base += tot;
+        __syncthreads();
+    }
+}
+
+// FP64 block by rows of X^T (m x n_pad) -> FP32 block by rows of X (n_pad x m)
+__global__ void k_to_rows(const double *Xt, int m, int n_pad, float *V) {
+    __shared__ float tile[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int r = ty; r < 32; r += 8)
+        if (j0 + r < m) tile[r][tx] = (float)Xt[(size_t)(j0 + r) * n_pad + i0 + tx];
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8)
+        if (j0 + tx < m) V[(size_t)(i0 + r) * m + j0 + tx] = tile[tx][r];
+}
+
+// one filter term on the CSR operator:
+//   O = alpha A Y + beta Y + gamma X   (rows < n; padding rows stay zero)
+// with Y, X and O by rows (FP32) and, where O64 is given, O also as FP64 by
+// rows of O^T.  One warp per row of A and lanes over the block's columns;
+// the products accumulate in FP32 with explicit fmaf in ascending column
+// order, the combination is FP64 like the dense path's k_combine.  A block is
+// 32 warps on 32 consecutive rows (one row each, so that short rows still put
+// many warps in flight), and the FP64 output leaves through shared memory in
+// coalesced rows of O^T.
+constexpr int kSpRows = 32;
+template <int JW>
+__global__ void __launch_bounds__(1024) k_sp_filter(const long long *rp, const int *cols, const float *vals, int n,
+                                                    int n_pad, int m, double alpha, double beta, double gamma,
+                                                    const float *Y, const float *X, float *O, double *O64) {
+    __shared__ double s64[kSpRows][JW * 32 + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * kSpRows;
+    {
+        const int r = warp;
+        const int i = i0 + r;
+        float acc[JW];
+#pragma unroll
+        for (int q = 0; q < JW; q++) acc[q] = 0.f;
+        if (i < n) {
+            const long long b = rp[i], e = rp[i + 1];
+            for (long long c0 = b; c0 < e; c0 += 32) {
+                const int cnt = (int)min((long long)32, e - c0);
+                int myc = 0;
+                float myv = 0.f;
+                if (lane < cnt) {
+                    myc = cols[c0 + lane];
+                    myv = vals[c0 + lane];
+                }
+#pragma unroll 4
+                for (int t = 0; t < cnt; t++) {
+                    const int k = __shfl_sync(0xFFFFFFFFu, myc, t);
+                    const float a = __shfl_sync(0xFFFFFFFFu, myv, t);
+                    const float *yr = Y + (size_t)k * m;
+#pragma unroll
+                    for (int q = 0; q < JW; q++) {
+                        const int j = lane + 32 * q;
+                        if (j < m) acc[q] = fmaf(a, yr[j], acc[q]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < JW; q++) {
+            const int j = lane + 32 * q;
+            if (j >= m) continue;
+            double v = 0.0;
+            if (i < n) {
+                v = alpha * (double)acc[q];
+                if (beta != 0.0) v += beta * (double)Y[(size_t)i * m + j];
+                if (gamma != 0.0) v += gamma * (double)X[(size_t)i * m + j];
+            }
+            if (O) O[(size_t)i * m + j] = (float)v;
+            s64[r][j] = v;
+        }
+    }
+    if (!O64) return;
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * kSpRows; e += blockDim.x) {
+        const int j = e / kSpRows, r = e % kSpRows;
+        O64[(size_t)j * n_pad + i0 + r] = s64[r][j];
     }
 }
 
@@ -635,9 +894,10 @@ static Plan plan_for(int n, int k, int guard) {
 struct Ws {
     float *Ahi, *Alo, *P;
     float *vh[4], *vl[4];   // tf32 parts of block vectors (m x n_pad)
-    double *Xt, *Zt, *Xt2, *G, *Gp, *R, *Rinv, *Qd, *theta, *res, *rowabs, *bound;
+    double *Xt, *Zt, *Xt2, *G, *Gp, *Rinv, *Qd, *theta, *res, *rowabs, *bound, *sinv;
     float *Q, *qev;
-    int *err;
+    int *err, *shifted;
+    long long *rp;  // CSR row pointers of the sparse operator (n + 1)
     size_t total;
 };
 
@@ -657,16 +917,18 @@ static Ws ws_layout(const Plan &p, char *base) {
     w.Xt2 = (double *)take(mv * 8);
     w.G = (double *)take((size_t)p.m * p.m * 8);
     w.Gp = (double *)take((size_t)kGramChunks * p.m * p.m * 8);
-    w.R = (double *)take((size_t)p.m * p.m * 8);
     w.Rinv = (double *)take((size_t)p.m * p.m * 8);
     w.Qd = (double *)take((size_t)p.m * p.m * 8);
     w.theta = (double *)take(p.m * 8);
     w.res = (double *)take(p.m * 8);
     w.rowabs = (double *)take((size_t)p.n * 8);
+    w.sinv = (double *)take((size_t)p.n * 8);
     w.bound = (double *)take(8);
     w.Q = (float *)take((size_t)p.m * p.m * 4);
     w.qev = (float *)take(p.m * 4);
     w.err = (int *)take(4);
+    w.shifted = (int *)take(4);
+    w.rp = (long long *)take((size_t)(p.n + 1) * 8);
     w.total = o;
     return w;
 }
@@ -676,6 +938,7 @@ struct Ctx {
     Ws w;
     cudaStream_t st;
     CUtensorMap mAh, mAl, mBh[4], mBl[4];
+    bool sparse = false;  // CSR operator: values in Ahi's space, columns in Alo's, vectors by rows in vh[]
 };
 
 // P <- A * (block b), the tensor-core product
@@ -696,6 +959,39 @@ static cudaError_t tc_product(Ctx &c, int b) {
 }
 
 static int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 16); }
+
+// one term O = alpha A Y + beta Y + gamma X on the CSR operator (vectors by rows)
+static cudaError_t sp_filter(Ctx &c, double alpha, double beta, double gamma, const float *Y, const float *X, float *O,
+                             double *O64) {
+    const int m = c.p.m, jw = (m + 31) / 32;
+    const dim3 grid(c.p.n_pad / kSpRows);
+    const long long *rp = c.w.rp;
+    const int *cols = (const int *)c.w.Alo;
+    const float *vals = c.w.Ahi;
+    note_launch();
+#define MCS_SP(JW)                                                                                                    \
+    k_sp_filter<JW><<<grid, 32 * kSpRows, 0, c.st>>>(rp, cols, vals, c.p.n, c.p.n_pad, m, alpha, beta, gamma, Y, X, O, O64)
+    switch (jw) {
+        case 1: MCS_SP(1); break;
+        case 2: MCS_SP(2); break;
+        case 3: MCS_SP(3); break;
+        case 4: MCS_SP(4); break;
+        default: MCS_SP(5); break;
+    }
+#undef MCS_SP
+    return cudaGetLastError();
+}
+
+// block X (FP64 by rows of X^T) into the product's operand buffer b: tf32
+// parts for the dense product, FP32 by rows for the sparse one
+static void to_operand(Ctx &c, const double *X, int b) {
+    const size_t mv = (size_t)c.p.m * c.p.n_pad;
+    note_launch();
+    if (c.sparse)
+        k_to_rows<<<dim3(c.p.n_pad / 32, (c.p.m + 31) / 32), 256, 0, c.st>>>(X, c.p.m, c.p.n_pad, c.w.vh[b]);
+    else
+        k_split<<<grid_for(mv), 256, 0, c.st>>>(X, mv, c.w.vh[b], c.w.vl[b]);
+}
 
 }  // namespace eig
 }  // namespace mcs
@@ -720,7 +1016,9 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     mcs_eig_params prm;
     mcs_default_eig_params(&prm);
     if (ep) prm = *ep;
-    MCS_ARG(prm.degree >= 1 && prm.degree <= 256 && prm.max_iters >= 1 && prm.tol > 0.0, "mcs_steklov_modes: bad params");
+    MCS_ARG(prm.degree >= 1 && prm.degree <= 256 && prm.max_iters >= 1 && prm.tol > 0.0 && prm.product >= 0 &&
+                prm.product <= 2,
+            "mcs_steklov_modes: bad params");
     Ctx c;
     c.p = plan_for(n, k, 32);
     c.st = as_stream(stream_);
@@ -740,24 +1038,37 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
             return MCS_ERR_CUDA;
         }
     MCS_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem));
-    const size_t smm = (size_t)m * m * sizeof(double);
-    MCS_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    MCS_CUDA(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    const size_t smm = (size_t)m * (m + 1) * sizeof(double);
+    MCS_CUDA(cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
     const size_t jsm = 2 * (size_t)m * (m + 1) * sizeof(float);
     MCS_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
     cudaStream_t st = c.st;
     const size_t mv = (size_t)m * p.n_pad;
     const int g = grid_for(mv);
     MCS_CUDA(cudaMemsetAsync(c.w.err, 0, sizeof(int), st));
+    // row nonzeros and Gershgorin sums of A, then the operator: CSR when A
+    // has at most one nonzero in 32 (or when asked), else the dense tf32 parts
     note_launch();
-    k_prep_A<<<p.n_pad, 256, 0, st>>>(Lambda, mass, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.rowabs);
+    k_inv_sqrt<<<(n + 255) / 256, 256, 0, st>>>(mass, n, c.w.sinv);
+    note_launch();
+    k_row_stats<<<n, 256, 0, st>>>(Lambda, c.w.sinv, n, c.w.rp, c.w.rowabs);
+    note_launch();
+    k_row_scan<<<1, 1024, 0, st>>>(c.w.rp, n);
     note_launch();
     k_max_reduce<<<1, 1024, 0, st>>>(c.w.rowabs, n, c.w.bound);
     note_launch();
     k_random_block<<<g, 256, 0, st>>>(c.w.Xt, m, n, p.n_pad);
     double bound = 0.0;
+    long long nnz = 0;
     MCS_CUDA(cudaMemcpyAsync(&bound, c.w.bound, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MCS_CUDA(cudaMemcpyAsync(&nnz, c.w.rp + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaStreamSynchronize(st));
+    c.sparse = prm.product == 2 || (prm.product == 0 && nnz * 32 <= (long long)n * n);
+    note_launch();
+    if (c.sparse)
+        k_csr_fill<<<n, 256, 0, st>>>(Lambda, c.w.sinv, n, c.w.rp, c.w.Ahi, (int *)c.w.Alo);
+    else
+        k_prep_A<<<p.n_pad, 256, 0, st>>>(Lambda, c.w.sinv, n, p.n_pad, c.w.Ahi, c.w.Alo, nullptr);
     if (!(bound > 0.0)) bound = 1.0;
     const double ub = bound * 1.01;
 
@@ -767,27 +1078,40 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     const dim3 bgrid(p.n_pad / 128, (m + kJG - 1) / kJG);
     const size_t bsm = (size_t)m * kJG * sizeof(double);
     auto gram = [&](const double *A, const double *B, int sym) {
+        const int upper = A == B;
         note_launch();
-        k_gram_part<<<ggrid, 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp);
+        k_gram_part<<<ggrid, 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp, upper);
         note_launch();
-        k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym);
+        k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym, upper);
     };
     // orthonormalise X: shifted CholeskyQR, then CholeskyQR2 (FP64)
-    auto orth = [&](bool shifted) -> cudaError_t {
-        const double shifts[3] = {11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16, 0.0, 0.0};
-        for (int pass = shifted ? 0 : 1; pass < 3; pass++) {
-            gram(X, X, 1);
-            note_launch();
-            k_cholesky<<<1, 256, smm, st>>>(c.w.G, m, shifts[pass], c.w.R, c.w.err);
-            note_launch();
-            k_tri_inverse<<<(m + 7) / 8, 256, smm, st>>>(c.w.R, m, c.w.Rinv);
-            note_launch();
-            k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T);
-            std::swap(X, T);
+    // one CholeskyQR pass: X <- X R^-1 with R^T R = X^T X (+ shift); mode as k_chol_inv's
+    const double shift_rel = 11.0 * ((double)p.n_pad * m + (double)m * (m + 1)) * 1.1102230246251565e-16;
+    auto cholqr = [&](int mode) {
+        gram(X, X, 1);
+        note_launch();
+        k_chol_inv<<<1, 1024, smm, st>>>(c.w.G, m, shift_rel, mode, c.w.Rinv, c.w.shifted, c.w.err);
+        note_launch();
+        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Rinv, X, m, p.n_pad, T, 1);
+        std::swap(X, T);
+    };
+    // orthonormalise X in FP64: CholeskyQR2, preceded by a shifted pass
+    // (CholeskyQR3) always (first = 1) or only when the first pass meets a
+    // pivot that is not clearly positive (first = 2: that pass then restarts
+    // shifted and a third pass follows)
+    auto orth = [&](int first) -> cudaError_t {
+        cholqr(first);
+        cholqr(0);
+        int extra = first == 1;
+        if (first == 2) {
+            cudaError_t e = cudaMemcpyAsync(&extra, c.w.shifted, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
         }
+        if (extra) cholqr(0);
         return cudaGetLastError();
     };
-    MCS_CUDA(orth(true));
+    MCS_CUDA(orth(1));
     std::vector<double> theta(m), res(m);
     double a_cut = ub / 8.0, a_low = 0.0;
     int iters = 0, converged = 0, gemms = 0;
@@ -798,18 +1122,35 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     int deg = prm.degree, best_conv = -1, stall = 0;
     for (iters = 0; iters < prm.max_iters; iters++) {
         // ---- Chebyshev filter of degree d on [a_cut, ub] applied to X
-        note_launch();
-        k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[0], c.w.vl[0]);
+        to_operand(c, X, 0);
         const double e = 0.5 * (ub - a_cut), cc = 0.5 * (ub + a_cut);
         double sigma = e / (a_low - cc);
         const double tau = 2.0 / sigma;
         int prev = -1, cur = 0;
         for (int d = 1; d <= deg; d++) {
-            MCS_CUDA(tc_product(c, cur));
             gemms++;
             int nxt = (cur + 1) % 3;
             if (nxt == prev) nxt = (nxt + 1) % 3;
             const bool last = d == deg;
+            if (c.sparse) {
+                double alpha, beta, gamma = 0.0;
+                if (d == 1) {
+                    alpha = sigma / e;
+                    beta = -cc * sigma / e;
+                } else {
+                    const double sig_new = 1.0 / (tau - sigma);
+                    alpha = 2.0 * sig_new / e;
+                    beta = -2.0 * sig_new * cc / e;
+                    gamma = -sigma * sig_new;
+                    sigma = sig_new;
+                }
+                MCS_CUDA(sp_filter(c, alpha, beta, gamma, c.w.vh[cur], d == 1 ? nullptr : c.w.vh[prev],
+                                   last ? nullptr : c.w.vh[nxt], last ? X : nullptr));
+                prev = cur;
+                cur = nxt;
+                continue;
+            }
+            MCS_CUDA(tc_product(c, cur));
             if (d == 1) {
                 const double alpha = sigma / e, beta = -cc * sigma / e;
                 note_launch();
@@ -828,25 +1169,32 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
             prev = cur;
             cur = nxt;
         }
-        MCS_CUDA(orth(false));
+        // a filter that amplifies the lowest eigenvalues by many orders over
+        // the top of the block can leave it numerically rank deficient
+        // (accurate products keep no noise floor): the unshifted Gram then
+        // has pivots that are not positive, and the shifted pass takes over
+        MCS_CUDA(orth(2));
         // ---- Rayleigh-Ritz
-        note_launch();
-        k_split<<<g, 256, 0, st>>>(X, mv, c.w.vh[3], c.w.vl[3]);
-        MCS_CUDA(tc_product(c, 3));
+        to_operand(c, X, 3);
         gemms++;
-        note_launch();
-        k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr, nullptr,
-                                    nullptr, nullptr, Z);
+        if (c.sparse) {
+            MCS_CUDA(sp_filter(c, 1.0, 0.0, 0.0, c.w.vh[3], nullptr, nullptr, Z));
+        } else {
+            MCS_CUDA(tc_product(c, 3));
+            note_launch();
+            k_combine<<<g, 256, 0, st>>>(c.w.P, p.splits, m, n, p.n_pad, 1.0, 0.0, 0.0, nullptr, nullptr, nullptr,
+                                        nullptr, nullptr, nullptr, Z);
+        }
         gram(X, Z, 1);
         note_launch();
         k_jacobi<<<1, 1024, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
         note_launch();
         k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
         note_launch();
-        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, X, m, p.n_pad, T);
+        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, X, m, p.n_pad, T, 0);
         std::swap(X, T);
         note_launch();
-        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, Z, m, p.n_pad, T);
+        k_block_times<<<bgrid, 128, bsm, st>>>(c.w.Qd, Z, m, p.n_pad, T, 0);
         std::swap(Z, T);
         note_launch();
         k_ritz<<<m, 256, 0, st>>>(X, Z, p.n_pad, c.w.theta, c.w.res);
@@ -868,7 +1216,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         a_low = std::min(0.0, theta[0]);
     }
     // the last rotation used the FP32 Jacobi vectors: restore FP64 orthonormality
-    if (evecs) MCS_CUDA(orth(false));
+    if (evecs) MCS_CUDA(orth(0));
     int err = 0;
     MCS_CUDA(cudaMemcpyAsync(&err, c.w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MCS_CUDA(cudaMemcpyAsync(evals, c.w.theta, k * sizeof(double), cudaMemcpyDefault, st));
@@ -887,6 +1235,8 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         stats->max_residual = 0.0;
         for (int j = 0; j < k; j++) stats->max_residual = std::max(stats->max_residual, res[j]);
         stats->device_error = err;
+        stats->product = c.sparse ? 2 : 1;
+        stats->nnz = nnz;
     }
     if (err & kErrTimeout) {
         set_error("mcs_steklov_modes: a tensor-core pipeline wait timed out");
@@ -931,7 +1281,9 @@ mcs_status mcs_tc_symm_product(const double *A, const double *Xt_in, int n, int 
     std::vector<double> h1(n, 1.0);
     MCS_CUDA(cudaMemcpyAsync(ones, h1.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     note_launch();
-    k_prep_A<<<p.n_pad, 256, 0, st>>>(A, ones, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.Zt);
+    k_inv_sqrt<<<(n + 255) / 256, 256, 0, st>>>(ones, n, c.w.sinv);
+    note_launch();
+    k_prep_A<<<p.n_pad, 256, 0, st>>>(A, c.w.sinv, n, p.n_pad, c.w.Ahi, c.w.Alo, c.w.Zt);
     const size_t mv = (size_t)p.m * p.n_pad;
     MCS_CUDA(cudaMemsetAsync(c.w.Xt, 0, mv * sizeof(double), st));
     MCS_CUDA(cudaMemcpy2DAsync(c.w.Xt, p.n_pad * sizeof(double), Xt_in, n * sizeof(double), n * sizeof(double), p.m,
@@ -971,6 +1323,7 @@ void mcs_default_eig_params(mcs_eig_params *p) {
     p->degree = 48;
     p->max_iters = 60;
     p->tol = 1e-5;
+    p->product = 0;
 }
 
 }  // extern "C"

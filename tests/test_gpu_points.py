@@ -156,7 +156,10 @@ def test_point_basis_sphere_spectrum():
     Phi, lev, st = mcs.point_basis(rows, 48)
     assert st["status"] == 0
     lev = lev.cpu().numpy()
-    assert abs(lev[0]) < 1e-6 * lev[8] and np.abs(lev[1:4] - 2).max() < 0.1 and np.abs(lev[4:9] - 6).max() < 0.3
+    # the constant mode: zero to the eigensolver's stated accuracy (residual
+    # <= tol x upper bound, tol = 1e-5), whichever product it took
+    assert abs(lev[0]) <= 1e-5 * st["upper_bound"], (lev[0], st["upper_bound"], st["product"])
+    assert np.abs(lev[1:4] - 2).max() < 0.1 and np.abs(lev[4:9] - 6).max() < 0.3
     res = mcs.estimate_dtn(mesh, rows, mcs.default_params(walks_per_row=256, prec=32, seed=1), record_exits=True,
                            record_bary=True)
     spacing = math.sqrt(4 * math.pi / m.nf)

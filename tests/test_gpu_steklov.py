@@ -194,3 +194,75 @@ def test_interior_steklov_heat_conserves_total_heat():
     lam0 = abs(float(ev[0]))
     assert lam0 < 1e-5 * st["upper_bound"]
     assert np.all(np.abs(tot - m0) <= m0 * (lam0 * times + 1e-3)), (tot, m0, lam0)
+
+
+def _knn_laplacian(n, nb=8, seed=0):
+    """A sparse Laplacian-form matrix (zero row sums, symmetric, positive
+    semidefinite): Gaussian weights of a symmetrised nb-nearest-neighbour graph
+    of random points on the unit sphere, with random positive masses."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    P = rng.normal(size=(n, 3))
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    d, idx = cKDTree(P).query(P, nb + 1)
+    h2 = np.mean(d[:, 1:] ** 2)
+    Wg = np.zeros((n, n))
+    for i in range(n):
+        Wg[i, idx[i, 1:]] = np.exp(-d[i, 1:] ** 2 / h2)
+    Wg = np.maximum(Wg, Wg.T)
+    L = np.diag(Wg.sum(1)) - Wg
+    mass = rng.uniform(0.5, 1.5, n) * (4 * np.pi / n)
+    return L, mass
+
+
+def _float_nonzeros(L, mass):
+    s = 1.0 / np.sqrt(mass)
+    return int(np.count_nonzero((L * (s[:, None] * s[None, :])).astype(np.float32)))
+
+
+@pytest.mark.parametrize("n,k,product", [(3000, 64, 0), (1000, 128, 2), (700, 16, 2), (3000, 64, 1)])
+def test_sparse_and_dense_products_match_lapack(n, k, product):
+    """The eigensolver on a sparse Laplacian-form matrix with the CSR product
+    (chosen automatically at 0.3 % density, or forced) and with the dense
+    tensor-core product: eigenvalues against LAPACK to the dense test's bound,
+    M-orthonormal vectors, the zero mode, and the reported nonzero count and
+    operator (the rule: sparse when at most one entry in 32 is nonzero).
+    Blocks of 48, 96 and 160 vectors take the sparse kernel's 2-, 3- and
+    5-word lane layouts."""
+    L, mass = _knn_laplacian(n, seed=n + k)
+    sq = np.sqrt(mass)
+    A = L / np.outer(sq, sq)
+    ref = np.linalg.eigvalsh(A)
+    lmax = ref.max()
+    p = mcs.default_eig_params(product=product)
+    ev, X, st = mcs.steklov_modes(torch.from_numpy(L).cuda(), torch.from_numpy(mass).cuda(), k, params=p)
+    assert st["status"] == 0, st
+    nnz = _float_nonzeros(L, mass)
+    assert st["nnz"] == nnz
+    want = product if product else (2 if nnz * 32 <= n * n else 1)
+    assert st["product"] == want
+    ev = ev.cpu().numpy()
+    assert np.abs(ev - ref[:k]).max() <= 1e-4 * lmax + 1e-6, (np.abs(ev - ref[:k]).max(), lmax)
+    assert abs(ev[0]) <= 1e-5 * st["upper_bound"]
+    X = X.cpu().numpy()
+    G = X.T @ (mass[:, None] * X)
+    assert np.abs(G - np.eye(k)).max() < 1e-6
+
+
+def test_sparse_product_on_an_estimated_lambda(oracle):
+    """The oracle's Lambda of the icosphere (vertex rows, W = 128) through the
+    forced sparse product gives LAPACK's spectrum like the dense product does;
+    the automatic choice follows the density rule."""
+    L, mass = _oracle_lambda(oracle)
+    ref, _ = oracle.steklov(L, mass, 32)
+    lmax = np.linalg.eigvalsh(L / np.sqrt(np.outer(mass, mass))).max()
+    Ld, md = torch.from_numpy(L).cuda(), torch.from_numpy(mass).cuda()
+    ev2, _, st2 = mcs.steklov_modes(Ld, md, 32, params=mcs.default_eig_params(product=2))
+    ev0, _, st0 = mcs.steklov_modes(Ld, md, 32)
+    assert st2["status"] == 0 and st0["status"] == 0
+    assert st2["product"] == 2
+    nnz = _float_nonzeros(L, mass)
+    assert st0["nnz"] == st2["nnz"] == nnz
+    assert st0["product"] == (2 if nnz * 32 <= L.shape[0] ** 2 else 1)
+    for ev in (ev2, ev0):
+        assert np.abs(ev.cpu().numpy() - ref).max() <= 1e-4 * lmax + 1e-6
