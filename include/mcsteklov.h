@@ -395,6 +395,7 @@ typedef struct {
     int device_error;
     int product;            /* the operator used: 1 dense, 2 sparse                          */
     long long nnz;          /* nonzeros of A (entries that round to a nonzero float)         */
+    int jacobi_sweeps;      /* Jacobi sweeps of the Rayleigh-Ritz steps, summed              */
 } mcs_eig_stats;
 void mcs_default_eig_params(mcs_eig_params *p);
 size_t mcs_steklov_workspace_size(int n, int k);

@@ -79,7 +79,7 @@ class EigParams(C.Structure):
 class EigStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("block", C.c_int), ("tc_products", C.c_int),
                 ("upper_bound", C.c_double), ("max_residual", C.c_double), ("device_error", C.c_int),
-                ("product", C.c_int), ("nnz", C.c_longlong)]
+                ("product", C.c_int), ("nnz", C.c_longlong), ("jacobi_sweeps", C.c_int)]
 
 
 _lib = None

@@ -323,16 +323,16 @@ __global__ void k_combine(const float *P, int splits, int m, int n, int n_pad, d
 // (one instruction, one rounding); the library is otherwise built without
 // contraction.
 // Gp[q][a][b] = sum_{i in chunk q} A[a][i] B[b][i] (FP64): 32 x 32 output
-// tiles per block, the n dimension split into chunks across blockIdx.z.  For
+// tiles per block, the n dimension split into gridDim.z chunks.  For
 // B = A (upper != 0) only the tiles on and above the diagonal are formed: an
 // entry and its mirror are the same products in the same order, so the lower
 // tiles would repeat the upper ones bit for bit.
-constexpr int kGramChunks = 16;
+constexpr int kGramChunksMax = 64;
 __global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, double *Gp, int upper) {
     __shared__ double sa[32][33], sb[32][33];
     if (upper && blockIdx.y > blockIdx.x) return;
     const int a0 = blockIdx.y * 32, b0 = blockIdx.x * 32;
-    const int chunk = (n_pad + kGramChunks - 1) / kGramChunks;
+    const int chunk = (n_pad + gridDim.z - 1) / gridDim.z;
     const int i0 = blockIdx.z * chunk, i1 = min(n_pad, i0 + chunk);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     double acc[4] = {0, 0, 0, 0};
@@ -356,7 +356,7 @@ __global__ void k_gram_part(const double *A, const double *B, int m, int n_pad, 
         if (a0 + r < m && b0 + tx < m) Gp[((size_t)blockIdx.z * m + a0 + r) * m + b0 + tx] = acc[q];
     }
 }
-__global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym, int upper) {
+__global__ void k_gram_reduce(const double *Gp, int m, int chunks, double *G, int sym, int upper) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m * m) return;
     double s = 0.0;
@@ -364,15 +364,15 @@ __global__ void k_gram_reduce(const double *Gp, int m, double *G, int sym, int u
         // (a, b) from the tile on or above the diagonal; exactly symmetric
         const int a = e / m, b = e % m;
         const int src = (a >> 5) <= (b >> 5) ? e : b * m + a;
-        for (int q = 0; q < kGramChunks; q++) s += Gp[(size_t)q * m * m + src];
+        for (int q = 0; q < chunks; q++) s += Gp[(size_t)q * m * m + src];
         G[e] = s;
         return;
     }
-    for (int q = 0; q < kGramChunks; q++) s += Gp[(size_t)q * m * m + e];
+    for (int q = 0; q < chunks; q++) s += Gp[(size_t)q * m * m + e];
     if (sym) {
         const int a = e / m, b = e % m;
         double t = 0.0;
-        for (int q = 0; q < kGramChunks; q++) t += Gp[(size_t)q * m * m + b * m + a];
+        for (int q = 0; q < chunks; q++) t += Gp[(size_t)q * m * m + b * m + a];
         s = 0.5 * (s + t);
     }
     G[e] = s;
@@ -548,7 +548,7 @@ __global__ void k_ritz(const double *Xt, const double *Zt, int n_pad, double *th
 // Jacobi (round-robin pair schedule) in FP32, one block; eigenvalues ascending,
 // eigenvectors in the columns of Q.  Shared rows are padded to m + 1 floats so
 // that column sweeps hit distinct banks.
-__global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int max_sweeps) {
+__global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int max_sweeps, int *sweeps_done) {
     extern __shared__ float sj[];
     const int ld = m + 1;
     float *H = sj, *V = sj + m * ld;
@@ -556,6 +556,7 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
     __shared__ int pp[80], qq[80];
     __shared__ float red_off[32], red_tot[32];
     __shared__ int stop;
+    float prev_off = 0.f;  // thread 0's
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e / m, c = e % m;
         H[r * ld + c] = (float)(0.5 * (Hd[r * m + c] + Hd[c * m + r]));
@@ -581,10 +582,17 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
         if (threadIdx.x == 0) {
             float so = 0.f, st = 0.f;
             for (int w = 0; w < nwarps; w++) { so += red_off[w]; st += red_tot[w]; }
-            stop = so <= 1e-12f * st;
+            // converged, or at FP32's rounding floor: a sweep that no longer
+            // halves the off-diagonal norm has stopped converging quadratically
+            stop = so <= 1e-12f * st || (sweep >= 4 && so > 0.25f * prev_off);
+            prev_off = so;
         }
         __syncthreads();
-        if (stop) break;
+        if (stop) {
+            if (threadIdx.x == 0) *sweeps_done += sweep;
+            break;
+        }
+        if (sweep == max_sweeps - 1 && threadIdx.x == 0) *sweeps_done += max_sweeps;
         for (int r = 0; r < m - 1; r++) {
             if (threadIdx.x < half) {
                 const int i = threadIdx.x;
@@ -676,7 +684,11 @@ __global__ void k_row_stats(const double *L, const double *sinv, int n, long lon
     double acc = 0.0;
     int c = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double v = L[(size_t)i * n + j] * (si * sinv[j]);
+        // zeros (most of a histogram Lambda) are skipped by an integer test of
+        // the bits: they add nothing, and B300's FP64 pipe is narrow
+        const double l = L[(size_t)i * n + j];
+        if ((__double_as_longlong(l) << 1) == 0) continue;
+        const double v = l * (si * sinv[j]);
         acc += fabs(v);
         c += (float)v != 0.f;
     }
@@ -731,7 +743,10 @@ __global__ void k_csr_fill(const double *L, const double *sinv, int n, const lon
     for (int j0 = 0; j0 < n; j0 += 256) {
         const int j = j0 + threadIdx.x;
         float f = 0.f;
-        if (j < n) f = (float)(L[(size_t)i * n + j] * (si * sinv[j]));
+        if (j < n) {
+            const double l = L[(size_t)i * n + j];
+            if ((__double_as_longlong(l) << 1) != 0) f = (float)(l * (si * sinv[j]));
+        }
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, f != 0.f);
         if (lane == 0) wcount[warp] = __popc(bal);
         __syncthreads();
@@ -767,7 +782,10 @@ __global__ void k_to_rows(const double *Xt, int m, int n_pad, float *V) {
 // with Y, X and O by rows (FP32) and, where O64 is given, O also as FP64 by
 // rows of O^T.  One warp per row of A and lanes over the block's columns;
 // the products accumulate in FP32 with explicit fmaf in ascending column
-// order, the combination is FP64 like the dense path's k_combine.  A block is
+// order.  A term that continues the recurrence combines in FP32 (its result is
+// stored in FP32, and B300's FP64 pipe would bound the kernel); the last term,
+// which writes X in FP64, combines in FP64 like the dense path's k_combine.
+// A block is
 // 32 warps on 32 consecutive rows (one row each, so that short rows still put
 // many warps in flight), and the FP64 output leaves through shared memory in
 // coalesced rows of O^T.
@@ -775,7 +793,8 @@ constexpr int kSpRows = 32;
 template <int JW>
 __global__ void __launch_bounds__(1024) k_sp_filter(const long long *rp, const int *cols, const float *vals, int n,
                                                     int n_pad, int m, double alpha, double beta, double gamma,
-                                                    const float *Y, const float *X, float *O, double *O64) {
+                                                    float alpha_f, float beta_f, float gamma_f, const float *Y,
+                                                    const float *X, float *O, double *O64) {
     __shared__ double s64[kSpRows][JW * 32 + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i0 = blockIdx.x * kSpRows;
@@ -795,31 +814,59 @@ __global__ void __launch_bounds__(1024) k_sp_filter(const long long *rp, const i
                     myc = cols[c0 + lane];
                     myv = vals[c0 + lane];
                 }
-#pragma unroll 4
-                for (int t = 0; t < cnt; t++) {
-                    const int k = __shfl_sync(0xFFFFFFFFu, myc, t);
-                    const float a = __shfl_sync(0xFFFFFFFFu, myv, t);
-                    const float *yr = Y + (size_t)k * m;
+                // U nonzeros at a time: all their Y loads issue before the
+                // multiply-adds, which keep the ascending column order; slots
+                // past the row's end carry weight 0 and read row k = 0
+                constexpr int U = JW <= 3 ? 8 : 4;
+                for (int t0 = 0; t0 < cnt; t0 += U) {
+                    float av[U], yv[U][JW];
 #pragma unroll
-                    for (int q = 0; q < JW; q++) {
-                        const int j = lane + 32 * q;
-                        if (j < m) acc[q] = fmaf(a, yr[j], acc[q]);
+                    for (int u = 0; u < U; u++) {
+                        const int t = t0 + u;
+                        const int k = __shfl_sync(0xFFFFFFFFu, myc, t & 31);
+                        const float a = __shfl_sync(0xFFFFFFFFu, myv, t & 31);
+                        av[u] = t < cnt ? a : 0.f;
+                        const float *yr = Y + (size_t)(t < cnt ? k : 0) * m;
+#pragma unroll
+                        for (int q = 0; q < JW; q++) {
+                            const int j = lane + 32 * q;
+                            yv[u][q] = j < m ? yr[j] : 0.f;
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+#pragma unroll
+                        for (int q = 0; q < JW; q++) acc[q] = fmaf(av[u], yv[u][q], acc[q]);
                 }
             }
         }
+        if (O64) {
 #pragma unroll
-        for (int q = 0; q < JW; q++) {
-            const int j = lane + 32 * q;
-            if (j >= m) continue;
-            double v = 0.0;
-            if (i < n) {
-                v = alpha * (double)acc[q];
-                if (beta != 0.0) v += beta * (double)Y[(size_t)i * m + j];
-                if (gamma != 0.0) v += gamma * (double)X[(size_t)i * m + j];
+            for (int q = 0; q < JW; q++) {
+                const int j = lane + 32 * q;
+                if (j >= m) continue;
+                double v = 0.0;
+                if (i < n) {
+                    v = alpha * (double)acc[q];
+                    if (beta != 0.0) v += beta * (double)Y[(size_t)i * m + j];
+                    if (gamma != 0.0) v += gamma * (double)X[(size_t)i * m + j];
+                }
+                if (O) O[(size_t)i * m + j] = (float)v;
+                s64[r][j] = v;
             }
-            if (O) O[(size_t)i * m + j] = (float)v;
-            s64[r][j] = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < JW; q++) {
+                const int j = lane + 32 * q;
+                if (j >= m) continue;
+                float v = 0.f;
+                if (i < n) {
+                    v = alpha_f * acc[q];
+                    if (beta != 0.0) v = fmaf(beta_f, Y[(size_t)i * m + j], v);
+                    if (gamma != 0.0) v = fmaf(gamma_f, X[(size_t)i * m + j], v);
+                }
+                O[(size_t)i * m + j] = v;
+            }
         }
     }
     if (!O64) return;
@@ -896,7 +943,7 @@ struct Ws {
     float *vh[4], *vl[4];   // tf32 parts of block vectors (m x n_pad)
     double *Xt, *Zt, *Xt2, *G, *Gp, *Rinv, *Qd, *theta, *res, *rowabs, *bound, *sinv;
     float *Q, *qev;
-    int *err, *shifted;
+    int *err, *shifted, *sweeps;
     long long *rp;  // CSR row pointers of the sparse operator (n + 1)
     size_t total;
 };
@@ -916,7 +963,7 @@ static Ws ws_layout(const Plan &p, char *base) {
     w.Zt = (double *)take(mv * 8);
     w.Xt2 = (double *)take(mv * 8);
     w.G = (double *)take((size_t)p.m * p.m * 8);
-    w.Gp = (double *)take((size_t)kGramChunks * p.m * p.m * 8);
+    w.Gp = (double *)take((size_t)kGramChunksMax * p.m * p.m * 8);
     w.Rinv = (double *)take((size_t)p.m * p.m * 8);
     w.Qd = (double *)take((size_t)p.m * p.m * 8);
     w.theta = (double *)take(p.m * 8);
@@ -928,6 +975,7 @@ static Ws ws_layout(const Plan &p, char *base) {
     w.qev = (float *)take(p.m * 4);
     w.err = (int *)take(4);
     w.shifted = (int *)take(4);
+    w.sweeps = (int *)take(4);
     w.rp = (long long *)take((size_t)(p.n + 1) * 8);
     w.total = o;
     return w;
@@ -970,7 +1018,8 @@ static cudaError_t sp_filter(Ctx &c, double alpha, double beta, double gamma, co
     const float *vals = c.w.Ahi;
     note_launch();
 #define MCS_SP(JW)                                                                                                    \
-    k_sp_filter<JW><<<grid, 32 * kSpRows, 0, c.st>>>(rp, cols, vals, c.p.n, c.p.n_pad, m, alpha, beta, gamma, Y, X, O, O64)
+    k_sp_filter<JW><<<grid, 32 * kSpRows, 0, c.st>>>(rp, cols, vals, c.p.n, c.p.n_pad, m, alpha, beta, gamma,        \
+                                                     (float)alpha, (float)beta, (float)gamma, Y, X, O, O64)
     switch (jw) {
         case 1: MCS_SP(1); break;
         case 2: MCS_SP(2); break;
@@ -1046,6 +1095,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     const size_t mv = (size_t)m * p.n_pad;
     const int g = grid_for(mv);
     MCS_CUDA(cudaMemsetAsync(c.w.err, 0, sizeof(int), st));
+    MCS_CUDA(cudaMemsetAsync(c.w.sweeps, 0, sizeof(int), st));
     // row nonzeros and Gershgorin sums of A, then the operator: CSR when A
     // has at most one nonzero in 32 (or when asked), else the dense tf32 parts
     note_launch();
@@ -1074,15 +1124,22 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
 
     // block buffers (m x n_pad FP64, by rows of X^T): X, Z and a spare, rotated by role
     double *X = c.w.Xt, *Z = c.w.Zt, *T = c.w.Xt2;
-    const dim3 ggrid((m + 31) / 32, (m + 31) / 32, kGramChunks);
+    // n split so that the active 32 x 32 tiles fill about two blocks per SM
+    const int gt = (m + 31) / 32;
+    auto gram_chunks = [&](int tiles) {
+        const int want = (2 * num_sms() + tiles - 1) / tiles;
+        return std::max(1, std::min({kGramChunksMax, p.n_pad / 32, std::max(16, want)}));
+    };
+    const int gch_full = gram_chunks(gt * gt), gch_upper = gram_chunks(gt * (gt + 1) / 2);
     const dim3 bgrid(p.n_pad / 128, (m + kJG - 1) / kJG);
     const size_t bsm = (size_t)m * kJG * sizeof(double);
     auto gram = [&](const double *A, const double *B, int sym) {
         const int upper = A == B;
+        const int ch = upper ? gch_upper : gch_full;
         note_launch();
-        k_gram_part<<<ggrid, 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp, upper);
+        k_gram_part<<<dim3(gt, gt, ch), 256, 0, st>>>(A, B, m, p.n_pad, c.w.Gp, upper);
         note_launch();
-        k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, c.w.G, sym, upper);
+        k_gram_reduce<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Gp, m, ch, c.w.G, sym, upper);
     };
     // orthonormalise X: shifted CholeskyQR, then CholeskyQR2 (FP64)
     // one CholeskyQR pass: X <- X R^-1 with R^T R = X^T X (+ shift); mode as k_chol_inv's
@@ -1187,7 +1244,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         }
         gram(X, Z, 1);
         note_launch();
-        k_jacobi<<<1, 1024, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30);
+        k_jacobi<<<1, 1024, jsm, st>>>(c.w.G, m, c.w.Q, c.w.qev, 30, c.w.sweeps);
         note_launch();
         k_f32_to_f64<<<(m * m + 255) / 256, 256, 0, st>>>(c.w.Q, m * m, c.w.Qd);
         note_launch();
@@ -1237,6 +1294,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
         stats->device_error = err;
         stats->product = c.sparse ? 2 : 1;
         stats->nnz = nnz;
+        MCS_CUDA(cudaMemcpy(&stats->jacobi_sweeps, c.w.sweeps, sizeof(int), cudaMemcpyDeviceToHost));
     }
     if (err & kErrTimeout) {
         set_error("mcs_steklov_modes: a tensor-core pipeline wait timed out");
