@@ -380,12 +380,12 @@ __global__ void k_gram_reduce(const double *Gp, int m, int chunks, double *G, in
 
 // R^-1 for the upper Cholesky factor R of G (+ shift I, shift = shift_rel *
 // trace G), FP64, one block of 1024 threads, S = m x (m + 1) in shared memory.
-// B300's FP64 pipe is narrow, so every FP64 warp instruction here does useful
-// work on its lanes (no reductions) and the FP64 divides and square roots are
-// done once per pivot.
+// B300's FP64 pipe is narrow: each step's elements are spread densely over
+// all 1024 threads (full lanes in every FP64 warp instruction), and the FP64
+// divides and square roots are done once per pivot.
 //  1. right-looking elimination on the upper triangle without square roots:
-//     S[a][b] -= S[j][a] S[j][b] / S[j][j] for j < a <= b, one barrier per
-//     step; the lane that updates the next pivot also forms its reciprocal;
+//     w[a] = S[j][a] / S[j][j], then S[a][b] -= w[a] S[j][b] for j < a <= b
+//     (the trailing triangle enumerated from its bottom row up);
 //  2. R[j][c] = S[j][c] / sqrt(S[j][j]); R's diagonal is 1 / rs;
 //  3. Z = R^-1, right-looking from the bottom row: once row k of Z is final,
 //     every row r < k takes acc[r][c] += R[r][k] Z[k][c] (c >= k, Z[k][k] =
@@ -398,11 +398,12 @@ __global__ void k_gram_reduce(const double *Gp, int m, int chunks, double *G, in
 __global__ void __launch_bounds__(1024) k_chol_inv(const double *G, int m, double shift_rel, int mode, double *Rinv,
                                                    int *shifted, int *err) {
     extern __shared__ double S[];  // m x (m + 1)
-    __shared__ double rpiv[160], rs[160];
-    __shared__ double tr;
+    __shared__ double w[160], rs[160];
+    __shared__ double tr, inv;
     __shared__ int bad;
     const int ld = m + 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         double t = 0.0;
         for (int j = lane; j < m; j += 32) t += G[j * m + j];
@@ -415,76 +416,74 @@ __global__ void __launch_bounds__(1024) k_chol_inv(const double *G, int m, doubl
         __syncthreads();
         const double shift = attempt ? shift_rel * tr : 0.0;
         const double floor_piv = mode == 2 && attempt == 0 ? 1e-15 * tr : 0.0;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        for (int e = tid; e < m * m; e += nt) {
             const int r = e / m, c = e % m;
             S[r * ld + c] = G[e] + (r == c ? shift : 0.0);
         }
-        if (threadIdx.x == 0) bad = 0;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
+            bad = 0;
             double d = S[0];
             if (!(d > floor_piv)) {
                 if (floor_piv > 0.0) bad = 1;
                 else atomicOr(err, kErrChol);
                 d = S[0] = 1e-300;
             }
-            rpiv[0] = 1.0 / d;
+            inv = 1.0 / d;
         }
         __syncthreads();
         for (int j = 0; j < m - 1; j++) {
-            const double inv = rpiv[j];
-            for (int a = j + 1 + warp; a < m; a += nw) {
-                const double ra = S[j * ld + a] * inv;
-                for (int b = a + lane; b < m; b += 32) S[a * ld + b] = fma(-ra, S[j * ld + b], S[a * ld + b]);
-                if (a == j + 1 && lane == 0) {
-                    double d = S[a * ld + a];
-                    if (!(d > floor_piv)) {
+            for (int a = j + 1 + tid; a < m; a += nt) w[a] = S[j * ld + a] * inv;
+            __syncthreads();
+            // trailing triangle rows a > j, columns b >= a: element e counts
+            // from the bottom row (row m - 1 - s holds s + 1 elements); the
+            // thread that updates the next pivot checks it and forms its
+            // reciprocal (inv is no longer read in this step)
+            const int T = (m - j - 1) * (m - j) / 2;
+            for (int e = tid; e < T; e += nt) {
+                int s = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                while ((s + 1) * (s + 2) / 2 <= e) s++;
+                while (s * (s + 1) / 2 > e) s--;
+                const int a = m - 1 - s, b = a + (e - s * (s + 1) / 2);
+                double v = fma(-w[a], S[j * ld + b], S[a * ld + b]);
+                if (a == j + 1 && b == a) {
+                    if (!(v > floor_piv)) {
                         if (floor_piv > 0.0) bad = 1;
                         else atomicOr(err, kErrChol);
-                        d = S[a * ld + a] = 1e-300;
+                        v = 1e-300;
                     }
-                    rpiv[a] = 1.0 / d;
+                    inv = 1.0 / v;
                 }
+                S[a * ld + b] = v;
             }
             __syncthreads();
         }
-        if (!bad) break;  // uniform: read after the last barrier
+        if (!bad) break;  // uniform: read after the barrier
     }
-    if (threadIdx.x == 0 && shifted) *shifted = used_shift;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) rs[j] = 1.0 / sqrt(S[j * ld + j]);
+    if (tid == 0 && shifted) *shifted = used_shift;
+    for (int j = tid; j < m; j += nt) rs[j] = 1.0 / sqrt(S[j * ld + j]);
     __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    for (int e = tid; e < m * m; e += nt) {
         const int r = e / m, c = e % m;
         if (c > r) S[r * ld + c] *= rs[r];
         else if (c < r) S[r * ld + c] = 0.0;
     }
     __syncthreads();
+    // R's diagonal is 1 / rs; R^-1[k][c] (k < c) lives at S[c][k], its diagonal in rs
     for (int k = m - 1; k >= 1; k--) {
+        const int wdt = m - k;  // columns c = k .. m - 1 of rows r = 0 .. k - 1
+        const float rw = 1.f / (float)wdt;
         const double zk = rs[k];
-        if (m - k >= 32) {
-            // warp per row r < k, lanes over columns c >= k
-            for (int r = warp; r < k; r += nw) {
-                const double rk = S[r * ld + k];
-                for (int c = k + lane; c < m; c += 32) {
-                    double v = fma(rk, c == k ? zk : S[c * ld + k], S[c * ld + r]);
-                    if (r == k - 1) v *= -rs[r];
-                    S[c * ld + r] = v;
-                }
-            }
-        } else {
-            // warp per column c >= k, lanes over rows r < k
-            for (int c = k + warp; c < m; c += nw) {
-                const double z = c == k ? zk : S[c * ld + k];
-                for (int r = lane; r < k; r += 32) {
-                    double v = fma(S[r * ld + k], z, S[c * ld + r]);
-                    if (r == k - 1) v *= -rs[r];
-                    S[c * ld + r] = v;
-                }
-            }
+        for (int e = tid; e < k * wdt; e += nt) {
+            // r = e / wdt exactly: (e + 0.5) / wdt stays at least 0.5 / wdt
+            // away from an integer, far beyond the FP32 error for e < 2^14
+            const int r = (int)(((float)e + 0.5f) * rw), c = k + (e - r * wdt);
+            double v = fma(S[r * ld + k], c == k ? zk : S[c * ld + k], S[c * ld + r]);
+            if (r == k - 1) v *= -rs[r];
+            S[c * ld + r] = v;
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    for (int e = tid; e < m * m; e += nt) {
         const int r = e / m, c = e % m;
         Rinv[e] = c > r ? S[c * ld + r] : c == r ? rs[r] : 0.0;
     }
@@ -552,8 +551,8 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
     extern __shared__ float sj[];
     const int ld = m + 1;
     float *H = sj, *V = sj + m * ld;
-    __shared__ float cs[80], sn[80];
-    __shared__ int pp[80], qq[80];
+    __shared__ float cs[2][80], sn[2][80];  // rotations of the current and the next round
+    __shared__ int pp[2][80], qq[2][80];
     __shared__ float red_off[32], red_tot[32];
     __shared__ int stop;
     float prev_off = 0.f;  // thread 0's
@@ -565,6 +564,39 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
     __syncthreads();
     const int half = m / 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // pair i of round r (round-robin: m - 1 fixed, the others rotate) and its
+    // rotation from the current H; c = 1 / sqrt(1 + t^2) by rsqrtf: the
+    // rotations need be orthogonal only to FP32 rounding, the block they
+    // rotate is re-orthonormalised in FP64 afterwards
+    auto rotation = [&](int r, int i, int buf) {
+        int p, q;
+        if (i == 0) {
+            p = m - 1;
+            q = r;
+        } else {
+            p = r + i;
+            if (p >= m - 1) p -= m - 1;
+            q = r - i;
+            if (q < 0) q += m - 1;
+        }
+        if (p > q) {
+            const int tt = p;
+            p = q;
+            q = tt;
+        }
+        pp[buf][i] = p;
+        qq[buf][i] = q;
+        const float apq = H[p * ld + q];
+        float c = 1.f, sv = 0.f;
+        if (fabsf(apq) > 1e-30f) {
+            const float tau = (H[q * ld + q] - H[p * ld + p]) / (2.f * apq);
+            const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + tt * tt);
+            sv = tt * c;
+        }
+        cs[buf][i] = c;
+        sn[buf][i] = sv;
+    };
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
         float o = 0.f, t = 0.f;
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
@@ -593,37 +625,21 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
             break;
         }
         if (sweep == max_sweeps - 1 && threadIdx.x == 0) *sweeps_done += max_sweeps;
+        if (threadIdx.x < half) rotation(0, threadIdx.x, 0);
+        __syncthreads();
         for (int r = 0; r < m - 1; r++) {
-            if (threadIdx.x < half) {
-                const int i = threadIdx.x;
-                int p, q;
-                if (i == 0) { p = m - 1; q = r; }
-                else { p = (r + i) % (m - 1); q = (r - i + (m - 1)) % (m - 1); }
-                if (p > q) { const int tt = p; p = q; q = tt; }
-                pp[i] = p; qq[i] = q;
-                const float apq = H[p * ld + q];
-                float c = 1.f, sv = 0.f;
-                if (fabsf(apq) > 1e-30f) {
-                    const float tau = (H[q * ld + q] - H[p * ld + p]) / (2.f * apq);
-                    const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                    c = 1.f / sqrtf(1.f + tt * tt);
-                    sv = tt * c;
-                }
-                cs[i] = c; sn[i] = sv;
-            }
-            __syncthreads();
+            const int cur = r & 1;
             // H <- J^T H J by 2 x 2 blocks: block (a, b) holds rows {p_a, q_a}
             // and columns {p_b, q_b}; the column rotation of pair b, then the
             // row rotation of pair a (the order of a column pass followed by
             // a row pass), written to (a, b) and mirrored to (b, a).  One warp
-            // per pair a, lanes over b >= a; V <- V J one warp per pair, lanes
-            // over rows.  Blocks are disjoint, so one barrier ends the round.
+            // per pair a, lanes over b >= a.  Blocks are disjoint.
             for (int a = warp; a < half; a += nwarps) {
-                const int pa = pp[a], qa = qq[a];
-                const float ca = cs[a], sa = sn[a];
+                const int pa = pp[cur][a], qa = qq[cur][a];
+                const float ca = cs[cur][a], sa = sn[cur][a];
                 for (int b = a + lane; b < half; b += 32) {
-                    const int pb = pp[b], qb = qq[b];
-                    const float cb = cs[b], sb = sn[b];
+                    const int pb = pp[cur][b], qb = qq[cur][b];
+                    const float cb = cs[cur][b], sb = sn[cur][b];
                     const float b00 = H[pa * ld + pb], b01 = H[pa * ld + qb];
                     const float b10 = H[qa * ld + pb], b11 = H[qa * ld + qb];
                     const float c00 = cb * b00 - sb * b01, c01 = sb * b00 + cb * b01;
@@ -642,9 +658,13 @@ __global__ void k_jacobi(const double *Hd, int m, float *Q, float *evals, int ma
                     }
                 }
             }
+            __syncthreads();
+            // the next round's rotations (from the rotated H) while the
+            // others rotate V <- V J, one warp per pair, lanes over rows
+            if (r + 1 < m - 1 && threadIdx.x < half) rotation(r + 1, threadIdx.x, cur ^ 1);
             for (int i = warp; i < half; i += nwarps) {
-                const int p = pp[i], q = qq[i];
-                const float c = cs[i], sv = sn[i];
+                const int p = pp[cur][i], q = qq[cur][i];
+                const float c = cs[cur][i], sv = sn[cur][i];
                 for (int row = lane; row < m; row += 32) {
                     const float vp = V[row * ld + p], vq = V[row * ld + q];
                     V[row * ld + p] = c * vp - sv * vq;
