@@ -264,8 +264,11 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps_cluster(FpsArgs a) {
     extern __shared__ float4 sub[];
     __shared__ float4 wc[NW];  // warp candidates: centroid, value
     __shared__ int wi[NW];
-    __shared__ float4 cta_c[2];  // this CTA's candidate (double-buffered), read by the others
-    __shared__ int cta_i[2];
+    // every CTA's candidate, pushed here by that CTA before the cluster
+    // barrier (double-buffered by selection parity): the fold after the
+    // barrier reads local shared memory only
+    __shared__ float4 all_c[2][16];
+    __shared__ int all_i[2][16];
     const unsigned rank = cl.block_rank(), ncta = cl.num_blocks();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int per = (a.nf + (int)ncta - 1) / (int)ncta;
@@ -378,9 +381,11 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps_cluster(FpsArgs a) {
             float v = c.w, x = c.x, y = c.y, z = c.z;
             int idx = wi[lane];
             warp_argmax_xyz(v, idx, x, y, z);
-            if (lane == 0) {
-                cta_c[par] = make_float4(x, y, z, v);
-                cta_i[par] = idx;
+            // lane r stores this CTA's candidate into CTA r's slot; the
+            // barrier (release on arrive, acquire on wait) orders the stores
+            if (lane < (int)ncta) {
+                *cl.map_shared_rank(&all_c[par][rank], lane) = make_float4(x, y, z, v);
+                *cl.map_shared_rank(&all_i[par][rank], lane) = idx;
             }
         }
         cl.sync();
@@ -388,9 +393,9 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps_cluster(FpsArgs a) {
         float v = -1.0f, x = 0.f, y = 0.f, z = 0.f;
         int idx = 0x7FFFFFFF;
         if (lane < (int)ncta) {
-            const float4 c = *cl.map_shared_rank(&cta_c[par], lane);
+            const float4 c = all_c[par][lane];
             v = c.w; x = c.x; y = c.y; z = c.z;
-            idx = *cl.map_shared_rank(&cta_i[par], lane);
+            idx = all_i[par][lane];
         }
         warp_argmax_xyz(v, idx, x, y, z);
         if (rank == 0 && threadIdx.x == 0) a.sel[i + 1] = idx;
