@@ -221,8 +221,12 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
 
 /* Sample rows of many meshes at once: each mesh's farthest-point sampling
  * runs as one block of a single launch (meshes in parallel), the rest as in
- * mcs_sample_rows.  Outputs per item as for mcs_sample_rows (orient_gap
- * optional).  workspace: device, 256-byte aligned, >=
+ * mcs_sample_rows, except that the hierarchical orientation of all meshes
+ * runs in two launches and orient 1 chooses it when the batch's faces x rows
+ * (summed over the meshes) reach 2^28.  The normals are those of
+ * mcs_sample_rows (both passes decide only certified rows); orient_gap of a
+ * row may come from the other pass.  Outputs per item as for mcs_sample_rows
+ * (orient_gap optional).  workspace: device, 256-byte aligned, >=
  * mcs_sample_rows_batched_workspace_size.  Synchronises `stream`. */
 typedef struct {
     mcs_mesh mesh;

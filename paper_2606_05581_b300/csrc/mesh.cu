@@ -11,6 +11,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -66,12 +67,19 @@ __global__ void k_bounds_partial(const double *V, int nv, double *part) {
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; k++) { part[6 * blockIdx.x + k] = smin[k][0]; part[6 * blockIdx.x + 3 + k] = smax[k][0]; }
 }
-__global__ void k_bounds_final(const double *part, int nb, double *out) {
+struct BoxFrame { double lo[3], inv[3]; };
+
+__global__ void k_bounds_final(const double *part, int nb, double *out, BoxFrame *fr) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int b = 0; b < nb; b++)
         for (int k = 0; k < 3; k++) { mn[k] = fmin(mn[k], part[6 * b + k]); mx[k] = fmax(mx[k], part[6 * b + 3 + k]); }
-    for (int k = 0; k < 3; k++) { out[k] = mn[k]; out[3 + k] = mx[k]; }
+    for (int k = 0; k < 3; k++) {
+        out[k] = mn[k];
+        out[3 + k] = mx[k];
+        fr->lo[k] = mn[k];
+        fr->inv[k] = 1.0 / (mx[k] - mn[k]);
+    }
 }
 
 __device__ __forceinline__ uint32_t spread10(uint32_t x) {
@@ -92,11 +100,14 @@ __device__ __forceinline__ uint32_t morton30(double x, double y, double z, const
     return (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
 }
 
-struct BoxFrame { double lo[3], inv[3]; };
-
-__global__ void k_tri_keys(const double *V, const int32_t *F, int nf, BoxFrame fr, unsigned long long *keys) {
+// the keys' frame, formed on the device from the bounds (no host round trip);
+// the kernels that index V through F return at once when validation flagged
+// the input (*bad != 0), which the build reports after its single sync
+__global__ void k_tri_keys(const double *V, const int32_t *F, int nf, const BoxFrame *frp, const int *bad,
+                           unsigned long long *keys) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
+    if (f >= nf || *bad) return;
+    const BoxFrame fr = *frp;
     const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
     const double cx = ((a[0] + b[0]) + c[0]) / 3.0, cy = ((a[1] + b[1]) + c[1]) / 3.0, cz = ((a[2] + b[2]) + c[2]) / 3.0;
     keys[f] = ((unsigned long long)morton30(cx, cy, cz, fr.lo, fr.inv) << 32) | (unsigned)f;
@@ -104,10 +115,10 @@ __global__ void k_tri_keys(const double *V, const int32_t *F, int nf, BoxFrame f
 
 // triangle slots in BVH order: (a, ab, ac) in FP64 and, from float-rounded
 // vertices, in FP32; box of each slot rounded outward to float
-__global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const unsigned long long *keys, Tri32 *t32,
-                            Tri64 *t64, float *slotbox) {
+__global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const unsigned long long *keys, const int *bad,
+                            Tri32 *t32, Tri64 *t64, float *slotbox) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nf) return;
+    if (s >= nf || *bad) return;
     const int f = (int)(keys[s] & 0xFFFFFFFFull);
     const double *A = V + 3 * F[3 * f], *B = V + 3 * F[3 * f + 1], *C = V + 3 * F[3 * f + 2];
     Tri64 t;
@@ -141,9 +152,10 @@ __device__ __forceinline__ int kdelta(const unsigned long long *k, int n, int i,
 
 // Karras 2012: internal node i covers a key range [min(i,j), max(i,j)] split
 // at gamma; children >= 0 internal, < 0 leaf (~slot)
-__global__ void k_karras(const unsigned long long *k, int n, int *child, int *parent_int, int *parent_leaf) {
+__global__ void k_karras(const unsigned long long *k, int n, const int *bad, int *child, int *parent_int,
+                         int *parent_leaf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+    if (i >= n - 1 || *bad) return;
     const int d = (kdelta(k, n, i, i + 1) - kdelta(k, n, i, i - 1)) >= 0 ? 1 : -1;
     const int dmin = kdelta(k, n, i, i - d);
     int lmax = 2;
@@ -172,9 +184,9 @@ __global__ void k_karras(const unsigned long long *k, int n, int *child, int *pa
 // bottom-up refit: one thread per leaf climbs; the second arrival at a node
 // unites its two child boxes and continues
 __global__ void k_refit(int n, const int *child, const int *parent_int, const int *parent_leaf, const float *slotbox,
-                        float *nodebox, int *arrive, int *err) {
+                        float *nodebox, int *arrive, int *err, const int *bad) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    if (s >= n || *bad) return;
     float box[6];
     for (int k = 0; k < 6; k++) box[k] = slotbox[6 * s + k];
     int me = ~s;
@@ -198,9 +210,9 @@ __global__ void k_refit(int n, const int *child, const int *parent_int, const in
     }
 }
 
-__global__ void k_pack_nodes(int n, const int *child, const float *nodebox, Node *nodes) {
+__global__ void k_pack_nodes(int n, const int *child, const float *nodebox, const int *bad, Node *nodes) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+    if (i >= n - 1 || *bad) return;
     const float *b = nodebox + 12 * i;
     Node nd;
     nd.a = make_float4(b[0], b[1], b[2], b[3]);
@@ -266,9 +278,10 @@ __global__ void k_incidence(const int32_t *F, int nf, unsigned long long *pairs)
     if (f >= nf) return;
     for (int k = 0; k < 3; k++) pairs[3 * f + k] = ((unsigned long long)(unsigned)F[3 * f + k] << 32) | (unsigned)f;
 }
-__global__ void k_incidence_csr(const unsigned long long *pairs, int m, int nv, int32_t *inc_f, int32_t *vstart) {
+__global__ void k_incidence_csr(const unsigned long long *pairs, int m, int nv, const int *bad, int32_t *inc_f,
+                                int32_t *vstart) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    if (i >= m || *bad) return;
     const unsigned long long p = pairs[i];
     const int v = (int)(p >> 32);
     inc_f[i] = (int)(p & 0xFFFFFFFFull);
@@ -353,6 +366,34 @@ static void mesh_free(mcs_mesh_s *m) {
     delete m;
 }
 
+// the pool of the BVH build's temporaries, one per device: stream-ordered
+// allocation, so that freeing them does not synchronise the device (as
+// cudaFree does) and consecutive builds reuse the memory (up to 1 GiB stays
+// reserved between builds)
+static cudaError_t temp_pool(int dev, cudaMemPool_t *out) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = pools.find(dev);
+    if (it != pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t p;
+    cudaError_t e = cudaMemPoolCreate(&p, &pp);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = 1ull << 30;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    pools[dev] = p;
+    *out = p;
+    return cudaSuccess;
+}
+
 extern "C" {
 
 const char *mcs_last_error(void) { return g_err.c_str(); }
@@ -381,7 +422,7 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     // build's temporaries (one block, freed before returning); parts 256-byte aligned
     void *tbuf = nullptr;
     auto fail = [&](mcs_status s) {
-        cudaFree(tbuf);
+        if (tbuf) cudaFreeAsync(tbuf, st);
         mesh_free(m);
         return s;
     };
@@ -424,14 +465,16 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes2, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
                                    3 * nf, 0, 64, st);
     const int nbp = 256;
-    const size_t tsz[11] = {sizeof(int) * 2,  sizeof(double) * 6 * nbp, sizeof(double) * 6,
+    const size_t tsz[12] = {sizeof(int) * 2,  sizeof(double) * 6 * nbp, sizeof(double) * 6,
                             sizeof(unsigned long long) * nf, sizeof(unsigned long long) * nf,
                             sizeof(unsigned long long) * 3 * nf, sizeof(unsigned long long) * 3 * nf,
                             std::max(sort_bytes, sort_bytes2), sizeof(float) * 6 * nf, sizeof(int) * nf,
-                            sizeof(int) * ni};
+                            sizeof(int) * ni, sizeof(BoxFrame)};
     size_t ttot = 0;
     for (size_t x : tsz) ttot += al(x);
-    MB_CUDA(cudaMalloc(&tbuf, ttot));
+    cudaMemPool_t pool;
+    MB_CUDA(temp_pool(m->device, &pool));
+    MB_CUDA(cudaMallocFromPoolAsync(&tbuf, ttot, pool, st));
     char *tp = (char *)tbuf;
     auto ttake = [&](size_t bytes) -> void * {
         void *r = tp;
@@ -449,6 +492,7 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     float *slotbox = (float *)ttake(tsz[8]);
     int *par_l = (int *)ttake(tsz[9]);
     int *arrive = (int *)ttake(tsz[10]);
+    BoxFrame *d_frame = (BoxFrame *)ttake(tsz[11]);
 
     MB_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), st));
     MB_CUDA(cudaMemcpyAsync(m->V, V, sizeof(double) * 3 * nv, vdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -459,14 +503,45 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     note_launch();
     k_bounds_partial<<<nbp, 256, 0, st>>>(m->V, nv, d_part);
     note_launch();
-    k_bounds_final<<<1, 32, 0, st>>>(d_part, nbp, d_box);
-    int bad = 0;
+    k_bounds_final<<<1, 32, 0, st>>>(d_part, nbp, d_box, d_frame);
+    const int tb = 256;
+    note_launch();
+    k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, d_frame, d_bad, keys);
+    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes, keys, keys_s, nf, 0, 62, st));
+    note_launch();
+    k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, d_bad, m->t32, m->t64, slotbox);
+    if (nf > 1) {
+        // links, parents and child boxes go straight into the mesh (kept for
+        // an on-demand 4-wide copy, mcs_mesh_build_wide)
+        MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
+        MB_CUDA(cudaMemsetAsync(m->parent, 0xFF, sizeof(int) * (nf - 1), st));
+        MB_CUDA(cudaMemsetAsync(par_l, 0xFF, sizeof(int) * nf, st));
+        note_launch();
+        k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, d_bad, m->child, m->parent, par_l);
+        note_launch();
+        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->parent, par_l, slotbox, m->nodebox, arrive,
+                                                     d_bad + 1, d_bad);
+        note_launch();
+        k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->nodebox, d_bad, m->nodes);
+    }
+    // vertex -> incident faces, ascending
+    note_launch();
+    k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
+    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
+    MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
+    note_launch();
+    k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, d_bad, m->inc_f, m->vstart);
+    MB_CUDA(cudaGetLastError());
+    // the build's one host round trip: validation flags, tree check, bounds
+    int flags[2] = {0, 0};
     double box[6];
-    MB_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MB_CUDA(cudaMemcpyAsync(flags, d_bad, sizeof(flags), cudaMemcpyDeviceToHost, st));
     MB_CUDA(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st));
+    MB_CUDA(cudaFreeAsync(tbuf, st));
+    tbuf = nullptr;
     MB_CUDA(cudaStreamSynchronize(st));
-    if (bad) {
-        set_error(bad & 1 ? "mcs_build_bvh: non-finite vertex coordinate" : "mcs_build_bvh: face index out of range");
+    if (flags[0]) {
+        set_error(flags[0] & 1 ? "mcs_build_bvh: non-finite vertex coordinate" : "mcs_build_bvh: face index out of range");
         return fail(MCS_ERR_DEGENERATE);
     }
     double side = INFINITY, scale = 0.0;
@@ -482,49 +557,10 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     }
     m->rmax = 0.5 * side;
     m->scale = (float)scale * (1.0f + 1e-6f);
-
-    BoxFrame fr;
-    for (int k = 0; k < 3; k++) {
-        fr.lo[k] = box[k];
-        fr.inv[k] = 1.0 / (box[3 + k] - box[k]);
-    }
-    const int tb = 256;
-    note_launch();
-    k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, fr, keys);
-    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes, keys, keys_s, nf, 0, 62, st));
-    note_launch();
-    k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, m->t32, m->t64, slotbox);
-    if (nf > 1) {
-        // links, parents and child boxes go straight into the mesh (kept for
-        // an on-demand 4-wide copy, mcs_mesh_build_wide)
-        MB_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
-        MB_CUDA(cudaMemsetAsync(m->parent, 0xFF, sizeof(int) * (nf - 1), st));
-        MB_CUDA(cudaMemsetAsync(par_l, 0xFF, sizeof(int) * nf, st));
-        note_launch();
-        k_karras<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(keys_s, nf, m->child, m->parent, par_l);
-        note_launch();
-        k_refit<<<(nf + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->parent, par_l, slotbox, m->nodebox, arrive,
-                                                     d_bad + 1);
-        note_launch();
-        k_pack_nodes<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(nf, m->child, m->nodebox, m->nodes);
-    }
-    // vertex -> incident faces, ascending
-    note_launch();
-    k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
-    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
-    MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
-    note_launch();
-    k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, m->inc_f, m->vstart);
-    MB_CUDA(cudaGetLastError());
-    int tree_err = 0;
-    MB_CUDA(cudaMemcpyAsync(&tree_err, d_bad + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    MB_CUDA(cudaStreamSynchronize(st));
-    if (tree_err) {
+    if (flags[1]) {
         set_error("mcs_build_bvh: internal error, malformed hierarchy");
         return fail(MCS_ERR_DEVICE);
     }
-    cudaFree(tbuf);
-    tbuf = nullptr;
 #undef MB_CUDA
     // mesh creation may allocate: load here what the allocation-free
     // estimate needs, so that it loads (and allocates) nothing itself; a

@@ -704,7 +704,13 @@ struct __align__(16) GwnAgg {
     float4 na;  // N.x N.y N.z A
     float4 cr;  // C.x C.y C.z r
 };
+// far-field acceptance r <= theta d, measured: one 2.0M-face union (10,000
+// rows) is fastest at 0.1 (0.05: +110 ms, 0.2: +4 ms, 0.3: +80 ms of
+// brute-force fallback); 512 meshes of 5k-200k faces in one batched pass at
+// 0.2 (0.1: +80 ms, 0.3: +6 ms, 0.5: +60 ms).  The normals are the same at
+// every theta: only the share of rows left to brute force moves.
 constexpr float kGwnTheta = 0.1f;
+constexpr float kGwnThetaBatched = 0.2f;
 constexpr double kGwnTreeMin = 268435456.0;  // 2^28 face-row pairs (~2 ms of brute force)
 constexpr int kGwnWarps = 4;
 constexpr int kGwnStack = 2048;  // frontier entries per warp (shared memory; ~32 x tree depth)
@@ -722,8 +728,10 @@ __device__ __forceinline__ void tri_moments(const Tri32 &t, float N[3], float &A
 
 // node aggregates bottom-up: threads start at the nodes with two leaf
 // children; the last internal child to finish continues to the parent
-__global__ void k_gwn_agg(DevMesh m, const int *child, const int *parent, int *arrive, GwnAgg *agg, int *err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// moments of the internal nodes above internal node i, when both of i's
+// children are leaves (the last of each node's two arrivals continues up)
+__device__ void gwn_agg_from(const DevMesh &m, const int *child, const int *parent, int *arrive, GwnAgg *agg, int *err,
+                             int i) {
     const int ni = m.nf - 1;
     if (i >= ni || child[2 * i] >= 0 || child[2 * i + 1] >= 0) return;
     int p = i;
@@ -768,6 +776,9 @@ __global__ void k_gwn_agg(DevMesh m, const int *child, const int *parent, int *a
         p = q;
     }
 }
+__global__ void k_gwn_agg(DevMesh m, const int *child, const int *parent, int *arrive, GwnAgg *agg, int *err) {
+    gwn_agg_from(m, child, parent, arrive, agg, err, blockIdx.x * blockDim.x + threadIdx.x);
+}
 
 // solid angle of triangle (a, a + ab, a + ac) seen from p (Van Oosterom &
 // Strackee), and a bound on its float rounding
@@ -788,14 +799,12 @@ __device__ __forceinline__ float tri_omega(const Tri32 &t, float px, float py, f
     return 2.f * atan2f(det, den);
 }
 
-__global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const GwnAgg *agg, const float4 *q, int n,
-                                                            float *Dout, float *Eout, int *ovf) {
-    __shared__ int stk[kGwnWarps][kGwnStack];
-    __shared__ int top[kGwnWarps];
+// one row's two points summed over the tree by one warp, its frontier in the
+// warp's shared stack stk (kGwnStack entries) with the depth in *top
+__device__ void gwn_tree_row(const DevMesh &m, const GwnAgg *agg, const float4 *q, int row, float *Dout, float *Eout,
+                             int *ovf, int *stk, int *top, float theta) {
     const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int row = blockIdx.x * kGwnWarps + w;
-    if (row >= n) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
     const float4 qm = q[2 * row], qp = q[2 * row + 1];
     const int excl = __float_as_int(qm.w);
     const float xm = 0.5f * (qm.x + qp.x), ym = 0.5f * (qm.y + qp.y), zm = 0.5f * (qm.z + qp.z);
@@ -805,14 +814,14 @@ __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const Gw
     double D = 0.0;  // FP64 running sum: its rounding stays far below E
     float E = 0.f;
     bool over = false;
-    if (lane == 0) { stk[w][0] = 0; top[w] = 1; }
+    if (lane == 0) { stk[0] = 0; *top = 1; }
     __syncwarp();
     for (int guard = 0;; guard++) {
-        const int t = top[w];
+        const int t = *top;
         if (t == 0) break;
         if (guard > 4 * m.nf + 64) { over = true; break; }
         const int take = min(32, t);
-        const int node = lane < take ? stk[w][t - 1 - lane] : -1;
+        const int node = lane < take ? stk[t - 1 - lane] : -1;
         __syncwarp();
         int push[2] = {-1, -1};
         if (node >= 0) {
@@ -838,7 +847,7 @@ __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const Gw
                 const float dz = fmaxf(fmaxf(bx[side][2] - zm, 0.f), zm - bx[side][5]);
                 const float d = sqrtf(dx * dx + dy * dy + dz * dz) * (1.0f - 1e-5f) - hd;
                 const float4 na = agg[c].na, cr = agg[c].cr;
-                if (d > 0.f && cr.w <= kGwnTheta * d) {
+                if (d > 0.f && cr.w <= theta * d) {
                     const float v1x = cr.x - qm.x, v1y = cr.y - qm.y, v1z = cr.z - qm.z;
                     const float v2x = cr.x - qp.x, v2y = cr.y - qp.y, v2z = cr.z - qp.z;
                     const float i1 = rsqrtf(v1x * v1x + v1y * v1y + v1z * v1z);
@@ -866,10 +875,10 @@ __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const Gw
         const int base = t - take;
         if (base + total > kGwnStack) { over = true; break; }
         int at = base + incl - k;
-        if (push[0] >= 0) stk[w][at++] = push[0];
-        if (push[1] >= 0) stk[w][at++] = push[1];
+        if (push[0] >= 0) stk[at++] = push[0];
+        if (push[1] >= 0) stk[at++] = push[1];
         __syncwarp();
-        if (lane == 0) top[w] = base + total;
+        if (lane == 0) *top = base + total;
         __syncwarp();
     }
 #pragma unroll
@@ -883,6 +892,63 @@ __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const Gw
         Eout[row] = E * (1.0f + 1e-3f) + 2.f * kGwnUlp * (float)fabs(D);
         ovf[row] = over ? 1 : 0;
     }
+}
+__global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const GwnAgg *agg, const float4 *q, int n,
+                                                            float *Dout, float *Eout, int *ovf) {
+    __shared__ int stk[kGwnWarps][kGwnStack];
+    __shared__ int top[kGwnWarps];
+    const int w = threadIdx.x >> 5;
+    const int row = blockIdx.x * kGwnWarps + w;
+    if (row >= n) return;  // warp-uniform
+    gwn_tree_row(m, agg, q, row, Dout, Eout, ovf, stk[w], &top[w], kGwnTheta);
+}
+
+// The tree pass of many meshes in two launches (a mesh's 1024 rows alone
+// would keep a few warps per SM busy): each mesh is one job; a thread finds
+// its job by binary search of the jobs' first internal node (aggregation) or
+// first row (sums).
+struct GwnJob {
+    DevMesh m;
+    const int *child, *parent;
+    int *arrive, *err, *ovf;
+    GwnAgg *agg;
+    const float4 *q;
+    float *D, *E;
+    int n, node0, row0;
+};
+constexpr int kGwnChunk = 24;
+struct GwnChunk {
+    GwnJob j[kGwnChunk];
+    int count, base;
+};
+__global__ void k_store_gwn(GwnChunk c, GwnJob *table) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) table[c.base + i] = c.j[i];
+}
+// the last job whose first index (node0 or row0) is <= g
+template <bool ROWS>
+__device__ __forceinline__ int gwn_job_of(const GwnJob *jobs, int count, int g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((ROWS ? jobs[mid].row0 : jobs[mid].node0) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__global__ void k_gwn_agg_batched(const GwnJob *jobs, int count, int total_nodes) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total_nodes) return;
+    const GwnJob &J = jobs[gwn_job_of<false>(jobs, count, g)];
+    gwn_agg_from(J.m, J.child, J.parent, J.arrive, J.agg, J.err, g - J.node0);
+}
+__global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree_batched(const GwnJob *jobs, int count, int total_rows) {
+    __shared__ int stk[kGwnWarps][kGwnStack];
+    __shared__ int top[kGwnWarps];
+    const int w = threadIdx.x >> 5;
+    const int g = blockIdx.x * kGwnWarps + w;
+    if (g >= total_rows) return;  // warp-uniform
+    const GwnJob &J = jobs[gwn_job_of<true>(jobs, count, g)];
+    gwn_tree_row(J.m, J.agg, J.q, g - J.row0, J.D, J.E, J.ovf, stk[w], &top[w], kGwnThetaBatched);
 }
 
 // decided rows take the sign of D; the rest go to the brute-force list
@@ -1119,6 +1185,43 @@ static mcs_status sample_prepare(const mcs_sample_item &it, char *w, const Layou
     return MCS_OK;
 }
 
+// orientation pieces of sample_finish: the two points of each row, the
+// tree pass of one mesh, and the decision (brute force for the rest)
+static void orient_points(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st) {
+    const int tb = 256;
+    note_launch();
+    k_gwn_points<<<(it.n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, (double *)(w + L.farea), it.sel, it.n,
+                                                       (float4 *)(w + L.q));
+}
+static void orient_tree(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st) {
+    mcs_mesh m = it.mesh;
+    const int nf = m->nf, n = it.n, tb = 256;
+    GwnAgg *agg = (GwnAgg *)(w + L.agg);
+    int *arrive = (int *)(w + L.arrive);
+    cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st);
+    note_launch();
+    k_gwn_agg<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(m->dev(), m->child, m->parent, arrive, agg, (int *)(w + L.err));
+    note_launch();
+    k_gwn_tree<<<(n + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(
+        m->dev(), agg, (const float4 *)(w + L.q), n, (float *)(w + L.gD), (float *)(w + L.gE), (int *)(w + L.govf));
+}
+static void orient_decide(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st, bool tree) {
+    mcs_mesh m = it.mesh;
+    const int nf = m->nf, n = it.n, tb = 256;
+    const float4 *q = (const float4 *)(w + L.q);
+    float *partial = (float *)(w + L.partial);
+    int *fb_list = (int *)(w + L.fb_list), *fb_count = (int *)(w + L.fb_count);
+    cudaMemsetAsync(fb_count, 0, sizeof(int), st);
+    note_launch();
+    k_gwn_decide<<<(n + tb - 1) / tb, tb, 0, st>>>(n, tree ? 0 : 1, (float *)(w + L.gD), (float *)(w + L.gE),
+                                                    (int *)(w + L.govf), it.nrm, it.orient_gap, fb_list, fb_count);
+    const int grid = gwn_fb_grid();
+    note_launch();
+    k_gwn_fb<<<grid, 256, 0, st>>>(m->V, m->F, nf, q, fb_list, fb_count, partial);
+    note_launch();
+    k_orient_fb<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, nf, grid, fb_list, fb_count, it.nrm, it.orient_gap);
+}
+
 // owners by face, quadrature areas, row points and normals (+ orientation)
 static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, const Layout &L, cudaStream_t st) {
     mcs_mesh m = it.mesh;
@@ -1147,32 +1250,10 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
         // bound; orient 2: brute force for every row; orient 1: the first
         // when faces x rows reach kGwnTreeMin, else the second (small meshes
         // pay more for the extra launches than for the brute-force sums)
-        float4 *q = (float4 *)(w + L.q);
-        float *partial = (float *)(w + L.partial);
-        float *gD = (float *)(w + L.gD), *gE = (float *)(w + L.gE);
-        int *govf = (int *)(w + L.govf), *fb_list = (int *)(w + L.fb_list), *fb_count = (int *)(w + L.fb_count);
         const bool tree = nf >= 2 && (orient == 3 || (orient == 1 && (double)nf * n >= kGwnTreeMin));
-        note_launch();
-        k_gwn_points<<<(n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, farea, it.sel, n, q);
-        if (tree) {
-            GwnAgg *agg = (GwnAgg *)(w + L.agg);
-            int *arrive = (int *)(w + L.arrive);
-            MCS_CUDA(cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st));
-            note_launch();
-            k_gwn_agg<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(m->dev(), m->child, m->parent, arrive, agg,
-                                                            (int *)(w + L.err));
-            note_launch();
-            k_gwn_tree<<<(n + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(m->dev(), agg, q, n, gD, gE, govf);
-        }
-        MCS_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(int), st));
-        note_launch();
-        k_gwn_decide<<<(n + tb - 1) / tb, tb, 0, st>>>(n, tree ? 0 : 1, gD, gE, govf, it.nrm, it.orient_gap, fb_list,
-                                                        fb_count);
-        const int grid = gwn_fb_grid();
-        note_launch();
-        k_gwn_fb<<<grid, 256, 0, st>>>(m->V, m->F, nf, q, fb_list, fb_count, partial);
-        note_launch();
-        k_orient_fb<<<(n + tb - 1) / tb, tb, 0, st>>>(partial, nf, grid, fb_list, fb_count, it.nrm, it.orient_gap);
+        orient_points(it, w, L, st);
+        if (tree) orient_tree(it, w, L, st);
+        orient_decide(it, w, L, st, tree);
     }
     MCS_CUDA(cudaGetLastError());
     return MCS_OK;
@@ -1246,7 +1327,7 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
 
 size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int count) {
     if (!items || count <= 0) return 0;
-    size_t o = a256(sizeof(FpsArgs) * (size_t)count);
+    size_t o = a256(sizeof(FpsArgs) * (size_t)count) + a256(sizeof(GwnJob) * (size_t)count);
     for (int i = 0; i < count; i++) {
         if (!items[i].mesh || items[i].n <= 0) return 0;
         o += a256(layout(items[i].mesh->nf, items[i].n, 1).total);
@@ -1269,6 +1350,8 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
     char *w = (char *)workspace;
     FpsArgs *table = (FpsArgs *)w;
     size_t o = a256(sizeof(FpsArgs) * (size_t)count);
+    GwnJob *gtable = (GwnJob *)(w + o);
+    o += a256(sizeof(GwnJob) * (size_t)count);
     std::vector<FpsArgs> args(count);
     std::vector<Layout> lay(count);
     std::vector<size_t> base(count);
@@ -1298,7 +1381,59 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
         k_fps_blocks_coarse<<<count, kFpsThreads, 0, st>>>(table);
     }
     for (int i = 0; i < count; i++)
-        if ((s = sample_finish(items[i], orient, w + base[i], lay[i], st)) != MCS_OK) return s;
+        if ((s = sample_finish(items[i], 0, w + base[i], lay[i], st)) != MCS_OK) return s;
+    if (orient) {
+        // the tree pass (orient 3, or orient 1 when the batch's faces x rows
+        // reach kGwnTreeMin) for all meshes in two launches, then each mesh's
+        // decision and brute force for its undecided rows
+        double pairs = 0.0;
+        for (int i = 0; i < count; i++) pairs += (double)items[i].mesh->nf * items[i].n;
+        const bool tree = orient == 3 || (orient == 1 && pairs >= kGwnTreeMin);
+        std::vector<GwnJob> jobs;
+        int nodes = 0, nrows = 0;
+        for (int i = 0; i < count; i++) {
+            orient_points(items[i], w + base[i], lay[i], st);
+            mcs_mesh m = items[i].mesh;
+            if (!tree || m->nf < 2) continue;
+            char *wb = w + base[i];
+            const Layout &L = lay[i];
+            MCS_CUDA(cudaMemsetAsync(wb + L.arrive, 0, sizeof(int) * (m->nf - 1), st));
+            GwnJob j;
+            j.m = m->dev();
+            j.child = m->child;
+            j.parent = m->parent;
+            j.arrive = (int *)(wb + L.arrive);
+            j.err = (int *)(wb + L.err);
+            j.ovf = (int *)(wb + L.govf);
+            j.agg = (GwnAgg *)(wb + L.agg);
+            j.q = (const float4 *)(wb + L.q);
+            j.D = (float *)(wb + L.gD);
+            j.E = (float *)(wb + L.gE);
+            j.n = items[i].n;
+            j.node0 = nodes;
+            j.row0 = nrows;
+            nodes += m->nf - 1;
+            nrows += items[i].n;
+            jobs.push_back(j);
+        }
+        if (!jobs.empty()) {
+            const int nj = (int)jobs.size();
+            for (int b0 = 0; b0 < nj; b0 += kGwnChunk) {
+                GwnChunk c;
+                c.count = std::min(kGwnChunk, nj - b0);
+                c.base = b0;
+                for (int k = 0; k < c.count; k++) c.j[k] = jobs[b0 + k];
+                note_launch();
+                k_store_gwn<<<1, 128, 0, st>>>(c, gtable);
+            }
+            note_launch();
+            k_gwn_agg_batched<<<(nodes + 255) / 256, 256, 0, st>>>(gtable, nj, nodes);
+            note_launch();
+            k_gwn_tree_batched<<<(nrows + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(gtable, nj, nrows);
+        }
+        for (int i = 0; i < count; i++)
+            orient_decide(items[i], w + base[i], lay[i], st, tree && items[i].mesh->nf >= 2);
+    }
     MCS_CUDA(cudaStreamSynchronize(st));
     return MCS_OK;
 }
