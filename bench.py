@@ -491,12 +491,10 @@ def _batch_setup(args, dev, rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     items = []
-    meshes = []
-    for h in hosts:
-        mesh = mcs.Mesh(h.V, h.F)
-        if args.bvh_layout != 2:
+    meshes = mcs.build_meshes([(h.V, h.F) for h in hosts])
+    if args.bvh_layout != 2:
+        for mesh in meshes:
             mesh.build_wide()  # the autotuner tries both layouts
-        meshes.append(mesh)
     for i, (mesh, rows) in enumerate(zip(meshes, mcs.sample_rows_batched(meshes, 1024, orient=True))):
         rows = {k: v for k, v in rows.items() if k in ("pos", "nrm", "area", "tri2bin")}
         items.append(dict(mesh=mesh, rows=rows, domain=i % 2, seed=i + 1_000_000 * rank))
@@ -675,13 +673,14 @@ def _batch_e2e(args, hosts, params, stream):
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record(stream)
     h2d = d2h = 0
-    meshes = []
+    dev_vf = []
     for V, F in VF:
-        mesh = mcs.Mesh(V.to("cuda", non_blocking=True), F.to("cuda", non_blocking=True))
-        if params.bvh_layout == 4:
-            mesh.build_wide()
+        dev_vf.append((V.to("cuda", non_blocking=True), F.to("cuda", non_blocking=True)))
         h2d += V.numel() * 8 + F.numel() * 4
-        meshes.append(mesh)
+    meshes = mcs.build_meshes(dev_vf)  # every BVH build enqueued before one synchronisation
+    if params.bvh_layout == 4:
+        for mesh in meshes:
+            mesh.build_wide()
     items = [dict(mesh=mesh, rows=rows, domain=i % 2, seed=i)
              for i, (mesh, rows) in enumerate(zip(meshes, mcs.sample_rows_batched(meshes, 1024, orient=True)))]
     b = mcs.Batch(items, params, assemble=True)

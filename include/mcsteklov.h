@@ -15,9 +15,11 @@
  *  - "device" pointers are CUDA global-memory pointers on the current device;
  *    "host" pointers are ordinary CPU memory.  Each argument says which.
  *  - Output buffers are allocated by the caller, in sizes stated here.  The
- *    library allocates only inside mcs_build_bvh (the mesh it owns until
- *    mcs_mesh_destroy) and nothing in the other calls: their scratch is the
- *    caller's workspace buffer (mcs_estimate_workspace_size bytes).
+ *    library allocates only inside mcs_build_bvh and mcs_build_bvh_batched
+ *    (the meshes it owns until mcs_mesh_destroy; the builds' temporaries come
+ *    from a stream-ordered pool the library keeps per device, up to 1 GiB
+ *    reserved between builds) and nothing in the other calls: their scratch
+ *    is the caller's workspace buffer (mcs_estimate_workspace_size bytes).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls enqueue their kernels on it and return without waiting,
  *    except where a host-side result (mcs_stats, a mesh handle) is requested:
@@ -174,6 +176,13 @@ void mcs_default_params(mcs_params *p);
  * (nv < 3, nf < 1, NULL), DEGENERATE (non-finite vertex, index out of range,
  * zero-extent bounding box), CUDA, OOM.  Synchronises `stream`. */
 mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream, mcs_mesh *out);
+/* Build `count` meshes as mcs_build_bvh does (same records and hierarchy),
+ * all enqueued on `stream` before one synchronisation: V[i], nv[i], F[i],
+ * nf[i] describe mesh i; out[i] receives it.  On an error no mesh is
+ * returned (all out[i] NULL), the status is that of the first failing mesh
+ * and mcs_last_error names its index. */
+mcs_status mcs_build_bvh_batched(int count, const double *const *V, const int *nv, const int32_t *const *F,
+                                 const int *nf, void *stream, mcs_mesh *out);
 void mcs_mesh_destroy(mcs_mesh m);
 /* The mesh's 4-wide BVH (mcs_params.bvh_layout = 4): the binary tree
  * collapsed two levels at a time, built on request (allocates mesh-owned

@@ -98,6 +98,8 @@ def lib():
         L.mcs_launch_count.restype = C.c_ulonglong
         L.mcs_default_params.argtypes = [C.POINTER(Params)]
         L.mcs_build_bvh.argtypes = [vp, i32, vp, i32, vp, C.POINTER(vp)]
+        L.mcs_build_bvh_batched.argtypes = [i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp), C.POINTER(i32), vp,
+                                            C.POINTER(vp)]
         L.mcs_mesh_destroy.argtypes = [vp]
         L.mcs_mesh_nv.argtypes = [vp]
         L.mcs_mesh_nf.argtypes = [vp]
@@ -198,20 +200,46 @@ def default_params(**kw) -> Params:
     return p
 
 
+def _mesh_arrays(V, F):
+    V = V if isinstance(V, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(V, np.float64))
+    F = F if isinstance(F, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(F, np.int32))
+    return V.to(torch.float64).contiguous(), F.to(torch.int32).contiguous()
+
+
+def build_meshes(pairs) -> "list[Mesh]":
+    """Many meshes, [(V, F), ...], built by mcs_build_bvh_batched: every
+    build enqueued before one synchronisation."""
+    arrs = [_mesh_arrays(V, F) for V, F in pairs]
+    n = len(arrs)
+    Vp = (C.c_void_p * n)(*[V.data_ptr() for V, _ in arrs])
+    Fp = (C.c_void_p * n)(*[F.data_ptr() for _, F in arrs])
+    nv = (C.c_int * n)(*[int(V.shape[0]) for V, _ in arrs])
+    nf = (C.c_int * n)(*[int(F.shape[0]) for _, F in arrs])
+    out = (C.c_void_p * n)()
+    _check(lib().mcs_build_bvh_batched(n, Vp, nv, Fp, nf, _stream(), out))
+    return [Mesh._adopt(C.c_void_p(out[i]), V, F) for i, (V, F) in enumerate(arrs)]
+
+
 class Mesh:
     """A mesh on the device with its BVH (owned by the library)."""
 
     def __init__(self, V, F):
-        V = V if isinstance(V, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(V, np.float64))
-        F = F if isinstance(F, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(F, np.int32))
-        V = V.to(torch.float64).contiguous()
-        F = F.to(torch.int32).contiguous()
+        V, F = _mesh_arrays(V, F)
         self._keep = (V, F)
         h = C.c_void_p()
         _check(lib().mcs_build_bvh(_ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(), C.byref(h)))
         self.handle = h
         self.nv = int(V.shape[0])
         self.nf = int(F.shape[0])
+
+    @classmethod
+    def _adopt(cls, handle, V, F):
+        obj = cls.__new__(cls)
+        obj._keep = (V, F)
+        obj.handle = handle
+        obj.nv = int(V.shape[0])
+        obj.nf = int(F.shape[0])
+        return obj
 
     def build_wide(self):
         """Build the 4-wide BVH (bvh_layout 4) of this mesh."""

@@ -69,11 +69,19 @@ __global__ void k_bounds_partial(const double *V, int nv, double *part) {
 }
 struct BoxFrame { double lo[3], inv[3]; };
 
+// one warp folds the partial boxes (min and max are exact in any order)
 __global__ void k_bounds_final(const double *part, int nb, double *out, BoxFrame *fr) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nb; b++)
+    for (int b = lane; b < nb; b += 32)
         for (int k = 0; k < 3; k++) { mn[k] = fmin(mn[k], part[6 * b + k]); mx[k] = fmax(mx[k], part[6 * b + 3 + k]); }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; k++) {
+            mn[k] = fmin(mn[k], __shfl_xor_sync(0xFFFFFFFFu, mn[k], o));
+            mx[k] = fmax(mx[k], __shfl_xor_sync(0xFFFFFFFFu, mx[k], o));
+        }
+    if (lane != 0) return;
     for (int k = 0; k < 3; k++) {
         out[k] = mn[k];
         out[3 + k] = mx[k];
@@ -104,22 +112,26 @@ __device__ __forceinline__ uint32_t morton30(double x, double y, double z, const
 // the kernels that index V through F return at once when validation flagged
 // the input (*bad != 0), which the build reports after its single sync
 __global__ void k_tri_keys(const double *V, const int32_t *F, int nf, const BoxFrame *frp, const int *bad,
-                           unsigned long long *keys) {
+                           uint32_t *mort, int32_t *fidx) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf || *bad) return;
     const BoxFrame fr = *frp;
     const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
     const double cx = ((a[0] + b[0]) + c[0]) / 3.0, cy = ((a[1] + b[1]) + c[1]) / 3.0, cz = ((a[2] + b[2]) + c[2]) / 3.0;
-    keys[f] = ((unsigned long long)morton30(cx, cy, cz, fr.lo, fr.inv) << 32) | (unsigned)f;
+    // sorted stably by the code with the face as value: the order of the
+    // unique keys (code << 32 | f) in half the radix passes
+    mort[f] = morton30(cx, cy, cz, fr.lo, fr.inv);
+    fidx[f] = f;
 }
 
 // triangle slots in BVH order: (a, ab, ac) in FP64 and, from float-rounded
 // vertices, in FP32; box of each slot rounded outward to float
-__global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const unsigned long long *keys, const int *bad,
-                            Tri32 *t32, Tri64 *t64, float *slotbox) {
+__global__ void k_tri_slots(const double *V, const int32_t *F, int nf, const uint32_t *mort_s, const int32_t *fidx_s,
+                            const int *bad, unsigned long long *keys, Tri32 *t32, Tri64 *t64, float *slotbox) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nf || *bad) return;
-    const int f = (int)(keys[s] & 0xFFFFFFFFull);
+    const int f = fidx_s[s];
+    keys[s] = ((unsigned long long)mort_s[s] << 32) | (unsigned)f;
     const double *A = V + 3 * F[3 * f], *B = V + 3 * F[3 * f + 1], *C = V + 3 * F[3 * f + 2];
     Tri64 t;
     Tri32 u;
@@ -273,19 +285,23 @@ __global__ void k_collapse4(int n, const int *child, const float *nodebox, const
     nodes4[idx4[i]] = nd;
 }
 
-__global__ void k_incidence(const int32_t *F, int nf, unsigned long long *pairs) {
+// (vertex, face) incidences, sorted stably by vertex: faces ascend within a
+// vertex because they enter in face order
+__global__ void k_incidence(const int32_t *F, int nf, uint32_t *vkey, int32_t *fval) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
-    for (int k = 0; k < 3; k++) pairs[3 * f + k] = ((unsigned long long)(unsigned)F[3 * f + k] << 32) | (unsigned)f;
+    for (int k = 0; k < 3; k++) {
+        vkey[3 * f + k] = (uint32_t)F[3 * f + k];
+        fval[3 * f + k] = f;
+    }
 }
-__global__ void k_incidence_csr(const unsigned long long *pairs, int m, int nv, const int *bad, int32_t *inc_f,
-                                int32_t *vstart) {
+__global__ void k_incidence_csr(const uint32_t *vkey, const int32_t *fval, int m, int nv, const int *bad,
+                                int32_t *inc_f, int32_t *vstart) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m || *bad) return;
-    const unsigned long long p = pairs[i];
-    const int v = (int)(p >> 32);
-    inc_f[i] = (int)(p & 0xFFFFFFFFull);
-    const int vprev = i == 0 ? -1 : (int)(pairs[i - 1] >> 32);
+    const int v = (int)vkey[i];
+    inc_f[i] = fval[i];
+    const int vprev = i == 0 ? -1 : (int)vkey[i - 1];
     for (int w = vprev + 1; w <= v; w++) vstart[w] = i;
     if (i == m - 1)
         for (int w = v + 1; w <= nv; w++) vstart[w] = m;
@@ -405,14 +421,22 @@ void mcs_mesh_destroy(mcs_mesh m) { mesh_free(m); }
 int mcs_mesh_nv(mcs_mesh m) { return m ? m->nv : 0; }
 int mcs_mesh_nf(mcs_mesh m) { return m ? m->nf : 0; }
 
-mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream_, mcs_mesh *out) {
-    NvtxRange nvtx_range("mcs_build_bvh");
-    MCS_ARG(out != nullptr, "mcs_build_bvh: out is NULL");
-    *out = nullptr;
-    MCS_ARG(V != nullptr && F != nullptr, "mcs_build_bvh: V or F is NULL");
-    MCS_ARG(nv >= 3 && nf >= 1, "mcs_build_bvh: need nv >= 3 and nf >= 1");
-    MCS_ARG((long long)nf * 3 < (1LL << 31) && (long long)nv * 3 < (1LL << 31), "mcs_build_bvh: mesh too large");
-    cudaStream_t st = as_stream(stream_);
+}  // extern "C"
+
+static mcs_status build_args(const double *V, int nv, const int32_t *F, int nf, const char *who) {
+    MCS_ARG(V != nullptr && F != nullptr, std::string(who) + ": V or F is NULL");
+    MCS_ARG(nv >= 3 && nf >= 1, std::string(who) + ": need nv >= 3 and nf >= 1");
+    MCS_ARG((long long)nf * 3 < (1LL << 31) && (long long)nv * 3 < (1LL << 31), std::string(who) + ": mesh too large");
+    return MCS_OK;
+}
+
+// a BVH build enqueued on st without a host round trip: the mesh's arrays
+// (one block it owns) and the build's temporaries (pool memory freed in
+// stream order); the validation flags (2 ints) and the bounds (6 doubles)
+// are copied to flags_dev / box_dev for build_finish.  *out is the mesh
+// (its host fields lo, hi, rmax, scale set by build_finish)
+static mcs_status build_enqueue(const double *V, int nv, const int32_t *F, int nf, cudaStream_t st, int *flags_dev,
+                                double *box_dev, mcs_mesh_s **out) {
     const bool vdev = is_device_ptr(V), fdev = is_device_ptr(F);
     mcs_mesh_s *m = new mcs_mesh_s();
     m->nv = nv;
@@ -459,11 +483,14 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     m->inc_f = (int32_t *)mtake(msz[9]);
     m->vstart = (int32_t *)mtake(msz[10]);
 
+    // radix passes over the bits that vary: 30 for the Morton codes, those of
+    // the largest vertex id for the incidences
+    const int vbits = nv > 1 ? 32 - __builtin_clz((unsigned)(nv - 1)) : 1;
     size_t sort_bytes = 0, sort_bytes2 = 0;
-    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
-                                   nf, 0, 62, st);
-    cub::DeviceRadixSort::SortKeys(nullptr, sort_bytes2, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
-                                   3 * nf, 0, 64, st);
+    cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (uint32_t *)nullptr, (uint32_t *)nullptr, (int32_t *)nullptr,
+                                    (int32_t *)nullptr, nf, 0, 30, st);
+    cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes2, (uint32_t *)nullptr, (uint32_t *)nullptr, (int32_t *)nullptr,
+                                    (int32_t *)nullptr, 3 * nf, 0, vbits, st);
     const int nbp = 256;
     const size_t tsz[12] = {sizeof(int) * 2,  sizeof(double) * 6 * nbp, sizeof(double) * 6,
                             sizeof(unsigned long long) * nf, sizeof(unsigned long long) * nf,
@@ -506,10 +533,15 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     k_bounds_final<<<1, 32, 0, st>>>(d_part, nbp, d_box, d_frame);
     const int tb = 256;
     note_launch();
-    k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, d_frame, d_bad, keys);
-    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes, keys, keys_s, nf, 0, 62, st));
+    // Morton codes and faces in the keys' space, sorted into the incidences'
+    // (both used again only later)
+    uint32_t *mort = (uint32_t *)keys, *mort_s = (uint32_t *)pairs_s;
+    int32_t *fidx = (int32_t *)(mort + nf), *fidx_s = (int32_t *)(mort_s + nf);
+    k_tri_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, d_frame, d_bad, mort, fidx);
+    MB_CUDA(cub::DeviceRadixSort::SortPairs(d_sort, sort_bytes, mort, mort_s, fidx, fidx_s, nf, 0, 30, st));
     note_launch();
-    k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, keys_s, d_bad, m->t32, m->t64, slotbox);
+    k_tri_slots<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, nf, mort_s, fidx_s, d_bad, keys_s, m->t32, m->t64,
+                                                    slotbox);
     if (nf > 1) {
         // links, parents and child boxes go straight into the mesh (kept for
         // an on-demand 4-wide copy, mcs_mesh_build_wide)
@@ -526,23 +558,28 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     }
     // vertex -> incident faces, ascending
     note_launch();
-    k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, pairs);
-    MB_CUDA(cub::DeviceRadixSort::SortKeys(d_sort, sort_bytes2, pairs, pairs_s, 3 * nf, 0, 64, st));
+    uint32_t *vkey = (uint32_t *)pairs, *vkey_s = (uint32_t *)pairs_s;
+    int32_t *fval = (int32_t *)(vkey + 3 * (size_t)nf), *fval_s = (int32_t *)(vkey_s + 3 * (size_t)nf);
+    k_incidence<<<(nf + tb - 1) / tb, tb, 0, st>>>(m->F, nf, vkey, fval);
+    MB_CUDA(cub::DeviceRadixSort::SortPairs(d_sort, sort_bytes2, vkey, vkey_s, fval, fval_s, 3 * nf, 0, vbits, st));
     MB_CUDA(cudaMemsetAsync(m->vstart, 0, sizeof(int32_t) * (nv + 1), st));
     note_launch();
-    k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(pairs_s, 3 * nf, nv, d_bad, m->inc_f, m->vstart);
+    k_incidence_csr<<<(3 * nf + tb - 1) / tb, tb, 0, st>>>(vkey_s, fval_s, 3 * nf, nv, d_bad, m->inc_f, m->vstart);
     MB_CUDA(cudaGetLastError());
-    // the build's one host round trip: validation flags, tree check, bounds
-    int flags[2] = {0, 0};
-    double box[6];
-    MB_CUDA(cudaMemcpyAsync(flags, d_bad, sizeof(flags), cudaMemcpyDeviceToHost, st));
-    MB_CUDA(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st));
+    MB_CUDA(cudaMemcpyAsync(flags_dev, d_bad, sizeof(int) * 2, cudaMemcpyDeviceToDevice, st));
+    MB_CUDA(cudaMemcpyAsync(box_dev, d_box, sizeof(double) * 6, cudaMemcpyDeviceToDevice, st));
     MB_CUDA(cudaFreeAsync(tbuf, st));
     tbuf = nullptr;
-    MB_CUDA(cudaStreamSynchronize(st));
+#undef MB_CUDA
+    *out = m;
+    return MCS_OK;
+}
+
+// the checks of a build once its flags and bounds are on the host
+static mcs_status build_finish(mcs_mesh_s *m, const int *flags, const double *box) {
     if (flags[0]) {
         set_error(flags[0] & 1 ? "mcs_build_bvh: non-finite vertex coordinate" : "mcs_build_bvh: face index out of range");
-        return fail(MCS_ERR_DEGENERATE);
+        return MCS_ERR_DEGENERATE;
     }
     double side = INFINITY, scale = 0.0;
     for (int k = 0; k < 3; k++) {
@@ -553,20 +590,81 @@ mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void
     }
     if (!(side > 0.0)) {
         set_error("mcs_build_bvh: the bounding box has a zero-length side");
-        return fail(MCS_ERR_DEGENERATE);
+        return MCS_ERR_DEGENERATE;
     }
     m->rmax = 0.5 * side;
     m->scale = (float)scale * (1.0f + 1e-6f);
     if (flags[1]) {
         set_error("mcs_build_bvh: internal error, malformed hierarchy");
-        return fail(MCS_ERR_DEVICE);
+        return MCS_ERR_DEVICE;
     }
-#undef MB_CUDA
+    return MCS_OK;
+}
+
+extern "C" {
+
+mcs_status mcs_build_bvh(const double *V, int nv, const int32_t *F, int nf, void *stream_, mcs_mesh *out) {
+    NvtxRange nvtx_range("mcs_build_bvh");
+    MCS_ARG(out != nullptr, "mcs_build_bvh: out is NULL");
+    *out = nullptr;
+    mcs_status s = build_args(V, nv, F, nf, "mcs_build_bvh");
+    if (s != MCS_OK) return s;
+    return mcs_build_bvh_batched(1, &V, &nv, &F, &nf, stream_, out);
+}
+
+mcs_status mcs_build_bvh_batched(int count, const double *const *V, const int *nv, const int32_t *const *F,
+                                 const int *nf, void *stream_, mcs_mesh *out) {
+    NvtxRange nvtx_range("mcs_build_bvh_batched");
+    MCS_ARG(count >= 1 && V && nv && F && nf && out, "mcs_build_bvh_batched: NULL array or count < 1");
+    for (int i = 0; i < count; i++) out[i] = nullptr;
+    for (int i = 0; i < count; i++) {
+        const mcs_status s = build_args(V[i], nv[i], F[i], nf[i], "mcs_build_bvh_batched");
+        if (s != MCS_OK) return s;
+    }
+    cudaStream_t st = as_stream(stream_);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    MCS_CUDA(temp_pool(dev, &pool));
+    // every build's flags (2 ints) and bounds (6 doubles) in one 64-byte slot
+    void *stat = nullptr;
+    MCS_CUDA(cudaMallocFromPoolAsync(&stat, 64 * (size_t)count, pool, st));
+    std::vector<mcs_mesh_s *> ms(count, nullptr);
+    auto free_all = [&]() {
+        for (mcs_mesh_s *m : ms) mesh_free(m);
+        if (stat) cudaFreeAsync(stat, st);
+    };
+    for (int i = 0; i < count; i++) {
+        char *slot = (char *)stat + 64 * (size_t)i;
+        const mcs_status s = build_enqueue(V[i], nv[i], F[i], nf[i], st, (int *)slot, (double *)(slot + 16), &ms[i]);
+        if (s != MCS_OK) {
+            free_all();
+            return s;
+        }
+    }
+    std::vector<unsigned char> host(64 * (size_t)count);
+    cudaError_t e = cudaMemcpyAsync(host.data(), stat, host.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaFreeAsync(stat, st);
+    stat = nullptr;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_all();
+        return cuda_fail(e, "mcs_build_bvh_batched");
+    }
+    for (int i = 0; i < count; i++) {
+        const unsigned char *slot = host.data() + 64 * (size_t)i;
+        const mcs_status s = build_finish(ms[i], (const int *)slot, (const double *)(slot + 16));
+        if (s != MCS_OK) {
+            if (count > 1) set_error("mesh " + std::to_string(i) + ": " + g_err);
+            free_all();
+            return s;
+        }
+    }
+    for (int i = 0; i < count; i++) out[i] = ms[i];
     // mesh creation may allocate: load here what the allocation-free
     // estimate needs, so that it loads (and allocates) nothing itself; a
     // failure here only surfaces when that entry point is called
     (void)noalloc_prepare();
-    *out = m;
     return MCS_OK;
 }
 

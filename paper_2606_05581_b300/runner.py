@@ -135,11 +135,11 @@ def gpu_estimate(make_mesh: Callable, rows_per_mesh: int, params, domain_of: Cal
     each mesh's k smallest Steklov pairs, copied to host arrays."""
     import torch
 
-    from . import Batch, Mesh, sample_rows_batched, steklov_modes
+    from . import Batch, build_meshes, sample_rows_batched, steklov_modes
 
     def estimate(ids):
         hosts = [make_mesh(i) for i in ids]
-        meshes = [Mesh(h.V, h.F) for h in hosts]
+        meshes = build_meshes([(h.V, h.F) for h in hosts])
         rows = sample_rows_batched(meshes, rows_per_mesh, orient=True)
         items = [dict(mesh=m, rows={q: r[q] for q in ("pos", "nrm", "area", "tri2bin")}, domain=int(domain_of(i)),
                       seed=int(seed_of(i))) for i, m, r in zip(ids, meshes, rows)]

@@ -184,3 +184,24 @@ def test_batched_sample_rows_equal_single():
         one = mcs.sample_rows(mesh, 200, orient=True)
         for k in ("sel", "tri2bin", "area", "pos", "nrm"):
             assert torch.equal(g[k], one[k]), k
+
+
+def test_batched_builds_equal_single_builds():
+    """mcs_build_bvh_batched (every build enqueued before one sync) builds
+    the same hierarchies as one mcs_build_bvh per mesh: the same estimate
+    on either gives the same hit counts and Lambda bit for bit; a batch with
+    one invalid mesh fails, naming it, and returns no mesh."""
+    hosts = [meshgen.icosphere(2), meshgen.wild_union(6, 5000, seed=9), meshgen.two_spheres(2, 0.5, 1.5)]
+    one = [mcs.Mesh(h.V, h.F) for h in hosts]
+    many = mcs.build_meshes([(h.V, h.F) for h in hosts])
+    for dom, (a, b) in enumerate(zip(one, many)):
+        assert (a.nv, a.nf) == (b.nv, b.nf)
+        p = mcs.default_params(walks_per_row=32, prec=32, seed=7, domain=dom % 2,
+                               killing_walks=4096 if dom % 2 else 0)
+        ra = mcs.estimate_dtn(a, mcs.vertex_rows(a), p)
+        rb = mcs.estimate_dtn(b, mcs.vertex_rows(b), p)
+        assert torch.equal(mcs.dense_hist(ra, a.nv), mcs.dense_hist(rb, b.nv))
+        assert torch.equal(ra["Lambda"], rb["Lambda"])
+    bad = hosts[1].F + 100000
+    with pytest.raises(mcs.MCSError, match="mesh 1"):
+        mcs.build_meshes([(hosts[0].V, hosts[0].F), (hosts[1].V, bad), (hosts[2].V, hosts[2].F)])
