@@ -333,8 +333,10 @@ void mcs_graph_destroy(mcs_graph g);
 
 /* Autotuner of the walk launch.  Runs the batch's row setup, then times the
  * walk kernel on a sample (every s-th row of every mesh's row schedule,
- * s = floor(1 / sample_fraction), no killing walks) for the queue orders (row
- * order, mesh order), the BVH node layouts (when p->bvh_layout is 0),
+ * s = floor(1 / sample_fraction), no killing walks) for the row order of
+ * the queue (a batch of several meshes always dispenses them longest first,
+ * queue_order bit 1: its benefit, a shorter tail, grows with the walks per
+ * mesh and does not show in the sample), the BVH node layouts (when p->bvh_layout is 0),
  * candidate block sizes (64, 128 threads) and resident blocks per SM (the
  * three largest residencies the kernel allows), by coordinate search in that
  * order; each trial takes the best of three runs, and a candidate replaces
