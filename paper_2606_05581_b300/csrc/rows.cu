@@ -652,8 +652,22 @@ __global__ void k_sample_rows(const double *V, const int32_t *F, const double *c
                               double *nrm, double *area) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ns) return;
+    // the cell's faces in ascending order, their loads issued 8 at a time
+    // ahead of the additions (same summation order)
     double s = 0.0;
-    for (int e = start[i]; e < start[i + 1]; e++) s += farea[sfaces[e]];
+    const int e1 = start[i + 1];
+    int e = start[i];
+    for (; e + 8 <= e1; e += 8) {
+        int id[8];
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) id[k] = sfaces[e + k];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = farea[id[k]];
+#pragma unroll
+        for (int k = 0; k < 8; k++) s += v[k];
+    }
+    for (; e < e1; e++) s += farea[sfaces[e]];
     area[i] = s;
     const int f = sel[i];
     const double *a = V + 3 * F[3 * f], *b = V + 3 * F[3 * f + 1], *c = V + 3 * F[3 * f + 2];
@@ -1238,7 +1252,10 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
     note_launch();
     k_owner_keys<<<(nf + tb - 1) / tb, tb, 0, st>>>(owner, nf, keys, vals);
     size_t sb = L.sort_bytes;
-    MCS_CUDA(cub::DeviceRadixSort::SortPairs(w + L.sort, sb, keys, skeys, vals, svals, nf, 0, 32, st));
+    // owners lie in [0, n): radix passes over their bits only (the workspace
+    // was sized for all 32, an upper bound)
+    const int obits = n > 1 ? 32 - __builtin_clz((unsigned)(n - 1)) : 1;
+    MCS_CUDA(cub::DeviceRadixSort::SortPairs(w + L.sort, sb, keys, skeys, vals, svals, nf, 0, obits, st));
     MCS_CUDA(cudaMemsetAsync(start, 0, sizeof(int32_t) * (n + 1), st));
     note_launch();
     k_segments<<<(nf + tb - 1) / tb, tb, 0, st>>>(skeys, nf, n, start);
