@@ -119,16 +119,52 @@ __device__ __forceinline__ double fp32_band(const DevMesh &m, double x, double y
     return 1.52587890625e-05 * ((double)m.scale + fmax(fabs(x), fmax(fabs(y), fabs(z))));
 }
 
-// dist(p) in FP64 (the exact argmin distance): an FP32 query bounds it, then
-// the FP64 query searches only the triangles within that bound
-__device__ __forceinline__ double wdist(const DevMesh &m, double x, double y, double z, int *front, int *err) {
+// dist(p) in FP64 (the exact argmin distance): an FP32 query bounds it by
+// bound = its distance + 2E.  Every triangle at the FP64 minimum (the
+// argmin and its ties) has a float distance below bound + E, so with cand
+// given an FP32 pass collects those triangles and they are tested in FP64,
+// one per lane, under the FP64 query's (d^2, id) order; otherwise (or when
+// more than kCandMax qualify) the FP64 query searches within the bound
+__device__ __forceinline__ double wdist(const DevMesh &m, double x, double y, double z, int *front, int *err,
+                                        int *cand = nullptr) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
     Hit<double> h;
     const float xf = (float)x, yf = (float)y, zf = (float)z;
     double bound = 0.0;
     if (isfinite(xf) && isfinite(yf) && isfinite(zf)) {
         Hit<float> hf;
         warp_query<float, kFull>(m, xf, yf, zf, 0.0f, hf, front, err);
-        if (hf.slot >= 0 && isfinite(hf.d2)) bound = sqrt((double)hf.d2) + 2.0 * fp32_band(m, x, y, z);
+        const double E = fp32_band(m, x, y, z);
+        if (hf.slot >= 0 && isfinite(hf.d2)) bound = sqrt((double)hf.d2) + 2.0 * E;
+        if (cand && bound > 0.0) {
+            int *ncand = cand + kCandMax;
+            if (lane == 0) *ncand = 0;
+            __syncwarp();
+            Hit<float> hc;
+            warp_query<float, kCollect>(m, xf, yf, zf, (float)(bound + E), hc, front, err, 0.0f, cand, ncand);
+            __syncwarp();
+            const int nc = *ncand;
+            if (nc >= 1 && nc <= kCandMax) {
+                double d2 = INFINITY;
+                int id = 0x7FFFFFFF;
+                for (int k = lane; k < nc; k += 32) {
+                    double b[3];
+                    int kid;
+                    const double e2 = Slot<double>::test(m, cand[k], x, y, z, b, kid);
+                    if (e2 < d2 || (e2 == d2 && kid < id)) { d2 = e2; id = kid; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double od2 = __shfl_xor_sync(FULL, d2, o);
+                    const int oid = __shfl_xor_sync(FULL, id, o);
+                    if (od2 < d2 || (od2 == d2 && oid < id)) { d2 = od2; id = oid; }
+                }
+                __syncwarp();
+                return sqrt(d2);
+            }
+            __syncwarp();
+        }
     }
     warp_query<double, kFull>(m, x, y, z, bound, h, front, err);
     if (h.slot < 0 && bound > 0.0) warp_query<double, kFull>(m, x, y, z, 0.0, h, front, err);
@@ -185,7 +221,7 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
         // naive estimator (Alg. 1): the ball of the first walk-on-spheres step
         // from the inset point
         b.c[0] = s0 - fr.inset * n0; b.c[1] = s1 - fr.inset * n1; b.c[2] = s2 - fr.inset * n2;
-        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err);
+        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err, cand);
         b.r = fr.inset;
     } else if (nz) {
         const double rmax = fr.rmax;
@@ -202,7 +238,7 @@ __device__ void tangent_int_row(const DevMesh &m, const double *pos, const doubl
             r = lo;
         }
         b.c[0] = s0 - r * n0; b.c[1] = s1 - r * n1; b.c[2] = s2 - r * n2;
-        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err);
+        b.rho = wdist(m, b.c[0], b.c[1], b.c[2], front, &err, cand);
         b.r = r;
     }
     b.valid = nz && (b.rho >= fr.rho_min_factor * fr.eps);
@@ -403,7 +439,7 @@ __device__ void tangent_ext_row(const DevMesh &m, const double *pos, const doubl
             if (den > 1e-6 * cc) {
                 const double invd = 1.0 / den;
                 const double C0 = ct0 * invd, C1 = ct1 * invd, C2 = ct2 * invd;
-                const double D = wdist(m, C0 + o[0], C1 + o[1], C2 + o[2], front, &err);
+                const double D = wdist(m, C0 + o[0], C1 + o[1], C2 + o[2], front, &err, cand);
                 const double CC = C0 * C0 + C1 * C1 + C2 * C2;
                 const double den2 = CC - D * D;
                 // |C|^2 - D^2 cancels when the empty ball nearly reaches the centre
