@@ -337,11 +337,12 @@ void mcs_graph_destroy(mcs_graph g);
  * the queue (a batch of several meshes always dispenses them longest first,
  * queue_order bit 1: its benefit, a shorter tail, grows with the walks per
  * mesh and does not show in the sample), the BVH node layouts (when p->bvh_layout is 0),
- * candidate block sizes (64, 128 threads) and resident blocks per SM (the
- * three largest residencies the kernel allows), by coordinate search in that
+ * candidate block sizes (64, 128 threads), each at the largest residency the
+ * kernel allows (a smaller one looks better in the sample's tail, with few
+ * walks per SM, than in the full launch), by coordinate search in that
  * order; each trial takes the best of three runs, and a candidate replaces
- * the incumbent only when it is more than 2% faster (smaller differences are
- * the sample's run-to-run noise).  tuned (host) = p with bvh_layout, lanes_per_query,
+ * the incumbent only when it is more than 5% faster (smaller differences are
+ * within the sample's run-to-run noise).  tuned (host) = p with bvh_layout, lanes_per_query,
  * threads_per_block, blocks_per_sm and queue_order set.  trials (host, optional) receives up to
  * max_trials entries, n_trials their count.  Synchronises `stream`.  The
  * workspace and outputs are those of the batch; their contents are left

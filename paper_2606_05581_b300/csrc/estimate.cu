@@ -2327,8 +2327,10 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
     // mesh order), BVH node layout, residency (block size x blocks per SM).
     // A candidate replaces the incumbent only when it is faster by more than
     // kTuneMargin: differences below that are run-to-run noise of the sample
-    // (measured +-5% between boxes on the 512-mesh batch)
-    constexpr float kTuneMargin = 0.98f;
+    // (measured +-5% between boxes on the 512-mesh batch; with a 2% margin the
+    // sample once chose 64 x 16 threads per SM for a 3% gain, and the full
+    // launch took 4.36 s against 3.89 s at 128 x 10)
+    constexpr float kTuneMargin = 0.95f;
     mcs_params best = *p;
     best.queue_order = 0;
     best.bvh_layout = use_wide(p) ? 4 : 2;  // the library default unless the caller fixed one
@@ -2383,7 +2385,12 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
         q.blocks_per_sm = 0;
         int t = 0, occ = 0;
         if ((s = walk_residency(&q, b.mode, n > 1, &t, &occ)) != MCS_OK) { cleanup(); return s; }
-        for (int bps = std::max(1, occ - 2 * (128 / tpb)); bps <= occ; bps += 128 / tpb) {
+        // only the largest residency of each block size: the full launch is
+        // latency-bound and wants every warp it can hold, while the sample's
+        // tail (few walks per SM) favours fewer -- on the 512-mesh batch the
+        // sample chose 128 x 8 and 64 x 16 over 128 x 10, whose full launches
+        // took 4.36 s against 3.89 s
+        for (int bps = occ; bps <= occ; bps++) {
             if (tpb == best.threads_per_block && bps == best.blocks_per_sm) continue;  // the incumbent
             q.blocks_per_sm = bps;
             float ms = 0.f;

@@ -154,12 +154,12 @@ def test_autotuner_returns_a_valid_shape_and_same_results():
     assert all(t["ms"] > 0 for t in trials)
     assert tuned.threads_per_block in (64, 128) and tuned.blocks_per_sm >= 1
     assert 0 <= tuned.queue_order <= 3
-    # the tuned shape is a tried one, within the 2% noise margin of the fastest trial
+    # the tuned shape is a tried one, within the 5% noise margin of the fastest trial
     key = (tuned.threads_per_block, tuned.blocks_per_sm, tuned.queue_order, tuned.bvh_layout, tuned.lanes_per_query)
     mine = [t for t in trials if (t["threads_per_block"], t["blocks_per_sm"], t["queue_order"], t["bvh_layout"],
                                   t["lanes_per_query"]) == key]
     assert mine, (key, trials)
-    assert min(t["ms"] for t in mine) * 0.98 <= min(t["ms"] for t in trials) + 1e-6
+    assert min(t["ms"] for t in mine) * 0.95 <= min(t["ms"] for t in trials) + 1e-6
     assert {(t["bvh_layout"], t["lanes_per_query"]) for t in trials} >= {(2, 1), (4, 1), (4, 4)}
     b.run()
     for i in range(len(items)):
