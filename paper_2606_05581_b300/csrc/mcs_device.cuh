@@ -664,8 +664,9 @@ __device__ __forceinline__ T warp_min(T v) {
 
 //   kCollect: true if some triangle has sqrt(d^2) < lo (early exit); else
 //           the slots of the triangles with lo <= sqrt(d^2) < thr are stored
-//           in cand (shared, kCandMax entries; *ncand counts them, possibly
-//           beyond kCandMax, and must be zero on entry)
+//           in cand (shared, kCandMax entries; *ncand counts them and must be
+//           zero on entry); once it passes kCandMax the traversal stops, and
+//           the result says nothing beyond that overflow
 template <typename T, int MODE>
 __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &out, int *front, int *err,
                            T lo = (T)0, int *cand = nullptr, int *ncand = nullptr) {
@@ -755,6 +756,9 @@ __device__ bool warp_query(const DevMesh &m, T px, T py, T pz, T thr, Hit<T> &ou
     while (true) {
         refresh();
         if (MODE != kFull && __any_sync(FULL, hit)) { hit = true; break; }
+        // kCollect past kCandMax: the caller falls back to an exact FP64
+        // query, so the rest of this traversal would be wasted
+        if (MODE == kCollect && __any_sync(FULL, *ncand > kCandMax)) break;
         const bool active = node != kNone;
         if (!__any_sync(FULL, active)) break;
         if (!active) continue;
