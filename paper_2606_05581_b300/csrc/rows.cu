@@ -647,11 +647,9 @@ __global__ void k_segments(const int32_t *skeys, int nf, int ns, int32_t *start)
     if (e == nf - 1)
         for (int w = k + 1; w <= ns; w++) start[w] = nf;
 }
-__global__ void k_sample_rows(const double *V, const int32_t *F, const double *cen, const double *farea,
-                              const int32_t *sel, const int32_t *sfaces, const int32_t *start, int ns, double *pos,
-                              double *nrm, double *area) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
+__device__ void sample_row(const double *V, const int32_t *F, const double *cen, const double *farea,
+                           const int32_t *sel, const int32_t *sfaces, const int32_t *start, int i, double *pos,
+                           double *nrm, double *area) {
     // the cell's faces in ascending order, their loads issued 8 at a time
     // ahead of the additions (same summation order)
     double s = 0.0;
@@ -680,12 +678,16 @@ __global__ void k_sample_rows(const double *V, const int32_t *F, const double *c
     nrm[3 * i + 2] = l > 0.0 ? N2 / l : 0.0;
     for (int k = 0; k < 3; k++) pos[3 * i + k] = cen[3 * f + k];
 }
+__global__ void k_sample_rows(const double *V, const int32_t *F, const double *cen, const double *farea,
+                              const int32_t *sel, const int32_t *sfaces, const int32_t *start, int ns, double *pos,
+                              double *nrm, double *area) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ns) sample_row(V, F, cen, farea, sel, sfaces, start, i, pos, nrm, area);
+}
 
 // query points x -/+ delta n of every sample (FP32), and the face each excludes
-__global__ void k_gwn_points(const double *pos, const double *nrm, const double *farea, const int32_t *sel, int ns,
-                             float4 *q) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
+__device__ void gwn_point(const double *pos, const double *nrm, const double *farea, const int32_t *sel, int i,
+                          float4 *q) {
     const double delta = 0.25 * sqrt(farea[sel[i]]);
     for (int side = 0; side < 2; side++) {
         const double sg = side == 0 ? -1.0 : 1.0;
@@ -693,6 +695,44 @@ __global__ void k_gwn_points(const double *pos, const double *nrm, const double 
                                       (float)(pos[3 * i + 1] + sg * delta * nrm[3 * i + 1]),
                                       (float)(pos[3 * i + 2] + sg * delta * nrm[3 * i + 2]), __int_as_float(sel[i]));
     }
+}
+__global__ void k_gwn_points(const double *pos, const double *nrm, const double *farea, const int32_t *sel, int ns,
+                             float4 *q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ns) gwn_point(pos, nrm, farea, sel, i, q);
+}
+
+// the rows (and, with q, the orientation query points) of many meshes in one
+// launch: each mesh's launch would wait alone for its largest cell, whose
+// area is summed face by face in ascending order
+struct RowsJob {
+    const double *V, *cen, *farea;
+    const int32_t *F, *sel, *sfaces, *start;
+    double *pos, *nrm, *area;
+    float4 *q;
+    int row0;
+};
+constexpr int kRowsChunk = 40;
+struct RowsChunk {
+    RowsJob j[kRowsChunk];
+    int count, base;
+};
+__global__ void k_store_rows(RowsChunk c, RowsJob *table) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) table[c.base + i] = c.j[i];
+}
+__global__ void k_rows_batched(const RowsJob *jobs, int count, int total) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo = 0, hi = count - 1;  // the last job whose first row is <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].row0 <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const RowsJob &J = jobs[lo];
+    const int i = g - J.row0;
+    sample_row(J.V, J.F, J.cen, J.farea, J.sel, J.sfaces, J.start, i, J.pos, J.nrm, J.area);
+    if (J.q) gwn_point(J.pos, J.nrm, J.farea, J.sel, i, J.q);
 }
 
 // ---------------------------------------------------------------------------
@@ -1237,7 +1277,9 @@ static void orient_decide(const mcs_sample_item &it, char *w, const Layout &L, c
 }
 
 // owners by face, quadrature areas, row points and normals (+ orientation)
-static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, const Layout &L, cudaStream_t st) {
+// rows = false leaves the row kernel (k_sample_rows) to the caller's batched launch
+static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, const Layout &L, cudaStream_t st,
+                                bool rows = true) {
     mcs_mesh m = it.mesh;
     const int nf = m->nf, n = it.n, tb = 256;
     double *cen = (double *)(w + L.cen), *farea = (double *)(w + L.farea);
@@ -1259,9 +1301,11 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
     MCS_CUDA(cudaMemsetAsync(start, 0, sizeof(int32_t) * (n + 1), st));
     note_launch();
     k_segments<<<(nf + tb - 1) / tb, tb, 0, st>>>(skeys, nf, n, start);
-    note_launch();
-    k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, it.sel, svals, start, n, it.pos, it.nrm,
-                                                    it.area);
+    if (rows) {
+        note_launch();
+        k_sample_rows<<<(n + tb - 1) / tb, tb, 0, st>>>(m->V, m->F, cen, farea, it.sel, svals, start, n, it.pos,
+                                                        it.nrm, it.area);
+    }
     if (orient) {
         // orient 3: hierarchical sums, brute force for the rows within their
         // bound; orient 2: brute force for every row; orient 1: the first
@@ -1344,7 +1388,8 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
 
 size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int count) {
     if (!items || count <= 0) return 0;
-    size_t o = a256(sizeof(FpsArgs) * (size_t)count) + a256(sizeof(GwnJob) * (size_t)count);
+    size_t o = a256(sizeof(FpsArgs) * (size_t)count) + a256(sizeof(GwnJob) * (size_t)count) +
+               a256(sizeof(RowsJob) * (size_t)count);
     for (int i = 0; i < count; i++) {
         if (!items[i].mesh || items[i].n <= 0) return 0;
         o += a256(layout(items[i].mesh->nf, items[i].n, 1).total);
@@ -1369,6 +1414,8 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
     size_t o = a256(sizeof(FpsArgs) * (size_t)count);
     GwnJob *gtable = (GwnJob *)(w + o);
     o += a256(sizeof(GwnJob) * (size_t)count);
+    RowsJob *rtable = (RowsJob *)(w + o);
+    o += a256(sizeof(RowsJob) * (size_t)count);
     std::vector<FpsArgs> args(count);
     std::vector<Layout> lay(count);
     std::vector<size_t> base(count);
@@ -1398,7 +1445,40 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
         k_fps_blocks_coarse<<<count, kFpsThreads, 0, st>>>(table);
     }
     for (int i = 0; i < count; i++)
-        if ((s = sample_finish(items[i], 0, w + base[i], lay[i], st)) != MCS_OK) return s;
+        if ((s = sample_finish(items[i], 0, w + base[i], lay[i], st, false)) != MCS_OK) return s;
+    // every mesh's rows (and query points when orienting) in one launch
+    {
+        std::vector<RowsJob> rj(count);
+        int total = 0;
+        for (int i = 0; i < count; i++) {
+            const Layout &L = lay[i];
+            char *wb = w + base[i];
+            RowsJob &j = rj[i];
+            j.V = items[i].mesh->V;
+            j.F = items[i].mesh->F;
+            j.cen = (const double *)(wb + L.cen);
+            j.farea = (const double *)(wb + L.farea);
+            j.sel = items[i].sel;
+            j.sfaces = (const int32_t *)(wb + L.svals);
+            j.start = (const int32_t *)(wb + L.start);
+            j.pos = items[i].pos;
+            j.nrm = items[i].nrm;
+            j.area = items[i].area;
+            j.q = orient ? (float4 *)(wb + L.q) : nullptr;
+            j.row0 = total;
+            total += items[i].n;
+        }
+        for (int b0 = 0; b0 < count; b0 += kRowsChunk) {
+            RowsChunk c;
+            c.count = std::min(kRowsChunk, count - b0);
+            c.base = b0;
+            for (int k = 0; k < c.count; k++) c.j[k] = rj[b0 + k];
+            note_launch();
+            k_store_rows<<<1, 128, 0, st>>>(c, rtable);
+        }
+        note_launch();
+        k_rows_batched<<<(total + 255) / 256, 256, 0, st>>>(rtable, count, total);
+    }
     if (orient) {
         // the tree pass (orient 3, or orient 1 when the batch's faces x rows
         // reach kGwnTreeMin) for all meshes in two launches, then each mesh's
@@ -1409,7 +1489,6 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
         std::vector<GwnJob> jobs;
         int nodes = 0, nrows = 0;
         for (int i = 0; i < count; i++) {
-            orient_points(items[i], w + base[i], lay[i], st);
             mcs_mesh m = items[i].mesh;
             if (!tree || m->nf < 2) continue;
             char *wb = w + base[i];
