@@ -1006,10 +1006,8 @@ __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree_batched(const GwnJo
 }
 
 // decided rows take the sign of D; the rest go to the brute-force list
-__global__ void k_gwn_decide(int n, int force_all, const float *D, const float *E, const int *ovf, double *nrm,
-                             float *gap, int *fb_list, int *fb_count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void gwn_decide_row(int i, int force_all, const float *D, const float *E, const int *ovf,
+                                               double *nrm, float *gap, int *fb_list, int *fb_count) {
     if (!force_all && !ovf[i] && fabsf(D[i]) > E[i]) {
         if (gap) gap[i] = D[i] * 0.07957747154594767f;
         if (D[i] < 0.f)
@@ -1017,6 +1015,11 @@ __global__ void k_gwn_decide(int n, int force_all, const float *D, const float *
         return;
     }
     fb_list[atomicAdd(fb_count, 1)] = i;
+}
+__global__ void k_gwn_decide(int n, int force_all, const float *D, const float *E, const int *ovf, double *nrm,
+                             float *gap, int *fb_list, int *fb_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) gwn_decide_row(i, force_all, D, E, ovf, nrm, gap, fb_list, fb_count);
 }
 
 // brute-force sums of the listed rows; the face range is split into as many
@@ -1026,15 +1029,16 @@ __device__ __forceinline__ int fb_chunks(int cnt, int nf, int grid) {
     int ch = max(16, (grid + qg - 1) / qg);
     return max(1, min(ch, (nf + 255) / 256));
 }
-__global__ void __launch_bounds__(256) k_gwn_fb(const double *V, const int32_t *F, int nf, const float4 *q,
-                                                const int *fb_list, const int *fb_count, float *partial) {
-    __shared__ float tri[256][9];
+// units u = b, b + grid, ... of one mesh's brute force (grid: the launch's
+// x extent, which fixes the chunks and so the summation order)
+__device__ void gwn_fb_units(const double *V, const int32_t *F, int nf, const float4 *q, const int *fb_list,
+                             const int *fb_count, float *partial, int b, int grid, float (*tri)[9]) {
     const int cnt = *fb_count;
     if (cnt == 0) return;
     const int nq = 2 * cnt, qg = (nq + 255) / 256;
-    const int chunks = fb_chunks(cnt, nf, gridDim.x);
+    const int chunks = fb_chunks(cnt, nf, grid);
     const int csize = (nf + chunks - 1) / chunks;
-    for (int u = blockIdx.x; u < qg * chunks; u += gridDim.x) {
+    for (int u = b; u < qg * chunks; u += grid) {
         const int g = u % qg, c = u / qg;
         const int j = g * 256 + threadIdx.x;
         const float4 p = j < nq ? q[2 * fb_list[j >> 1] + (j & 1)] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
@@ -1070,9 +1074,13 @@ __global__ void __launch_bounds__(256) k_gwn_fb(const double *V, const int32_t *
         if (j < nq) partial[(size_t)c * nq + j] = acc;
     }
 }
-__global__ void k_orient_fb(const float *partial, int nf, int grid, const int *fb_list, const int *fb_count,
-                            double *nrm, float *gap) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_gwn_fb(const double *V, const int32_t *F, int nf, const float4 *q,
+                                                const int *fb_list, const int *fb_count, float *partial) {
+    __shared__ float tri[256][9];
+    gwn_fb_units(V, F, nf, q, fb_list, fb_count, partial, blockIdx.x, gridDim.x, tri);
+}
+__device__ void orient_fb_row(int k, const float *partial, int nf, int grid, const int *fb_list, const int *fb_count,
+                              double *nrm, float *gap) {
     const int cnt = *fb_count;
     if (k >= cnt) return;
     const int nq = 2 * cnt, chunks = fb_chunks(cnt, nf, grid);
@@ -1088,6 +1096,58 @@ __global__ void k_orient_fb(const float *partial, int nf, int grid, const int *f
     if (gap) gap[i] = gi - go;
     if (!(gi > go))
         for (int d = 0; d < 3; d++) nrm[3 * i + d] = -nrm[3 * i + d];
+}
+__global__ void k_orient_fb(const float *partial, int nf, int grid, const int *fb_list, const int *fb_count,
+                            double *nrm, float *gap) {
+    orient_fb_row(blockIdx.x * blockDim.x + threadIdx.x, partial, nf, grid, fb_list, fb_count, nrm, gap);
+}
+
+// the decisions and brute-force sums of many meshes in one launch each: a
+// 2-D grid with the mesh in y, and for the brute force the single-mesh
+// launch's x extent, so that every mesh keeps its chunks and summation order
+struct OrientJob {
+    const double *V;
+    const int32_t *F;
+    const float4 *q;
+    const float *D, *E;
+    const int *ovf;
+    double *nrm;
+    float *gap, *partial;
+    int *fb_list, *fb_count;
+    int nf, n, force_all;
+};
+constexpr int kOrientChunk = 36;
+struct OrientChunk {
+    OrientJob j[kOrientChunk];
+    int count, base;
+};
+__global__ void k_store_orient(OrientChunk c, OrientJob *table) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) table[c.base + i] = c.j[i];
+}
+__global__ void k_zero_fb(const OrientJob *jobs, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) *jobs[i].fb_count = 0;
+}
+__global__ void k_gwn_decide_batched(const OrientJob *jobs, int count) {
+    for (int y = blockIdx.y; y < count; y += gridDim.y) {
+        const OrientJob &J = jobs[y];
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < J.n) gwn_decide_row(i, J.force_all, J.D, J.E, J.ovf, J.nrm, J.gap, J.fb_list, J.fb_count);
+    }
+}
+__global__ void __launch_bounds__(256) k_gwn_fb_batched(const OrientJob *jobs, int count) {
+    __shared__ float tri[256][9];
+    for (int y = blockIdx.y; y < count; y += gridDim.y) {
+        const OrientJob &J = jobs[y];
+        gwn_fb_units(J.V, J.F, J.nf, J.q, J.fb_list, J.fb_count, J.partial, blockIdx.x, gridDim.x, tri);
+    }
+}
+__global__ void k_orient_fb_batched(const OrientJob *jobs, int count, int grid) {
+    for (int y = blockIdx.y; y < count; y += gridDim.y) {
+        const OrientJob &J = jobs[y];
+        orient_fb_row(blockIdx.x * blockDim.x + threadIdx.x, J.partial, J.nf, grid, J.fb_list, J.fb_count, J.nrm,
+                      J.gap);
+    }
 }
 
 struct Layout {
@@ -1389,7 +1449,7 @@ mcs_status mcs_sample_rows(mcs_mesh m, int n, int orient, int32_t *sel, double *
 size_t mcs_sample_rows_batched_workspace_size(const mcs_sample_item *items, int count) {
     if (!items || count <= 0) return 0;
     size_t o = a256(sizeof(FpsArgs) * (size_t)count) + a256(sizeof(GwnJob) * (size_t)count) +
-               a256(sizeof(RowsJob) * (size_t)count);
+               a256(sizeof(RowsJob) * (size_t)count) + a256(sizeof(OrientJob) * (size_t)count);
     for (int i = 0; i < count; i++) {
         if (!items[i].mesh || items[i].n <= 0) return 0;
         o += a256(layout(items[i].mesh->nf, items[i].n, 1).total);
@@ -1416,6 +1476,8 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
     o += a256(sizeof(GwnJob) * (size_t)count);
     RowsJob *rtable = (RowsJob *)(w + o);
     o += a256(sizeof(RowsJob) * (size_t)count);
+    OrientJob *otable = (OrientJob *)(w + o);
+    o += a256(sizeof(OrientJob) * (size_t)count);
     std::vector<FpsArgs> args(count);
     std::vector<Layout> lay(count);
     std::vector<size_t> base(count);
@@ -1527,8 +1589,48 @@ mcs_status mcs_sample_rows_batched(const mcs_sample_item *items, int count, int 
             note_launch();
             k_gwn_tree_batched<<<(nrows + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(gtable, nj, nrows);
         }
-        for (int i = 0; i < count; i++)
-            orient_decide(items[i], w + base[i], lay[i], st, tree && items[i].mesh->nf >= 2);
+        // decisions, brute force for the undecided rows, and their signs:
+        // one launch each for all meshes
+        std::vector<OrientJob> oj(count);
+        int nmax = 0;
+        for (int i = 0; i < count; i++) {
+            const Layout &L = lay[i];
+            char *wb = w + base[i];
+            OrientJob &j = oj[i];
+            j.V = items[i].mesh->V;
+            j.F = items[i].mesh->F;
+            j.q = (const float4 *)(wb + L.q);
+            j.D = (const float *)(wb + L.gD);
+            j.E = (const float *)(wb + L.gE);
+            j.ovf = (const int *)(wb + L.govf);
+            j.nrm = items[i].nrm;
+            j.gap = items[i].orient_gap;
+            j.partial = (float *)(wb + L.partial);
+            j.fb_list = (int *)(wb + L.fb_list);
+            j.fb_count = (int *)(wb + L.fb_count);
+            j.nf = items[i].mesh->nf;
+            j.n = items[i].n;
+            j.force_all = (tree && j.nf >= 2) ? 0 : 1;
+            nmax = std::max(nmax, j.n);
+        }
+        for (int b0 = 0; b0 < count; b0 += kOrientChunk) {
+            OrientChunk c;
+            c.count = std::min(kOrientChunk, count - b0);
+            c.base = b0;
+            for (int k = 0; k < c.count; k++) c.j[k] = oj[b0 + k];
+            note_launch();
+            k_store_orient<<<1, 128, 0, st>>>(c, otable);
+        }
+        const int gy = std::min(count, 65535), G = gwn_fb_grid();
+        const dim3 rgrid((nmax + 255) / 256, gy);
+        note_launch();
+        k_zero_fb<<<(count + 255) / 256, 256, 0, st>>>(otable, count);
+        note_launch();
+        k_gwn_decide_batched<<<rgrid, 256, 0, st>>>(otable, count);
+        note_launch();
+        k_gwn_fb_batched<<<dim3(G, gy), 256, 0, st>>>(otable, count);
+        note_launch();
+        k_orient_fb_batched<<<rgrid, 256, 0, st>>>(otable, count, G);
     }
     MCS_CUDA(cudaStreamSynchronize(st));
     return MCS_OK;
