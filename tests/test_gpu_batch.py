@@ -205,3 +205,23 @@ def test_batched_builds_equal_single_builds():
     bad = hosts[1].F + 100000
     with pytest.raises(mcs.MCSError, match="mesh 1"):
         mcs.build_meshes([(hosts[0].V, hosts[0].F), (hosts[1].V, bad), (hosts[2].V, hosts[2].F)])
+
+
+def test_batched_hierarchical_orientation_equals_brute_force():
+    """The batched tree pass (one aggregation and one tree launch over all
+    meshes, far field at theta = 0.2, then batched decisions and brute force
+    for the undecided rows) against each mesh's brute force: the same
+    normals wherever the brute-force gap is not a near tie, and every other
+    output bit for bit."""
+    hosts = [meshgen.wild_union(6, 5000, seed=9), meshgen.wild_union(8, 12000, seed=3), meshgen.icosphere(3)]
+    meshes = mcs.build_meshes([(h.V, h.F) for h in hosts])
+    got = mcs.sample_rows_batched(meshes, 300, orient=3)
+    for mesh, g in zip(meshes, got):
+        b = mcs.sample_rows(mesh, 300, orient=2)
+        for k in ("sel", "tri2bin", "area", "pos"):
+            assert torch.equal(g[k], b[k]), k
+        gap = b["gap"].cpu().numpy()
+        clear = np.abs(gap) > 1e-3
+        assert clear.sum() > 0.9 * len(gap)
+        same = (g["nrm"] == b["nrm"]).all(1).cpu().numpy()
+        assert same[clear].all()
