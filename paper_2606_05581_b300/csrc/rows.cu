@@ -947,13 +947,15 @@ __device__ void gwn_tree_row(const DevMesh &m, const GwnAgg *agg, const float4 *
         ovf[row] = over ? 1 : 0;
     }
 }
+// rows in the given order (order[i]: the row the i-th warp sums; NULL: 0..n-1)
 __global__ void __launch_bounds__(32 * kGwnWarps) k_gwn_tree(DevMesh m, const GwnAgg *agg, const float4 *q, int n,
-                                                            float *Dout, float *Eout, int *ovf) {
+                                                            float *Dout, float *Eout, int *ovf, const int *order) {
     __shared__ int stk[kGwnWarps][kGwnStack];
     __shared__ int top[kGwnWarps];
     const int w = threadIdx.x >> 5;
-    const int row = blockIdx.x * kGwnWarps + w;
-    if (row >= n) return;  // warp-uniform
+    const int g = blockIdx.x * kGwnWarps + w;
+    if (g >= n) return;  // warp-uniform
+    const int row = order ? order[g] : g;
     gwn_tree_row(m, agg, q, row, Dout, Eout, ovf, stk[w], &top[w], kGwnTheta);
 }
 
@@ -1299,6 +1301,32 @@ static mcs_status sample_prepare(const mcs_sample_item &it, char *w, const Layou
     return MCS_OK;
 }
 
+// Morton code (10 bits per axis in the mesh's box) of each row's two query
+// points' midpoint
+__device__ __forceinline__ uint32_t spread10_rows(uint32_t x) {
+    x &= 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+__global__ void k_gwn_row_keys(const float4 *q, int n, float lx, float ly, float lz, float ix, float iy, float iz,
+                               uint32_t *keys, int32_t *idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = q[2 * i], b = q[2 * i + 1];
+    const float c[3] = {0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)};
+    const float l[3] = {lx, ly, lz}, v[3] = {ix, iy, iz};
+    uint32_t u[3];
+    for (int k = 0; k < 3; k++) {
+        const float f = fminf(fmaxf((c[k] - l[k]) * v[k], 0.f), 1.f);
+        u[k] = (uint32_t)(f * 1023.f);
+    }
+    keys[i] = spread10_rows(u[0]) | (spread10_rows(u[1]) << 1) | (spread10_rows(u[2]) << 2);
+    idx[i] = i;
+}
+
 // orientation pieces of sample_finish: the two points of each row, the
 // tree pass of one mesh, and the decision (brute force for the rest)
 static void orient_points(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st) {
@@ -1307,7 +1335,7 @@ static void orient_points(const mcs_sample_item &it, char *w, const Layout &L, c
     k_gwn_points<<<(it.n + tb - 1) / tb, tb, 0, st>>>(it.pos, it.nrm, (double *)(w + L.farea), it.sel, it.n,
                                                        (float4 *)(w + L.q));
 }
-static void orient_tree(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st) {
+static mcs_status orient_tree(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st) {
     mcs_mesh m = it.mesh;
     const int nf = m->nf, n = it.n, tb = 256;
     GwnAgg *agg = (GwnAgg *)(w + L.agg);
@@ -1315,9 +1343,25 @@ static void orient_tree(const mcs_sample_item &it, char *w, const Layout &L, cud
     cudaMemsetAsync(arrive, 0, sizeof(int) * (nf - 1), st);
     note_launch();
     k_gwn_agg<<<(nf - 1 + tb - 1) / tb, tb, 0, st>>>(m->dev(), m->child, m->parent, arrive, agg, (int *)(w + L.err));
+    // rows by the Morton code of their points (in the owner sort's arrays, free
+    // by now): warps resident together sum nearby rows and share the nodes
+    // they open in the caches; each row's sum is unchanged
+    const float4 *q = (const float4 *)(w + L.q);
+    uint32_t *keys = (uint32_t *)(w + L.keys), *skeys = (uint32_t *)(w + L.skeys);
+    int32_t *idx = (int32_t *)(w + L.vals), *order = (int32_t *)(w + L.svals);
+    float lo[3], inv[3];
+    for (int k = 0; k < 3; k++) {
+        lo[k] = (float)m->lo[k];
+        inv[k] = (float)(1.0 / (m->hi[k] - m->lo[k]));
+    }
+    note_launch();
+    k_gwn_row_keys<<<(n + tb - 1) / tb, tb, 0, st>>>(q, n, lo[0], lo[1], lo[2], inv[0], inv[1], inv[2], keys, idx);
+    size_t sb = L.sort_bytes;
+    MCS_CUDA(cub::DeviceRadixSort::SortPairs(w + L.sort, sb, keys, skeys, idx, order, n, 0, 30, st));
     note_launch();
     k_gwn_tree<<<(n + kGwnWarps - 1) / kGwnWarps, 32 * kGwnWarps, 0, st>>>(
-        m->dev(), agg, (const float4 *)(w + L.q), n, (float *)(w + L.gD), (float *)(w + L.gE), (int *)(w + L.govf));
+        m->dev(), agg, q, n, (float *)(w + L.gD), (float *)(w + L.gE), (int *)(w + L.govf), order);
+    return MCS_OK;
 }
 static void orient_decide(const mcs_sample_item &it, char *w, const Layout &L, cudaStream_t st, bool tree) {
     mcs_mesh m = it.mesh;
@@ -1373,7 +1417,10 @@ static mcs_status sample_finish(const mcs_sample_item &it, int orient, char *w, 
         // pay more for the extra launches than for the brute-force sums)
         const bool tree = nf >= 2 && (orient == 3 || (orient == 1 && (double)nf * n >= kGwnTreeMin));
         orient_points(it, w, L, st);
-        if (tree) orient_tree(it, w, L, st);
+        if (tree) {
+            const mcs_status s = orient_tree(it, w, L, st);
+            if (s != MCS_OK) return s;
+        }
         orient_decide(it, w, L, st, tree);
     }
     MCS_CUDA(cudaGetLastError());
