@@ -8,8 +8,6 @@
 // runs the same estimator with its scratch taken from one fixed array that
 // the library reserves in device memory when it is loaded, so the call itself
 // allocates nothing.
-#include <atomic>
-
 #include "mcs_internal.h"
 
 namespace {
@@ -37,18 +35,13 @@ mcs_status scratch_address(void **out) {
 // loading noalloc.cu's module reserves the scratch array, and the estimate's
 // kernels are loaded too, so that the entry point below loads nothing
 mcs_status mcs::noalloc_prepare() {
-    // once per device (every mesh creation calls this)
-    static std::atomic<unsigned long long> done{0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
-    if (bit && (done.load(std::memory_order_acquire) & bit)) return MCS_OK;
+    // at every mesh creation (once per batched build): after a device reset
+    // the modules load again, so no memo of an earlier load is kept; once
+    // loaded, these queries are cheap
     void *p = nullptr;
-    mcs_status s = scratch_address(&p);
+    const mcs_status s = scratch_address(&p);
     if (s != MCS_OK) return s;
-    s = mcs::preload_estimate_kernels();
-    if (s == MCS_OK) done.fetch_or(bit, std::memory_order_release);
-    return s;
+    return mcs::preload_estimate_kernels();
 }
 
 extern "C" {
