@@ -396,7 +396,8 @@ mcs_status mcs_estimate_dtn_noalloc(mcs_mesh m, const mcs_rows *rows, const mcs_
  * whose block has lost numerical rank), Rayleigh-Ritz with a
  * parallel Jacobi on the block, Ritz values as FP64 Rayleigh quotients. */
 typedef struct {
-    int degree;             /* Chebyshev filter degree per iteration (48; <= 256); halved
+    int degree;             /* Chebyshev filter degree per iteration (<= 256; 0, the default:
+                               48 with the dense product, 96 with the sparse one); halved
                                (down to 8) after two iterations that add no converged pair */
     int max_iters;          /* outer iterations (60)                             */
     double tol;             /* residual |A x - theta x| <= tol * upper bound (1e-5) */

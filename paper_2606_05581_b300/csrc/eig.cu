@@ -1085,7 +1085,7 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     mcs_eig_params prm;
     mcs_default_eig_params(&prm);
     if (ep) prm = *ep;
-    MCS_ARG(prm.degree >= 1 && prm.degree <= 256 && prm.max_iters >= 1 && prm.tol > 0.0 && prm.product >= 0 &&
+    MCS_ARG(prm.degree >= 0 && prm.degree <= 256 && prm.max_iters >= 1 && prm.tol > 0.0 && prm.product >= 0 &&
                 prm.product <= 2,
             "mcs_steklov_modes: bad params");
     Ctx c;
@@ -1196,7 +1196,12 @@ mcs_status mcs_steklov_modes(const double *Lambda, const double *mass, int n, in
     // a row add no converged pair -- a filter of too high a degree spreads the
     // wanted components over more magnitudes than the FP32-accurate products
     // keep, and the last ones stop converging
-    int deg = prm.degree, best_conv = -1, stall = 0;
+    // degree 0: 48 with the dense product, 96 with the sparse one, whose
+    // FP32 products (no tf32 truncation) keep the higher degree converging
+    // (10,000-row union: 23.2 ms at 48, 21.3 at 64, 19.6 at 96 in 3
+    // iterations; the dense two-sphere solve stalls above 48: 24.0 ms at 48,
+    // 43 at 64)
+    int deg = prm.degree > 0 ? prm.degree : (c.sparse ? 96 : 48), best_conv = -1, stall = 0;
     for (iters = 0; iters < prm.max_iters; iters++) {
         // ---- Chebyshev filter of degree d on [a_cut, ub] applied to X
         to_operand(c, X, 0);
@@ -1392,13 +1397,14 @@ size_t mcs_tc_symm_product_workspace_size(int n, int m) {
 
 void mcs_default_eig_params(mcs_eig_params *p) {
     if (!p) return;
-    // degree 48 (measured, k = 64: two-sphere exterior n = 5124: degree 48
-    // 34.5 ms, 64 57.7 ms, 80 48.7 ms; 10,000-row union: 92.2, 90.5, 104 ms;
-    // icosphere s3 interior n = 642: 13.9, 25.1, 31.5 ms): higher degrees
-    // spread the wanted components over more magnitudes than the FP32-accurate
-    // products keep, stall, and pay for the halving; 24 needs more FP64
-    // orthogonalisations and Rayleigh-Ritz steps per converged block
-    p->degree = 48;
+    // degree 0: chosen by the product (see mcs_steklov_modes).  For the dense
+    // tf32-split product 48 (measured, k = 64: two-sphere exterior n = 5124:
+    // degree 48 34.5 ms, 64 57.7 ms, 80 48.7 ms; icosphere s3 interior n = 642:
+    // 13.9, 25.1, 31.5 ms): higher degrees spread the wanted components over
+    // more magnitudes than those products keep, stall, and pay for the
+    // halving; 24 needs more FP64 orthogonalisations and Rayleigh-Ritz steps
+    // per converged block
+    p->degree = 0;
     p->max_iters = 60;
     p->tol = 1e-5;
     p->product = 0;
