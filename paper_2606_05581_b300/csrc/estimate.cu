@@ -694,6 +694,20 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                            (double)h.b0, (double)h.b1, (double)h.b2);
                     return;
                 }
+                // sample rows without recorded barycentrics need only the
+                // decision d64 < eps (the bin is tri2bin[f]); the FP32
+                // distance, from the same point to the same float triangle,
+                // settles it below a band E of rounding under eps (E bounds
+                // the float rounding of the point and the test many times
+                // over); inside the band the FP64 re-check decides
+                if (J.tri2bin && !J.exit_bary) {
+                    const double E = 1.52587890625e-05 * ((double)J.m.scale +
+                                                         fmax(fabs((double)s.x.x), fmax(fabs((double)s.x.y), fabs((double)s.x.z))));
+                    if ((double)d + E < a.eps) {
+                        finish(J, J.tri2bin[h.id], h.id, false, false);
+                        return;
+                    }
+                }
                 double b[3];
                 const double d64 = sqrt(recheck64(J.m, h.slot, (double)s.x.x, (double)s.x.y, (double)s.x.z, b));
                 if (d64 < a.eps || s.k == a.max_steps) {
