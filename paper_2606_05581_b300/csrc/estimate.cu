@@ -580,6 +580,21 @@ template <typename T> struct WalkState {
 // TRAV: 0 binary BVH, one lane per query; 1 4-wide BVH, one lane per query;
 // 2 4-wide BVH, a group of 4 lanes per query (the group runs one walk, every
 // lane holding its state; lane 0 of the group writes results and counters)
+// Binary traversal: a round of node visits ends when at most kLeafStop lanes
+// can still visit without testing their queued triangles, and the traversal
+// stops for service once kServe lanes wait for a decision, a query or a walk;
+// with at most kLeafStop live lanes (a launch's tail) queries run to the end
+// per lane.  Measured on the two-sphere exterior launch / a 64-mesh batch,
+// FP32, against 162 / 666 ms for one whole query per lane and loop pass:
+// kServe 8: 169 / 663; 16: 156 / 613; 24: 165 / 641; 28: 178 / 692;
+// kLeafStop 0 (every lane queued) 206 / 822 at kServe 8, 4 or 12 no better
+// than 8; an L1 prefetch of queued triangles no gain; with the tail rules
+// 149 / 568, and with decisions before refills 148 / 550 (kServe 24: 147 /
+// 546, slower on short launches; the 2M-face union, whose walks take ~2
+// steps: 80 ms per query loop, 86 with refills first, 76)
+constexpr int kLeafStop = 8;
+constexpr int kServe = 16;
+
 template <typename T, int MODE, bool COUNT, bool MULTI, int TRAV>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __grid_constant__ MultiArgs a) {
     const unsigned FULL = 0xFFFFFFFFu;
@@ -754,7 +769,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
         advance(rho, J);
     };
 
-    while (true) {
+    // lanes without a walk take the next ones from the global queue
+    auto refill = [&]() {
         const bool need = !active && more;
         // groups: one queue entry per group, taken by its lane 0
         const unsigned nm = __ballot_sync(FULL, need && writer);
@@ -829,19 +845,82 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                 }
             }
         }
-        if (!__any_sync(FULL, active || more)) break;
-        if (!active) continue;
-        // ---- one walk-on-spheres step: the query point (exterior: the primal
-        // image of x~), the closest-point query, the decision
-        const WalkJob &J = job_of<MULTI>(a, s.job);
-        const bool ext = MODE == 1 || (MODE == 2 && J.ext);
-        T qx, qy, qz;
-        if (!query_point(J, ext, qx, qy, qz)) continue;
+    };
+
+    if constexpr (TRAV == 0) {
+        // Binary BVH: the warp interleaves its lanes' queries.  A lane whose
+        // query completes waits (its walk's decision, next query point, or next
+        // walk) while the others keep traversing, until kServe lanes wait; the
+        // traversal itself alternates node visits with rounds of queued
+        // triangle tests (bq_*), so neither the warp's longest query nor a
+        // few lanes' triangle tests hold the rest back.
+        int qstack[kStackDepth];
+        float qsdist[kStackDepth];
+        BinQuery<T> q;
+        q.nq = 0;
         Hit<T> h;
-        if constexpr (TRAV == 2) closest_g4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work, gmask, gr);
-        else if constexpr (TRAV == 1) closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
-        else closest<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
-        decide(J, ext, h);
+        int phase = 0;  // 0: the walk needs its next query, 1: query in flight, 2: query complete
+        while (true) {
+            // service: decisions first, so that a lane whose walk ends takes
+            // its next walk (and that walk's first query) in the same round
+            if (active && phase == 2) {
+                phase = 0;
+                const WalkJob &J = job_of<MULTI>(a, s.job);
+                decide(J, MODE == 1 || (MODE == 2 && J.ext), h);
+            }
+            refill();
+            if (!__any_sync(FULL, active || more)) break;
+            if (active && phase == 0) {
+                const WalkJob &J = job_of<MULTI>(a, s.job);
+                T qx, qy, qz;
+                if (query_point(J, MODE == 1 || (MODE == 2 && J.ext), qx, qy, qz))
+                    phase = bq_begin<T, COUNT>(J.m, q, h, qx, qy, qz, s.prev, &work) ? 1 : 2;
+            }
+            const int live = __popc(__ballot_sync(FULL, active || more));
+            if (live <= kLeafStop) {
+                // the launch's tail: too few walks to interleave; each query
+                // runs to completion (the same visits and tests, per lane)
+                if (phase == 1) {
+                    const DevMesh &m = job_of<MULTI>(a, s.job).m;
+                    do {
+                        while (q.nq > 0) bq_flush<T, COUNT>(m, q, h, &work);
+                    } while (bq_step<T, COUNT>(m, q, qstack, qsdist, &err, &work));
+                    phase = 2;
+                }
+                continue;
+            }
+            while (__any_sync(FULL, phase == 1)) {
+                while (true) {
+                    if (phase == 1 && q.nq == 0 &&
+                        !bq_step<T, COUNT>(job_of<MULTI>(a, s.job).m, q, qstack, qsdist, &err, &work))
+                        phase = 2;
+                    if (__popc(__ballot_sync(FULL, phase == 1 && q.nq == 0)) <= kLeafStop) break;
+                }
+                while (__any_sync(FULL, q.nq > 0))
+                    if (q.nq > 0) bq_flush<T, COUNT>(job_of<MULTI>(a, s.job).m, q, h, &work);
+                // serve at kServe waiting lanes, or at half the live ones once
+                // fewer than 2 kServe lanes hold or can take a walk (the
+                // launch's tail, where waiting for kServe would stall walks)
+                if (__popc(__ballot_sync(FULL, phase != 1 && (active || more))) >= min(kServe, (live + 1) >> 1))
+                    break;
+            }
+        }
+    } else {
+        while (true) {
+            refill();
+            if (!__any_sync(FULL, active || more)) break;
+            if (!active) continue;
+            // ---- one walk-on-spheres step: the query point (exterior: the
+            // primal image of x~), the closest-point query, the decision
+            const WalkJob &J = job_of<MULTI>(a, s.job);
+            const bool ext = MODE == 1 || (MODE == 2 && J.ext);
+            T qx, qy, qz;
+            if (!query_point(J, ext, qx, qy, qz)) continue;
+            Hit<T> h;
+            if constexpr (TRAV == 2) closest_g4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work, gmask, gr);
+            else closest4<T, COUNT>(J.m, qx, qy, qz, s.prev, h, &err, &work);
+            decide(J, ext, h);
+        }
     }
     if constexpr (MULTI) {
         flush();

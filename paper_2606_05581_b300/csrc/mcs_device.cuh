@@ -432,6 +432,115 @@ __device__ void closest(const DevMesh &m, T px, T py, T pz, int guess, Hit<T> &b
     }
 }
 
+// Resumable form of `closest` for loops that interleave the queries of many
+// walks in one warp.  A lane advances its traversal one node per bq_step; the
+// leaf triangles it meets are queued (at most two) and tested by bq_flush in
+// rounds of the whole warp, so the costly triangle test runs on many lanes at
+// once instead of a few per node.  A lane steps only with an empty queue, so
+// its own sequence of visits and tests is exactly `closest`'s.  Every
+// node is pruned only against a bound attained by a tested triangle (plus the
+// slack tau), and the (d^2, id) minimum does not depend on the order of the
+// tests, so the result equals `closest`'s.
+template <typename T> struct BinQuery {
+    T px, py, pz, tau, thr2;
+    T nd2;      // box distance of `node`, re-checked before the visit
+    int node;   // next node; -1: pop the stack first
+    int sp, nq, q0, q1, guard;
+};
+
+template <typename T, bool COUNT>
+__device__ __forceinline__ void bq_test(const DevMesh &m, BinQuery<T> &q, Hit<T> &best, int s, Work *work) {
+    if (COUNT) work->tris++;
+    T b[3];
+    int id;
+    const T d2 = Slot<T>::test(m, s, q.px, q.py, q.pz, b, id);
+    if (d2 < best.d2 || (d2 == best.d2 && id < best.id)) {
+        best.d2 = d2; best.id = id; best.slot = s;
+        best.b0 = b[0]; best.b1 = b[1]; best.b2 = b[2];
+        const T r = rsq<T>(d2) + q.tau;
+        q.thr2 = r * r;
+    }
+}
+
+// starts a query at p (guess >= 0: a slot tested at once); false when the
+// query is already complete (non-finite point: best.slot stays -1; or a
+// one-triangle mesh)
+template <typename T, bool COUNT>
+__device__ __forceinline__ bool bq_begin(const DevMesh &m, BinQuery<T> &q, Hit<T> &best, T px, T py, T pz, int guess,
+                                         Work *work) {
+    best.d2 = (T)INFINITY;
+    best.id = 0x7FFFFFFF;
+    best.slot = -1;
+    best.b0 = best.b1 = best.b2 = (T)0;
+    q.nq = 0; q.sp = 0; q.guard = 0; q.node = -1;
+    if (!(isfinite(px) && isfinite(py) && isfinite(pz))) return false;
+    q.px = px; q.py = py; q.pz = pz;
+    q.tau = prune_rel<T>() * ((T)m.scale + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
+    q.thr2 = (T)INFINITY;
+    if (guess >= 0) bq_test<T, COUNT>(m, q, best, guess, work);
+    if (m.nf == 1) {
+        if (guess != 0) bq_test<T, COUNT>(m, q, best, 0, work);
+        return false;
+    }
+    q.node = 0;
+    q.nd2 = (T)0;
+    return true;
+}
+
+// one node of a lane with no queued triangle (the stack is popped first when
+// no node is pending); false when the query is complete
+template <typename T, bool COUNT>
+__device__ __forceinline__ bool bq_step(const DevMesh &m, BinQuery<T> &q, int *stack, float *sdist, int *err,
+                                        Work *work) {
+    if (q.node >= 0 && q.nd2 > q.thr2) q.node = -1;
+    if (q.node < 0) {
+        while (q.sp > 0) {
+            q.sp--;
+            if ((T)sdist[q.sp] <= q.thr2) { q.node = stack[q.sp]; break; }
+        }
+        if (q.node < 0) return false;
+    }
+    if (q.guard++ > 2 * m.nf + 64) { *err |= kErrTree; q.node = -1; q.sp = 0; return false; }
+    if (COUNT) work->nodes++;
+    const Node nd = m.nodes[q.node];
+    const T d0 = box_d2<T>(q.px, q.py, q.pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);
+    const T d1 = box_d2<T>(q.px, q.py, q.pz, nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w);
+    const int c0 = nd.d.x, c1 = nd.d.y;
+    bool h0 = d0 <= q.thr2, h1 = d1 <= q.thr2;
+    if (h0 && c0 < 0) { q.q0 = ~c0; q.nq = 1; h0 = false; }
+    if (h1 && c1 < 0) {
+        if (q.nq) q.q1 = ~c1; else q.q0 = ~c1;
+        q.nq++;
+        h1 = false;
+    }
+    if (h0 && h1) {
+        const bool first0 = d0 <= d1;
+        if (q.sp < kStackDepth) {
+            stack[q.sp] = first0 ? c1 : c0;
+            sdist[q.sp] = store_down<T>(first0 ? d1 : d0);
+            q.sp++;
+        } else {
+            *err |= kErrStack;
+        }
+        q.node = first0 ? c0 : c1;
+        q.nd2 = first0 ? d0 : d1;
+    } else if (h0 || h1) {
+        q.node = h0 ? c0 : c1;
+        q.nd2 = h0 ? d0 : d1;
+    } else {
+        q.node = -1;
+    }
+    return true;
+}
+
+// tests one queued triangle
+template <typename T, bool COUNT>
+__device__ __forceinline__ void bq_flush(const DevMesh &m, BinQuery<T> &q, Hit<T> &best, Work *work) {
+    const int s = q.nq == 2 ? q.q1 : q.q0;
+    q.nq--;
+    bq_test<T, COUNT>(m, q, best, s, work);
+}
+
 constexpr int kStack4 = 96;  // 4-wide traversal: up to 3 deferred children per level
 
 // closest triangle by traversal of the 4-wide BVH: the children in reach are
