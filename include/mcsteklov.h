@@ -333,7 +333,10 @@ void mcs_graph_destroy(mcs_graph g);
 
 /* Autotuner of the walk launch.  Runs the batch's row setup, then times the
  * walk kernel on a sample (every s-th row of every mesh's row schedule,
- * s = floor(1 / sample_fraction), no killing walks) for the row order of
+ * s = floor(1 / sample_fraction), lowered so that the sample holds at least
+ * 32 walks per resident lane of the default launch, or the whole batch when
+ * it has fewer: a shorter sample is dominated by the launch's tail and
+ * misranks the layouts; no killing walks) for the row order of
  * the queue (a batch of several meshes always dispenses them longest first,
  * queue_order bit 1: its benefit, a shorter tail, grows with the walks per
  * mesh and does not show in the sample), the BVH node layouts (when p->bvh_layout is 0),

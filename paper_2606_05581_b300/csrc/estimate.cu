@@ -2371,7 +2371,27 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
     MCS_CUDA(cudaEventCreate(&e1));
     auto cleanup = [&]() { cudaEventDestroy(e0); cudaEventDestroy(e1); };
     int cur_rows = -1;
-    // sample: the first rows of every mesh (in the candidate's row order), no killing walks
+    // the sample holds at least kTuneLaneWalks walks per resident lane of the
+    // default launch (the whole batch if it has fewer): a shorter one is
+    // dominated by the launch's tail and misranks the layouts (an 8-mesh
+    // batch, 4.2M walks, sampled at 1/64: 2 walks per lane; the sample
+    // preferred 4-wide nodes, whose full launch took 81 ms against 62 ms)
+    constexpr long long kTuneLaneWalks = 32;
+    int stride = std::max(1, (int)std::floor(1.0 / sample_fraction));
+    {
+        int dev = 0, sms = 0, tpb0 = 0, bps0 = 0;
+        MCS_CUDA(cudaGetDevice(&dev));
+        MCS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        mcs_params d = *p;
+        d.threads_per_block = 0;
+        d.blocks_per_sm = 0;
+        if ((s = walk_residency(&d, b.mode, b.n > 1, &tpb0, &bps0)) != MCS_OK) { cleanup(); return s; }
+        long long walks = 0;
+        for (const Plan &pl : b.plans) walks += (long long)pl.rows.n_rows * pl.W;
+        const long long floor_walks = kTuneLaneWalks * sms * tpb0 * bps0;
+        stride = (int)std::max(1LL, std::min((long long)stride, walks / std::max(1LL, floor_walks)));
+    }
+    // sample: every stride-th row of every mesh (in the candidate's row order), no killing walks
     auto trial = [&](const mcs_params &q, float *ms, int *bps_used) -> mcs_status {
         mcs_status r;
         if ((q.queue_order & 1) != cur_rows) {
@@ -2385,7 +2405,6 @@ mcs_status mcs_autotune_walks(const mcs_batch_item *items, int n, const mcs_para
             // every stride-th row of the mesh's schedule: a sample spread over the whole mesh
             const Plan &pl = b.plans[i];
             const int R = pl.rows.n_rows;
-            const int stride = std::max(1, (int)std::floor(1.0 / sample_fraction));
             const unsigned long long rows = (unsigned long long)((R + stride - 1) / stride);
             WalkJob J = make_job(pl, rows * pl.W, 0);
             J.row_stride = stride;
