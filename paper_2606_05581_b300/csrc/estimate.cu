@@ -591,7 +591,9 @@ template <typename T> struct WalkState {
 // than 8; an L1 prefetch of queued triangles no gain; with the tail rules
 // 149 / 568, and with decisions before refills 148 / 550 (kServe 24: 147 /
 // 546, slower on short launches; the 2M-face union, whose walks take ~2
-// steps: 80 ms per query loop, 86 with refills first, 76)
+// steps: 80 ms per query loop, 86 with refills first, 76); the tree pointer
+// held per query rather than read from the job per node: 556 -> 549 on the
+// 64-mesh batch
 constexpr int kLeafStop = 8;
 constexpr int kServe = 16;
 
@@ -884,7 +886,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
                     const DevMesh &m = job_of<MULTI>(a, s.job).m;
                     do {
                         while (q.nq > 0) bq_flush<T, COUNT>(m, q, h, &work);
-                    } while (bq_step<T, COUNT>(m, q, qstack, qsdist, &err, &work));
+                    } while (bq_step<T, COUNT>(q, qstack, qsdist, &err, &work));
                     phase = 2;
                 }
                 continue;
@@ -892,7 +894,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 10) k_walks(const __
             while (__any_sync(FULL, phase == 1)) {
                 while (true) {
                     if (phase == 1 && q.nq == 0 &&
-                        !bq_step<T, COUNT>(job_of<MULTI>(a, s.job).m, q, qstack, qsdist, &err, &work))
+                        !bq_step<T, COUNT>(q, qstack, qsdist, &err, &work))
                         phase = 2;
                     if (__popc(__ballot_sync(FULL, phase == 1 && q.nq == 0)) <= kLeafStop) break;
                 }

@@ -446,6 +446,8 @@ template <typename T> struct BinQuery {
     T nd2;      // box distance of `node`, re-checked before the visit
     int node;   // next node; -1: pop the stack first
     int sp, nq, q0, q1, guard;
+    const Node *nodes;  // the mesh's tree and visit bound, held per query so that a
+    int lim;            // node's address does not wait on a load of the job's mesh
 };
 
 template <typename T, bool COUNT>
@@ -484,14 +486,15 @@ __device__ __forceinline__ bool bq_begin(const DevMesh &m, BinQuery<T> &q, Hit<T
     }
     q.node = 0;
     q.nd2 = (T)0;
+    q.nodes = m.nodes;
+    q.lim = 2 * m.nf + 64;
     return true;
 }
 
 // one node of a lane with no queued triangle (the stack is popped first when
 // no node is pending); false when the query is complete
 template <typename T, bool COUNT>
-__device__ __forceinline__ bool bq_step(const DevMesh &m, BinQuery<T> &q, int *stack, float *sdist, int *err,
-                                        Work *work) {
+__device__ __forceinline__ bool bq_step(BinQuery<T> &q, int *stack, float *sdist, int *err, Work *work) {
     if (q.node >= 0 && q.nd2 > q.thr2) q.node = -1;
     if (q.node < 0) {
         while (q.sp > 0) {
@@ -500,9 +503,9 @@ __device__ __forceinline__ bool bq_step(const DevMesh &m, BinQuery<T> &q, int *s
         }
         if (q.node < 0) return false;
     }
-    if (q.guard++ > 2 * m.nf + 64) { *err |= kErrTree; q.node = -1; q.sp = 0; return false; }
+    if (q.guard++ > q.lim) { *err |= kErrTree; q.node = -1; q.sp = 0; return false; }
     if (COUNT) work->nodes++;
-    const Node nd = m.nodes[q.node];
+    const Node nd = q.nodes[q.node];
     const T d0 = box_d2<T>(q.px, q.py, q.pz, nd.a.x, nd.a.y, nd.a.z, nd.a.w, nd.b.x, nd.b.y);
     const T d1 = box_d2<T>(q.px, q.py, q.pz, nd.b.z, nd.b.w, nd.c.x, nd.c.y, nd.c.z, nd.c.w);
     const int c0 = nd.d.x, c1 = nd.d.y;
